@@ -1,0 +1,217 @@
+// CPU oracle for the hash-table hot path.  TEST INFRASTRUCTURE ONLY.
+//
+// Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+// load this library.  The CUDA path never links, includes or calls it, and
+// it shares no code with the CUDA path.
+//
+// What it computes is the plain definition of each operation, written
+// single-threaded on top of the C++ standard library's hash containers:
+//
+//  * find-or-put (Section 5 of the paper: every element of the sequence is
+//    first looked up; if present nothing happens, otherwise it is inserted;
+//    the time to find-or-insert the whole sequence is what is measured).
+//    Processed in batch order: is_new[i] = (keys[i] not in S); S += keys[i].
+//  * insert-if-absent with a 32-bit value (a duplicate insert keeps the
+//    value already stored, Section 5.1.1's duplicate handling), and lookup.
+//  * breadth-first state-space exploration (Section 3.2: open and closed
+//    sets; successor vectors built from each process's enabled transitions):
+//    L_0 = {s0}, L_{d+1} = succ(L_d) minus every state seen so far.
+//
+// The successor relation follows the model format documented in
+// workloads/statespace.py (interleaving of local actions plus binary
+// synchronisation on pair labels); that format is the project's own, since
+// the paper's models are not available.
+//
+// Nothing here models hash functions, buckets, slots or eviction: those are
+// not observable in the results, so parity is checked on sets, flags and
+// values only.
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+struct Table {
+    std::unordered_map<uint64_t, uint32_t> m;
+};
+
+}  // namespace
+
+extern "C" {
+
+void* orc_new(uint64_t reserve) {
+    Table* t = new Table();
+    if (reserve) t->m.reserve(reserve);
+    return t;
+}
+
+void orc_free(void* h) { delete static_cast<Table*>(h); }
+
+uint64_t orc_size(const void* h) { return static_cast<const Table*>(h)->m.size(); }
+
+// Section 5: for each element in sequence order, look it up; insert it if it
+// is absent.  is_new[i] records which of the two happened.  A stored value of
+// 0 is used for maps (find-or-put carries no value).
+void orc_find_or_put(void* h, const uint64_t* keys, uint64_t n, uint8_t* is_new) {
+    Table* t = static_cast<Table*>(h);
+    for (uint64_t i = 0; i < n; ++i) {
+        bool inserted = t->m.emplace(keys[i], 0u).second;
+        if (is_new) is_new[i] = inserted ? 1 : 0;
+    }
+}
+
+// Insert-if-absent: the first value stored for a key is kept.
+void orc_insert(void* h, const uint64_t* keys, const uint32_t* vals, uint64_t n) {
+    Table* t = static_cast<Table*>(h);
+    for (uint64_t i = 0; i < n; ++i) t->m.emplace(keys[i], vals ? vals[i] : 0u);
+}
+
+// Lookup: found[i] = keys[i] in S; vals[i] = its stored value (0 if absent).
+void orc_lookup(const void* h, const uint64_t* keys, uint64_t n, uint8_t* found, uint32_t* vals) {
+    const Table* t = static_cast<const Table*>(h);
+    for (uint64_t i = 0; i < n; ++i) {
+        auto it = t->m.find(keys[i]);
+        bool f = it != t->m.end();
+        if (found) found[i] = f ? 1 : 0;
+        if (vals) vals[i] = f ? it->second : 0u;
+    }
+}
+
+// Copy out up to cap (key, value) pairs in unspecified order; returns |S|.
+uint64_t orc_export(const void* h, uint64_t* keys, uint32_t* vals, uint64_t cap) {
+    const Table* t = static_cast<const Table*>(h);
+    uint64_t i = 0;
+    for (const auto& kv : t->m) {
+        if (i < cap) {
+            if (keys) keys[i] = kv.first;
+            if (vals) vals[i] = kv.second;
+        }
+        ++i;
+    }
+    return i;
+}
+
+// ---------------------------------------------------------------------------
+// State-space models.  Same field layout as the tables drawn by
+// workloads/statespace.py (16 components, 32 local states, 4 transitions per
+// local state, 8 sync pairs).
+// ---------------------------------------------------------------------------
+struct orc_model {
+    int32_t C;
+    int32_t P;
+    uint8_t bits[16];
+    uint8_t pc1[8];
+    uint8_t pc2[8];
+    uint8_t deg[16][32];
+    uint8_t tgt[16][32][4];
+    uint8_t lab[16][32][4];
+};
+
+}  // extern "C"
+
+namespace {
+
+struct Layout {
+    int off[16];
+    uint64_t mask[16];
+};
+
+Layout layout_of(const orc_model* m) {
+    Layout l{};
+    int o = 0;
+    for (int c = 0; c < m->C; ++c) {
+        l.off[c] = o;
+        l.mask[c] = (uint64_t(1) << m->bits[c]) - 1;
+        o += m->bits[c];
+    }
+    return l;
+}
+
+inline uint64_t local_of(const Layout& l, uint64_t s, int c) { return (s >> l.off[c]) & l.mask[c]; }
+
+inline uint64_t with_local(const Layout& l, uint64_t s, int c, uint64_t v) {
+    return (s & ~(l.mask[c] << l.off[c])) | (v << l.off[c]);
+}
+
+// Successors of s, in a fixed order (components' local actions, then pairs).
+template <class Emit>
+void successors(const orc_model* m, const Layout& l, uint64_t s, Emit emit) {
+    for (int c = 0; c < m->C; ++c) {
+        uint64_t u = local_of(l, s, c);
+        for (int j = 0; j < m->deg[c][u]; ++j)
+            if (m->lab[c][u][j] == 0) emit(with_local(l, s, c, m->tgt[c][u][j]));
+    }
+    for (int p = 0; p < m->P; ++p) {
+        int c1 = m->pc1[p], c2 = m->pc2[p];
+        uint64_t u1 = local_of(l, s, c1), u2 = local_of(l, s, c2);
+        for (int j1 = 0; j1 < m->deg[c1][u1]; ++j1) {
+            if (m->lab[c1][u1][j1] != p + 1) continue;
+            for (int j2 = 0; j2 < m->deg[c2][u2]; ++j2) {
+                if (m->lab[c2][u2][j2] != p + 1) continue;
+                uint64_t t = with_local(l, s, c1, m->tgt[c1][u1][j1]);
+                emit(with_local(l, t, c2, m->tgt[c2][u2][j2]));
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+// All successors of one state; returns how many there are (writes at most cap).
+uint64_t orc_successors(const orc_model* m, uint64_t s, uint64_t* out, uint64_t cap) {
+    Layout l = layout_of(m);
+    uint64_t n = 0;
+    successors(m, l, s, [&](uint64_t t) {
+        if (n < cap) out[n] = t;
+        ++n;
+    });
+    return n;
+}
+
+// Level-synchronous BFS from s0.  level_sizes[d] = |L_d|; level_succ[d] =
+// number of successors generated from L_d (with repeats).  states_out (may be
+// NULL) receives the states level by level, up to states_cap.  Returns 0 when
+// the exploration finished, 1 if more than max_states states were reached,
+// 2 if more than max_levels levels were needed.
+int orc_bfs(const orc_model* m, uint64_t s0, uint64_t max_states, uint32_t max_levels,
+            uint64_t* level_sizes, uint64_t* level_succ, uint64_t* states_out,
+            uint64_t states_cap, uint32_t* nlevels, uint64_t* total) {
+    Layout l = layout_of(m);
+    std::unordered_map<uint64_t, uint32_t> seen;  // closed + open sets
+    seen.reserve(max_states < (uint64_t(1) << 28) ? max_states + 1 : (uint64_t(1) << 28));
+    std::vector<uint64_t> cur{s0}, nxt;
+    seen.emplace(s0, 0u);
+    uint64_t stored = 0;
+    auto keep = [&](uint64_t s) {
+        if (states_out && stored < states_cap) states_out[stored] = s;
+        ++stored;
+    };
+    keep(s0);
+    uint32_t d = 0;
+    int rc = 0;
+    while (!cur.empty()) {
+        if (d >= max_levels) { rc = 2; break; }
+        level_sizes[d] = cur.size();
+        uint64_t gen = 0;
+        nxt.clear();
+        for (uint64_t s : cur) {
+            successors(m, l, s, [&](uint64_t t) {
+                ++gen;
+                if (seen.emplace(t, d + 1).second) nxt.push_back(t);
+            });
+        }
+        if (level_succ) level_succ[d] = gen;
+        ++d;
+        for (uint64_t t : nxt) keep(t);
+        if (seen.size() > max_states) { rc = 1; break; }
+        cur.swap(nxt);
+    }
+    *nlevels = d;
+    *total = seen.size();
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+"""The seeded input generators produce what their docstrings promise."""
+import numpy as np
+import pytest
+
+from workloads import keys as wk
+from workloads import statespace as ss
+
+
+@pytest.mark.parametrize("width", [32, 64])
+def test_distinct_keys_are_distinct_and_valid(width):
+    k = wk.distinct_keys(1 << 16, width, seed=5)
+    assert len(np.unique(k)) == len(k)
+    if width == 32:
+        assert k.dtype == np.uint32 and not (k == np.uint32(wk.EMPTY32)).any()
+    else:
+        assert k.dtype == np.uint64 and (k >> np.uint64(63) == 0).all()
+    other = wk.distinct_keys(1 << 12, width, seed=5, start=1 << 16)
+    assert len(np.intersect1d(k, other)) == 0
+
+
+def test_mix32_perm_is_a_bijection_on_a_small_domain():
+    # The cycle-walking permutation maps [0, 2^32-1) onto itself; check the
+    # top of the domain explicitly (where the reserved value lives).
+    x = np.arange((1 << 32) - (1 << 16), (1 << 32) - 1, dtype=np.uint64)
+    y = wk.mix32_perm(x, seed=9)
+    assert len(np.unique(y)) == len(y)
+    assert not (y == wk.EMPTY32).any()
+
+
+@pytest.mark.parametrize("d", [0.0, 0.25, 0.5])
+@pytest.mark.parametrize("width", [32, 64])
+def test_fill_stream_shape(d, width):
+    n, B = 5000, 1024
+    fs = wk.fill_stream(n, B, d, width, seed=3)
+    assert len(np.unique(fs.keys)) == n
+    assert fs.fresh_counts.sum() == n
+    seen = set()
+    for b in range(fs.n_batches):
+        kb = fs.batch(b).tolist()
+        first = set(kb) - seen
+        assert len(first) == fs.fresh_counts[b]
+        seen |= set(kb)
+    if d == 0.0:
+        assert fs.n_issued == n
+    else:
+        assert abs(fs.n_issued - n / (1 - d)) < fs.n_batches + 2
+
+
+def test_lookup_batch_split():
+    keys, present = wk.lookup_batch(1000, 2001, 64, seed=1)
+    stored = set(wk.distinct_keys(1000, 64, seed=1).tolist())
+    assert present.sum() == 1000
+    for k, p in zip(keys.tolist(), present.tolist()):
+        assert (k in stored) == bool(p)
+
+
+def test_models_fit_their_format():
+    m = ss.config3_model()
+    assert m.C == 12 and m.total_bits == 60 and m.key_width == 64 and m.P == 4
+    assert (m.deg[:12, :32] >= 1).all() and (m.deg[:12, :32] <= 3).all()
+    for c in range(m.C):
+        for u in range(32):
+            for j in range(m.deg[c, u]):
+                lab = int(m.lab[c, u, j])
+                assert lab == 0 or c in m.pairs[lab - 1]
+    ms = ss.batched_models(16, seed=2)
+    for mm in ms:
+        assert 6 <= mm.C <= 10 and mm.total_bits <= 63

@@ -1,0 +1,427 @@
+"""Benchmark: batched find-or-put into both hash-table schemes on one GB300.
+
+A step is the paper's timed quantity (Section 5: the time to find-or-insert
+every element of a sequence) on the random-key workload at load 0.8: an
+empty table of ceil(n/0.8) slots is filled with n distinct uniformly random
+64-bit keys by find-or-put batches of 2^24 keys, 25% of each batch repeats of
+keys already issued; once with the bucket scheme and once with Cuckoo
+hashing.  `value` = find-or-put keys processed per second over the whole
+step, both schemes.
+
+Prints one JSON line.  Under torchrun each rank runs its own replica (the
+path has no exchange step) and rank 0 reports the whole-job throughput.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "find-or-put Mops/s per scheme at load 0.8; % HBM random-access roofline; p99 lat"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--schemes", default="bucket,cuckoo")
+    ap.add_argument("--n-log2", type=int, default=27)
+    ap.add_argument("--lf", type=float, default=0.8)
+    ap.add_argument("--batch-log2", type=int, default=24)
+    ap.add_argument("--dup", type=float, default=0.25)
+    ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a, schemes):
+    n = 1 << a.n_log2
+    return {
+        "workload": "random 64-bit keys, fill to load %.2f: n=2^%d distinct, find-or-put batches of 2^%d, "
+                    "%d%% repeats; schemes %s" % (a.lf, a.n_log2, a.batch_log2, round(a.dup * 100), "+".join(schemes)),
+        "n_distinct": n,
+        "capacity_slots": int(np.ceil(n / a.lf)),
+        "load": a.lf,
+        "batch": 1 << a.batch_log2,
+        "dup_rate": a.dup,
+        "key_width": 64,
+        "schemes": schemes,
+        "l2": "inputs larger than L2 (table %.2f GB, keys %.2f GB, L2 129 MB); no flush needed"
+              % (np.ceil(n / a.lf) * 8 / 1e9, n / (1 - a.dup) * 8 / 1e9),
+    }
+
+
+# ----------------------------------------------------------------- helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel's source has not changed since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    for m in re.finditer(r"^traffic\s+(\S+)\s+(\S+)\s+(\d+)\s+(\w+)\s*$", text, re.M):
+        name, src, nbytes, sha = m.groups()
+        if name != kernel:
+            continue
+        try:
+            cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+        except OSError:
+            return None, None
+        if cur == sha:
+            return int(nbytes), src
+    return None, None
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(a, rank, world, local):
+    import torch
+    import paper_1712_09494_gb300 as ht
+    from workloads import keys as wk
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    schemes = [s for s in a.schemes.split(",") if s]
+    n = 1 << a.n_log2
+    B = 1 << a.batch_log2
+    fs = wk.fill_stream(n, B, a.dup, 64, seed=a.seed + rank)
+    keys_h = torch.from_numpy(fs.keys.view(np.int64))
+    keys_d = keys_h.to(dev)
+    offs = fs.offsets.tolist()
+    is_new_d = torch.empty(B, dtype=torch.uint8, device=dev)
+    cap = int(np.ceil(n / a.lf))
+    tables = {s: ht.HashTable(cap, s, 64) for s in schemes}
+    stream = torch.cuda.current_stream(dev)
+    n_ops = fs.n_issued * len(schemes)
+
+    def fill(t):
+        ht.ht_clear(t.handle)
+        for b in range(fs.n_batches):
+            ht.ht_find_or_put(t.handle, keys_d[offs[b]:offs[b + 1]], is_new_d[:offs[b + 1] - offs[b]])
+
+    ev = {s: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for s in schemes}
+    per_ms = {s: 0.0 for s in schemes}
+    for _ in range(a.warmup):
+        for s in schemes:
+            fill(tables[s])
+    torch.cuda.synchronize()
+    for s in schemes:
+        rc = tables[s].sync()
+        if rc != 0 or tables[s].size() != n:
+            raise RuntimeError("warm-up fill of %s ended with status %d, size %d" % (s, rc, tables[s].size()))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    ht.ht_prof_reset()
+    ht.ht_prof_enable(True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms_each = {s: [] for s in schemes}
+    barrier()
+    clocks.start()
+    t0.record(stream)
+    for _ in range(a.steps):
+        for s in schemes:
+            ev[s][0].record(stream)
+            fill(tables[s])
+            ev[s][1].record(stream)
+            step_ms_each[s].append((ev[s][0], ev[s][1]))
+            ev[s] = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ht.ht_prof_enable(False)
+    kern = ht.ht_prof_read()
+    ms_total = t0.elapsed_time(t1)
+    for s in schemes:
+        per_ms[s] = sum(e0.elapsed_time(e1) for e0, e1 in step_ms_each[s]) / a.steps
+    ms_step = ms_total / a.steps
+    if world > 1:
+        import torch.distributed as dist
+        tm = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms_step = float(tm.item())
+    for s in schemes:
+        if tables[s].sync() != 0 or tables[s].size() != n:
+            raise RuntimeError("timed fill of %s did not end exact" % s)
+    value = n_ops * world / (ms_step / 1e3) / 1e6
+
+    # Roofline of the dominant kernel: algorithmic bytes per launch / event time.
+    p_new = fs.n_distinct / fs.n_issued
+    per_key = {
+        # key read + flag write + one 128-byte bucket + the claimed sector for new keys
+        "bucket_find_or_put": 8 + 1 + 128 + p_new * 32,
+        # key read + flag write + 32-byte sector of h_1 for hits; k sectors plus the
+        # 16-byte winner record for misses (k = 4)
+        "cuckoo_probe": 8 + 1 + (1 - p_new) * 32 + p_new * (4 * 32 + 16),
+        # winner record + one exchange (32-byte read + 32-byte write) per winner
+        "cuckoo_insert": 16 + 64,
+    }
+    units_per_launch = {"bucket_find_or_put": fs.n_issued / fs.n_batches,
+                        "cuckoo_probe": fs.n_issued / fs.n_batches,
+                        "cuckoo_insert": fs.n_distinct / fs.n_batches}
+    peak, peak_src = measured_peaks()
+    kernels = {}
+    for name, (launches, tot) in kern.items():
+        entry = {"launches": launches, "total_ms": round(tot, 3), "avg_ms": round(tot / launches, 4)}
+        if name in per_key:
+            alg = per_key[name] * units_per_launch[name]
+            entry["alg_bytes_per_launch"] = int(alg)
+            entry["achieved_gbs"] = round(alg / (tot / launches / 1e3) / 1e9, 1)
+            entry["frac_of_" + peak_src] = round(entry["achieved_gbs"] / peak, 3)
+        kernels[name] = entry
+    dom = max((k for k in kernels if k in per_key), key=lambda k: kernels[k]["total_ms"])
+    traffic, _ = recorded_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"], "peak": peak,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, copy burst)" if peak_src == "measured"
+                else "fallback 6.8 TB/s",
+                "unit": "GB/s", "frac": round(kernels[dom]["achieved_gbs"] / peak, 3),
+                "traffic": traffic, "alg_bytes_per_key": round(per_key[dom], 1)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "Mops/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(a, schemes),
+        "per_scheme": {s: {"ms_per_fill": round(per_ms[s], 3),
+                           "mops": round(fs.n_issued / (per_ms[s] / 1e3) / 1e6, 1)} for s in schemes},
+        "roofline": roofline, "kernels": kernels, "clocks": clk,
+        "gpu_launches": int(sum(v[0] for v in kern.values())),
+    }
+
+    # End to end through the C ABI from pinned host buffers.
+    if not a.no_e2e:
+        out["e2e"] = run_e2e(a, ht, torch, dev, fs, tables, schemes, world)
+    if not a.no_probe and rank == 0:
+        out["random_read_roofline"] = run_probe(ht, torch, dev)
+    for t in tables.values():
+        t.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def run_e2e(a, ht, torch, dev, fs, tables, schemes, world):
+    """Same step, inputs from pinned host memory and is_new back to pinned host
+    memory, all copies inside the timed region (one stream, batch by batch)."""
+    B = 1 << a.batch_log2
+    keys_h = torch.from_numpy(fs.keys.view(np.int64)).pin_memory()
+    out_h = torch.empty(fs.n_issued, dtype=torch.uint8).pin_memory()
+    kbuf = torch.empty(B, dtype=torch.int64, device=dev)
+    fbuf = torch.empty(B, dtype=torch.uint8, device=dev)
+    offs = fs.offsets.tolist()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for s in schemes:
+            t = tables[s]
+            ht.ht_clear(t.handle)
+            for b in range(fs.n_batches):
+                m = offs[b + 1] - offs[b]
+                kbuf[:m].copy_(keys_h[offs[b]:offs[b + 1]], non_blocking=True)
+                ht.ht_find_or_put(t.handle, kbuf[:m], fbuf[:m])
+                out_h[offs[b]:offs[b + 1]].copy_(fbuf[:m], non_blocking=True)
+
+    for _ in range(max(1, a.warmup)):
+        step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(a.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / a.steps
+    if world > 1:
+        import torch.distributed as dist
+        tm = torch.tensor([ms], device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm.item())
+    # the last step's flags must count exactly the distinct keys
+    if int(out_h.sum()) != fs.n_distinct:
+        raise RuntimeError("e2e flags do not count the distinct keys")
+    return {"value": round(fs.n_issued * len(schemes) * world / (ms / 1e3) / 1e6, 1), "unit": "Mops/s",
+            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(fs.n_issued * 8 * len(schemes)),
+            "d2h_bytes_per_step": int(fs.n_issued * len(schemes))}
+
+
+def run_probe(ht, torch, dev):
+    """Random-read throughput at 32/128-byte granularity over a 4 GiB buffer
+    (>> L2): the ceiling for hash probes, reported beside the copy peak."""
+    buf = torch.empty(1 << 29, dtype=torch.int64, device=dev)
+    buf.fill_(1)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    res = {}
+    for gran in (32, 128):
+        n_acc = (1 << 31) // gran * 4   # 8 GiB of reads
+        ht.ht_probe_random_read(buf, gran, n_acc, 7, sink)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r in range(3):
+            ht.ht_probe_random_read(buf, gran, n_acc, 11 + r, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        res["%dB_gbs" % gran] = round(n_acc * gran / (ms / 1e3) / 1e9, 1)
+    del buf
+    return res
+
+
+# ----------------------------------------------------------------- CPU legs
+def run_cpu_oracle(a, sample_batches=4):
+    """The oracle (single-threaded std::unordered_map) on the first batches of
+    the same stream; returns (Mops/s, description)."""
+    import oracle
+    from workloads import keys as wk
+    n = 1 << a.n_log2
+    fs = wk.fill_stream(n, 1 << a.batch_log2, a.dup, 64, seed=a.seed)
+    nb = min(sample_batches, fs.n_batches)
+    keys = fs.keys[:fs.offsets[nb]]
+    t = oracle.OracleTable(reserve=n)
+    t0 = time.perf_counter()
+    t.find_or_put(keys)
+    dt = time.perf_counter() - t0
+    return len(keys) / dt / 1e6, "first %d of %d batches of the stream (%d keys, one scheme-free set)" % (
+        nb, fs.n_batches, len(keys))
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return None
+    schemes = [s for s in a.schemes.split(",") if s]
+    vals = []
+    desc = None
+    for _ in range(a.warmup):
+        run_cpu_oracle(a, sample_batches=1)
+    t_start = time.perf_counter()
+    for _ in range(a.steps):
+        v, desc = run_cpu_oracle(a, sample_batches=1)
+        vals.append(v)
+    wall = time.perf_counter() - t_start
+    v = statistics.median(vals)
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": "Mops/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(wall / a.steps * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": workload_config(a, schemes),
+        "cpu_baseline": {"value": round(v, 2), "unit": "Mops/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(v, 2), "unit": "Mops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    a = parse()
+    rank, world, local = dist_env()
+    if a.impl == "reference":
+        out = run_reference(a, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = run_ours(a, rank, world, local)
+    if rank == 0:
+        if not a.no_cpu and world == 1:
+            v, desc = run_cpu_oracle(a)
+            out["cpu_baseline"] = {"value": round(v, 2), "unit": "Mops/s", "cores": 1, "kind": "oracle",
+                                   "sample": desc}
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

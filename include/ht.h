@@ -1,0 +1,191 @@
+/* ht.h -- C ABI of a GPU hash set/map for state-space exploration (sm_103a).
+ *
+ * The operations follow the problem statement of Cassee & Wijs, "Analysing
+ * the Performance of GPU Hash Tables for State Space Exploration" (GaM 2017):
+ *
+ *   Section 5      "find, else insert": for every element of a sequence,
+ *                  look it up; if found do nothing, otherwise insert it.
+ *   Section 4.1    Cuckoo hashing (Alcantara et al.): k hash functions,
+ *                  eviction chains, a stash, rebuild with new constants.
+ *   Section 4.2    The GPUexplore bucket table: hash to a bucket of slots
+ *                  read cooperatively by a group of lanes, atomic claim of a
+ *                  free slot, the next hash function when a bucket is full.
+ *   Section 3.2    BFS over state vectors with open/closed sets kept in the
+ *                  hash table.
+ *
+ * Conventions for every call
+ * --------------------------
+ *  * Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *    pointers owned by the caller.  Nothing keeps a caller pointer after the
+ *    call returns, except that the work it enqueued reads/writes it later in
+ *    stream order.
+ *  * `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *    stream-ordered and asynchronous unless they say "synchronises".
+ *  * Operations on one table must be issued in order on one stream at a time.
+ *    Different tables are independent.
+ *  * Keys: key_width 32 -> uint32 keys, 0xFFFFFFFF reserved (empty marker);
+ *    key_width 64 -> uint64 keys whose top bit must be 0.  A reserved key in a
+ *    batch is skipped (is_new/found = 0) and makes the next synchronising call
+ *    on the table return HT_ERR_INVALID; the rest of the batch is processed.
+ *  * Values (maps): only tables with key_width 32 carry a uint32 value, packed
+ *    with the key in one 64-bit slot so that a slot moves atomically.
+ *  * Table memory is allocated by ht_create and freed by ht_destroy.
+ *  * Errors found on the device (reserved key, table full) are sticky and are
+ *    reported by the next synchronising call (ht_sync, ht_size, ht_export).
+ *    HT_ERR_CUDA is returned when a CUDA call or launch fails.
+ */
+#ifndef HT_H_
+#define HT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { HT_BUCKET = 0, HT_CUCKOO = 1 } ht_scheme;
+
+typedef enum {
+    HT_OK = 0,
+    HT_ERR_INVALID = 1,  /* bad argument, or a reserved key was seen */
+    HT_ERR_OOM = 2,      /* device allocation failed */
+    HT_ERR_FULL = 3,     /* keys could not be placed even after rebuilds */
+    HT_ERR_CUDA = 4,     /* a CUDA call or kernel launch failed */
+    HT_ERR_TIMEOUT = 5   /* a bounded device wait gave up */
+} ht_status;
+
+/* Tunables.  A zero field means "default".  Section 5 of the paper fixes a
+ * table of 1.25x the unique keys (load 0.8) and about four hash functions;
+ * the defaults below are chosen for that load on large tables:
+ *   num_hashes     bucket: 16 (hashes are computed lazily, a later one only
+ *                  when the earlier buckets are full); cuckoo: 4.  Max 16 /
+ *                  8 respectively.
+ *   max_evictions  cuckoo eviction-chain bound, default 256, max 4096.
+ *   stash_slots    default 101 (both schemes).
+ *   bucket_slots   8, 16 or 32 slots of 8 bytes; default 16 (128 bytes).
+ *   lanes_per_key  lanes that read one bucket: bucket_slots/lanes in 1..4;
+ *                  default bucket_slots/2.
+ *   max_rebuilds   rebuild attempts with fresh hash constants, default 8.
+ *   max_batch      cuckoo keys per probe/insert launch pair (sizes the
+ *                  in-batch dedup scratch), default 2^22.
+ *   seed           hash-constant seed.
+ *   l2_persist     1: mark the slot array persisting in L2 when it fits.  */
+typedef struct ht_params {
+    uint32_t num_hashes;
+    uint32_t max_evictions;
+    uint32_t stash_slots;
+    uint32_t bucket_slots;
+    uint32_t lanes_per_key;
+    uint32_t max_rebuilds;
+    uint64_t max_batch;
+    uint64_t seed;
+    int32_t l2_persist;
+    int32_t reserved_[3];
+} ht_params;
+
+typedef struct ht_table ht_table;
+
+/* Fills *p with the defaults of `scheme`.  Host only. */
+ht_status ht_default_params(ht_scheme scheme, ht_params* p);
+
+/* Creates an empty table of at least `capacity` slots (rounded up to whole
+ * buckets, for both schemes) on the current device.  Section 5: the paper
+ * sizes the table at 1.25x the number of unique keys.  params may be NULL.
+ * Allocates the slot array, stash, overflow set and counters (and, for
+ * Cuckoo, the dedup scratch) with cudaMalloc, and clears them on `stream`.
+ * Errors: HT_ERR_INVALID (capacity 0 or > 2^40, key_width not 32/64, bad
+ * params), HT_ERR_OOM, HT_ERR_CUDA.  *out is NULL on error. */
+ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width,
+                    const ht_params* params, void* stream, ht_table** out);
+
+/* Frees the table (synchronises the device).  NULL is accepted. */
+ht_status ht_destroy(ht_table* t);
+
+/* Batched find-or-put (Section 5): for each key, insert it if it is absent.
+ * d_keys: n keys (uint32 or uint64 by key_width).  d_is_new (nullable): n
+ * bytes, 1 where this call stored the key.  Among equal keys of one batch
+ * exactly one is flagged (which one is unspecified).  On a map the stored
+ * value is 0. */
+ht_status ht_find_or_put(ht_table* t, const void* d_keys, uint64_t n,
+                         uint8_t* d_is_new, void* stream);
+
+/* find-or-put that also appends each newly stored key to d_new_keys at
+ * positions reserved by atomically adding to *d_new_count (a device uint64
+ * counter the caller zeroes; the call does not reset it).  d_new_keys must
+ * have room for every key of the batch plus *d_new_count.  Used to turn a
+ * BFS level's successors into the next frontier (Section 3.2's open set). */
+ht_status ht_find_or_put_append(ht_table* t, const void* d_keys, uint64_t n,
+                                uint8_t* d_is_new, void* d_new_keys,
+                                unsigned long long* d_new_count, void* stream);
+
+/* Insert-if-absent with values (key_width 32 maps; d_values must be NULL for
+ * key_width 64).  A key already present keeps its value; among equal keys in
+ * one batch one of the supplied values wins. */
+ht_status ht_insert(ht_table* t, const void* d_keys, const uint32_t* d_values,
+                    uint64_t n, void* stream);
+
+/* Lookup (Section 4.1: at most k slots; Section 4.2: at most k buckets).
+ * d_found (nullable): n bytes, 1 if present.  d_values (nullable, maps only):
+ * n uint32, the stored value or 0. */
+ht_status ht_lookup(ht_table* t, const void* d_keys, uint64_t n,
+                    uint32_t* d_values, uint8_t* d_found, void* stream);
+
+/* Synchronises `stream`, runs a pending rebuild (Section 4.1: when the stash
+ * is full and an insertion fails, rebuild with new hash constants) and
+ * returns the table's sticky status. */
+ht_status ht_sync(ht_table* t, void* stream);
+
+/* Number of stored keys (synchronises; runs ht_sync first). */
+ht_status ht_size(ht_table* t, uint64_t* out, void* stream);
+
+/* Copies every stored key (and value, if d_values_out is non-NULL) into the
+ * caller's buffers of `cap` entries, in unspecified order; *count = number of
+ * stored keys (synchronises).  HT_ERR_INVALID if cap < count (nothing is
+ * guaranteed about the buffers then). */
+ht_status ht_export(ht_table* t, void* d_keys_out, uint32_t* d_values_out,
+                    uint64_t cap, uint64_t* count, void* stream);
+
+/* Empties the table, keeping its capacity and hash constants. */
+ht_status ht_clear(ht_table* t, void* stream);
+
+/* Table facts: slots, hash functions, rebuilds done so far. */
+ht_status ht_info(const ht_table* t, uint64_t* slots, uint32_t* num_hashes,
+                  uint32_t* rebuilds);
+
+const char* ht_status_str(ht_status s);
+
+/* ---------------------------------------------------------------------------
+ * Frontier compaction (the BFS open set, Section 3.2): appends d_keys[i] for
+ * every i with d_flags[i] != 0 to d_out at positions reserved on the device
+ * counter *d_count (not reset by the call).  Order is unspecified.
+ * ------------------------------------------------------------------------- */
+ht_status ht_compact(const void* d_keys, const uint8_t* d_flags, uint64_t n,
+                     uint32_t key_width, void* d_out, unsigned long long* d_count,
+                     void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Kernel timing (CUDA events around every launch the library makes, on the
+ * launch's stream).  ht_prof_read synchronises on the recorded events.
+ * ------------------------------------------------------------------------- */
+ht_status ht_prof_enable(int on);
+ht_status ht_prof_reset(void);
+/* Number of kernel kinds; names are stable strings. */
+uint32_t ht_prof_num_kernels(void);
+const char* ht_prof_kernel_name(uint32_t id);
+ht_status ht_prof_read(uint32_t id, uint64_t* launches, double* total_ms);
+
+/* ---------------------------------------------------------------------------
+ * Random-access roofline probe: reads n_access blocks of `gran` bytes (32,
+ * 64 or 128) at uniformly random gran-aligned offsets of d_buf[0..bytes) and
+ * folds them into *d_sink.  Measures the random-gather throughput that bounds
+ * the probes of both schemes.  Not part of the hash table.
+ * ------------------------------------------------------------------------- */
+ht_status ht_probe_random_read(const void* d_buf, uint64_t bytes, uint32_t gran,
+                               uint64_t n_access, uint64_t seed,
+                               unsigned long long* d_sink, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HT_H_ */

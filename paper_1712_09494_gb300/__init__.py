@@ -1,0 +1,247 @@
+"""GPU hash set/map for state-space exploration on GB300 (sm_103a).
+
+A thin Python binding over the C ABI in include/ht.h.  Each ``ht_*`` function
+here has the C function's name and only marshals arguments (tensor data
+pointers, the current CUDA stream); every step of every operation runs in
+the CUDA kernels of libht.so.  There is no CPU fallback: if the library is
+missing, importing the functions raises.
+
+The schemes are the two compared by Cassee & Wijs (GaM 2017): the
+GPUexplore bucket table (Section 4.2) and Cuckoo hashing after Alcantara et
+al. (Section 4.1); the operations follow Section 5's find-or-insert.
+"""
+import ctypes
+
+import torch
+
+from ._lib import HT_BUCKET, HT_CUCKOO, HtError, HtParams, load
+
+__all__ = [
+    "HT_BUCKET", "HT_CUCKOO", "HtError", "HtParams", "HashTable", "load",
+    "ht_default_params", "ht_create", "ht_destroy", "ht_find_or_put", "ht_find_or_put_append",
+    "ht_insert", "ht_lookup", "ht_sync", "ht_size", "ht_export", "ht_clear", "ht_info",
+    "ht_compact", "ht_prof_enable", "ht_prof_reset", "ht_prof_read", "ht_prof_kernels",
+    "ht_probe_random_read", "scheme_of",
+]
+
+_KEY_DTYPES = {32: (torch.int32, torch.uint32), 64: (torch.int64, torch.uint64)}
+
+
+def scheme_of(name):
+    if isinstance(name, int):
+        return name
+    return {"bucket": HT_BUCKET, "cuckoo": HT_CUCKOO}[name]
+
+
+def _check(status, where):
+    if status != 0:
+        raise HtError(status, where)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dptr(t, what):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _key_width(keys):
+    es = keys.element_size()
+    if es not in (4, 8):
+        raise ValueError("keys must be 32- or 64-bit integers")
+    return es * 8
+
+
+def _params(params, scheme):
+    if params is None:
+        return None
+    if isinstance(params, HtParams):
+        return params
+    p = ht_default_params(scheme)
+    for k, v in dict(params).items():
+        setattr(p, k, v)
+    return p
+
+
+# ----------------------------------------------------------------- C ABI
+def ht_default_params(scheme):
+    p = HtParams()
+    _check(load().ht_default_params(scheme_of(scheme), ctypes.byref(p)), "ht_default_params")
+    return p
+
+
+def ht_create(capacity, scheme, key_width, params=None, stream=None):
+    scheme = scheme_of(scheme)
+    p = _params(params, scheme)
+    out = ctypes.c_void_p()
+    _check(load().ht_create(int(capacity), scheme, int(key_width),
+                            ctypes.byref(p) if p is not None else None, _stream(stream),
+                            ctypes.byref(out)), "ht_create")
+    return out
+
+
+def ht_destroy(table):
+    _check(load().ht_destroy(table), "ht_destroy")
+
+
+def ht_find_or_put(table, keys, is_new=None, stream=None):
+    _check(load().ht_find_or_put(table, _dptr(keys, "keys"), keys.numel(), _dptr(is_new, "is_new"),
+                                 _stream(stream)), "ht_find_or_put")
+
+
+def ht_find_or_put_append(table, keys, new_keys, new_count, is_new=None, stream=None):
+    _check(load().ht_find_or_put_append(table, _dptr(keys, "keys"), keys.numel(), _dptr(is_new, "is_new"),
+                                        _dptr(new_keys, "new_keys"), _dptr(new_count, "new_count"),
+                                        _stream(stream)), "ht_find_or_put_append")
+
+
+def ht_insert(table, keys, values=None, stream=None):
+    _check(load().ht_insert(table, _dptr(keys, "keys"), _dptr(values, "values"), keys.numel(),
+                            _stream(stream)), "ht_insert")
+
+
+def ht_lookup(table, keys, values=None, found=None, stream=None):
+    _check(load().ht_lookup(table, _dptr(keys, "keys"), keys.numel(), _dptr(values, "values"),
+                            _dptr(found, "found"), _stream(stream)), "ht_lookup")
+
+
+def ht_sync(table, stream=None):
+    return load().ht_sync(table, _stream(stream))
+
+
+def ht_size(table, stream=None):
+    n = ctypes.c_uint64()
+    _check(load().ht_size(table, ctypes.byref(n), _stream(stream)), "ht_size")
+    return n.value
+
+
+def ht_export(table, keys_out, values_out=None, stream=None):
+    n = ctypes.c_uint64()
+    _check(load().ht_export(table, _dptr(keys_out, "keys_out"), _dptr(values_out, "values_out"),
+                            keys_out.numel(), ctypes.byref(n), _stream(stream)), "ht_export")
+    return n.value
+
+
+def ht_clear(table, stream=None):
+    _check(load().ht_clear(table, _stream(stream)), "ht_clear")
+
+
+def ht_info(table):
+    s, k, r = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().ht_info(table, ctypes.byref(s), ctypes.byref(k), ctypes.byref(r)), "ht_info")
+    return dict(slots=s.value, num_hashes=k.value, rebuilds=r.value)
+
+
+def ht_compact(keys, flags, out, count, stream=None):
+    _check(load().ht_compact(_dptr(keys, "keys"), _dptr(flags, "flags"), keys.numel(), _key_width(keys),
+                             _dptr(out, "out"), _dptr(count, "count"), _stream(stream)), "ht_compact")
+
+
+def ht_prof_enable(on=True):
+    _check(load().ht_prof_enable(1 if on else 0), "ht_prof_enable")
+
+
+def ht_prof_reset():
+    _check(load().ht_prof_reset(), "ht_prof_reset")
+
+
+def ht_prof_kernels():
+    lib = load()
+    return [lib.ht_prof_kernel_name(i).decode() for i in range(lib.ht_prof_num_kernels())]
+
+
+def ht_prof_read():
+    """{kernel name: (launches, total_ms)} over the launches since the last reset."""
+    lib = load()
+    out = {}
+    for i, name in enumerate(ht_prof_kernels()):
+        n, ms = ctypes.c_uint64(), ctypes.c_double()
+        _check(lib.ht_prof_read(i, ctypes.byref(n), ctypes.byref(ms)), "ht_prof_read")
+        if n.value:
+            out[name] = (n.value, ms.value)
+    return out
+
+
+def ht_probe_random_read(buf, gran, n_access, seed, sink, stream=None):
+    _check(load().ht_probe_random_read(_dptr(buf, "buf"), buf.numel() * buf.element_size(), int(gran),
+                                       int(n_access), int(seed), _dptr(sink, "sink"), _stream(stream)),
+           "ht_probe_random_read")
+
+
+# ----------------------------------------------------------------- helper
+class HashTable:
+    """Owns one table; methods allocate their outputs with torch on the keys' device."""
+
+    def __init__(self, capacity, scheme="bucket", key_width=64, params=None, stream=None):
+        self.scheme = scheme_of(scheme)
+        self.key_width = int(key_width)
+        self._h = ht_create(capacity, self.scheme, self.key_width, params, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            ht_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _keys(self, keys):
+        if _key_width(keys) != self.key_width:
+            raise ValueError("table has %d-bit keys" % self.key_width)
+        return keys.contiguous()
+
+    def find_or_put(self, keys, stream=None):
+        keys = self._keys(keys)
+        is_new = torch.empty(keys.numel(), dtype=torch.uint8, device=keys.device)
+        ht_find_or_put(self._h, keys, is_new, stream)
+        return is_new
+
+    def insert(self, keys, values=None, stream=None):
+        keys = self._keys(keys)
+        ht_insert(self._h, keys, None if values is None else values.contiguous(), stream)
+
+    def lookup(self, keys, stream=None):
+        keys = self._keys(keys)
+        found = torch.empty(keys.numel(), dtype=torch.uint8, device=keys.device)
+        values = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device) if self.key_width == 32 else None
+        ht_lookup(self._h, keys, values, found, stream)
+        return found, values
+
+    def sync(self, stream=None):
+        return ht_sync(self._h, stream)
+
+    def size(self, stream=None):
+        return ht_size(self._h, stream)
+
+    def export(self, stream=None):
+        n = self.size(stream)
+        dt = torch.int32 if self.key_width == 32 else torch.int64
+        dev = torch.device("cuda", torch.cuda.current_device())
+        keys = torch.empty(max(n, 1), dtype=dt, device=dev)
+        vals = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if self.key_width == 32 else None
+        got = ht_export(self._h, keys, vals, stream)
+        return keys[:got], (vals[:got] if vals is not None else None)
+
+    def clear(self, stream=None):
+        ht_clear(self._h, stream)
+
+    def info(self):
+        return ht_info(self._h)

@@ -1,0 +1,78 @@
+"""ctypes loader for libht.so: declares every C-ABI signature of include/ht.h."""
+import ctypes
+import os
+
+from . import _build
+
+HT_BUCKET, HT_CUCKOO = 0, 1
+STATUS = {0: "HT_OK", 1: "HT_ERR_INVALID", 2: "HT_ERR_OOM", 3: "HT_ERR_FULL",
+          4: "HT_ERR_CUDA", 5: "HT_ERR_TIMEOUT"}
+
+
+class HtParams(ctypes.Structure):
+    _fields_ = [
+        ("num_hashes", ctypes.c_uint32), ("max_evictions", ctypes.c_uint32),
+        ("stash_slots", ctypes.c_uint32), ("bucket_slots", ctypes.c_uint32),
+        ("lanes_per_key", ctypes.c_uint32), ("max_rebuilds", ctypes.c_uint32),
+        ("max_batch", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+        ("l2_persist", ctypes.c_int32), ("reserved_", ctypes.c_int32 * 3),
+    ]
+
+
+class HtError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s failed: %s" % (where, STATUS.get(status, status)))
+
+
+_VP, _U64, _U32, _I32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32
+_P = ctypes.POINTER
+
+# name -> (restype, argtypes); mirrors include/ht.h.
+SIGNATURES = {
+    "ht_default_params": (_I32, [_I32, _P(HtParams)]),
+    "ht_create": (_I32, [_U64, _I32, _U32, _P(HtParams), _VP, _P(_VP)]),
+    "ht_destroy": (_I32, [_VP]),
+    "ht_find_or_put": (_I32, [_VP, _VP, _U64, _VP, _VP]),
+    "ht_find_or_put_append": (_I32, [_VP, _VP, _U64, _VP, _VP, _VP, _VP]),
+    "ht_insert": (_I32, [_VP, _VP, _VP, _U64, _VP]),
+    "ht_lookup": (_I32, [_VP, _VP, _U64, _VP, _VP, _VP]),
+    "ht_sync": (_I32, [_VP, _VP]),
+    "ht_size": (_I32, [_VP, _P(_U64), _VP]),
+    "ht_export": (_I32, [_VP, _VP, _VP, _U64, _P(_U64), _VP]),
+    "ht_clear": (_I32, [_VP, _VP]),
+    "ht_info": (_I32, [_VP, _P(_U64), _P(_U32), _P(_U32)]),
+    "ht_status_str": (ctypes.c_char_p, [_I32]),
+    "ht_compact": (_I32, [_VP, _VP, _U64, _U32, _VP, _VP, _VP]),
+    "ht_prof_enable": (_I32, [ctypes.c_int]),
+    "ht_prof_reset": (_I32, []),
+    "ht_prof_num_kernels": (_U32, []),
+    "ht_prof_kernel_name": (ctypes.c_char_p, [_U32]),
+    "ht_prof_read": (_I32, [_U32, _P(_U64), _P(ctypes.c_double)]),
+    "ht_probe_random_read": (_I32, [_VP, _U64, _U32, _U64, _U64, _VP, _VP]),
+}
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load():
+    """Loads the in-tree libht.so.  Raises if it has not been built: there is
+    no fallback implementation of any operation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError("libht.so is missing (%s); run __graft_entry__.build() or "
+                          "python paper_1712_09494_gb300/_build.py" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

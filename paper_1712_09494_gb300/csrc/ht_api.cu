@@ -1,0 +1,433 @@
+// Host side of the C ABI: table lifecycle, batching, rebuild and status.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "ht_internal.cuh"
+
+using namespace ht;
+
+struct ht_table {
+    int device;
+    ht_scheme scheme;
+    uint32_t kw;
+    ht_params p;
+    DevTable dt;
+    DevScratch sc;
+    uint64_t chunk;              // Cuckoo keys per probe/insert launch pair
+    uint32_t parity;
+    uint32_t rebuilds;
+    bool rebuild_exhausted;
+    ht_status sticky;            // HT_ERR_FULL once a key was dropped
+    uint64_t seed_base;
+};
+
+namespace {
+
+constexpr uint64_t kMaxCapacity = 1ull << 40;
+
+uint64_t next_pow2(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+void derive_seeds(ht_table* t) {
+    for (int a = 0; a < kMaxHashes; ++a) t->dt.seed[a] = mix64(t->seed_base + uint64_t(a + 1) * 0x9E3779B97F4A7C15ull);
+    t->dt.aux_seed = mix64(t->seed_base ^ 0xD1B54A32D192ED03ull);
+}
+
+BucketCfg bucket_cfg(const ht_table* t) {
+    return BucketCfg{int(t->kw), int(t->p.bucket_slots), int(t->p.lanes_per_key)};
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+ht_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return HT_OK;
+    if (e == cudaErrorMemoryAllocation) return HT_ERR_OOM;
+    return HT_ERR_CUDA;
+}
+
+#define HT_TRY(expr)                                 \
+    do {                                             \
+        cudaError_t e_ = (expr);                     \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+ht_status clear_table(ht_table* t, cudaStream_t s) {
+    HT_TRY(fill_words(t->dt.slots, t->dt.nslots, kEmpty, s));
+    HT_TRY(fill_words(t->dt.stash, t->dt.stash_slots, kEmpty, s));
+    HT_TRY(fill_words(t->dt.ovf, t->dt.ovf_slots, kEmpty, s));
+    HT_TRY(cudaMemsetAsync(t->dt.ctr, 0, sizeof(DevCounters), s));
+    return HT_OK;
+}
+
+// Runs find-or-put / insert over a batch without touching rebuild state.
+ht_status run_put(ht_table* t, const void* keys, const uint32_t* vals, uint64_t n, uint8_t* is_new,
+                  void* new_out, unsigned long long* new_count, cudaStream_t s) {
+    if (n == 0) return HT_OK;
+    if (t->scheme == HT_BUCKET) {
+        return cuda_status(bucket_find_or_put(bucket_cfg(t), t->dt, keys, vals, n, is_new, new_out,
+                                              new_count, s));
+    }
+    const size_t ksz = t->kw / 8;
+    for (uint64_t off = 0; off < n; off += t->chunk) {
+        const uint64_t m = std::min(t->chunk, n - off);
+        const void* k = static_cast<const char*>(keys) + off * ksz;
+        HT_TRY(cuckoo_probe(int(t->kw), t->dt, t->sc, t->parity, k, vals ? vals + off : nullptr, m,
+                            is_new ? is_new + off : nullptr, s));
+        HT_TRY(cuckoo_insert(int(t->kw), t->dt, t->sc, t->parity, new_out, new_count, m, s));
+        t->parity ^= 1u;
+    }
+    return HT_OK;
+}
+
+ht_status read_counters(ht_table* t, DevCounters* c, cudaStream_t s) {
+    HT_TRY(cudaMemcpyAsync(c, t->dt.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    HT_TRY(cudaStreamSynchronize(s));
+    return HT_OK;
+}
+
+// Section 4.1: when the stash is full and an insertion fails, rebuild the
+// table with new hash constants.  All stored words (table, stash, overflow
+// set) are copied out, the table is cleared, the constants are re-drawn and
+// the words are inserted again; repeated up to max_rebuilds times.
+ht_status rebuild(ht_table* t, cudaStream_t s) {
+    DevCounters c;
+    ht_status st = read_counters(t, &c, s);
+    if (st != HT_OK) return st;
+    const uint64_t n = c.size;
+    void* keys = nullptr;
+    uint32_t* vals = nullptr;
+    unsigned long long* cnt = nullptr;
+    HT_TRY(cudaMalloc(&keys, std::max<uint64_t>(n, 1) * (t->kw / 8)));
+    if (t->kw == 32 && cudaMalloc(&vals, std::max<uint64_t>(n, 1) * 4) != cudaSuccess) {
+        cudaFree(keys);
+        return HT_ERR_OOM;
+    }
+    if (cudaMalloc(&cnt, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaFree(keys);
+        cudaFree(vals);
+        return HT_ERR_OOM;
+    }
+    st = HT_OK;
+    do {
+        if (cudaMemsetAsync(cnt, 0, sizeof(*cnt), s) != cudaSuccess ||
+            table_export(int(t->kw), t->dt, keys, vals, cnt, n, s) != cudaSuccess) {
+            st = HT_ERR_CUDA;
+            break;
+        }
+        unsigned long long got = 0;
+        if (cudaMemcpyAsync(&got, cnt, sizeof(got), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = HT_ERR_CUDA;
+            break;
+        }
+        const unsigned long long dropped = c.dropped;
+        const uint32_t keep_flags = c.flags & (kFlagDropped | kFlagInvalidKey);
+        bool ok = false;
+        for (uint32_t attempt = 0; attempt < t->p.max_rebuilds; ++attempt) {
+            t->rebuilds += 1;
+            t->seed_base = mix64(t->seed_base + 0x9E3779B97F4A7C15ull * t->rebuilds);
+            derive_seeds(t);
+            if ((st = clear_table(t, s)) != HT_OK) break;
+            if ((st = run_put(t, keys, vals, got, nullptr, nullptr, nullptr, s)) != HT_OK) break;
+            if ((st = read_counters(t, &c, s)) != HT_OK) break;
+            if (!(c.flags & (kFlagRebuild | kFlagDropped))) {
+                ok = true;
+                break;
+            }
+        }
+        if (st != HT_OK) break;
+        if (!ok) {
+            // Keep the last attempt only if it lost nothing; otherwise the
+            // table is over-full for its capacity.
+            if (c.flags & kFlagDropped) t->sticky = HT_ERR_FULL;
+            t->rebuild_exhausted = true;
+        }
+        // Carry the sticky facts of the old table over.
+        if (dropped || keep_flags) {
+            DevCounters nc = c;
+            nc.dropped += dropped;
+            nc.flags |= keep_flags;
+            cudaMemcpyAsync(t->dt.ctr, &nc, sizeof(nc), cudaMemcpyHostToDevice, s);
+            cudaStreamSynchronize(s);
+        }
+    } while (false);
+    cudaFree(keys);
+    cudaFree(vals);
+    cudaFree(cnt);
+    return st;
+}
+
+ht_status sync_and_status(ht_table* t, cudaStream_t s) {
+    DevCounters c;
+    ht_status st = read_counters(t, &c, s);
+    if (st != HT_OK) return st;
+    if ((c.flags & kFlagRebuild) && !t->rebuild_exhausted) {
+        st = rebuild(t, s);
+        if (st != HT_OK) return st;
+        st = read_counters(t, &c, s);
+        if (st != HT_OK) return st;
+    }
+    if (c.flags & kFlagDropped) t->sticky = HT_ERR_FULL;
+    if (c.flags & kFlagInvalidKey) {
+        // Reported once, then cleared.
+        unsigned int f = c.flags & ~kFlagInvalidKey;
+        HT_TRY(cudaMemcpyAsync(&t->dt.ctr->flags, &f, sizeof(f), cudaMemcpyHostToDevice, s));
+        HT_TRY(cudaStreamSynchronize(s));
+        return t->sticky != HT_OK ? t->sticky : HT_ERR_INVALID;
+    }
+    return t->sticky;
+}
+
+bool valid_params(ht_scheme scheme, const ht_params& p) {
+    if (scheme == HT_BUCKET) {
+        if (p.num_hashes < 1 || p.num_hashes > uint32_t(kMaxHashes)) return false;
+        if (p.bucket_slots != 8 && p.bucket_slots != 16 && p.bucket_slots != 32) return false;
+        const uint32_t g = p.lanes_per_key;
+        if (g == 0 || g > 32 || p.bucket_slots % g != 0) return false;
+        const uint32_t spl = p.bucket_slots / g;
+        if (!((p.bucket_slots == 8 && (g == 4 || g == 8)) || (p.bucket_slots == 16 && (g == 4 || g == 8 || g == 16)) ||
+              (p.bucket_slots == 32 && (g == 8 || g == 16 || g == 32))))
+            return false;
+        (void)spl;
+    } else {
+        if (p.num_hashes < 2 || p.num_hashes > uint32_t(kMaxCuckooHashes)) return false;
+        if (p.max_evictions < 1 || p.max_evictions > 4096) return false;
+        if (p.bucket_slots != 8 && p.bucket_slots != 16 && p.bucket_slots != 32) return false;
+    }
+    if (p.stash_slots > 4096) return false;
+    if (p.max_batch < 1 || p.max_batch > (1ull << 26)) return false;
+    if (p.max_rebuilds > 64) return false;
+    return true;
+}
+
+ht_params complete_params(ht_scheme scheme, const ht_params* in) {
+    ht_params d;
+    ht_default_params(scheme, &d);
+    if (!in) return d;
+    ht_params p = *in;
+    if (!p.num_hashes) p.num_hashes = d.num_hashes;
+    if (!p.max_evictions) p.max_evictions = d.max_evictions;
+    if (!p.stash_slots) p.stash_slots = d.stash_slots;
+    if (!p.bucket_slots) p.bucket_slots = d.bucket_slots;
+    if (!p.lanes_per_key) p.lanes_per_key = p.bucket_slots / 2;
+    if (!p.max_rebuilds) p.max_rebuilds = d.max_rebuilds;
+    if (!p.max_batch) p.max_batch = d.max_batch;
+    return p;
+}
+
+void free_table(ht_table* t) {
+    if (!t) return;
+    cudaFree(t->dt.slots);
+    cudaFree(t->dt.stash);
+    cudaFree(t->dt.ovf);
+    cudaFree(t->dt.ctr);
+    cudaFree(t->sc.set);
+    cudaFree(t->sc.win);
+    delete t;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ht_status_str(ht_status s) {
+    switch (s) {
+        case HT_OK: return "ok";
+        case HT_ERR_INVALID: return "invalid argument or reserved key";
+        case HT_ERR_OOM: return "device allocation failed";
+        case HT_ERR_FULL: return "table full: keys could not be placed";
+        case HT_ERR_CUDA: return "CUDA error";
+        case HT_ERR_TIMEOUT: return "bounded device wait timed out";
+    }
+    return "unknown status";
+}
+
+ht_status ht_default_params(ht_scheme scheme, ht_params* p) {
+    if (!p || (scheme != HT_BUCKET && scheme != HT_CUCKOO)) return HT_ERR_INVALID;
+    std::memset(p, 0, sizeof(*p));
+    p->num_hashes = scheme == HT_BUCKET ? 16 : 4;
+    p->max_evictions = 256;
+    p->stash_slots = 101;
+    p->bucket_slots = 16;
+    p->lanes_per_key = 8;
+    p->max_rebuilds = 8;
+    p->max_batch = 1ull << 22;
+    p->seed = 0x243F6A8885A308D3ull;
+    p->l2_persist = 0;
+    return HT_OK;
+}
+
+ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, const ht_params* params,
+                    void* stream, ht_table** out) {
+    if (!out) return HT_ERR_INVALID;
+    *out = nullptr;
+    if (capacity == 0 || capacity > kMaxCapacity) return HT_ERR_INVALID;
+    if (scheme != HT_BUCKET && scheme != HT_CUCKOO) return HT_ERR_INVALID;
+    if (key_width != 32 && key_width != 64) return HT_ERR_INVALID;
+    const ht_params p = complete_params(scheme, params);
+    if (!valid_params(scheme, p)) return HT_ERR_INVALID;
+
+    ht_table* t = new (std::nothrow) ht_table();
+    if (!t) return HT_ERR_OOM;
+    std::memset(&t->dt, 0, sizeof(t->dt));
+    std::memset(&t->sc, 0, sizeof(t->sc));
+    t->scheme = scheme;
+    t->kw = key_width;
+    t->p = p;
+    t->sticky = HT_OK;
+    t->seed_base = p.seed;
+    if (cudaGetDevice(&t->device) != cudaSuccess) {
+        delete t;
+        return HT_ERR_CUDA;
+    }
+    const uint64_t bs = p.bucket_slots;
+    t->dt.nslots = (capacity + bs - 1) / bs * bs;             // whole buckets for both schemes
+    t->dt.nbuckets = t->dt.nslots / bs;
+    t->dt.stash_slots = p.stash_slots;
+    t->dt.ovf_slots = uint32_t(std::min<uint64_t>(kOvfSlots, std::max<uint64_t>(1024, next_pow2(t->dt.nslots / 64))));
+    t->dt.k = p.num_hashes;
+    t->dt.max_evict = p.max_evictions;
+    derive_seeds(t);
+
+    auto fail = [&](cudaError_t e) {
+        free_table(t);
+        return cuda_status(e);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&t->dt.slots, t->dt.nslots * 8)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&t->dt.stash, std::max<uint32_t>(t->dt.stash_slots, 1) * 8)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&t->dt.ovf, uint64_t(t->dt.ovf_slots) * 8)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&t->dt.ctr, sizeof(DevCounters))) != cudaSuccess) return fail(e);
+    if (scheme == HT_CUCKOO) {
+        // A chunk never holds more absent distinct keys than the table can
+        // take, so the scratch is sized by the smaller of the two.
+        t->chunk = std::min<uint64_t>(p.max_batch, next_pow2(t->dt.nslots + t->dt.stash_slots + t->dt.ovf_slots));
+        const uint64_t sslots = next_pow2(2 * t->chunk);
+        t->sc.mask = sslots - 1;
+        if ((e = cudaMalloc(&t->sc.set, sslots * 8)) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&t->sc.win, t->chunk * sizeof(Winner))) != cudaSuccess) return fail(e);
+        if ((e = fill_words(t->sc.set, sslots, kEmpty, as_stream(stream))) != cudaSuccess) return fail(e);
+    }
+    ht_status st = clear_table(t, as_stream(stream));
+    if (st != HT_OK) {
+        free_table(t);
+        return st;
+    }
+    *out = t;
+    return HT_OK;
+}
+
+ht_status ht_destroy(ht_table* t) {
+    if (!t) return HT_OK;
+    DeviceGuard g(t->device);
+    cudaDeviceSynchronize();
+    free_table(t);
+    return HT_OK;
+}
+
+static ht_status put_common(ht_table* t, const void* keys, const uint32_t* vals, uint64_t n,
+                            uint8_t* is_new, void* new_out, unsigned long long* new_count, void* stream) {
+    if (!t) return HT_ERR_INVALID;
+    if (n && !keys) return HT_ERR_INVALID;
+    if (vals && t->kw != 32) return HT_ERR_INVALID;
+    if ((new_out == nullptr) != (new_count == nullptr)) return HT_ERR_INVALID;
+    DeviceGuard g(t->device);
+    return run_put(t, keys, vals, n, is_new, new_out, new_count, as_stream(stream));
+}
+
+ht_status ht_find_or_put(ht_table* t, const void* d_keys, uint64_t n, uint8_t* d_is_new, void* stream) {
+    return put_common(t, d_keys, nullptr, n, d_is_new, nullptr, nullptr, stream);
+}
+
+ht_status ht_find_or_put_append(ht_table* t, const void* d_keys, uint64_t n, uint8_t* d_is_new,
+                                void* d_new_keys, unsigned long long* d_new_count, void* stream) {
+    if (!d_new_keys || !d_new_count) return HT_ERR_INVALID;
+    return put_common(t, d_keys, nullptr, n, d_is_new, d_new_keys, d_new_count, stream);
+}
+
+ht_status ht_insert(ht_table* t, const void* d_keys, const uint32_t* d_values, uint64_t n, void* stream) {
+    return put_common(t, d_keys, d_values, n, nullptr, nullptr, nullptr, stream);
+}
+
+ht_status ht_lookup(ht_table* t, const void* d_keys, uint64_t n, uint32_t* d_values, uint8_t* d_found,
+                    void* stream) {
+    if (!t || (n && !d_keys)) return HT_ERR_INVALID;
+    if (n == 0) return HT_OK;
+    DeviceGuard g(t->device);
+    const cudaStream_t s = as_stream(stream);
+    if (t->scheme == HT_BUCKET) return cuda_status(bucket_lookup(bucket_cfg(t), t->dt, d_keys, n, d_values, d_found, s));
+    return cuda_status(cuckoo_lookup(int(t->kw), t->dt, d_keys, n, d_values, d_found, s));
+}
+
+ht_status ht_sync(ht_table* t, void* stream) {
+    if (!t) return HT_ERR_INVALID;
+    DeviceGuard g(t->device);
+    return sync_and_status(t, as_stream(stream));
+}
+
+ht_status ht_size(ht_table* t, uint64_t* out, void* stream) {
+    if (!t || !out) return HT_ERR_INVALID;
+    DeviceGuard g(t->device);
+    const cudaStream_t s = as_stream(stream);
+    ht_status st = sync_and_status(t, s);
+    DevCounters c;
+    ht_status st2 = read_counters(t, &c, s);
+    if (st2 != HT_OK) return st2;
+    *out = c.size;
+    return st;
+}
+
+ht_status ht_export(ht_table* t, void* d_keys_out, uint32_t* d_values_out, uint64_t cap, uint64_t* count,
+                    void* stream) {
+    if (!t || !count || (cap && !d_keys_out) || (d_values_out && t->kw != 32)) return HT_ERR_INVALID;
+    DeviceGuard g(t->device);
+    const cudaStream_t s = as_stream(stream);
+    ht_status st = sync_and_status(t, s);
+    if (st == HT_ERR_CUDA) return st;
+    unsigned long long* cnt = nullptr;
+    HT_TRY(cudaMalloc(&cnt, sizeof(*cnt)));
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(*cnt), s);
+    if (e == cudaSuccess) e = table_export(int(t->kw), t->dt, d_keys_out, d_values_out, cnt, cap, s);
+    unsigned long long got = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&got, cnt, sizeof(got), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(cnt);
+    if (e != cudaSuccess) return cuda_status(e);
+    *count = got;
+    if (got > cap) return HT_ERR_INVALID;
+    return st;
+}
+
+ht_status ht_clear(ht_table* t, void* stream) {
+    if (!t) return HT_ERR_INVALID;
+    DeviceGuard g(t->device);
+    t->sticky = HT_OK;
+    t->rebuild_exhausted = false;
+    return clear_table(t, as_stream(stream));
+}
+
+ht_status ht_info(const ht_table* t, uint64_t* slots, uint32_t* num_hashes, uint32_t* rebuilds) {
+    if (!t) return HT_ERR_INVALID;
+    if (slots) *slots = t->dt.nslots;
+    if (num_hashes) *num_hashes = t->dt.k;
+    if (rebuilds) *rebuilds = t->rebuilds;
+    return HT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// Internal definitions shared by the CUDA translation units of libht.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ht.h"
+
+namespace ht {
+
+constexpr uint64_t kEmpty = ~0ull;          // an empty slot: every bit set
+constexpr int kMaxHashes = 16;              // bucket scheme upper bound
+constexpr int kMaxCuckooHashes = 8;
+constexpr uint32_t kOvfSlots = 1u << 16;    // overflow set behind the stash
+constexpr int kBlock = 256;
+
+// Sticky device flags.
+enum : uint32_t {
+    kFlagInvalidKey = 1u,   // a reserved key was seen
+    kFlagRebuild = 2u,      // the stash overflowed: rebuild with new constants
+    kFlagDropped = 4u,      // a key found no place at all (table full)
+};
+
+struct DevCounters {
+    unsigned long long size;      // keys stored (table + stash + overflow)
+    unsigned long long dropped;   // keys that could not be placed
+    unsigned int stash_used;
+    unsigned int ovf_used;
+    unsigned int flags;
+    unsigned int winners[2];      // Cuckoo dedup winners per chunk parity
+    unsigned int pad_[9];
+};
+
+// Everything a kernel needs to address a table; passed by value.
+struct DevTable {
+    uint64_t* slots;
+    uint64_t nslots;          // capacity in slots
+    uint64_t nbuckets;        // nslots / bucket_slots (bucket scheme)
+    uint64_t* stash;
+    uint64_t* ovf;
+    DevCounters* ctr;
+    uint32_t stash_slots;
+    uint32_t ovf_slots;
+    uint32_t k;               // hash functions
+    uint32_t max_evict;       // Cuckoo eviction bound
+    uint64_t aux_seed;        // stash / overflow / dedup start positions
+    uint64_t seed[kMaxHashes];
+};
+
+// A Cuckoo insertion job: the packed word and where its dedup claim sits.
+struct Winner {
+    uint64_t word;
+    uint32_t spos;
+    uint32_t pad_;
+};
+
+// Dedup scratch of one Cuckoo table: a linear-probing set of keys.
+struct DevScratch {
+    uint64_t* set;
+    uint64_t mask;            // slots - 1 (power of two)
+    Winner* win;
+};
+
+// ---------------------------------------------------------------------------
+// Hash family.  h_a(k) = floor(mix64(k xor s_a) * m / 2^64): the SplitMix64
+// output finaliser (Steele, Lea & Flood 2014) as the mixer and Lemire's
+// multiply-high range reduction.  The paper names only "hash constants"
+// copied to the GPU (Section 5); s_a are those constants.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t hidx(uint64_t key, uint64_t s, uint64_t m) {
+    return __umul64hi(mix64(key ^ s), m);
+}
+
+// Key <-> slot word.  32-bit keys sit in the low word with the value above;
+// 64-bit keys fill the word.  keyof(kEmpty) is the reserved key, so
+// "keyof(w) == reserved" means "empty".
+template <int KW> struct Keys;
+template <> struct Keys<32> {
+    using T = uint32_t;
+    static constexpr uint64_t kMask = 0xFFFFFFFFull;
+    __device__ __forceinline__ static uint64_t keyof(uint64_t w) { return w & kMask; }
+    __device__ __forceinline__ static bool empty(uint64_t w) { return (w & kMask) == kMask; }
+    __device__ __forceinline__ static bool reserved(uint64_t k) { return k == kMask; }
+    __device__ __forceinline__ static uint64_t word(uint64_t k, uint32_t v) { return (uint64_t(v) << 32) | k; }
+    __device__ __forceinline__ static uint32_t value(uint64_t w) { return uint32_t(w >> 32); }
+    __device__ __forceinline__ static uint64_t load(const void* p, uint64_t i) {
+        return static_cast<const uint32_t*>(p)[i];
+    }
+};
+template <> struct Keys<64> {
+    using T = uint64_t;
+    __device__ __forceinline__ static uint64_t keyof(uint64_t w) { return w; }
+    __device__ __forceinline__ static bool empty(uint64_t w) { return w == kEmpty; }
+    __device__ __forceinline__ static bool reserved(uint64_t k) { return (k >> 63) != 0; }
+    __device__ __forceinline__ static uint64_t word(uint64_t k, uint32_t) { return k; }
+    __device__ __forceinline__ static uint32_t value(uint64_t) { return 0u; }
+    __device__ __forceinline__ static uint64_t load(const void* p, uint64_t i) {
+        return static_cast<const uint64_t*>(p)[i];
+    }
+};
+
+__device__ __forceinline__ void set_flag(DevCounters* c, uint32_t f) {
+    if ((*(volatile unsigned int*)&c->flags & f) != f) atomicOr(&c->flags, f);
+}
+
+// Linear-probing set with CAS claims (the stash, the overflow set, the dedup
+// scratch).  Slots only ever go from empty to a fixed word, and every caller
+// scans the same fixed order from the same start, so a key is claimed at
+// most once: a later claimant passes the earlier claim's slot first.
+// Returns 1 if `word` was stored here, 0 if its key was already present,
+// -1 if all `n` slots are taken by other keys.
+template <int KW>
+__device__ __forceinline__ int lp_insert(uint64_t* arr, uint32_t n, uint64_t start,
+                                         uint64_t key, uint64_t word, uint32_t* at) {
+    uint32_t p = uint32_t(start);
+    for (uint32_t i = 0; i < n; ++i) {
+        uint64_t w = __ldcg(reinterpret_cast<const unsigned long long*>(arr + p));
+        if (Keys<KW>::empty(w)) {
+            w = atomicCAS(reinterpret_cast<unsigned long long*>(arr + p), kEmpty, word);
+            if (w == kEmpty) { if (at) *at = p; return 1; }
+        }
+        if (Keys<KW>::keyof(w) == key) { if (at) *at = p; return 0; }
+        p = (p + 1 == n) ? 0 : p + 1;
+    }
+    return -1;
+}
+
+// Lookup in a linear-probing set: stops at the first empty slot.
+template <int KW>
+__device__ __forceinline__ bool lp_find(const uint64_t* arr, uint32_t n, uint64_t start,
+                                        uint64_t key, uint64_t* out) {
+    uint32_t p = uint32_t(start);
+    for (uint32_t i = 0; i < n; ++i) {
+        uint64_t w = __ldcg(reinterpret_cast<const unsigned long long*>(arr + p));
+        if (Keys<KW>::empty(w)) return false;
+        if (Keys<KW>::keyof(w) == key) { *out = w; return true; }
+        p = (p + 1 == n) ? 0 : p + 1;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint64_t stash_start(const DevTable& t, uint64_t key) {
+    return mix64(key ^ t.aux_seed) % t.stash_slots;
+}
+__device__ __forceinline__ uint64_t ovf_start(const DevTable& t, uint64_t key) {
+    return mix64(key ^ ~t.aux_seed) & (t.ovf_slots - 1);
+}
+
+// Places a word that found no slot in the main table: stash first, then the
+// overflow set (which asks the host for a rebuild), else it is dropped.
+// Returns 1 stored, 0 key already present, -1 dropped.
+template <int KW>
+__device__ __forceinline__ int place_spill(const DevTable& t, uint64_t key, uint64_t word) {
+    int r = -1;
+    if (t.stash_slots) {
+        r = lp_insert<KW>(t.stash, t.stash_slots, stash_start(t, key), key, word, nullptr);
+        if (r == 1) atomicAdd(&t.ctr->stash_used, 1u);
+    }
+    if (r < 0) {
+        r = lp_insert<KW>(t.ovf, t.ovf_slots, ovf_start(t, key), key, word, nullptr);
+        if (r == 1) {
+            atomicAdd(&t.ctr->ovf_used, 1u);
+            set_flag(t.ctr, kFlagRebuild);
+        }
+    }
+    if (r < 0) {
+        atomicAdd(&t.ctr->dropped, 1ull);
+        set_flag(t.ctr, kFlagDropped);
+    }
+    return r;
+}
+
+// Looks a key up in the stash and then the overflow set.
+template <int KW>
+__device__ __forceinline__ bool find_spill(const DevTable& t, uint64_t key, uint32_t stash_used,
+                                           uint32_t ovf_used, uint64_t* w) {
+    if (stash_used && lp_find<KW>(t.stash, t.stash_slots, stash_start(t, key), key, w)) return true;
+    if (ovf_used && lp_find<KW>(t.ovf, t.ovf_slots, ovf_start(t, key), key, w)) return true;
+    return false;
+}
+
+// Warp-aggregated append of `v` (when `pred`) to out[] at *counter.
+template <typename T>
+__device__ __forceinline__ void warp_append(bool pred, T v, T* out, unsigned long long* counter) {
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (pred) out[base + __popc(mask & ((1u << lane) - 1))] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel timing (ht_prof_*).
+// ---------------------------------------------------------------------------
+enum KernelId : uint32_t {
+    kKBucketFop = 0,
+    kKBucketLookup,
+    kKCuckooProbe,
+    kKCuckooInsert,
+    kKCuckooLookup,
+    kKExport,
+    kKClear,
+    kKCompact,
+    kKProbeRead,
+    kKSuccessors,
+    kKNumKernels
+};
+
+struct ProfScope {
+    ProfScope(uint32_t id, cudaStream_t s);
+    ~ProfScope();
+    uint32_t id_;
+    cudaStream_t s_;
+    int slot_;
+};
+
+int launch_blocks(const void* kernel, int block, size_t smem = 0);
+
+// ---------------------------------------------------------------------------
+// Launchers implemented by the scheme translation units.  All return the
+// cudaGetLastError() of the launch.
+// ---------------------------------------------------------------------------
+struct BucketCfg {
+    int kw;
+    int bucket_slots;
+    int lanes;
+};
+
+cudaError_t bucket_find_or_put(const BucketCfg& c, const DevTable& t, const void* keys,
+                               const uint32_t* vals, uint64_t n, uint8_t* is_new,
+                               void* new_out, unsigned long long* new_count, cudaStream_t s);
+cudaError_t bucket_lookup(const BucketCfg& c, const DevTable& t, const void* keys, uint64_t n,
+                          uint32_t* vals, uint8_t* found, cudaStream_t s);
+
+cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
+                         const void* keys, const uint32_t* vals, uint64_t n, uint8_t* is_new,
+                         cudaStream_t s);
+cudaError_t cuckoo_insert(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
+                          void* new_out, unsigned long long* new_count, uint64_t max_winners,
+                          cudaStream_t s);
+cudaError_t cuckoo_lookup(int kw, const DevTable& t, const void* keys, uint64_t n,
+                          uint32_t* vals, uint8_t* found, cudaStream_t s);
+
+cudaError_t table_export(int kw, const DevTable& t, void* keys_out, uint32_t* vals_out,
+                         unsigned long long* count, uint64_t cap, cudaStream_t s);
+cudaError_t fill_words(uint64_t* p, uint64_t n, uint64_t v, cudaStream_t s);
+cudaError_t compact(int kw, const void* keys, const uint8_t* flags, uint64_t n, void* out,
+                    unsigned long long* count, cudaStream_t s);
+cudaError_t probe_random_read(const void* buf, uint64_t bytes, uint32_t gran, uint64_t n_access,
+                              uint64_t seed, unsigned long long* sink, cudaStream_t s);
+
+}  // namespace ht

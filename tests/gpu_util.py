@@ -1,0 +1,46 @@
+"""Helpers for the GPU parity tests: marshal numpy inputs to CUDA tensors and
+compare CUDA results with the oracle under the rules of a set/map."""
+import numpy as np
+import torch
+
+
+def to_dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    elif a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).cuda()
+
+
+def to_np(t, dtype=None):
+    a = t.cpu().numpy()
+    if dtype is not None:
+        a = a.view(dtype)
+    return a
+
+
+def keys_np(t, key_width):
+    return to_np(t, np.uint32 if key_width == 32 else np.uint64)
+
+
+def assert_flags_per_key(keys, got, expected):
+    """Among equal keys of one batch exactly as many flags as the oracle's
+    (which flags the first occurrence); which occurrence is unspecified."""
+    got = np.asarray(got).astype(np.int64)
+    expected = np.asarray(expected).astype(np.int64)
+    assert set(np.unique(got).tolist()) <= {0, 1}
+    uk, inv = np.unique(np.asarray(keys), return_inverse=True)
+    sg = np.bincount(inv, weights=got, minlength=len(uk))
+    se = np.bincount(inv, weights=expected, minlength=len(uk))
+    bad = np.nonzero(sg != se)[0]
+    assert len(bad) == 0, "per-key flag counts differ for %d keys, e.g. %s: gpu %s oracle %s" % (
+        len(bad), uk[bad[:3]], sg[bad[:3]], se[bad[:3]])
+
+
+def assert_same_set(gpu_keys, oracle_keys):
+    a = np.sort(np.asarray(gpu_keys).astype(np.uint64))
+    b = np.sort(np.asarray(oracle_keys).astype(np.uint64))
+    assert len(a) == len(b), "sizes differ: gpu %d oracle %d" % (len(a), len(b))
+    assert len(np.unique(a)) == len(a), "a key is stored twice"
+    assert np.array_equal(a, b)

@@ -1,0 +1,238 @@
+"""Parity of the CUDA find-or-put / insert / lookup path with the CPU oracle.
+
+Every comparison is exact (integer work): per distinct key of a batch the
+number of is_new flags equals the oracle's, the stored set equals the
+oracle's set, found flags are identical and values are the oracle's (or, for
+a key first inserted by a batch that held it several times, one of the
+values supplied for it in that batch).
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1712_09494_gb300 as ht
+from workloads import keys as wk
+
+from gpu_util import assert_flags_per_key, assert_same_set, keys_np, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+SCHEMES = ["bucket", "cuckoo"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1712_09494_gb300 import _build
+    _build.build()
+    assert torch.cuda.is_available()
+    ht.load()
+
+
+def _fill_and_check(oracle_lib, scheme, kw, n_distinct, batch, dup, lf, params=None, seed=1):
+    fs = wk.fill_stream(n_distinct, batch, dup, kw, seed=seed)
+    cap = int(np.ceil(n_distinct / lf))
+    t = ht.HashTable(cap, scheme, kw, params)
+    orc = oracle_lib.OracleTable()
+    for b in range(fs.n_batches):
+        kb = fs.batch(b)
+        got = to_np(t.find_or_put(to_dev(kb)))
+        exp = orc.find_or_put(kb)
+        assert_flags_per_key(kb, got, exp)
+        assert got.sum() == fs.fresh_counts[b]
+    assert t.sync() == 0
+    assert t.size() == orc.size() == n_distinct
+    k, _ = t.export()
+    assert_same_set(keys_np(k, kw), orc.export()[0])
+    return t, orc, fs
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kw", [32, 64])
+@pytest.mark.parametrize("dup", [0.0, 0.25, 0.5])
+def test_find_or_put_parity(oracle_lib, scheme, kw, dup):
+    # Several batches, a ragged last batch, load 0.8.
+    _fill_and_check(oracle_lib, scheme, kw, n_distinct=100_003, batch=1 << 15, dup=dup, lf=0.8)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("lf", [0.5, 0.9])
+def test_find_or_put_loads(oracle_lib, scheme, lf):
+    _fill_and_check(oracle_lib, scheme, 64, n_distinct=(1 << 18) + 77, batch=1 << 16, dup=0.25, lf=lf, seed=7)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("slots,lanes", [(8, 4), (8, 8), (16, 4), (16, 16), (32, 8), (32, 16), (32, 32)])
+def test_bucket_shapes_and_cuckoo_hashes(oracle_lib, scheme, slots, lanes):
+    if scheme == "bucket":
+        params = dict(bucket_slots=slots, lanes_per_key=lanes)
+    else:
+        params = dict(num_hashes=2 + (slots * lanes) % 7, bucket_slots=slots)
+    _fill_and_check(oracle_lib, scheme, 64, n_distinct=50_000, batch=20_000, dup=0.5, lf=0.8, params=params)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_single_key_repeated(oracle_lib, scheme):
+    keys = np.full(1 << 16, 12345, dtype=np.uint64)
+    t = ht.HashTable(1024, scheme, 64)
+    got = to_np(t.find_or_put(to_dev(keys)))
+    assert got.sum() == 1
+    got = to_np(t.find_or_put(to_dev(keys)))
+    assert got.sum() == 0
+    assert t.size() == 1
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kw", [32, 64])
+def test_empty_and_tiny_batches(oracle_lib, scheme, kw):
+    t = ht.HashTable(64, scheme, kw)
+    dt = torch.int32 if kw == 32 else torch.int64
+    empty = torch.empty(0, dtype=dt, device="cuda")
+    assert t.find_or_put(empty).numel() == 0
+    f, _ = t.lookup(empty)
+    assert f.numel() == 0
+    one = torch.tensor([5], dtype=dt, device="cuda")
+    assert to_np(t.find_or_put(one)).tolist() == [1]
+    assert to_np(t.lookup(one)[0]).tolist() == [1]
+    assert t.size() == 1
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_map_insert_lookup_parity(oracle_lib, scheme):
+    rng = np.random.default_rng(5)
+    n = 60_000
+    t = ht.HashTable(int(n / 0.8), scheme, 32)
+    orc = oracle_lib.OracleTable()
+    pool = wk.distinct_keys(n, 32, seed=11)
+    first_batch_vals = {}
+    for b in range(3):
+        kb = pool[rng.integers(0, n, size=40_000)]
+        vb = rng.integers(0, 2**32 - 1, size=len(kb), dtype=np.uint64).astype(np.uint32)
+        absent_before = {int(k) for k in np.unique(kb)} - set(orc.export()[0].tolist())
+        for k, v in zip(kb.tolist(), vb.tolist()):
+            if k in absent_before:
+                first_batch_vals.setdefault(k, set()).add(v)
+        t.insert(to_dev(kb), to_dev(vb))
+        orc.insert(kb, vb)
+        q = np.concatenate([pool, wk.distinct_keys(5000, 32, seed=11, start=n + 10)])
+        found, vals = t.lookup(to_dev(q))
+        of, ov = orc.lookup(q)
+        np.testing.assert_array_equal(to_np(found), of)
+        gv = to_np(vals, np.uint32)
+        for i in np.nonzero(of)[0][::7]:
+            assert int(gv[i]) in first_batch_vals[int(q[i])]
+        assert t.size() == orc.size()
+    # A second insert of present keys keeps the first values.
+    before = to_np(t.lookup(to_dev(pool))[1], np.uint32)
+    t.insert(to_dev(pool), to_dev(np.zeros(n, dtype=np.uint32)))
+    after = to_np(t.lookup(to_dev(pool))[1], np.uint32)
+    np.testing.assert_array_equal(before, after)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kw", [32, 64])
+def test_lookup_half_present(oracle_lib, scheme, kw):
+    n = 1 << 17
+    t = ht.HashTable(int(n / 0.8), scheme, kw)
+    t.insert(to_dev(wk.distinct_keys(n, kw, seed=2)))
+    q, present = wk.lookup_batch(n, (1 << 17) + 5, kw, seed=2)
+    found, _ = t.lookup(to_dev(q))
+    np.testing.assert_array_equal(to_np(found), present)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_reserved_key_reports_invalid(oracle_lib, scheme):
+    t = ht.HashTable(256, scheme, 32)
+    keys = np.array([1, 2, 0xFFFFFFFF, 3, 2], dtype=np.uint32)
+    got = to_np(t.find_or_put(to_dev(keys)))
+    assert got.tolist()[2] == 0 and got.sum() == 3
+    assert t.sync() == 1          # HT_ERR_INVALID, reported once
+    assert t.sync() == 0
+    assert t.size() == 3
+    t64 = ht.HashTable(256, scheme, 64)
+    k64 = np.array([1, 1 << 63, 7], dtype=np.uint64)
+    assert to_np(t64.find_or_put(to_dev(k64))).tolist() == [1, 0, 1]
+    assert t64.sync() == 1
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_stash_overflow_and_rebuild(oracle_lib, scheme):
+    # A small table with one hash function per bucket (or two for Cuckoo), a
+    # 4-slot stash and one eviction: many keys spill, the overflow set asks
+    # for a rebuild and the next synchronising call runs it.  Results stay
+    # exact throughout.
+    if scheme == "bucket":
+        params = dict(num_hashes=1, bucket_slots=8, lanes_per_key=4, stash_slots=4)
+    else:
+        params = dict(num_hashes=2, max_evictions=1, stash_slots=4)
+    n = 700
+    fs = wk.fill_stream(n, 256, 0.3, 64, seed=4)
+    t = ht.HashTable(1024, scheme, 64, params)
+    orc = oracle_lib.OracleTable()
+    for b in range(fs.n_batches):
+        kb = fs.batch(b)
+        got = to_np(t.find_or_put(to_dev(kb)))
+        assert_flags_per_key(kb, got, orc.find_or_put(kb))
+        q = fs.keys[:fs.offsets[b + 1]]
+        np.testing.assert_array_equal(to_np(t.lookup(to_dev(q))[0]), np.ones(len(q), np.uint8))
+    assert t.sync() == 0
+    assert t.info()["rebuilds"] >= 1
+    assert t.size() == n
+    k, _ = t.export()
+    assert_same_set(keys_np(k, 64), orc.export()[0])
+    absent = wk.distinct_keys(1000, 64, seed=4, start=n + 1)
+    assert to_np(t.lookup(to_dev(absent))[0]).sum() == 0
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_overfull_table_reports_full(oracle_lib, scheme):
+    # 3000 keys into 64 slots + 4 stash + 1024 overflow: keys are dropped and
+    # the table reports HT_ERR_FULL; nothing hangs.
+    params = dict(num_hashes=2, stash_slots=4, max_rebuilds=2, max_evictions=8)
+    t = ht.HashTable(64, scheme, 64, params)
+    t.find_or_put(to_dev(wk.distinct_keys(3000, 64, seed=9)))
+    assert t.sync() == 3
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kw", [32, 64])
+def test_find_or_put_append_and_compact(oracle_lib, scheme, kw):
+    fs = wk.fill_stream(30_000, 1 << 14, 0.5, kw, seed=8)
+    t = ht.HashTable(40_000, scheme, kw)
+    dt = torch.int32 if kw == 32 else torch.int64
+    for b in range(fs.n_batches):
+        kb = to_dev(fs.batch(b))
+        out = torch.empty(kb.numel(), dtype=dt, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        is_new = torch.empty(kb.numel(), dtype=torch.uint8, device="cuda")
+        ht.ht_find_or_put_append(t.handle, kb, out, cnt, is_new)
+        c = int(cnt.item())
+        assert c == fs.fresh_counts[b]
+        exp = np.unique(keys_np(kb[is_new.bool()], kw))
+        assert_same_set(keys_np(out[:c], kw), exp)
+        out2 = torch.empty_like(out)
+        cnt2 = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ht.ht_compact(kb, is_new, out2, cnt2)
+        assert int(cnt2.item()) == c
+        assert_same_set(keys_np(out2[:c], kw), exp)
+
+
+def test_compact_matches_numpy():
+    rng = np.random.default_rng(3)
+    for n in [0, 1, 31, 33, 1000, 123_457]:
+        keys = rng.integers(0, 2**63 - 1, size=n, dtype=np.uint64)
+        flags = (rng.random(n) < 0.3).astype(np.uint8)
+        out = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ht.ht_compact(to_dev(keys), to_dev(flags), out, cnt)
+        c = int(cnt.item())
+        assert c == flags.sum()
+        np.testing.assert_array_equal(np.sort(to_np(out[:c], np.uint64)), np.sort(keys[flags == 1]))
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_clear_empties(oracle_lib, scheme):
+    t = ht.HashTable(4096, scheme, 64)
+    k = to_dev(wk.distinct_keys(3000, 64, seed=1))
+    assert to_np(t.find_or_put(k)).sum() == 3000
+    t.clear()
+    assert t.size() == 0
+    assert to_np(t.find_or_put(k)).sum() == 3000

@@ -251,15 +251,16 @@ def run_ours(a, rank, world, local):
         # winner record + one exchange (32-byte read + 32-byte write) per winner
         "cuckoo_insert": 16 + 64,
     }
-    units_per_launch = {"bucket_find_or_put": fs.n_issued / fs.n_batches,
-                        "cuckoo_probe": fs.n_issued / fs.n_batches,
-                        "cuckoo_insert": fs.n_distinct / fs.n_batches}
+    # units over the timed region; divided by each kernel's launch count below
+    units_total = {"bucket_find_or_put": fs.n_issued * a.steps,
+                   "cuckoo_probe": fs.n_issued * a.steps,
+                   "cuckoo_insert": fs.n_distinct * a.steps}
     peak, peak_src = measured_peaks()
     kernels = {}
     for name, (launches, tot) in kern.items():
         entry = {"launches": launches, "total_ms": round(tot, 3), "avg_ms": round(tot / launches, 4)}
         if name in per_key:
-            alg = per_key[name] * units_per_launch[name]
+            alg = per_key[name] * units_total[name] / launches
             entry["alg_bytes_per_launch"] = int(alg)
             entry["achieved_gbs"] = round(alg / (tot / launches / 1e3) / 1e9, 1)
             entry["frac_of_" + peak_src] = round(entry["achieved_gbs"] / peak, 3)

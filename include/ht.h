@@ -184,6 +184,44 @@ ht_status ht_probe_random_read(const void* d_buf, uint64_t bytes, uint32_t gran,
                                uint64_t n_access, uint64_t seed,
                                unsigned long long* d_sink, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Cuckoo find-or-put that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code
+ * whose device memory is all reserved up front (an arena, or a framework's
+ * caching allocator that already holds the GPU), or code on a path where an
+ * allocation is not allowed (cudaMalloc can synchronise the device and is
+ * refused during stream capture).  Such a caller supplies the table memory
+ * itself; the per-call dedup set and winner list come from one static
+ * device array inside the library (8 MiB, held on every GPU that uses the
+ * library until the process exits).  No cudaMalloc or cudaFree is called.
+ *
+ * d_slots   caller-owned device array of nslots uint64 words: the table.
+ * d_state   caller-owned device block of HT_NOALLOC_STATE_BYTES bytes,
+ *           16-byte aligned: counters, a 101-word stash and a 64-word
+ *           overflow area.  After the work completes, bytes 0..7 hold the
+ *           number of stored keys (uint64) and bytes 8..15 the number of
+ *           keys dropped because no slot, stash or overflow word was left
+ *           (non-zero means the set is incomplete; there is no rebuild).
+ * seed      hash-constant seed; use the same seed for every call on a table.
+ * d_keys    n uint64 keys, top bit 0; n <= HT_NOALLOC_MAX_BATCH, else
+ *           HT_ERR_INVALID (split larger batches).
+ * d_is_new  nullable; n bytes as in ht_find_or_put.
+ * reset     non-zero: first empty the table and state (required on the
+ *           first call for a table; uses fills, no allocation).
+ * Semantics per call are those of ht_find_or_put on a Cuckoo table with 4
+ * hash functions and an eviction bound of 256.
+ * The first call on each device looks up the static array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and each call clears the part it needs, so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race:
+ * order them on one stream.
+ * ------------------------------------------------------------------------- */
+#define HT_NOALLOC_STATE_BYTES 2048
+#define HT_NOALLOC_MAX_BATCH (1u << 18)
+ht_status ht_cuckoo_find_or_put_noalloc(uint64_t* d_slots, uint64_t nslots, void* d_state,
+                                        uint64_t seed, const uint64_t* d_keys, uint64_t n,
+                                        uint8_t* d_is_new, int reset, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,8 +21,12 @@ __all__ = [
     "ht_default_params", "ht_create", "ht_destroy", "ht_find_or_put", "ht_find_or_put_append",
     "ht_insert", "ht_lookup", "ht_sync", "ht_size", "ht_export", "ht_clear", "ht_info",
     "ht_compact", "ht_prof_enable", "ht_prof_reset", "ht_prof_read", "ht_prof_kernels",
-    "ht_probe_random_read", "scheme_of",
+    "ht_probe_random_read", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
+    "NOALLOC_MAX_BATCH", "scheme_of",
 ]
+
+NOALLOC_STATE_BYTES = 2048      # HT_NOALLOC_STATE_BYTES
+NOALLOC_MAX_BATCH = 1 << 18     # HT_NOALLOC_MAX_BATCH
 
 _KEY_DTYPES = {32: (torch.int32, torch.uint32), 64: (torch.int64, torch.uint64)}
 
@@ -177,6 +181,14 @@ def ht_probe_random_read(buf, gran, n_access, seed, sink, stream=None):
     _check(load().ht_probe_random_read(_dptr(buf, "buf"), buf.numel() * buf.element_size(), int(gran),
                                        int(n_access), int(seed), _dptr(sink, "sink"), _stream(stream)),
            "ht_probe_random_read")
+
+
+def ht_cuckoo_find_or_put_noalloc(slots, state, seed, keys, is_new=None, reset=False, stream=None):
+    """Find-or-put into a Cuckoo set held in caller tensors (``slots``: int64
+    table words, ``state``: NOALLOC_STATE_BYTES bytes); allocates nothing."""
+    return load().ht_cuckoo_find_or_put_noalloc(
+        _dptr(slots, "slots"), slots.numel() * slots.element_size() // 8, _dptr(state, "state"), int(seed),
+        _dptr(keys, "keys"), keys.numel(), _dptr(is_new, "is_new"), 1 if reset else 0, _stream(stream))
 
 
 # ----------------------------------------------------------------- helper

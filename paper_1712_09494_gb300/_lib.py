@@ -50,6 +50,7 @@ SIGNATURES = {
     "ht_prof_kernel_name": (ctypes.c_char_p, [_U32]),
     "ht_prof_read": (_I32, [_U32, _P(_U64), _P(ctypes.c_double)]),
     "ht_probe_random_read": (_I32, [_VP, _U64, _U32, _U64, _U64, _VP, _VP]),
+    "ht_cuckoo_find_or_put_noalloc": (_I32, [_VP, _U64, _VP, _U64, _VP, _U64, _VP, ctypes.c_int, _VP]),
 }
 
 _lib = None

@@ -63,8 +63,9 @@ typedef enum {
  *   max_evictions  cuckoo eviction-chain bound, default 256, max 4096.
  *   stash_slots    default 101 (both schemes).
  *   bucket_slots   8, 16 or 32 slots of 8 bytes; default 16 (128 bytes).
- *   lanes_per_key  lanes that read one bucket: bucket_slots/lanes in 1..4;
- *                  default bucket_slots/2.
+ *   lanes_per_key  lanes that read one bucket (2..32, with 1 to 8 slots per
+ *                  lane); default 2 (measured fastest on GB300: fewer lanes
+ *                  per key spread each round's fixed cost over more keys).
  *   max_rebuilds   rebuild attempts with fresh hash constants, default 8.
  *   max_batch      cuckoo keys per probe/insert launch pair (sizes the
  *                  in-batch dedup scratch), default 2^22.

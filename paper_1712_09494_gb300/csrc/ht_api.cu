@@ -199,12 +199,12 @@ bool valid_params(ht_scheme scheme, const ht_params& p) {
         if (p.num_hashes < 1 || p.num_hashes > uint32_t(kMaxHashes)) return false;
         if (p.bucket_slots != 8 && p.bucket_slots != 16 && p.bucket_slots != 32) return false;
         const uint32_t g = p.lanes_per_key;
-        if (g == 0 || g > 32 || p.bucket_slots % g != 0) return false;
-        const uint32_t spl = p.bucket_slots / g;
-        if (!((p.bucket_slots == 8 && (g == 4 || g == 8)) || (p.bucket_slots == 16 && (g == 4 || g == 8 || g == 16)) ||
-              (p.bucket_slots == 32 && (g == 8 || g == 16 || g == 32))))
-            return false;
-        (void)spl;
+        // (bucket_slots, lanes) pairs the bucket kernels are instantiated for.
+        static const uint32_t kShapes[][2] = {{8, 2}, {8, 4}, {8, 8}, {16, 2}, {16, 4}, {16, 8},
+                                              {16, 16}, {32, 4}, {32, 8}, {32, 16}, {32, 32}};
+        bool shape_ok = false;
+        for (const auto& sh : kShapes) shape_ok |= sh[0] == p.bucket_slots && sh[1] == g;
+        if (!shape_ok) return false;
     } else {
         if (p.num_hashes < 2 || p.num_hashes > uint32_t(kMaxCuckooHashes)) return false;
         if (p.max_evictions < 1 || p.max_evictions > 4096) return false;
@@ -225,7 +225,7 @@ ht_params complete_params(ht_scheme scheme, const ht_params* in) {
     if (!p.max_evictions) p.max_evictions = d.max_evictions;
     if (!p.stash_slots) p.stash_slots = d.stash_slots;
     if (!p.bucket_slots) p.bucket_slots = d.bucket_slots;
-    if (!p.lanes_per_key) p.lanes_per_key = p.bucket_slots / 2;
+    if (!p.lanes_per_key) p.lanes_per_key = 2;
     if (!p.max_rebuilds) p.max_rebuilds = d.max_rebuilds;
     if (!p.max_batch) p.max_batch = d.max_batch;
     return p;
@@ -265,7 +265,7 @@ ht_status ht_default_params(ht_scheme scheme, ht_params* p) {
     p->max_evictions = 256;
     p->stash_slots = 101;
     p->bucket_slots = 16;
-    p->lanes_per_key = 8;
+    p->lanes_per_key = 2;
     p->max_rebuilds = 8;
     p->max_batch = 1ull << 22;
     p->seed = 0x243F6A8885A308D3ull;

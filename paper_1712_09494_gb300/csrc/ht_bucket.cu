@@ -24,46 +24,133 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+#ifndef HT_BUCKET_MIN_BLOCKS
+#define HT_BUCKET_MIN_BLOCKS 3
+#endif
+
+// One lane's share of a bucket: SPL consecutive slots, read through L2
+// (the table is written by atomics, so L1 copies would be stale).  Shares of
+// 32 bytes or more use 256-bit loads.
 template <int SPL>
 __device__ __forceinline__ void load_lane(const uint64_t* p, uint64_t (&w)[SPL]) {
     if constexpr (SPL == 1) {
         w[0] = __ldcg(reinterpret_cast<const unsigned long long*>(p));
+    } else if constexpr (SPL == 2) {
+        const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+        w[0] = v.x;
+        w[1] = v.y;
     } else {
 #pragma unroll
-        for (int j = 0; j < SPL; j += 2) {
-            ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(p + j));
-            w[j] = v.x;
-            w[j + 1] = v.y;
+        for (int j = 0; j < SPL; j += 4) {
+            unsigned long long a, b, c, d;
+            asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
+                         : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+                         : "l"(p + j));
+            w[j] = a;
+            w[j + 1] = b;
+            w[j + 2] = c;
+            w[j + 3] = d;
         }
     }
 }
 
-// Group masks in "claim position" order: position q = j*G + sub names slot
-// sub*SPL + j of the bucket, so each ballot contributes one contiguous run
-// of G bits and no bit interleaving is needed.
-template <int G, int SPL>
-__device__ __forceinline__ uint32_t group_mask(const bool (&pred)[SPL], int gbase) {
-    constexpr uint32_t kGMask = (G == 32) ? 0xFFFFFFFFu : ((1u << G) - 1u);
-    uint32_t m = 0;
+enum : int { kDone = 0, kRead = 1, kSpill = 3 };
+
+// Per-lane view of its SPL slots: which hold the key, which are free.
+template <int KW, int SPL>
+__device__ __forceinline__ void scan_lane(const uint64_t (&w)[SPL], uint64_t key, uint32_t& m, uint32_t& e) {
+    using K = Keys<KW>;
+    m = 0;
+    e = 0;
 #pragma unroll
     for (int j = 0; j < SPL; ++j) {
-        const uint32_t b = __ballot_sync(kFull, pred[j]);
-        m |= ((b >> gbase) & kGMask) << (j * G);
+        m |= uint32_t(K::keyof(w[j]) == key) << j;
+        e |= uint32_t(K::empty(w[j])) << j;
     }
-    return m;
 }
 
-enum : int { kDone = 0, kRead = 1, kClaim = 2, kSpill = 3 };
+// Rounds whose first bucket reads are issued together: up to 128 bytes of
+// slot words per lane in flight.
+template <int G, int SPL>
+struct Prefetch {
+    static constexpr int kCap = (16 / SPL) < 8 ? (16 / SPL) : 8;   // <= 128 B of words per lane
+    static constexpr int kRounds = kCap < G ? kCap : G;
+};
 
+// The general claim loop of one round, for the rare keys whose first claim
+// lost or whose first bucket was full.  `le` is this lane's view of its free
+// slots in bucket b (no match was seen there).  Returns the group's result
+// (1 = stored) on every lane of the group.
+template <int KW, int BS, int G>
+__device__ __noinline__ uint32_t claim_slow(const DevTable t, bool active, uint64_t key, uint64_t word,
+                                            uint64_t b, uint32_t le, int sub, int gbase, int lane) {
+    using K = Keys<KW>;
+    constexpr int SPL = BS / G;
+    constexpr uint32_t kGMask = (G == 32) ? 0xFFFFFFFFu : ((1u << G) - 1u);
+    int state = active ? kRead : kDone;
+    uint32_t lm = 0, f = 0, res = 0;
+    // Bounded: every pass ends the key, takes one free slot out of the
+    // group's view (<= BS per bucket) or moves to the next of k buckets;
+    // after the last one the spill path ends it.
+    while (__any_sync(kFull, state != kDone)) {
+        const uint32_t M = (__ballot_sync(kFull, state == kRead && lm != 0) >> gbase) & kGMask;
+        const uint32_t E = (__ballot_sync(kFull, state == kRead && le != 0) >> gbase) & kGMask;
+        int owner = -1;
+        if (state == kRead) {
+            if (M) {
+                state = kDone;
+            } else if (E) {
+                owner = gbase + __ffs(E) - 1;
+            } else if (++f < t.k) {
+                b = hidx(key, t.seed[f], t.nbuckets);
+                uint64_t nw[SPL];
+                load_lane<SPL>(t.slots + b * BS + sub * SPL, nw);
+                scan_lane<KW, SPL>(nw, key, lm, le);
+            } else {
+                state = kSpill;
+            }
+        }
+        uint32_t code = 0;
+        if (lane == owner) {
+            const int j = __ffs(le) - 1;
+            const uint64_t old =
+                atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + b * BS + sub * SPL + j), kEmpty, word);
+            code = old == kEmpty ? 0u : (K::keyof(old) == key ? 1u : 2u);
+            le &= ~(1u << j);
+        }
+        code = __shfl_sync(kFull, code, owner >= 0 ? owner : lane);
+        if (owner >= 0 && code != 2u) {
+            state = kDone;
+            res = code == 0u;
+        }
+        if (state == kSpill) {
+            if (sub == 0) res = place_spill<KW>(t, key, word) == 1 ? 1u : 0u;
+            state = kDone;
+        }
+    }
+    return __shfl_sync(kFull, res, gbase);
+}
+
+// find-or-put / insert.  A warp takes 32 keys; lane l hashes key l once.  In
+// round r, group g (G lanes) serves key r*(32/G)+g.  The first bucket of
+// every round is read up front; the rounds' first claims are then decided
+// from those reads and all their CASes issued together, so a tile waits for
+// about three memory round trips (keys, buckets, claims).  Claims go in
+// slot-index order: the lowest lane of the group holding a free slot (in the
+// group's view) CASes its lowest free slot; a failed CAS marks that slot
+// taken and claim_slow tries the next one.
 template <int KW, int BS, int G, bool VALUES, bool APPEND>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, HT_BUCKET_MIN_BLOCKS)
 bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_t* __restrict__ vals,
                   uint64_t n, uint8_t* __restrict__ is_new, typename Keys<KW>::T* __restrict__ new_out,
                   unsigned long long* __restrict__ new_count) {
     using K = Keys<KW>;
     constexpr int SPL = BS / G;
     constexpr int GPW = 32 / G;
-    static_assert(SPL >= 1 && SPL <= 4 && BS % G == 0, "bucket/lane split");
+    constexpr int PF = Prefetch<G, SPL>::kRounds;
+    constexpr uint32_t kGMask = (G == 32) ? 0xFFFFFFFFu : ((1u << G) - 1u);
+    constexpr uint32_t kLMask = (1u << SPL) - 1u;
+    static_assert(SPL >= 1 && SPL <= 8 && BS % G == 0 && G % PF == 0 && PF * SPL <= 32, "bucket/lane split");
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G, gbase = grp * G;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
@@ -71,101 +158,101 @@ bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_
 
     for (uint64_t base = ((uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32; base < n;
          base += nwarps * 32) {
+        const bool mine = base + lane < n;
         uint64_t mykey = 0;
         uint32_t myval = 0;
-        const bool mine = base + lane < n;
         if (mine) {
             mykey = K::load(keys, base + lane);
             if (VALUES) myval = vals[base + lane];
         }
-        uint32_t my_new = 0;
+        const bool myok = mine && !K::reserved(mykey);
+        if (mine && !myok) set_flag(t.ctr, kFlagInvalidKey);
+        const uint64_t mybkt = hidx(mykey, t.seed[0], t.nbuckets);
+        const uint64_t myword = K::word(mykey, myval);
+        uint32_t res_all = 0;            // bit r: the group's key of round r was stored
 #pragma unroll 1
-        for (int r = 0; r < G; ++r) {
-            const int kidx = r * GPW + grp;
-            const uint64_t key = __shfl_sync(kFull, mykey, kidx);
-            const uint32_t val = VALUES ? __shfl_sync(kFull, myval, kidx) : 0u;
-            int state = kDone;
-            if (base + kidx < n) {
-                if (K::reserved(key)) {
-                    if (sub == 0) set_flag(t.ctr, kFlagInvalidKey);
-                } else {
-                    state = kRead;
-                }
-            }
-            const uint64_t word = K::word(key, val);
-            uint32_t f = 0;
-            uint64_t b = hidx(key, t.seed[0], t.nbuckets);
-            uint32_t free_mask = 0;
-            uint32_t res = 0;
-            // Bounded: each pass either ends the key, consumes a free slot of
-            // the current bucket (<= BS per bucket) or moves to the next hash
-            // function (<= k buckets), then the spill path ends it.
-            while (__any_sync(kFull, state != kDone)) {
-                bool m[SPL], e[SPL];
-                if (state == kRead) {
-                    uint64_t w[SPL];
-                    load_lane<SPL>(t.slots + b * BS + sub * SPL, w);
+        for (int r0 = 0; r0 < G; r0 += PF) {
+            // Read the first bucket of PF rounds.
+            uint64_t w[PF][SPL];
 #pragma unroll
-                    for (int j = 0; j < SPL; ++j) {
-                        m[j] = K::keyof(w[j]) == key;
-                        e[j] = K::empty(w[j]);
-                    }
+            for (int q = 0; q < PF; ++q) {
+                const int kidx = (r0 + q) * GPW + grp;
+                const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
+                if (__shfl_sync(kFull, myok, kidx)) {
+                    load_lane<SPL>(t.slots + b * BS + sub * SPL, w[q]);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < SPL; ++j) m[j] = e[j] = false;
-                }
-                const uint32_t M = group_mask<G, SPL>(m, gbase);
-                const uint32_t E = group_mask<G, SPL>(e, gbase);
-                if (state == kRead) {
-                    if (M) {
-                        state = kDone;
-                    } else if (E) {
-                        state = kClaim;
-                        free_mask = E;
-                    } else if (++f < t.k) {
-                        b = hidx(key, t.seed[f], t.nbuckets);
-                    } else {
-                        state = kSpill;
-                    }
-                }
-                int owner = lane;
-                uint64_t old = 0;
-                uint64_t* target = nullptr;
-                if (state == kClaim) {
-                    const int q = __ffs(free_mask) - 1;
-                    owner = gbase + (q % G);
-                    target = t.slots + b * BS + (q % G) * SPL + q / G;
-                }
-                if (lane == owner && target)
-                    old = atomicCAS(reinterpret_cast<unsigned long long*>(target), kEmpty, word);
-                old = __shfl_sync(kFull, old, owner);
-                if (state == kClaim) {
-                    if (old == kEmpty) {
-                        state = kDone;
-                        res = 1;
-                    } else if (K::keyof(old) == key) {
-                        state = kDone;
-                    } else {
-                        free_mask &= free_mask - 1;
-                        if (!free_mask) {
-                            if (++f < t.k) {
-                                b = hidx(key, t.seed[f], t.nbuckets);
-                                state = kRead;
-                            } else {
-                                state = kSpill;
-                            }
-                        }
-                    }
-                }
-                if (state == kSpill) {
-                    if (sub == 0) res = place_spill<KW>(t, key, word) == 1 ? 1u : 0u;
-                    state = kDone;
+                    for (int j = 0; j < SPL; ++j) w[q][j] = kEmpty;
                 }
             }
-            // Key r*GPW+grp's result lives on its group's first lane.
-            const uint32_t got = __shfl_sync(kFull, res, (lane % GPW) * G);
-            if (lane / GPW == r) my_new = got;
+            // Decide each round from its read: found, claim, or slow path.
+            uint32_t le_pack = 0, claim = 0, slow = 0, valid = 0;
+            uint64_t owner_pack = 0;
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kidx = (r0 + q) * GPW + grp;
+                const uint64_t key = __shfl_sync(kFull, mykey, kidx);
+                const bool ok = __shfl_sync(kFull, myok, kidx);
+                uint32_t lm, le;
+                scan_lane<KW, SPL>(w[q], key, lm, le);
+                const uint32_t M = (__ballot_sync(kFull, ok && lm != 0) >> gbase) & kGMask;
+                const uint32_t E = (__ballot_sync(kFull, ok && le != 0) >> gbase) & kGMask;
+                le_pack |= le << (q * SPL);
+                valid |= uint32_t(ok) << q;
+                if (ok && !M) {
+                    if (E) {
+                        claim |= 1u << q;
+                        owner_pack |= uint64_t(__ffs(E) - 1) << (5 * q);
+                    } else {
+                        slow |= 1u << q;
+                    }
+                }
+            }
+            // Issue every round's first CAS, then read the results.
+            uint64_t old[PF];
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kidx = (r0 + q) * GPW + grp;
+                const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
+                const uint64_t word = __shfl_sync(kFull, myword, kidx);
+                old[q] = kEmpty;
+                if (((claim >> q) & 1u) && sub == int((owner_pack >> (5 * q)) & 31u)) {
+                    const int j = __ffs((le_pack >> (q * SPL)) & kLMask) - 1;
+                    old[q] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + b * BS + sub * SPL + j),
+                                       kEmpty, word);
+                    le_pack &= ~(1u << (q * SPL + j));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kidx = (r0 + q) * GPW + grp;
+                const uint64_t key = __shfl_sync(kFull, mykey, kidx);
+                const uint32_t code = old[q] == kEmpty ? 0u : (K::keyof(old[q]) == key ? 1u : 2u);
+                const int src = gbase + int((owner_pack >> (5 * q)) & 31u);
+                const uint32_t c = __shfl_sync(kFull, code, src);
+                if ((claim >> q) & 1u) {
+                    if (c == 0u) res_all |= 1u << (r0 + q);
+                    else if (c == 2u) slow |= 1u << q;
+                }
+            }
+            // Rare: claims that lost to another key, and full first buckets.
+            if (__any_sync(kFull, slow != 0)) {
+#pragma unroll 1
+                for (int q = 0; q < PF; ++q) {
+                    if (!__any_sync(kFull, (slow >> q) & 1u)) continue;
+                    const int kidx = (r0 + q) * GPW + grp;
+                    const uint64_t key = __shfl_sync(kFull, mykey, kidx);
+                    const uint64_t word = __shfl_sync(kFull, myword, kidx);
+                    const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
+                    const uint32_t r = claim_slow<KW, BS, G>(t, (slow >> q) & 1u, key, word, b,
+                                                             (le_pack >> (q * SPL)) & kLMask, sub, gbase, lane);
+                    if (r) res_all |= 1u << (r0 + q);
+                }
+            }
+            (void)valid;
         }
+        // Lane l's key was served by group l % GPW in round l / GPW.
+        const uint32_t my_new = (__shfl_sync(kFull, res_all, (lane % GPW) * G) >> (lane / GPW)) & 1u;
         if (mine && is_new) is_new[base + lane] = uint8_t(my_new);
         if (APPEND) warp_append<typename K::T>(mine && my_new, typename K::T(mykey), new_out, new_count);
         stored += __popc(__ballot_sync(kFull, my_new != 0));
@@ -173,6 +260,8 @@ bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_
     if ((threadIdx.x & 31) == 0 && stored) atomicAdd(&t.ctr->size, stored);
 }
 
+// Lookup: like find-or-put without claims; a bucket with a free slot ends the
+// search (a key only moves on from a full bucket), all k full -> the spill.
 template <int KW, int BS, int G>
 __global__ void __launch_bounds__(kBlock)
 bucket_lookup_kernel(const DevTable t, const void* __restrict__ keys, uint64_t n,
@@ -180,6 +269,8 @@ bucket_lookup_kernel(const DevTable t, const void* __restrict__ keys, uint64_t n
     using K = Keys<KW>;
     constexpr int SPL = BS / G;
     constexpr int GPW = 32 / G;
+    constexpr int PF = Prefetch<G, SPL>::kRounds;
+    constexpr uint32_t kGMask = (G == 32) ? 0xFFFFFFFFu : ((1u << G) - 1u);
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G, gbase = grp * G;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
@@ -190,76 +281,82 @@ bucket_lookup_kernel(const DevTable t, const void* __restrict__ keys, uint64_t n
          base += nwarps * 32) {
         const bool mine = base + lane < n;
         const uint64_t mykey = mine ? K::load(keys, base + lane) : 0;
+        const bool myok = mine && !K::reserved(mykey);
+        if (mine && !myok) set_flag(t.ctr, kFlagInvalidKey);
+        const uint64_t mybkt = hidx(mykey, t.seed[0], t.nbuckets);
         uint32_t my_found = 0, my_val = 0;
 #pragma unroll 1
-        for (int r = 0; r < G; ++r) {
-            const int kidx = r * GPW + grp;
-            const uint64_t key = __shfl_sync(kFull, mykey, kidx);
-            int state = (base + kidx < n && !K::reserved(key)) ? kRead : kDone;
-            if (base + kidx < n && K::reserved(key) && sub == 0) set_flag(t.ctr, kFlagInvalidKey);
-            uint32_t f = 0;
-            uint64_t b = hidx(key, t.seed[0], t.nbuckets);
-            uint32_t res_found = 0, res_val = 0;
-            while (__any_sync(kFull, state != kDone)) {
-                bool m[SPL], e[SPL];
-                uint64_t w[SPL];
-                if (state == kRead) {
-                    load_lane<SPL>(t.slots + b * BS + sub * SPL, w);
+        for (int r0 = 0; r0 < G; r0 += PF) {
+            uint64_t w[PF][SPL];
 #pragma unroll
-                    for (int j = 0; j < SPL; ++j) {
-                        m[j] = K::keyof(w[j]) == key;
-                        e[j] = K::empty(w[j]);
-                    }
+            for (int q = 0; q < PF; ++q) {
+                const int kidx = (r0 + q) * GPW + grp;
+                const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
+                const bool ok = __shfl_sync(kFull, myok, kidx);
+                if (ok) {
+                    load_lane<SPL>(t.slots + b * BS + sub * SPL, w[q]);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < SPL; ++j) {
-                        m[j] = e[j] = false;
-                        w[j] = 0;
-                    }
-                }
-                const uint32_t M = group_mask<G, SPL>(m, gbase);
-                const uint32_t E = group_mask<G, SPL>(e, gbase);
-                int owner = lane;
-                int q = 0;
-                if (state == kRead && M) {
-                    q = __ffs(M) - 1;
-                    owner = gbase + (q % G);
-                }
-                uint64_t mw = 0;
-#pragma unroll
-                for (int j = 0; j < SPL; ++j)
-                    if (j == q / G) mw = w[j];
-                mw = __shfl_sync(kFull, mw, owner);
-                if (state == kRead) {
-                    if (M) {
-                        res_found = 1;
-                        res_val = K::value(mw);
-                        state = kDone;
-                    } else if (E) {
-                        state = kDone;              // a non-full bucket ends the search
-                    } else if (++f < t.k) {
-                        b = hidx(key, t.seed[f], t.nbuckets);
-                    } else {
-                        state = kSpill;
-                    }
-                }
-                if (state == kSpill) {
-                    if (sub == 0) {
-                        uint64_t sw;
-                        if (find_spill<KW>(t, key, stash_used, ovf_used, &sw)) {
-                            res_found = 1;
-                            res_val = K::value(sw);
-                        }
-                    }
-                    state = kDone;
+                    for (int j = 0; j < SPL; ++j) w[q][j] = kEmpty;
                 }
             }
-            const int src = (lane % GPW) * G;
-            const uint32_t gf = __shfl_sync(kFull, res_found, src);
-            const uint32_t gv = __shfl_sync(kFull, res_val, src);
-            if (lane / GPW == r) {
-                my_found = gf;
-                my_val = gv;
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int kidx = (r0 + q) * GPW + grp;
+                const uint64_t key = __shfl_sync(kFull, mykey, kidx);
+                int state = __shfl_sync(kFull, myok, kidx) ? kRead : kDone;
+                uint64_t cur[SPL];
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) cur[j] = w[q][j];
+                uint32_t lm, le;
+                scan_lane<KW, SPL>(cur, key, lm, le);
+                uint32_t f = 0, res_found = 0, res_val = 0;
+                while (__any_sync(kFull, state != kDone)) {
+                    const uint32_t Mb = __ballot_sync(kFull, state == kRead && lm != 0);
+                    const uint32_t M = (Mb >> gbase) & kGMask;
+                    const uint32_t E = (__ballot_sync(kFull, state == kRead && le != 0) >> gbase) & kGMask;
+                    uint32_t v = 0;
+                    if (lm) {
+                        const int j = __ffs(lm) - 1;
+#pragma unroll
+                        for (int jj = 0; jj < SPL; ++jj)
+                            if (jj == j) v = K::value(cur[jj]);
+                    }
+                    const int owner = M ? gbase + __ffs(M) - 1 : lane;
+                    v = __shfl_sync(kFull, v, owner);
+                    if (state == kRead) {
+                        if (M) {
+                            res_found = 1;
+                            res_val = v;
+                            state = kDone;
+                        } else if (E) {
+                            state = kDone;
+                        } else if (++f < t.k) {
+                            const uint64_t b = hidx(key, t.seed[f], t.nbuckets);
+                            load_lane<SPL>(t.slots + b * BS + sub * SPL, cur);
+                            scan_lane<KW, SPL>(cur, key, lm, le);
+                        } else {
+                            state = kSpill;
+                        }
+                    }
+                    if (state == kSpill) {
+                        if (sub == 0) {
+                            uint64_t sw;
+                            if (find_spill<KW>(t, key, stash_used, ovf_used, &sw)) {
+                                res_found = 1;
+                                res_val = K::value(sw);
+                            }
+                        }
+                        state = kDone;
+                    }
+                }
+                const int src = ((lane - (r0 + q) * GPW) & (GPW - 1)) * G;
+                const uint32_t gf = __shfl_sync(kFull, res_found, src);
+                const uint32_t gv = __shfl_sync(kFull, res_val, src);
+                if (lane / GPW == r0 + q) {
+                    my_found = gf;
+                    my_val = gv;
+                }
             }
         }
         if (mine) {
@@ -303,7 +400,7 @@ cudaError_t launch_lookup(const DevTable& t, const void* keys, uint64_t n, uint3
 
 // (bucket_slots, lanes) pairs that are instantiated.
 #define HT_BUCKET_CONFIGS(X) \
-    X(8, 4) X(8, 8) X(16, 4) X(16, 8) X(16, 16) X(32, 8) X(32, 16) X(32, 32)
+    X(8, 2) X(8, 4) X(8, 8) X(16, 2) X(16, 4) X(16, 8) X(16, 16) X(32, 4) X(32, 8) X(32, 16) X(32, 32)
 
 }  // namespace
 

@@ -26,6 +26,15 @@
 namespace ht {
 namespace {
 
+#ifndef HT_CUCKOO_KEYS_PER_THREAD
+#define HT_CUCKOO_KEYS_PER_THREAD 4
+#endif
+constexpr int kU = HT_CUCKOO_KEYS_PER_THREAD;   // keys in flight per thread
+
+// Probe (and, for find-or-put, dedup).  Each thread holds U keys of a round,
+// strided by the grid so every load of keys stays coalesced; all U first
+// probes are issued together, then all remaining probes of the misses, then
+// every miss's first dedup claim, so U memory latencies overlap.
 template <int KW, bool VALUES, bool LOOKUP>
 __global__ void __launch_bounds__(kBlock)
 cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
@@ -35,64 +44,111 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     const uint32_t stash_used = __ldcg(&t.ctr->stash_used);
     const uint32_t ovf_used = __ldcg(&t.ctr->ovf_used);
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    const uint64_t rounds = (n + stride - 1) / stride;     // warp-uniform trip count
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t rounds = (n + stride * kU - 1) / (stride * kU);     // warp-uniform trip count
+    const uint64_t dseed = t.aux_seed * 3 + 1;
+    const int lane = threadIdx.x & 31;
     for (uint64_t r = 0; r < rounds; ++r) {
-        const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x + r * stride;
-        const bool active = i < n;
-        const uint64_t key = active ? K::load(keys, i) : 0;
-        uint32_t flag = 0, value = 0;
-        bool winner = false;
-        uint64_t word = 0;
-        uint32_t spos = 0;
-        if (!active) {
-        } else if (K::reserved(key)) {
-            set_flag(t.ctr, kFlagInvalidKey);
-        } else {
-            // Section 4.1: a key is found in at most k probes.
-            uint64_t w = __ldcg(reinterpret_cast<const unsigned long long*>(
-                t.slots + hidx(key, t.seed[0], t.nslots)));
-            bool found = K::keyof(w) == key;
-            if (!found) {
-                uint64_t ws[kMaxCuckooHashes];
+        uint64_t key[kU], w[kU];
+        bool act[kU], found[kU];
 #pragma unroll
-                for (int a = 1; a < kMaxCuckooHashes; ++a)
-                    if (a < int(t.k))
-                        ws[a] = __ldcg(reinterpret_cast<const unsigned long long*>(
-                            t.slots + hidx(key, t.seed[a], t.nslots)));
-#pragma unroll
-                for (int a = 1; a < kMaxCuckooHashes; ++a)
-                    if (a < int(t.k) && !found && K::keyof(ws[a]) == key) {
-                        found = true;
-                        w = ws[a];
-                    }
-            }
-            if (!found && (stash_used | ovf_used)) found = find_spill<KW>(t, key, stash_used, ovf_used, &w);
-            if (LOOKUP) {
-                flag = found;
-                value = found ? K::value(w) : 0u;
-            } else if (!found) {
-                word = K::word(key, VALUES ? vals[i] : 0u);
-                const int claim = lp_insert<KW>(sc.set, uint32_t(sc.mask + 1),
-                                            mix64(key ^ (t.aux_seed * 3 + 1)) & sc.mask, key, key, &spos);
-                winner = claim == 1;
-                flag = winner;
+        for (int u = 0; u < kU; ++u) {
+            const uint64_t i = (r * kU + u) * stride + tid;
+            act[u] = i < n;
+            key[u] = act[u] ? K::load(keys, i) : 0;
+            if (act[u] && K::reserved(key[u])) {
+                set_flag(t.ctr, kFlagInvalidKey);
+                act[u] = false;
             }
         }
-        if (active && out_flag) out_flag[i] = uint8_t(flag);
-        if (LOOKUP && active && out_val) out_val[i] = value;
-        if (!LOOKUP) {
+        // Section 4.1: a key is found in at most k probes; h_1 first.
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (act[u]) w[u] = __ldcg(reinterpret_cast<const unsigned long long*>(t.slots + hidx(key[u], t.seed[0], t.nslots)));
+#pragma unroll
+        for (int u = 0; u < kU; ++u) found[u] = act[u] && K::keyof(w[u]) == key[u];
+        uint64_t ws[kU][kMaxCuckooHashes];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+#pragma unroll
+            for (int a = 1; a < kMaxCuckooHashes; ++a)
+                if (a < int(t.k) && act[u] && !found[u])
+                    ws[u][a] = __ldcg(reinterpret_cast<const unsigned long long*>(t.slots + hidx(key[u], t.seed[a], t.nslots)));
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+#pragma unroll
+            for (int a = 1; a < kMaxCuckooHashes; ++a)
+                if (a < int(t.k) && act[u] && !found[u] && K::keyof(ws[u][a]) == key[u]) {
+                    found[u] = true;
+                    w[u] = ws[u][a];
+                }
+        if (stash_used | ovf_used) {
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (act[u] && !found[u]) found[u] = find_spill<KW>(t, key[u], stash_used, ovf_used, &w[u]);
+        }
+        if (LOOKUP) {
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint64_t i = (r * kU + u) * stride + tid;
+                if (i < n) {
+                    if (out_flag) out_flag[i] = uint8_t(found[u]);
+                    if (out_val) out_val[i] = found[u] ? K::value(w[u]) : 0u;
+                }
+            }
+            continue;
+        }
+        // In-batch dedup: the one claimant of each absent key wins.  First
+        // claim attempt of every miss together; collisions fall back to the
+        // linear-probing loop.
+        uint32_t spos[kU];
+        uint64_t sw[kU];
+        bool need[kU], winner[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            need[u] = act[u] && !found[u];
+            spos[u] = uint32_t(mix64(key[u] ^ dseed) & sc.mask);
+            sw[u] = kEmpty;
+            if (need[u]) sw[u] = __ldcg(reinterpret_cast<const unsigned long long*>(sc.set + spos[u]));
+        }
+        bool won[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            won[u] = false;
+            if (need[u] && sw[u] == kEmpty) {
+                const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(sc.set + spos[u]), kEmpty, key[u]);
+                won[u] = old == kEmpty;
+                sw[u] = old;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            winner[u] = false;
+            if (!need[u]) continue;
+            if (won[u]) {
+                winner[u] = true;                          // our CAS filled the empty slot
+            } else if (K::keyof(sw[u]) != key[u]) {        // another key sits there: probe on
+                uint32_t at = 0;
+                const uint32_t next = spos[u] + 1 == uint32_t(sc.mask + 1) ? 0u : spos[u] + 1;
+                winner[u] = lp_insert<KW>(sc.set, uint32_t(sc.mask + 1), next, key[u], key[u], &at) == 1;
+                spos[u] = at;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint64_t i = (r * kU + u) * stride + tid;
+            if (i < n && out_flag) out_flag[i] = uint8_t(winner[u]);
             // Warp-aggregated append of the winners to the insert list.
-            const unsigned wm = __ballot_sync(0xFFFFFFFFu, winner);
+            const unsigned wm = __ballot_sync(0xFFFFFFFFu, winner[u]);
             if (wm) {
-                const int lane = threadIdx.x & 31;
                 const int leader = __ffs(wm) - 1;
                 unsigned int b = 0;
                 if (lane == leader) b = atomicAdd(&t.ctr->winners[parity], unsigned(__popc(wm)));
                 b = __shfl_sync(0xFFFFFFFFu, b, leader);
-                if (winner) {
+                if (winner[u]) {
                     Winner wn;
-                    wn.word = word;
-                    wn.spos = spos;
+                    wn.word = K::word(key[u], VALUES ? vals[i] : 0u);
+                    wn.spos = spos[u];
                     wn.pad_ = 0;
                     sc.win[b + __popc(wm & ((1u << lane) - 1))] = wn;
                 }
@@ -101,6 +157,8 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     }
 }
 
+// Eviction-chain insert of the winners; each thread runs U chains in step so
+// their exchanges overlap.
 template <int KW, bool APPEND>
 __global__ void __launch_bounds__(kBlock)
 cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uint64_t max_winners,
@@ -111,40 +169,67 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
     // this stream; reset its counter for the next probe kernel.
     if (blockIdx.x == 0 && threadIdx.x == 0) t.ctr->winners[parity ^ 1u] = 0;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t rounds = (count + stride * kU - 1) / (stride * kU);
     unsigned long long placed = 0;
-    const uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint64_t rounds = (count + stride - 1) / stride;
     for (uint64_t r = 0; r < rounds; ++r) {
-        const uint64_t i = i0 + r * stride;
-        const bool active = i < count;
-        uint64_t first_key = 0;
-        if (active) {
-            const Winner wn = sc.win[i];
-            sc.set[wn.spos] = kEmpty;          // leave the dedup set empty for the next batch
-            uint64_t word = wn.word;
-            first_key = K::keyof(word);
-            uint64_t key = first_key;
-            uint64_t pos = hidx(key, t.seed[0], t.nslots);
-            bool done = false;
-            for (uint32_t e = 0; e <= t.max_evict; ++e) {
-                const uint64_t old = atomicExch(reinterpret_cast<unsigned long long*>(t.slots + pos), word);
-                if (K::empty(old)) {
-                    done = true;
-                    break;
+        uint64_t word[kU], pos[kU], first[kU];
+        bool live[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint64_t i = (r * kU + u) * stride + tid;
+            live[u] = i < count;
+            first[u] = 0;
+            word[u] = 0;
+            pos[u] = 0;
+            if (live[u]) {
+                const Winner wn = sc.win[i];
+                sc.set[wn.spos] = kEmpty;      // leave the dedup set empty for the next batch
+                word[u] = wn.word;
+                first[u] = K::keyof(wn.word);
+                pos[u] = hidx(first[u], t.seed[0], t.nslots);
+            }
+        }
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) any |= live[u];
+        for (uint32_t e = 0; any && e <= t.max_evict; ++e) {
+            uint64_t old[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (live[u]) old[u] = atomicExch(reinterpret_cast<unsigned long long*>(t.slots + pos[u]), word[u]);
+            any = false;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                if (!live[u]) continue;
+                if (K::empty(old[u])) {
+                    live[u] = false;
+                    ++placed;
+                    continue;
                 }
                 // Section 4.1: the evicted key k' sat at h_a(k') = pos; it
                 // moves on to h_{a+1}(k') (cyclically after h_k).
-                word = old;
-                key = K::keyof(old);
+                word[u] = old[u];
+                const uint64_t key = K::keyof(old[u]);
                 uint32_t a = 0;
                 for (; a + 1 < t.k; ++a)
-                    if (hidx(key, t.seed[a], t.nslots) == pos) break;
+                    if (hidx(key, t.seed[a], t.nslots) == pos[u]) break;
                 const uint32_t nxt = (a + 1 == t.k) ? 0u : a + 1;
-                pos = hidx(key, t.seed[nxt], t.nslots);
+                pos[u] = hidx(key, t.seed[nxt], t.nslots);
+                any = true;
             }
-            if (done || place_spill<KW>(t, key, word) == 1) ++placed;
         }
-        if (APPEND) warp_append<typename K::T>(active, typename K::T(first_key), new_out, new_count);
+        // Chains that hit the eviction bound hold a word that goes to the stash.
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (live[u] && place_spill<KW>(t, K::keyof(word[u]), word[u]) == 1) ++placed;
+        if (APPEND) {
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint64_t i = (r * kU + u) * stride + tid;
+                warp_append<typename K::T>(i < count, typename K::T(first[u]), new_out, new_count);
+            }
+        }
     }
     for (int o = 16; o; o >>= 1) placed += __shfl_down_sync(0xFFFFFFFFu, placed, o);
     if ((threadIdx.x & 31) == 0 && placed) atomicAdd(&t.ctr->size, placed);

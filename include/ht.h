@@ -165,6 +165,71 @@ ht_status ht_compact(const void* d_keys, const uint8_t* d_flags, uint64_t n,
                      void* stream);
 
 /* ---------------------------------------------------------------------------
+ * State-space exploration (Section 3.2: a model is a set of finite-state
+ * processes in parallel composition; BFS from the vector of initial local
+ * states keeps the open and closed sets in the hash table; successor vectors
+ * are built from each process's enabled transitions).
+ *
+ * Model layout (host struct, copied to the device by each call):
+ *   component c < num_components (<= 16) has local states stored in bits[c]
+ *   bits, packed LSB-first: c occupies bits [o_c, o_c + bits[c]) with
+ *   o_c = bits[0] + ... + bits[c-1]; the packed vector must fit the table's
+ *   key width (<= 31 bits for 32-bit keys, <= 63 for 64-bit keys).
+ *   Local state u (< 32) of component c has deg[c][u] (<= 4) transitions j
+ *   to tgt[c][u][j] with label lab[c][u][j]: 0 = local action, p+1 = member
+ *   of synchronising pair p = (pair_c1[p], pair_c2[p]), p < num_pairs <= 8.
+ * Successors of a state s: for every component c and every label-0
+ * transition of c at s_c, s with s_c replaced by its target; for every pair
+ * p and every combination of a label-(p+1) transition of pair_c1[p] at its
+ * local state and one of pair_c2[p] at its local state, s with both local
+ * states replaced.  Labelled transitions never fire alone.
+ * ------------------------------------------------------------------------- */
+typedef struct ht_model {
+    int32_t num_components;
+    int32_t num_pairs;
+    uint8_t bits[16];
+    uint8_t pair_c1[8];
+    uint8_t pair_c2[8];
+    uint8_t deg[16][32];
+    uint8_t tgt[16][32][4];
+    uint8_t lab[16][32][4];
+} ht_model;
+
+/* Writes the successors of n states (key_width-bit vectors) to d_succ at
+ * positions reserved on the device counter *d_count (not reset; order
+ * unspecified).  HT_ERR_INVALID for a malformed model.  If more than `cap`
+ * successors would be written, the excess is not written and *d_count still
+ * counts them, so the caller can detect it (cap >= n * the model's largest
+ * per-state successor count never overflows). */
+ht_status ht_successors(const ht_model* h_model, uint32_t key_width, const void* d_states,
+                        uint64_t n, void* d_succ, uint64_t cap,
+                        unsigned long long* d_count, void* stream);
+
+typedef struct ht_bfs_result {
+    uint64_t levels;        /* non-empty BFS levels */
+    uint64_t states;        /* reachable states stored */
+    uint64_t successors;    /* successor vectors generated (with repeats) */
+    int32_t complete;       /* 1 if the exploration finished within the limits */
+    int32_t reserved_;
+} ht_bfs_result;
+
+/* Level-synchronous BFS from state s0 over `model`, with the table `t` as the
+ * set of visited states (it should be empty; every reachable state is
+ * find-or-put into it once per generating transition).  Each level: generate
+ * the successors of the frontier, find-or-put them, and the new ones (the
+ * is_new keys) become the next frontier.  d_states (nullable, key_width-bit
+ * entries, states_cap of them) receives every reachable state in level
+ * order: level d occupies [sum of sizes of levels < d, + size of level d).
+ * h_level_sizes (nullable, max_levels entries) receives the level sizes.
+ * Stops when a level is empty (complete = 1), or when max_levels or
+ * states_cap would be exceeded (complete = 0).  Synchronises once per level.
+ * Allocates its work buffers with cudaMalloc and frees them before
+ * returning. */
+ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max_levels,
+                 uint64_t* h_level_sizes, void* d_states, uint64_t states_cap,
+                 ht_bfs_result* result, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Kernel timing (CUDA events around every launch the library makes, on the
  * launch's stream).  ht_prof_read synchronises on the recorded events.
  * ------------------------------------------------------------------------- */

@@ -14,7 +14,7 @@ import ctypes
 
 import torch
 
-from ._lib import HT_BUCKET, HT_CUCKOO, HtError, HtParams, load
+from ._lib import HT_BUCKET, HT_CUCKOO, HtBfsResult, HtError, HtModel, HtParams, load
 
 __all__ = [
     "HT_BUCKET", "HT_CUCKOO", "HtError", "HtParams", "HashTable", "load",
@@ -22,7 +22,7 @@ __all__ = [
     "ht_insert", "ht_lookup", "ht_sync", "ht_size", "ht_export", "ht_clear", "ht_info",
     "ht_compact", "ht_prof_enable", "ht_prof_reset", "ht_prof_read", "ht_prof_kernels",
     "ht_probe_random_read", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
-    "NOALLOC_MAX_BATCH", "scheme_of",
+    "NOALLOC_MAX_BATCH", "scheme_of", "HtModel", "HtBfsResult", "make_model", "ht_successors", "ht_bfs",
 ]
 
 NOALLOC_STATE_BYTES = 2048      # HT_NOALLOC_STATE_BYTES
@@ -189,6 +189,48 @@ def ht_cuckoo_find_or_put_noalloc(slots, state, seed, keys, is_new=None, reset=F
     return load().ht_cuckoo_find_or_put_noalloc(
         _dptr(slots, "slots"), slots.numel() * slots.element_size() // 8, _dptr(state, "state"), int(seed),
         _dptr(keys, "keys"), keys.numel(), _dptr(is_new, "is_new"), 1 if reset else 0, _stream(stream))
+
+
+def make_model(num_components, bits, deg, tgt, lab, pairs):
+    """Pack model tables (array-likes shaped like ht_model's fields) into an HtModel."""
+    import numpy as np
+    m = HtModel()
+    m.num_components = int(num_components)
+    pairs = np.asarray(pairs, dtype=np.uint8).reshape(-1, 2)
+    m.num_pairs = int(pairs.shape[0])
+
+    def put(field, arr, size):
+        a = np.ascontiguousarray(np.asarray(arr, dtype=np.uint8).ravel()[:size])
+        ctypes.memmove(field, a.ctypes.data, a.nbytes)
+
+    put(m.bits, bits, 16)
+    c1 = np.zeros(8, dtype=np.uint8)
+    c2 = np.zeros(8, dtype=np.uint8)
+    c1[:m.num_pairs] = pairs[:, 0]
+    c2[:m.num_pairs] = pairs[:, 1]
+    put(m.pair_c1, c1, 8)
+    put(m.pair_c2, c2, 8)
+    put(m.deg, deg, 16 * 32)
+    put(m.tgt, tgt, 16 * 32 * 4)
+    put(m.lab, lab, 16 * 32 * 4)
+    return m
+
+
+def ht_successors(model, states, succ, count, stream=None):
+    _check(load().ht_successors(ctypes.byref(model), _key_width(states), _dptr(states, "states"), states.numel(),
+                                _dptr(succ, "succ"), succ.numel(), _dptr(count, "count"), _stream(stream)),
+           "ht_successors")
+
+
+def ht_bfs(table, model, s0=0, max_levels=4096, states=None, states_cap=0, stream=None):
+    """Returns (HtBfsResult, level sizes list); `states` (optional tensor)
+    receives every reachable state in level order."""
+    sizes = (ctypes.c_uint64 * max_levels)()
+    res = HtBfsResult()
+    cap = states.numel() if states is not None else int(states_cap)
+    _check(load().ht_bfs(table, ctypes.byref(model), int(s0), int(max_levels), sizes,
+                         _dptr(states, "states"), cap, ctypes.byref(res), _stream(stream)), "ht_bfs")
+    return res, [int(sizes[i]) for i in range(res.levels)]
 
 
 # ----------------------------------------------------------------- helper

@@ -19,6 +19,23 @@ class HtParams(ctypes.Structure):
     ]
 
 
+class HtModel(ctypes.Structure):
+    _fields_ = [
+        ("num_components", ctypes.c_int32), ("num_pairs", ctypes.c_int32),
+        ("bits", ctypes.c_uint8 * 16),
+        ("pair_c1", ctypes.c_uint8 * 8), ("pair_c2", ctypes.c_uint8 * 8),
+        ("deg", ctypes.c_uint8 * (16 * 32)),
+        ("tgt", ctypes.c_uint8 * (16 * 32 * 4)),
+        ("lab", ctypes.c_uint8 * (16 * 32 * 4)),
+    ]
+
+
+class HtBfsResult(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_uint64), ("states", ctypes.c_uint64),
+                ("successors", ctypes.c_uint64), ("complete", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
+
+
 class HtError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -51,6 +68,8 @@ SIGNATURES = {
     "ht_prof_read": (_I32, [_U32, _P(_U64), _P(ctypes.c_double)]),
     "ht_probe_random_read": (_I32, [_VP, _U64, _U32, _U64, _U64, _VP, _VP]),
     "ht_cuckoo_find_or_put_noalloc": (_I32, [_VP, _U64, _VP, _U64, _VP, _U64, _VP, ctypes.c_int, _VP]),
+    "ht_successors": (_I32, [_P(HtModel), _U32, _VP, _U64, _VP, _U64, _VP, _VP]),
+    "ht_bfs": (_I32, [_VP, _P(HtModel), _U64, _U32, _VP, _VP, _U64, _P(HtBfsResult), _VP]),
 }
 
 _lib = None

@@ -77,19 +77,20 @@ ht_status clear_table(ht_table* t, cudaStream_t s) {
 
 // Runs find-or-put / insert over a batch without touching rebuild state.
 ht_status run_put(ht_table* t, const void* keys, const uint32_t* vals, uint64_t n, uint8_t* is_new,
-                  void* new_out, unsigned long long* new_count, cudaStream_t s) {
+                  void* new_out, unsigned long long* new_count, cudaStream_t s,
+                  const unsigned long long* d_n = nullptr, uint64_t new_cap = ~0ull) {
     if (n == 0) return HT_OK;
     if (t->scheme == HT_BUCKET) {
-        return cuda_status(bucket_find_or_put(bucket_cfg(t), t->dt, keys, vals, n, is_new, new_out,
-                                              new_count, s));
+        return cuda_status(bucket_find_or_put(bucket_cfg(t), t->dt, keys, vals, n, d_n, is_new, new_out,
+                                              new_count, new_cap, s));
     }
     const size_t ksz = t->kw / 8;
     for (uint64_t off = 0; off < n; off += t->chunk) {
         const uint64_t m = std::min(t->chunk, n - off);
         const void* k = static_cast<const char*>(keys) + off * ksz;
-        HT_TRY(cuckoo_probe(int(t->kw), t->dt, t->sc, t->parity, k, vals ? vals + off : nullptr, m,
-                            is_new ? is_new + off : nullptr, s));
-        HT_TRY(cuckoo_insert(int(t->kw), t->dt, t->sc, t->parity, new_out, new_count, m, s));
+        HT_TRY(cuckoo_probe(int(t->kw), t->dt, t->sc, t->parity, k, vals ? vals + off : nullptr, m, d_n,
+                            off, is_new ? is_new + off : nullptr, s));
+        HT_TRY(cuckoo_insert(int(t->kw), t->dt, t->sc, t->parity, new_out, new_count, new_cap, m, s));
         t->parity ^= 1u;
     }
     return HT_OK;
@@ -428,6 +429,161 @@ ht_status ht_info(const ht_table* t, uint64_t* slots, uint32_t* num_hashes, uint
     if (num_hashes) *num_hashes = t->dt.k;
     if (rebuilds) *rebuilds = t->rebuilds;
     return HT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// State-space exploration.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Checks the model's fields against the layout documented in ht.h and
+// returns the largest number of successors one state can have (0 = invalid).
+uint64_t model_max_successors(const ht_model* m, uint32_t key_width) {
+    if (!m || m->num_components < 1 || m->num_components > 16 || m->num_pairs < 0 || m->num_pairs > 8) return 0;
+    uint32_t bits = 0;
+    for (int c = 0; c < m->num_components; ++c) {
+        if (m->bits[c] < 1 || m->bits[c] > 5) return 0;
+        bits += m->bits[c];
+    }
+    if (bits > (key_width == 32 ? 31u : 63u)) return 0;
+    for (int p = 0; p < m->num_pairs; ++p)
+        if (m->pair_c1[p] >= m->num_components || m->pair_c2[p] >= m->num_components ||
+            m->pair_c1[p] == m->pair_c2[p])
+            return 0;
+    uint64_t total = 0;
+    for (int c = 0; c < m->num_components; ++c) {
+        uint32_t most = 0;
+        for (uint32_t u = 0; u < (1u << m->bits[c]); ++u) {
+            if (m->deg[c][u] > 4) return 0;
+            uint32_t local = 0;
+            for (int j = 0; j < m->deg[c][u]; ++j) {
+                if (m->tgt[c][u][j] >= (1u << m->bits[c]) || m->lab[c][u][j] > m->num_pairs) return 0;
+                local += m->lab[c][u][j] == 0;
+            }
+            most = std::max(most, local);
+        }
+        total += most;
+    }
+    for (int p = 0; p < m->num_pairs; ++p) {
+        uint32_t most[2] = {0, 0};
+        const int cs[2] = {m->pair_c1[p], m->pair_c2[p]};
+        for (int side = 0; side < 2; ++side)
+            for (uint32_t u = 0; u < (1u << m->bits[cs[side]]); ++u) {
+                uint32_t k = 0;
+                for (int j = 0; j < m->deg[cs[side]][u]; ++j) k += m->lab[cs[side]][u][j] == p + 1;
+                most[side] = std::max(most[side], k);
+            }
+        total += uint64_t(most[0]) * most[1];
+    }
+    return total ? total : 1;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { cudaFree(p); }
+};
+
+}  // namespace
+
+extern "C" {
+
+ht_status ht_successors(const ht_model* h_model, uint32_t key_width, const void* d_states, uint64_t n,
+                        void* d_succ, uint64_t cap, unsigned long long* d_count, void* stream) {
+    if ((key_width != 32 && key_width != 64) || !d_count || (n && (!d_states || !d_succ))) return HT_ERR_INVALID;
+    if (!model_max_successors(h_model, key_width)) return HT_ERR_INVALID;
+    if (n == 0) return HT_OK;
+    const cudaStream_t s = as_stream(stream);
+    DevBuf dm;
+    HT_TRY(cudaMalloc(&dm.p, sizeof(ht_model)));
+    HT_TRY(cudaMemcpyAsync(dm.p, h_model, sizeof(ht_model), cudaMemcpyHostToDevice, s));
+    HT_TRY(successors(int(key_width), static_cast<const ht_model*>(dm.p), d_states, n, nullptr, 0, d_succ, cap,
+                      d_count, nullptr, s));
+    HT_TRY(cudaStreamSynchronize(s));        // the model copy is freed on return
+    return HT_OK;
+}
+
+ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max_levels, uint64_t* h_level_sizes,
+                 void* d_states, uint64_t states_cap, ht_bfs_result* result, void* stream) {
+    if (!t || !result) return HT_ERR_INVALID;
+    const uint64_t msucc = model_max_successors(h_model, t->kw);
+    if (!msucc) return HT_ERR_INVALID;
+    if (t->kw == 32 ? s0 >= 0xFFFFFFFFull : (s0 >> 63) != 0) return HT_ERR_INVALID;
+    DeviceGuard g(t->device);
+    const cudaStream_t s = as_stream(stream);
+    std::memset(result, 0, sizeof(*result));
+    const size_t ksz = t->kw / 8;
+    if (!d_states) {
+        if (!states_cap) states_cap = t->dt.nslots + t->dt.stash_slots + t->dt.ovf_slots;
+    } else if (!states_cap) {
+        return HT_ERR_INVALID;
+    }
+    // Successor buffer: up to 2^26 vectors per find-or-put launch sequence.
+    const uint64_t succ_cap = std::min<uint64_t>(1ull << 26, std::max<uint64_t>(msucc, (t->dt.nslots + 1) * msucc));
+    const uint64_t chunk_states = std::max<uint64_t>(1, succ_cap / msucc);
+    DevBuf dm, states_own, succ, ctr;
+    HT_TRY(cudaMalloc(&dm.p, sizeof(ht_model)));
+    HT_TRY(cudaMemcpyAsync(dm.p, h_model, sizeof(ht_model), cudaMemcpyHostToDevice, s));
+    if (!d_states) {
+        HT_TRY(cudaMalloc(&states_own.p, states_cap * ksz));
+        d_states = states_own.p;
+    }
+    HT_TRY(cudaMalloc(&succ.p, succ_cap * ksz));
+    // ctr[0]: states stored so far; ctr[1]: successors of the current chunk;
+    // ctr[2]: successors generated in total; ctr[3]: the initial state.
+    HT_TRY(cudaMalloc(&ctr.p, 4 * sizeof(unsigned long long)));
+    unsigned long long* c = static_cast<unsigned long long*>(ctr.p);
+    unsigned long long init[4] = {0, 0, 0, s0};
+    HT_TRY(cudaMemcpyAsync(c, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    // Level 0: the initial state (the open set starts with it).
+    ht_status st = run_put(t, t->kw == 32 ? static_cast<const void*>(reinterpret_cast<const uint32_t*>(c + 3))
+                                          : static_cast<const void*>(c + 3),
+                           nullptr, 1, nullptr, d_states, c, s, nullptr, states_cap);
+    if (st != HT_OK) return st;
+    char* states = static_cast<char*>(d_states);
+    uint64_t lo = 0;
+    uint32_t level = 0;
+    for (;;) {
+        unsigned long long hi = 0;
+        HT_TRY(cudaMemcpyAsync(&hi, c, sizeof(hi), cudaMemcpyDeviceToHost, s));
+        HT_TRY(cudaStreamSynchronize(s));
+        if (hi > states_cap) {               // the states buffer overflowed: stop
+            result->states = states_cap;
+            result->levels = level;
+            break;
+        }
+        const uint64_t nd = hi - lo;
+        if (nd == 0) {
+            result->complete = 1;
+            result->states = hi;
+            result->levels = level;
+            break;
+        }
+        if (level >= max_levels) {
+            result->states = hi;
+            result->levels = level;
+            break;
+        }
+        if (h_level_sizes) h_level_sizes[level] = nd;
+        for (uint64_t c0 = lo; c0 < hi; c0 += chunk_states) {
+            const uint64_t m = std::min<uint64_t>(chunk_states, hi - c0);
+            HT_TRY(cudaMemsetAsync(c + 1, 0, sizeof(unsigned long long), s));
+            HT_TRY(successors(int(t->kw), static_cast<const ht_model*>(dm.p), states + c0 * ksz, m, nullptr, 0, succ.p,
+                              succ_cap, c + 1, c + 2, s));
+            st = run_put(t, succ.p, nullptr, std::min<uint64_t>(succ_cap, m * msucc), nullptr, d_states, c, s, c + 1,
+                         states_cap);
+            if (st != HT_OK) return st;
+        }
+        lo = hi;
+        ++level;
+    }
+    unsigned long long gen = 0;
+    HT_TRY(cudaMemcpyAsync(&gen, c + 2, sizeof(gen), cudaMemcpyDeviceToHost, s));
+    HT_TRY(cudaStreamSynchronize(s));
+    result->successors = gen;
+    const ht_status ts = sync_and_status(t, s);
+    return ts;
 }
 
 }  // extern "C"

@@ -1,0 +1,140 @@
+// Successor generation for state-space exploration (Section 3.2 of the
+// paper: successor state vectors are built by combining the enabled
+// transitions of the processes).  The model's transition tables live in
+// shared memory, read-only, as the paper keeps them in texture memory.
+#include "ht_internal.cuh"
+
+namespace ht {
+namespace {
+
+struct SmemModel {
+    uint8_t deg[16][32];
+    uint8_t tgt[16][32][4];
+    uint8_t lab[16][32][4];
+    uint8_t off[16];
+    uint8_t bits[16];
+    uint8_t pc1[8];
+    uint8_t pc2[8];
+    int C;
+    int P;
+};
+
+__device__ __forceinline__ uint32_t local_of(const SmemModel& m, uint64_t s, int c) {
+    return uint32_t(s >> m.off[c]) & ((1u << m.bits[c]) - 1u);
+}
+
+__device__ __forceinline__ uint64_t with_local(const SmemModel& m, uint64_t s, int c, uint32_t v) {
+    const uint64_t mask = ((1ull << m.bits[c]) - 1ull) << m.off[c];
+    return (s & ~mask) | (uint64_t(v) << m.off[c]);
+}
+
+// Visits every successor of s: local actions of each component, then every
+// combination of the two members' transitions of each synchronising pair.
+template <class F>
+__device__ __forceinline__ void for_each_successor(const SmemModel& m, uint64_t s, F&& emit) {
+    for (int c = 0; c < m.C; ++c) {
+        const uint32_t u = local_of(m, s, c);
+        const int d = m.deg[c][u];
+        for (int j = 0; j < d; ++j)
+            if (m.lab[c][u][j] == 0) emit(with_local(m, s, c, m.tgt[c][u][j]));
+    }
+    for (int p = 0; p < m.P; ++p) {
+        const int c1 = m.pc1[p], c2 = m.pc2[p];
+        const uint32_t u1 = local_of(m, s, c1), u2 = local_of(m, s, c2);
+        const int d1 = m.deg[c1][u1], d2 = m.deg[c2][u2];
+        for (int j1 = 0; j1 < d1; ++j1) {
+            if (m.lab[c1][u1][j1] != p + 1) continue;
+            const uint64_t s1 = with_local(m, s, c1, m.tgt[c1][u1][j1]);
+            for (int j2 = 0; j2 < d2; ++j2)
+                if (m.lab[c2][u2][j2] == p + 1) emit(with_local(m, s1, c2, m.tgt[c2][u2][j2]));
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+successors_kernel(const ht_model* __restrict__ model, const T* __restrict__ states, uint64_t n,
+                  const unsigned long long* __restrict__ d_n, uint64_t off, T* __restrict__ succ,
+                  uint64_t cap, unsigned long long* __restrict__ count,
+                  unsigned long long* __restrict__ total) {
+    __shared__ SmemModel sm;
+    {
+        // Copy the tables (16-byte aligned, sizes multiples of 4 bytes).
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(model->deg);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(sm.deg);
+        constexpr int kWords = (sizeof(sm.deg) + sizeof(sm.tgt) + sizeof(sm.lab)) / 4;
+        for (int i = threadIdx.x; i < kWords; i += blockDim.x) dst[i] = src[i];
+        if (threadIdx.x == 0) {
+            sm.C = model->num_components;
+            sm.P = model->num_pairs;
+            int o = 0;
+            for (int c = 0; c < 16; ++c) {
+                sm.bits[c] = model->bits[c];
+                sm.off[c] = uint8_t(o);
+                if (c < sm.C) o += model->bits[c];
+            }
+            for (int p = 0; p < 8; ++p) {
+                sm.pc1[p] = model->pair_c1[p];
+                sm.pc2[p] = model->pair_c2[p];
+            }
+        }
+    }
+    __syncthreads();
+    if (d_n) {
+        const uint64_t all = __ldcg(d_n);
+        n = all > off ? min(n, all - off) : 0;
+    }
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t rounds = (n + stride - 1) / stride;       // warp-uniform trip count
+    unsigned long long made = 0;
+    for (uint64_t r = 0; r < rounds; ++r) {
+        const uint64_t i = r * stride + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+        const bool act = i < n;
+        const uint64_t s = act ? uint64_t(states[i]) : 0;
+        uint32_t cnt = 0;
+        if (act) for_each_successor(sm, s, [&](uint64_t) { ++cnt; });
+        // Warp-wide exclusive scan of the counts, one reservation per warp.
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 0 && tot) base = atomicAdd(count, (unsigned long long)tot);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        uint64_t pos = base + (incl - cnt);
+        if (act)
+            for_each_successor(sm, s, [&](uint64_t v) {
+                if (pos < cap) succ[pos] = T(v);
+                ++pos;
+            });
+        made += cnt;
+    }
+    if (total) {
+        for (int o = 16; o; o >>= 1) made += __shfl_down_sync(0xFFFFFFFFu, made, o);
+        if (lane == 0 && made) atomicAdd(total, made);
+    }
+}
+
+}  // namespace
+
+cudaError_t successors(int kw, const ht_model* model, const void* states, uint64_t n,
+                       const unsigned long long* d_n, uint64_t off, void* succ, uint64_t cap,
+                       unsigned long long* count, unsigned long long* total, cudaStream_t s) {
+    ProfScope ps(kKSuccessors, s);
+    if (kw == 32) {
+        auto k = successors_kernel<uint32_t>;
+        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(
+            model, static_cast<const uint32_t*>(states), n, d_n, off, static_cast<uint32_t*>(succ), cap, count, total);
+    } else {
+        auto k = successors_kernel<uint64_t>;
+        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(
+            model, static_cast<const uint64_t*>(states), n, d_n, off, static_cast<uint64_t*>(succ), cap, count, total);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ht

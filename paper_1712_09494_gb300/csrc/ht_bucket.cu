@@ -142,8 +142,10 @@ __device__ __noinline__ uint32_t claim_slow(const DevTable t, bool active, uint6
 template <int KW, int BS, int G, bool VALUES, bool APPEND>
 __global__ void __launch_bounds__(kBlock, HT_BUCKET_MIN_BLOCKS)
 bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_t* __restrict__ vals,
-                  uint64_t n, uint8_t* __restrict__ is_new, typename Keys<KW>::T* __restrict__ new_out,
-                  unsigned long long* __restrict__ new_count) {
+                  uint64_t n, const unsigned long long* __restrict__ d_n, uint8_t* __restrict__ is_new,
+                  typename Keys<KW>::T* __restrict__ new_out, unsigned long long* __restrict__ new_count,
+                  uint64_t new_cap) {
+    if (d_n) n = min(n, uint64_t(__ldcg(d_n)));        // batch size produced on the device
     using K = Keys<KW>;
     constexpr int SPL = BS / G;
     constexpr int GPW = 32 / G;
@@ -254,7 +256,7 @@ bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_
         // Lane l's key was served by group l % GPW in round l / GPW.
         const uint32_t my_new = (__shfl_sync(kFull, res_all, (lane % GPW) * G) >> (lane / GPW)) & 1u;
         if (mine && is_new) is_new[base + lane] = uint8_t(my_new);
-        if (APPEND) warp_append<typename K::T>(mine && my_new, typename K::T(mykey), new_out, new_count);
+        if (APPEND) warp_append<typename K::T>(mine && my_new, typename K::T(mykey), new_out, new_count, new_cap);
         stored += __popc(__ballot_sync(kFull, my_new != 0));
     }
     if ((threadIdx.x & 31) == 0 && stored) atomicAdd(&t.ctr->size, stored);
@@ -368,22 +370,22 @@ bucket_lookup_kernel(const DevTable t, const void* __restrict__ keys, uint64_t n
 
 template <int KW, int BS, int G>
 cudaError_t launch_fop(const DevTable& t, const void* keys, const uint32_t* vals, uint64_t n,
-                       uint8_t* is_new, void* new_out, unsigned long long* new_count,
-                       cudaStream_t s) {
+                       const unsigned long long* d_n, uint8_t* is_new, void* new_out,
+                       unsigned long long* new_count, uint64_t new_cap, cudaStream_t s) {
     using T = typename Keys<KW>::T;
     ProfScope ps(kKBucketFop, s);
     if (vals) {
         auto k = bucket_fop_kernel<KW, BS, G, true, false>;
         const int grid = launch_blocks((const void*)k, kBlock);
-        k<<<grid, kBlock, 0, s>>>(t, keys, vals, n, is_new, nullptr, nullptr);
+        k<<<grid, kBlock, 0, s>>>(t, keys, vals, n, d_n, is_new, nullptr, nullptr, 0);
     } else if (new_out) {
         auto k = bucket_fop_kernel<KW, BS, G, false, true>;
         const int grid = launch_blocks((const void*)k, kBlock);
-        k<<<grid, kBlock, 0, s>>>(t, keys, nullptr, n, is_new, static_cast<T*>(new_out), new_count);
+        k<<<grid, kBlock, 0, s>>>(t, keys, nullptr, n, d_n, is_new, static_cast<T*>(new_out), new_count, new_cap);
     } else {
         auto k = bucket_fop_kernel<KW, BS, G, false, false>;
         const int grid = launch_blocks((const void*)k, kBlock);
-        k<<<grid, kBlock, 0, s>>>(t, keys, nullptr, n, is_new, nullptr, nullptr);
+        k<<<grid, kBlock, 0, s>>>(t, keys, nullptr, n, d_n, is_new, nullptr, nullptr, 0);
     }
     return cudaGetLastError();
 }
@@ -405,12 +407,13 @@ cudaError_t launch_lookup(const DevTable& t, const void* keys, uint64_t n, uint3
 }  // namespace
 
 cudaError_t bucket_find_or_put(const BucketCfg& c, const DevTable& t, const void* keys,
-                               const uint32_t* vals, uint64_t n, uint8_t* is_new, void* new_out,
-                               unsigned long long* new_count, cudaStream_t s) {
-#define X(BS, G)                                                                          \
-    if (c.bucket_slots == BS && c.lanes == G)                                             \
-        return c.kw == 32 ? launch_fop<32, BS, G>(t, keys, vals, n, is_new, new_out, new_count, s) \
-                          : launch_fop<64, BS, G>(t, keys, vals, n, is_new, new_out, new_count, s);
+                               const uint32_t* vals, uint64_t n, const unsigned long long* d_n,
+                               uint8_t* is_new, void* new_out, unsigned long long* new_count,
+                               uint64_t new_cap, cudaStream_t s) {
+#define X(BS, G)                                                                                  \
+    if (c.bucket_slots == BS && c.lanes == G)                                                     \
+        return c.kw == 32 ? launch_fop<32, BS, G>(t, keys, vals, n, d_n, is_new, new_out, new_count, new_cap, s) \
+                          : launch_fop<64, BS, G>(t, keys, vals, n, d_n, is_new, new_out, new_count, new_cap, s);
     HT_BUCKET_CONFIGS(X)
 #undef X
     return cudaErrorInvalidValue;

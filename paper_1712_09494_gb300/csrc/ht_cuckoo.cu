@@ -39,8 +39,13 @@ template <int KW, bool VALUES, bool LOOKUP>
 __global__ void __launch_bounds__(kBlock)
 cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     const void* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t n,
+                    const unsigned long long* __restrict__ d_n, uint64_t off,
                     uint8_t* __restrict__ out_flag, uint32_t* __restrict__ out_val) {
     using K = Keys<KW>;
+    if (d_n) {                                   // batch size produced on the device
+        const uint64_t total = __ldcg(d_n);
+        n = total > off ? min(n, total - off) : 0;
+    }
     const uint32_t stash_used = __ldcg(&t.ctr->stash_used);
     const uint32_t ovf_used = __ldcg(&t.ctr->ovf_used);
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
@@ -162,7 +167,8 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
 template <int KW, bool APPEND>
 __global__ void __launch_bounds__(kBlock)
 cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uint64_t max_winners,
-                     typename Keys<KW>::T* __restrict__ new_out, unsigned long long* __restrict__ new_count) {
+                     typename Keys<KW>::T* __restrict__ new_out, unsigned long long* __restrict__ new_count,
+                     uint64_t new_cap) {
     using K = Keys<KW>;
     const uint64_t count = min(uint64_t(__ldcg(&t.ctr->winners[parity])), max_winners);
     // The other parity's list was consumed by the previous insert kernel on
@@ -227,7 +233,7 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const uint64_t i = (r * kU + u) * stride + tid;
-                warp_append<typename K::T>(i < count, typename K::T(first[u]), new_out, new_count);
+                warp_append<typename K::T>(i < count, typename K::T(first[u]), new_out, new_count, new_cap);
             }
         }
     }
@@ -238,14 +244,14 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
 }  // namespace
 
 cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
-                         const void* keys, const uint32_t* vals, uint64_t n, uint8_t* is_new,
-                         cudaStream_t s) {
+                         const void* keys, const uint32_t* vals, uint64_t n,
+                         const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s) {
     ProfScope ps(kKCuckooProbe, s);
 #define L(KW, V)                                                                    \
     {                                                                               \
         auto k = cuckoo_probe_kernel<KW, V, false>;                                 \
         const int grid = launch_blocks((const void*)k, kBlock);                     \
-        k<<<grid, kBlock, 0, s>>>(t, sc, parity, keys, vals, n, is_new, nullptr);   \
+        k<<<grid, kBlock, 0, s>>>(t, sc, parity, keys, vals, n, d_n, off, is_new, nullptr); \
     }
     if (kw == 32) {
         if (vals) L(32, true) else L(32, false)
@@ -257,15 +263,15 @@ cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32
 }
 
 cudaError_t cuckoo_insert(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
-                          void* new_out, unsigned long long* new_count, uint64_t max_winners,
-                          cudaStream_t s) {
+                          void* new_out, unsigned long long* new_count, uint64_t new_cap,
+                          uint64_t max_winners, cudaStream_t s) {
     ProfScope ps(kKCuckooInsert, s);
 #define L(KW, A)                                                                               \
     {                                                                                          \
         auto k = cuckoo_insert_kernel<KW, A>;                                                  \
         const int grid = launch_blocks((const void*)k, kBlock);                                \
         k<<<grid, kBlock, 0, s>>>(t, sc, parity, max_winners,                                  \
-                                  static_cast<typename Keys<KW>::T*>(new_out), new_count);     \
+                                  static_cast<typename Keys<KW>::T*>(new_out), new_count, new_cap); \
     }
     if (kw == 32) {
         if (new_out) L(32, true) else L(32, false)
@@ -283,11 +289,11 @@ cudaError_t cuckoo_lookup(int kw, const DevTable& t, const void* keys, uint64_t 
     if (kw == 32) {
         auto k = cuckoo_probe_kernel<32, false, true>;
         const int grid = launch_blocks((const void*)k, kBlock);
-        k<<<grid, kBlock, 0, s>>>(t, none, 0, keys, nullptr, n, found, vals);
+        k<<<grid, kBlock, 0, s>>>(t, none, 0, keys, nullptr, n, nullptr, 0, found, vals);
     } else {
         auto k = cuckoo_probe_kernel<64, false, true>;
         const int grid = launch_blocks((const void*)k, kBlock);
-        k<<<grid, kBlock, 0, s>>>(t, none, 0, keys, nullptr, n, found, vals);
+        k<<<grid, kBlock, 0, s>>>(t, none, 0, keys, nullptr, n, nullptr, 0, found, vals);
     }
     return cudaGetLastError();
 }

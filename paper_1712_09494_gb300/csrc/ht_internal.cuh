@@ -185,9 +185,11 @@ __device__ __forceinline__ bool find_spill(const DevTable& t, uint64_t key, uint
     return false;
 }
 
-// Warp-aggregated append of `v` (when `pred`) to out[] at *counter.
+// Warp-aggregated append of `v` (when `pred`) to out[] at *counter.  Slots at
+// or past `cap` are not written (the counter still counts them).
 template <typename T>
-__device__ __forceinline__ void warp_append(bool pred, T v, T* out, unsigned long long* counter) {
+__device__ __forceinline__ void warp_append(bool pred, T v, T* out, unsigned long long* counter,
+                                            uint64_t cap = ~0ull) {
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
     if (!mask) return;
     const int lane = threadIdx.x & 31;
@@ -195,7 +197,8 @@ __device__ __forceinline__ void warp_append(bool pred, T v, T* out, unsigned lon
     unsigned long long base = 0;
     if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (pred) out[base + __popc(mask & ((1u << lane) - 1))] = v;
+    const unsigned long long at = base + __popc(mask & ((1u << lane) - 1));
+    if (pred && at < cap) out[at] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -235,18 +238,23 @@ struct BucketCfg {
     int lanes;
 };
 
+// d_n (nullable): the batch size lives on the device; n is then an upper bound.
 cudaError_t bucket_find_or_put(const BucketCfg& c, const DevTable& t, const void* keys,
-                               const uint32_t* vals, uint64_t n, uint8_t* is_new,
-                               void* new_out, unsigned long long* new_count, cudaStream_t s);
+                               const uint32_t* vals, uint64_t n, const unsigned long long* d_n,
+                               uint8_t* is_new, void* new_out, unsigned long long* new_count,
+                               uint64_t new_cap, cudaStream_t s);
 cudaError_t bucket_lookup(const BucketCfg& c, const DevTable& t, const void* keys, uint64_t n,
                           uint32_t* vals, uint8_t* found, cudaStream_t s);
 
+// d_n (nullable): the batch size lives on the device; this launch covers keys
+// [off, off + n) of it.
 cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
-                         const void* keys, const uint32_t* vals, uint64_t n, uint8_t* is_new,
+                         const void* keys, const uint32_t* vals, uint64_t n,
+                         const unsigned long long* d_n, uint64_t off, uint8_t* is_new,
                          cudaStream_t s);
 cudaError_t cuckoo_insert(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
-                          void* new_out, unsigned long long* new_count, uint64_t max_winners,
-                          cudaStream_t s);
+                          void* new_out, unsigned long long* new_count, uint64_t new_cap,
+                          uint64_t max_winners, cudaStream_t s);
 cudaError_t cuckoo_lookup(int kw, const DevTable& t, const void* keys, uint64_t n,
                           uint32_t* vals, uint8_t* found, cudaStream_t s);
 
@@ -257,5 +265,12 @@ cudaError_t compact(int kw, const void* keys, const uint8_t* flags, uint64_t n, 
                     unsigned long long* count, cudaStream_t s);
 cudaError_t probe_random_read(const void* buf, uint64_t bytes, uint32_t gran, uint64_t n_access,
                               uint64_t seed, unsigned long long* sink, cudaStream_t s);
+
+// State-space successors (ht_bfs.cu).  `model` is a device copy of ht_model.
+// count: reservation counter for succ[]; total (nullable): running count of
+// successors generated.
+cudaError_t successors(int kw, const ht_model* model, const void* states, uint64_t n,
+                       const unsigned long long* d_n, uint64_t off, void* succ, uint64_t cap,
+                       unsigned long long* count, unsigned long long* total, cudaStream_t s);
 
 }  // namespace ht

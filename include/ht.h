@@ -230,6 +230,48 @@ ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max
                  ht_bfs_result* result, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched exploration: `count` independent explorations (models of uneven
+ * sizes) advanced together.  Each exploration gets its own bucket-scheme
+ * table of h_capacity[i] slots (h_params: NULL or `count` parameter sets;
+ * key width 32 when the model's vector fits 31 bits, else 64) and a states
+ * array holding its reachable states in level order.  One step expands a
+ * share of every active exploration's current level with three kernels over
+ * all explorations (advance cursors, generate successors, find-or-put and
+ * append); the step is captured once as a CUDA graph and replayed.
+ * Allocates everything at creation (cudaMalloc), frees at destroy.
+ * ------------------------------------------------------------------------- */
+typedef struct ht_multi ht_multi;
+
+ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64_t* h_s0,
+                          const uint64_t* h_capacity, const ht_params* h_params, uint32_t max_levels,
+                          void* stream, ht_multi** out);
+
+/* Empties every table and states array (required before every run but the
+ * first after creation). */
+ht_status ht_multi_reset(ht_multi* m, void* stream);
+
+/* Runs every exploration to completion (or to max_levels / a full states
+ * array).  mode 0: batched, graph-captured steps; mode 1: the same steps as
+ * plain launches; mode 2: one exploration after another with ht_bfs (one
+ * table per launch sequence, the baseline).  max_steps 0 = no limit beyond a
+ * safety bound.  Synchronises once per step. */
+ht_status ht_multi_run(ht_multi* m, int mode, uint64_t max_steps, void* stream);
+
+/* Result of exploration i after a run: non-empty levels, states, successors
+ * generated, complete flag, level sizes (host array of max_levels), the
+ * device pointer of its states array (level order, key-width entries) and,
+ * if h_states is non-NULL, a copy of up to h_states_cap of those states in
+ * host memory (synchronises).  Every output pointer may be NULL. */
+ht_status ht_multi_result(const ht_multi* m, uint32_t i, uint64_t* levels, uint64_t* states,
+                          uint64_t* successors, int32_t* complete, uint64_t* h_level_sizes,
+                          const void** d_states, void* h_states, uint64_t h_states_cap);
+
+/* Steps (graph launches, or levels in mode 2) the last run took. */
+uint64_t ht_multi_steps(const ht_multi* m);
+
+ht_status ht_multi_destroy(ht_multi* m);
+
+/* ---------------------------------------------------------------------------
  * Kernel timing (CUDA events around every launch the library makes, on the
  * launch's stream).  ht_prof_read synchronises on the recorded events.
  * ------------------------------------------------------------------------- */

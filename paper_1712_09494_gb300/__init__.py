@@ -23,6 +23,7 @@ __all__ = [
     "ht_compact", "ht_prof_enable", "ht_prof_reset", "ht_prof_read", "ht_prof_kernels",
     "ht_probe_random_read", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
     "NOALLOC_MAX_BATCH", "scheme_of", "HtModel", "HtBfsResult", "make_model", "ht_successors", "ht_bfs",
+    "MultiExploration",
 ]
 
 NOALLOC_STATE_BYTES = 2048      # HT_NOALLOC_STATE_BYTES
@@ -231,6 +232,64 @@ def ht_bfs(table, model, s0=0, max_levels=4096, states=None, states_cap=0, strea
     _check(load().ht_bfs(table, ctypes.byref(model), int(s0), int(max_levels), sizes,
                          _dptr(states, "states"), cap, ctypes.byref(res), _stream(stream)), "ht_bfs")
     return res, [int(sizes[i]) for i in range(res.levels)]
+
+
+class MultiExploration:
+    """Many explorations advanced together (ht_multi_*)."""
+
+    def __init__(self, models, s0, capacities, params=None, max_levels=4096, stream=None):
+        n = len(models)
+        arr_m = (HtModel * n)(*models)
+        arr_s0 = (ctypes.c_uint64 * n)(*[int(x) for x in s0])
+        arr_c = (ctypes.c_uint64 * n)(*[int(x) for x in capacities])
+        arr_p = None
+        if params is not None:
+            arr_p = (HtParams * n)(*[_params(p, HT_BUCKET) if p is not None else ht_default_params(HT_BUCKET)
+                                    for p in params])
+        out = ctypes.c_void_p()
+        _check(load().ht_multi_create(n, arr_m, arr_s0, arr_c, arr_p, int(max_levels), _stream(stream),
+                                      ctypes.byref(out)), "ht_multi_create")
+        self._h = out
+        self.count = n
+        self.max_levels = int(max_levels)
+        self._keepalive = (arr_m, arr_s0, arr_c, arr_p)
+
+    def reset(self, stream=None):
+        _check(load().ht_multi_reset(self._h, _stream(stream)), "ht_multi_reset")
+
+    def run(self, mode=0, max_steps=0, stream=None):
+        _check(load().ht_multi_run(self._h, int(mode), int(max_steps), _stream(stream)), "ht_multi_run")
+        return int(load().ht_multi_steps(self._h))
+
+    def result(self, i, with_states=False, key_width=64):
+        """Counts and level sizes of exploration i; with_states=True also
+        returns its states (numpy, level order) copied to the host."""
+        import numpy as np
+        lv, st, gen = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        comp = ctypes.c_int32()
+        sizes = (ctypes.c_uint64 * self.max_levels)()
+        ptr = ctypes.c_void_p()
+        _check(load().ht_multi_result(self._h, int(i), ctypes.byref(lv), ctypes.byref(st), ctypes.byref(gen),
+                                      ctypes.byref(comp), sizes, ctypes.byref(ptr), None, 0), "ht_multi_result")
+        out = dict(levels=lv.value, states=st.value, successors=gen.value, complete=comp.value,
+                   level_sizes=[int(sizes[j]) for j in range(lv.value)], states_ptr=ptr.value)
+        if with_states:
+            arr = np.empty(st.value, dtype=np.uint32 if key_width == 32 else np.uint64)
+            _check(load().ht_multi_result(self._h, int(i), None, None, None, None, None, None,
+                                          arr.ctypes.data_as(ctypes.c_void_p), st.value), "ht_multi_result")
+            out["states_host"] = arr
+        return out
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().ht_multi_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------- helper

@@ -438,9 +438,11 @@ ht_status ht_info(const ht_table* t, uint64_t* slots, uint32_t* num_hashes, uint
 // ---------------------------------------------------------------------------
 namespace {
 
+}  // namespace
+
 // Checks the model's fields against the layout documented in ht.h and
 // returns the largest number of successors one state can have (0 = invalid).
-uint64_t model_max_successors(const ht_model* m, uint32_t key_width) {
+uint64_t ht::model_max_successors(const ht_model* m, uint32_t key_width) {
     if (!m || m->num_components < 1 || m->num_components > 16 || m->num_pairs < 0 || m->num_pairs > 8) return 0;
     uint32_t bits = 0;
     for (int c = 0; c < m->num_components; ++c) {
@@ -480,6 +482,13 @@ uint64_t model_max_successors(const ht_model* m, uint32_t key_width) {
     return total ? total : 1;
 }
 
+const DevTable& ht::table_dev(const ht_table* t) { return t->dt; }
+BucketCfg ht::table_bucket_cfg(const ht_table* t) { return bucket_cfg(t); }
+ht_scheme ht::table_scheme(const ht_table* t) { return t->scheme; }
+uint32_t ht::table_key_width(const ht_table* t) { return t->kw; }
+
+namespace {
+
 struct DevBuf {
     void* p = nullptr;
     ~DevBuf() { cudaFree(p); }
@@ -496,9 +505,10 @@ ht_status ht_successors(const ht_model* h_model, uint32_t key_width, const void*
     if (n == 0) return HT_OK;
     const cudaStream_t s = as_stream(stream);
     DevBuf dm;
-    HT_TRY(cudaMalloc(&dm.p, sizeof(ht_model)));
-    HT_TRY(cudaMemcpyAsync(dm.p, h_model, sizeof(ht_model), cudaMemcpyHostToDevice, s));
-    HT_TRY(successors(int(key_width), static_cast<const ht_model*>(dm.p), d_states, n, nullptr, 0, d_succ, cap,
+    const PreparedModel pm = prepare_model(*h_model);
+    HT_TRY(cudaMalloc(&dm.p, sizeof(PreparedModel)));
+    HT_TRY(cudaMemcpyAsync(dm.p, &pm, sizeof(pm), cudaMemcpyHostToDevice, s));
+    HT_TRY(successors(int(key_width), static_cast<const PreparedModel*>(dm.p), d_states, n, nullptr, 0, d_succ, cap,
                       d_count, nullptr, s));
     HT_TRY(cudaStreamSynchronize(s));        // the model copy is freed on return
     return HT_OK;
@@ -523,8 +533,9 @@ ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max
     const uint64_t succ_cap = std::min<uint64_t>(1ull << 26, std::max<uint64_t>(msucc, (t->dt.nslots + 1) * msucc));
     const uint64_t chunk_states = std::max<uint64_t>(1, succ_cap / msucc);
     DevBuf dm, states_own, succ, ctr;
-    HT_TRY(cudaMalloc(&dm.p, sizeof(ht_model)));
-    HT_TRY(cudaMemcpyAsync(dm.p, h_model, sizeof(ht_model), cudaMemcpyHostToDevice, s));
+    const PreparedModel pm = prepare_model(*h_model);
+    HT_TRY(cudaMalloc(&dm.p, sizeof(PreparedModel)));
+    HT_TRY(cudaMemcpyAsync(dm.p, &pm, sizeof(pm), cudaMemcpyHostToDevice, s));
     if (!d_states) {
         HT_TRY(cudaMalloc(&states_own.p, states_cap * ksz));
         d_states = states_own.p;
@@ -569,7 +580,7 @@ ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max
         for (uint64_t c0 = lo; c0 < hi; c0 += chunk_states) {
             const uint64_t m = std::min<uint64_t>(chunk_states, hi - c0);
             HT_TRY(cudaMemsetAsync(c + 1, 0, sizeof(unsigned long long), s));
-            HT_TRY(successors(int(t->kw), static_cast<const ht_model*>(dm.p), states + c0 * ksz, m, nullptr, 0, succ.p,
+            HT_TRY(successors(int(t->kw), static_cast<const PreparedModel*>(dm.p), states + c0 * ksz, m, nullptr, 0, succ.p,
                               succ_cap, c + 1, c + 2, s));
             st = run_put(t, succ.p, nullptr, std::min<uint64_t>(succ_cap, m * msucc), nullptr, d_states, c, s, c + 1,
                          states_cap);

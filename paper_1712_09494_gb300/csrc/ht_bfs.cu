@@ -2,28 +2,18 @@
 // paper: successor state vectors are built by combining the enabled
 // transitions of the processes).  The model's transition tables live in
 // shared memory, read-only, as the paper keeps them in texture memory.
+#include <cstring>
+
 #include "ht_internal.cuh"
 
 namespace ht {
 namespace {
 
-struct SmemModel {
-    uint8_t deg[16][32];
-    uint8_t tgt[16][32][4];
-    uint8_t lab[16][32][4];
-    uint8_t off[16];
-    uint8_t bits[16];
-    uint8_t pc1[8];
-    uint8_t pc2[8];
-    int C;
-    int P;
-};
-
-__device__ __forceinline__ uint32_t local_of(const SmemModel& m, uint64_t s, int c) {
+__device__ __forceinline__ uint32_t local_of(const PreparedModel& m, uint64_t s, int c) {
     return uint32_t(s >> m.off[c]) & ((1u << m.bits[c]) - 1u);
 }
 
-__device__ __forceinline__ uint64_t with_local(const SmemModel& m, uint64_t s, int c, uint32_t v) {
+__device__ __forceinline__ uint64_t with_local(const PreparedModel& m, uint64_t s, int c, uint32_t v) {
     const uint64_t mask = ((1ull << m.bits[c]) - 1ull) << m.off[c];
     return (s & ~mask) | (uint64_t(v) << m.off[c]);
 }
@@ -31,7 +21,7 @@ __device__ __forceinline__ uint64_t with_local(const SmemModel& m, uint64_t s, i
 // Visits every successor of s: local actions of each component, then every
 // combination of the two members' transitions of each synchronising pair.
 template <class F>
-__device__ __forceinline__ void for_each_successor(const SmemModel& m, uint64_t s, F&& emit) {
+__device__ __forceinline__ void for_each_successor(const PreparedModel& m, uint64_t s, F&& emit) {
     for (int c = 0; c < m.C; ++c) {
         const uint32_t u = local_of(m, s, c);
         const int d = m.deg[c][u];
@@ -53,31 +43,15 @@ __device__ __forceinline__ void for_each_successor(const SmemModel& m, uint64_t 
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-successors_kernel(const ht_model* __restrict__ model, const T* __restrict__ states, uint64_t n,
+successors_kernel(const PreparedModel* __restrict__ model, const T* __restrict__ states, uint64_t n,
                   const unsigned long long* __restrict__ d_n, uint64_t off, T* __restrict__ succ,
                   uint64_t cap, unsigned long long* __restrict__ count,
                   unsigned long long* __restrict__ total) {
-    __shared__ SmemModel sm;
+    __shared__ PreparedModel sm;
     {
-        // Copy the tables (16-byte aligned, sizes multiples of 4 bytes).
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(model->deg);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(sm.deg);
-        constexpr int kWords = (sizeof(sm.deg) + sizeof(sm.tgt) + sizeof(sm.lab)) / 4;
-        for (int i = threadIdx.x; i < kWords; i += blockDim.x) dst[i] = src[i];
-        if (threadIdx.x == 0) {
-            sm.C = model->num_components;
-            sm.P = model->num_pairs;
-            int o = 0;
-            for (int c = 0; c < 16; ++c) {
-                sm.bits[c] = model->bits[c];
-                sm.off[c] = uint8_t(o);
-                if (c < sm.C) o += model->bits[c];
-            }
-            for (int p = 0; p < 8; ++p) {
-                sm.pc1[p] = model->pair_c1[p];
-                sm.pc2[p] = model->pair_c2[p];
-            }
-        }
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(model);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&sm);
+        for (int i = threadIdx.x; i < int(sizeof(PreparedModel) / 4); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
     if (d_n) {
@@ -119,9 +93,72 @@ successors_kernel(const ht_model* __restrict__ model, const T* __restrict__ stat
     }
 }
 
+// Multi-table successors: the expanded states of every exploration form one
+// index space [0, work_total); a thread finds its exploration by binary
+// search over the prefix work_off and appends to that exploration's segment
+// of the successor buffer.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) multi_successors_kernel(const MultiDev m, uint64_t max_work) {
+    const uint64_t work = min(uint64_t(__ldcg(m.work_total)), max_work);
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t v = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < work; v += stride) {
+        uint32_t a = 0, b = m.count;                   // largest e with work_off[e] <= v
+        while (b - a > 1) {
+            const uint32_t mid = (a + b) / 2;
+            if (__ldcg(m.work_off + mid) <= v) a = mid; else b = mid;
+        }
+        const uint32_t e = a;
+        const uint64_t idx = __ldcg(m.cur + e) + (v - __ldcg(m.work_off + e));
+        const T* st = static_cast<const T*>(m.states[e]);
+        const uint64_t s = uint64_t(st[idx]);
+        const PreparedModel& pm = m.models[e];
+        uint32_t cnt = 0;
+        for_each_successor(pm, s, [&](uint64_t) { ++cnt; });
+        if (!cnt) continue;
+        uint64_t pos = __ldcg(m.seg_off + e) + atomicAdd(m.seg_cnt + e, (unsigned long long)cnt);
+        const uint64_t end = __ldcg(m.seg_off + e) + __ldcg(m.take + e) * __ldcg(m.msucc + e);
+        for_each_successor(pm, s, [&](uint64_t x) {
+            if (pos < end && pos < m.succ_cap) m.succ[pos] = x;
+            ++pos;
+        });
+        atomicAdd(m.gen + e, (unsigned long long)cnt);
+    }
+}
+
 }  // namespace
 
-cudaError_t successors(int kw, const ht_model* model, const void* states, uint64_t n,
+PreparedModel prepare_model(const ht_model& h) {
+    PreparedModel p;
+    memset(&p, 0, sizeof(p));
+    memcpy(p.deg, h.deg, sizeof(p.deg));
+    memcpy(p.tgt, h.tgt, sizeof(p.tgt));
+    memcpy(p.lab, h.lab, sizeof(p.lab));
+    int o = 0;
+    for (int c = 0; c < 16; ++c) {
+        p.bits[c] = h.bits[c];
+        p.off[c] = uint8_t(o);
+        if (c < h.num_components) o += h.bits[c];
+    }
+    memcpy(p.pc1, h.pair_c1, 8);
+    memcpy(p.pc2, h.pair_c2, 8);
+    p.C = h.num_components;
+    p.P = h.num_pairs;
+    return p;
+}
+
+cudaError_t multi_successors(int kw, const MultiDev& m, uint64_t max_work, cudaStream_t s) {
+    ProfScope ps(kKSuccessors, s);
+    if (kw == 32) {
+        auto k = multi_successors_kernel<uint32_t>;
+        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(m, max_work);
+    } else {
+        auto k = multi_successors_kernel<uint64_t>;
+        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(m, max_work);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t successors(int kw, const PreparedModel* model, const void* states, uint64_t n,
                        const unsigned long long* d_n, uint64_t off, void* succ, uint64_t cap,
                        unsigned long long* count, unsigned long long* total, cudaStream_t s) {
     ProfScope ps(kKSuccessors, s);

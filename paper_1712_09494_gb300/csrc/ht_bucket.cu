@@ -17,6 +17,8 @@
 // finds the bucket full only after the word was written there.  A key goes
 // to bucket f+1 only after bucket f was observed full without it, and
 // fullness is permanent, so lookups may stop at the first non-full bucket.
+#include <algorithm>
+
 #include "ht_internal.cuh"
 
 namespace ht {
@@ -139,13 +141,12 @@ __device__ __noinline__ uint32_t claim_slow(const DevTable t, bool active, uint6
 // slot-index order: the lowest lane of the group holding a free slot (in the
 // group's view) CASes its lowest free slot; a failed CAS marks that slot
 // taken and claim_slow tries the next one.
-template <int KW, int BS, int G, bool VALUES, bool APPEND>
-__global__ void __launch_bounds__(kBlock, HT_BUCKET_MIN_BLOCKS)
-bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_t* __restrict__ vals,
-                  uint64_t n, const unsigned long long* __restrict__ d_n, uint8_t* __restrict__ is_new,
-                  typename Keys<KW>::T* __restrict__ new_out, unsigned long long* __restrict__ new_count,
-                  uint64_t new_cap) {
-    if (d_n) n = min(n, uint64_t(__ldcg(d_n)));        // batch size produced on the device
+// One warp serves one tile of up to 32 keys: lane l holds key l (myok false
+// on lanes without a valid key).  Returns 1 on the lanes whose key this call
+// stored.  Used by the plain find-or-put kernel and by the multi-table BFS
+// step, which passes a different table per tile.
+template <int KW, int BS, int G>
+__device__ __forceinline__ uint32_t bucket_tile(const DevTable& t, uint64_t mykey, uint32_t myval, bool myok) {
     using K = Keys<KW>;
     constexpr int SPL = BS / G;
     constexpr int GPW = 32 / G;
@@ -155,6 +156,103 @@ bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_
     static_assert(SPL >= 1 && SPL <= 8 && BS % G == 0 && G % PF == 0 && PF * SPL <= 32, "bucket/lane split");
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G, gbase = grp * G;
+    const uint64_t mybkt = hidx(mykey, t.seed[0], t.nbuckets);
+    const uint64_t myword = K::word(mykey, myval);
+    uint32_t res_all = 0;            // bit r: the group's key of round r was stored
+#pragma unroll 1
+    for (int r0 = 0; r0 < G; r0 += PF) {
+        // Read the first bucket of PF rounds.
+        uint64_t w[PF][SPL];
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            const int kidx = (r0 + q) * GPW + grp;
+            const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
+            if (__shfl_sync(kFull, myok, kidx)) {
+                load_lane<SPL>(t.slots + b * BS + sub * SPL, w[q]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < SPL; ++j) w[q][j] = kEmpty;
+            }
+        }
+        // Decide each round from its read: found, claim, or slow path.
+        uint32_t le_pack = 0, claim = 0, slow = 0, valid = 0;
+        uint64_t owner_pack = 0;
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            const int kidx = (r0 + q) * GPW + grp;
+            const uint64_t key = __shfl_sync(kFull, mykey, kidx);
+            const bool ok = __shfl_sync(kFull, myok, kidx);
+            uint32_t lm, le;
+            scan_lane<KW, SPL>(w[q], key, lm, le);
+            const uint32_t M = (__ballot_sync(kFull, ok && lm != 0) >> gbase) & kGMask;
+            const uint32_t E = (__ballot_sync(kFull, ok && le != 0) >> gbase) & kGMask;
+            le_pack |= le << (q * SPL);
+            valid |= uint32_t(ok) << q;
+            if (ok && !M) {
+                if (E) {
+                    claim |= 1u << q;
+                    owner_pack |= uint64_t(__ffs(E) - 1) << (5 * q);
+                } else {
+                    slow |= 1u << q;
+                }
+            }
+        }
+        // Issue every round's first CAS, then read the results.
+        uint64_t old[PF];
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            const int kidx = (r0 + q) * GPW + grp;
+            const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
+            const uint64_t word = __shfl_sync(kFull, myword, kidx);
+            old[q] = kEmpty;
+            if (((claim >> q) & 1u) && sub == int((owner_pack >> (5 * q)) & 31u)) {
+                const int j = __ffs((le_pack >> (q * SPL)) & kLMask) - 1;
+                old[q] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + b * BS + sub * SPL + j),
+                                   kEmpty, word);
+                le_pack &= ~(1u << (q * SPL + j));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            const int kidx = (r0 + q) * GPW + grp;
+            const uint64_t key = __shfl_sync(kFull, mykey, kidx);
+            const uint32_t code = old[q] == kEmpty ? 0u : (K::keyof(old[q]) == key ? 1u : 2u);
+            const int src = gbase + int((owner_pack >> (5 * q)) & 31u);
+            const uint32_t c = __shfl_sync(kFull, code, src);
+            if ((claim >> q) & 1u) {
+                if (c == 0u) res_all |= 1u << (r0 + q);
+                else if (c == 2u) slow |= 1u << q;
+            }
+        }
+        // Rare: claims that lost to another key, and full first buckets.
+        if (__any_sync(kFull, slow != 0)) {
+#pragma unroll 1
+            for (int q = 0; q < PF; ++q) {
+                if (!__any_sync(kFull, (slow >> q) & 1u)) continue;
+                const int kidx = (r0 + q) * GPW + grp;
+                const uint64_t key = __shfl_sync(kFull, mykey, kidx);
+                const uint64_t word = __shfl_sync(kFull, myword, kidx);
+                const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
+                const uint32_t r = claim_slow<KW, BS, G>(t, (slow >> q) & 1u, key, word, b,
+                                                         (le_pack >> (q * SPL)) & kLMask, sub, gbase, lane);
+                if (r) res_all |= 1u << (r0 + q);
+            }
+        }
+        (void)valid;
+    }
+    // Lane l's key was served by group l % GPW in round l / GPW.
+    return (__shfl_sync(kFull, res_all, (lane % GPW) * G) >> (lane / GPW)) & 1u;
+}
+
+template <int KW, int BS, int G, bool VALUES, bool APPEND>
+__global__ void __launch_bounds__(kBlock, HT_BUCKET_MIN_BLOCKS)
+bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_t* __restrict__ vals,
+                  uint64_t n, const unsigned long long* __restrict__ d_n, uint8_t* __restrict__ is_new,
+                  typename Keys<KW>::T* __restrict__ new_out, unsigned long long* __restrict__ new_count,
+                  uint64_t new_cap) {
+    if (d_n) n = min(n, uint64_t(__ldcg(d_n)));        // batch size produced on the device
+    using K = Keys<KW>;
+    const int lane = threadIdx.x & 31;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
     unsigned long long stored = 0;
 
@@ -169,92 +267,7 @@ bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_
         }
         const bool myok = mine && !K::reserved(mykey);
         if (mine && !myok) set_flag(t.ctr, kFlagInvalidKey);
-        const uint64_t mybkt = hidx(mykey, t.seed[0], t.nbuckets);
-        const uint64_t myword = K::word(mykey, myval);
-        uint32_t res_all = 0;            // bit r: the group's key of round r was stored
-#pragma unroll 1
-        for (int r0 = 0; r0 < G; r0 += PF) {
-            // Read the first bucket of PF rounds.
-            uint64_t w[PF][SPL];
-#pragma unroll
-            for (int q = 0; q < PF; ++q) {
-                const int kidx = (r0 + q) * GPW + grp;
-                const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
-                if (__shfl_sync(kFull, myok, kidx)) {
-                    load_lane<SPL>(t.slots + b * BS + sub * SPL, w[q]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < SPL; ++j) w[q][j] = kEmpty;
-                }
-            }
-            // Decide each round from its read: found, claim, or slow path.
-            uint32_t le_pack = 0, claim = 0, slow = 0, valid = 0;
-            uint64_t owner_pack = 0;
-#pragma unroll
-            for (int q = 0; q < PF; ++q) {
-                const int kidx = (r0 + q) * GPW + grp;
-                const uint64_t key = __shfl_sync(kFull, mykey, kidx);
-                const bool ok = __shfl_sync(kFull, myok, kidx);
-                uint32_t lm, le;
-                scan_lane<KW, SPL>(w[q], key, lm, le);
-                const uint32_t M = (__ballot_sync(kFull, ok && lm != 0) >> gbase) & kGMask;
-                const uint32_t E = (__ballot_sync(kFull, ok && le != 0) >> gbase) & kGMask;
-                le_pack |= le << (q * SPL);
-                valid |= uint32_t(ok) << q;
-                if (ok && !M) {
-                    if (E) {
-                        claim |= 1u << q;
-                        owner_pack |= uint64_t(__ffs(E) - 1) << (5 * q);
-                    } else {
-                        slow |= 1u << q;
-                    }
-                }
-            }
-            // Issue every round's first CAS, then read the results.
-            uint64_t old[PF];
-#pragma unroll
-            for (int q = 0; q < PF; ++q) {
-                const int kidx = (r0 + q) * GPW + grp;
-                const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
-                const uint64_t word = __shfl_sync(kFull, myword, kidx);
-                old[q] = kEmpty;
-                if (((claim >> q) & 1u) && sub == int((owner_pack >> (5 * q)) & 31u)) {
-                    const int j = __ffs((le_pack >> (q * SPL)) & kLMask) - 1;
-                    old[q] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + b * BS + sub * SPL + j),
-                                       kEmpty, word);
-                    le_pack &= ~(1u << (q * SPL + j));
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < PF; ++q) {
-                const int kidx = (r0 + q) * GPW + grp;
-                const uint64_t key = __shfl_sync(kFull, mykey, kidx);
-                const uint32_t code = old[q] == kEmpty ? 0u : (K::keyof(old[q]) == key ? 1u : 2u);
-                const int src = gbase + int((owner_pack >> (5 * q)) & 31u);
-                const uint32_t c = __shfl_sync(kFull, code, src);
-                if ((claim >> q) & 1u) {
-                    if (c == 0u) res_all |= 1u << (r0 + q);
-                    else if (c == 2u) slow |= 1u << q;
-                }
-            }
-            // Rare: claims that lost to another key, and full first buckets.
-            if (__any_sync(kFull, slow != 0)) {
-#pragma unroll 1
-                for (int q = 0; q < PF; ++q) {
-                    if (!__any_sync(kFull, (slow >> q) & 1u)) continue;
-                    const int kidx = (r0 + q) * GPW + grp;
-                    const uint64_t key = __shfl_sync(kFull, mykey, kidx);
-                    const uint64_t word = __shfl_sync(kFull, myword, kidx);
-                    const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
-                    const uint32_t r = claim_slow<KW, BS, G>(t, (slow >> q) & 1u, key, word, b,
-                                                             (le_pack >> (q * SPL)) & kLMask, sub, gbase, lane);
-                    if (r) res_all |= 1u << (r0 + q);
-                }
-            }
-            (void)valid;
-        }
-        // Lane l's key was served by group l % GPW in round l / GPW.
-        const uint32_t my_new = (__shfl_sync(kFull, res_all, (lane % GPW) * G) >> (lane / GPW)) & 1u;
+        const uint32_t my_new = bucket_tile<KW, BS, G>(t, mykey, myval, myok);
         if (mine && is_new) is_new[base + lane] = uint8_t(my_new);
         if (APPEND) warp_append<typename K::T>(mine && my_new, typename K::T(mykey), new_out, new_count, new_cap);
         stored += __popc(__ballot_sync(kFull, my_new != 0));
@@ -400,6 +413,82 @@ cudaError_t launch_lookup(const DevTable& t, const void* keys, uint64_t n, uint3
     return cudaGetLastError();
 }
 
+// Multi-table find-or-put: warp w takes tile w of the step's successor
+// segments (segment e starts at seg_off[e], a multiple of 32), runs it
+// against exploration e's table and appends the new states to its states.
+template <int KW, int BS, int G>
+__global__ void __launch_bounds__(kBlock, HT_BUCKET_MIN_BLOCKS)
+multi_bucket_fop_kernel(const MultiDev m, uint64_t max_tiles) {
+    using K = Keys<KW>;
+    using T = typename K::T;
+    const uint64_t tiles = min(uint64_t(__ldcg(m.tiles_total)), max_tiles);
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t tile = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; tile < tiles; tile += nwarps) {
+        uint32_t a = 0, b = m.count;                   // largest e with seg_off[e] <= 32 * tile
+        while (b - a > 1) {
+            const uint32_t mid = (a + b) / 2;
+            if (__ldcg(m.seg_off + mid) <= tile * 32) a = mid; else b = mid;
+        }
+        const uint32_t e = a;
+        const uint64_t base = __ldcg(m.seg_off + e);
+        const uint64_t cnt = min(uint64_t(__ldcg(m.seg_cnt + e)), uint64_t(__ldcg(m.take + e)) * uint64_t(__ldcg(m.msucc + e)));
+        const uint64_t i = tile * 32 - base + lane;
+        const bool mine = i < cnt;
+        if (!__any_sync(kFull, mine)) continue;
+        const uint64_t key = mine ? __ldcg(reinterpret_cast<const unsigned long long*>(m.succ + base + i)) : 0;
+        const bool ok = mine && !K::reserved(key);
+        const DevTable& t = m.tables[e];
+        const uint32_t my_new = bucket_tile<KW, BS, G>(t, key, 0, ok);
+        warp_append<T>(mine && my_new, T(key), static_cast<T*>(m.states[e]), m.total + e, m.states_cap[e]);
+        const unsigned nm = __ballot_sync(kFull, my_new != 0);
+        if (lane == 0 && nm) atomicAdd(&t.ctr->size, (unsigned long long)__popc(nm));
+    }
+}
+
+// One warp per exploration: level 0 is the initial state.
+template <int KW, int BS, int G>
+__global__ void __launch_bounds__(kBlock) multi_bucket_init_kernel(const MultiDev m) {
+    using K = Keys<KW>;
+    using T = typename K::T;
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t e = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; e < m.count; e += nwarps) {
+        const uint64_t key = m.s0[e];
+        const bool ok = lane == 0 && !K::reserved(key);
+        const DevTable& t = m.tables[e];
+        const uint32_t my_new = bucket_tile<KW, BS, G>(t, key, 0, ok);
+        warp_append<T>(ok && my_new, T(key), static_cast<T*>(m.states[e]), m.total + e, m.states_cap[e]);
+        __syncwarp();
+        if (lane == 0) {
+            if (my_new) atomicAdd(&t.ctr->size, 1ull);
+            const unsigned long long n0 = __ldcg(m.total + e);
+            m.lo[e] = 0;
+            m.hi[e] = n0;
+            m.cur[e] = 0;
+            m.take[e] = 0;
+            m.gen[e] = 0;
+            m.level[e] = 0;
+            m.done[e] = n0 ? 0u : 1u;
+            if (n0) m.level_sizes[e * m.max_levels] = n0;
+        }
+    }
+}
+
+template <int KW, int BS, int G>
+cudaError_t launch_multi(const MultiDev& m, uint64_t max_tiles, bool init, cudaStream_t s) {
+    if (init) {
+        auto k = multi_bucket_init_kernel<KW, BS, G>;
+        const int grid = int(std::min<uint64_t>(launch_blocks((const void*)k, kBlock), (m.count + 7) / 8));
+        k<<<grid, kBlock, 0, s>>>(m);
+    } else {
+        ProfScope ps(kKBucketFop, s);
+        auto k = multi_bucket_fop_kernel<KW, BS, G>;
+        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(m, max_tiles);
+    }
+    return cudaGetLastError();
+}
+
 // (bucket_slots, lanes) pairs that are instantiated.
 #define HT_BUCKET_CONFIGS(X) \
     X(8, 2) X(8, 4) X(8, 8) X(16, 2) X(16, 4) X(16, 8) X(16, 16) X(32, 4) X(32, 8) X(32, 16) X(32, 32)
@@ -414,6 +503,26 @@ cudaError_t bucket_find_or_put(const BucketCfg& c, const DevTable& t, const void
     if (c.bucket_slots == BS && c.lanes == G)                                                     \
         return c.kw == 32 ? launch_fop<32, BS, G>(t, keys, vals, n, d_n, is_new, new_out, new_count, new_cap, s) \
                           : launch_fop<64, BS, G>(t, keys, vals, n, d_n, is_new, new_out, new_count, new_cap, s);
+    HT_BUCKET_CONFIGS(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t multi_bucket_find_or_put(const BucketCfg& c, const MultiDev& m, uint64_t max_tiles, cudaStream_t s) {
+#define X(BS, G)                                                                       \
+    if (c.bucket_slots == BS && c.lanes == G)                                          \
+        return c.kw == 32 ? launch_multi<32, BS, G>(m, max_tiles, false, s)            \
+                          : launch_multi<64, BS, G>(m, max_tiles, false, s);
+    HT_BUCKET_CONFIGS(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t multi_bucket_init(const BucketCfg& c, const MultiDev& m, cudaStream_t s) {
+#define X(BS, G)                                                                       \
+    if (c.bucket_slots == BS && c.lanes == G)                                          \
+        return c.kw == 32 ? launch_multi<32, BS, G>(m, 0, true, s)                     \
+                          : launch_multi<64, BS, G>(m, 0, true, s);
     HT_BUCKET_CONFIGS(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -128,6 +128,8 @@ const char* kNames[kKNumKernels] = {
 ProfScope::ProfScope(uint32_t id, cudaStream_t s) : id_(id), s_(s), slot_(-1) {
     Prof& p = prof();
     if (!p.on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> g(p.mu);
     ProfRec r;
     r.id = id;

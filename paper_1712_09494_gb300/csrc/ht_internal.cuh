@@ -266,11 +266,76 @@ cudaError_t compact(int kw, const void* keys, const uint8_t* flags, uint64_t n, 
 cudaError_t probe_random_read(const void* buf, uint64_t bytes, uint32_t gran, uint64_t n_access,
                               uint64_t seed, unsigned long long* sink, cudaStream_t s);
 
+// A model with its bit offsets precomputed (device copy; the single-table
+// successor kernel stages it in shared memory).
+struct PreparedModel {
+    uint8_t deg[16][32];
+    uint8_t tgt[16][32][4];
+    uint8_t lab[16][32][4];
+    uint8_t off[16];
+    uint8_t bits[16];
+    uint8_t pc1[8];
+    uint8_t pc2[8];
+    int C;
+    int P;
+};
+
+PreparedModel prepare_model(const ht_model& m);
+// Largest number of successors of one state, or 0 for a malformed model.
+uint64_t model_max_successors(const ht_model* m, uint32_t key_width);
+
+// Read-only views of a table for the batched form (ht_api.cu).
+const DevTable& table_dev(const ht_table* t);
+BucketCfg table_bucket_cfg(const ht_table* t);
+ht_scheme table_scheme(const ht_table* t);
+uint32_t table_key_width(const ht_table* t);
+
 // State-space successors (ht_bfs.cu).  `model` is a device copy of ht_model.
 // count: reservation counter for succ[]; total (nullable): running count of
 // successors generated.
-cudaError_t successors(int kw, const ht_model* model, const void* states, uint64_t n,
+cudaError_t successors(int kw, const PreparedModel* model, const void* states, uint64_t n,
                        const unsigned long long* d_n, uint64_t off, void* succ, uint64_t cap,
                        unsigned long long* count, unsigned long long* total, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Batched exploration of many models at once (ht_multi.cu).  One step
+// processes a slice of every exploration's current BFS level.
+// ---------------------------------------------------------------------------
+struct MultiDev {
+    uint32_t count;                  // explorations in this group
+    uint32_t max_levels;
+    const DevTable* tables;          // [count]
+    const PreparedModel* models;     // [count]
+    void* const* states;             // [count] key-width vectors, level order
+    const unsigned long long* states_cap;  // [count]
+    const unsigned long long* msucc;       // [count] successors per state bound
+    unsigned long long* total;       // [count] states stored (append counters)
+    unsigned long long* lo;          // [count] start of the current level
+    unsigned long long* hi;          // [count] end of the current level
+    unsigned long long* cur;         // [count] next frontier state to expand
+    unsigned long long* take;        // [count] states expanded this step
+    unsigned long long* work_off;    // [count] prefix of take (states)
+    unsigned long long* seg_off;     // [count] start of the successor segment
+    unsigned long long* seg_cnt;     // [count] successors written this step
+    unsigned long long* gen;         // [count] successors generated in total
+    unsigned int* level;             // [count] current level number
+    unsigned int* done;              // [count] 1 = finished (2 = hit a limit)
+    unsigned long long* level_sizes; // [count * max_levels]
+    unsigned long long* work_total;  // [1] states expanded this step, all explorations
+    unsigned long long* tiles_total; // [1] 32-key tiles of successors this step
+    unsigned int* active;            // [1] explorations not finished
+    uint64_t* succ;                  // successor buffer (64-bit words)
+    uint64_t succ_cap;
+    const unsigned long long* s0;    // [count] initial states
+};
+
+// budget: successors the step may generate (the buffer holds budget + slack).
+cudaError_t multi_advance(const MultiDev& m, uint64_t budget, cudaStream_t s);
+cudaError_t multi_successors(int kw, const MultiDev& m, uint64_t max_work, cudaStream_t s);
+// Tiles of 32 successors, each against its own exploration's table; new
+// states are appended to that exploration's states.
+cudaError_t multi_bucket_find_or_put(const BucketCfg& c, const MultiDev& m, uint64_t max_tiles, cudaStream_t s);
+// Stores every exploration's initial state (level 0) and resets its cursors.
+cudaError_t multi_bucket_init(const BucketCfg& c, const MultiDev& m, cudaStream_t s);
 
 }  // namespace ht

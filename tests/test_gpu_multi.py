@@ -1,0 +1,102 @@
+"""Parity of the batched exploration form with the oracle, in all three modes.
+
+Each exploration's BFS levels must equal the oracle's levels as sets, whether
+the explorations run together (graph-captured or plainly launched steps) or
+one after another.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1712_09494_gb300 as ht
+from workloads import statespace as ss
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1712_09494_gb300 import _build
+    _build.build()
+    assert torch.cuda.is_available()
+    ht.load()
+
+
+def hmodel(m):
+    return ht.make_model(m.C, m.bits, m.deg, m.tgt, m.lab, m.pairs)
+
+
+def _run_and_check(oracle_lib, models, params=None, modes=(0, 1, 2)):
+    refs = [oracle_lib.bfs(m, max_states=1 << 22) for m in models]
+    caps = [max(256, int(r.total / 0.7)) for r in refs]
+    mx = ht.MultiExploration([hmodel(m) for m in models], [0] * len(models), caps, params=params)
+    for mode in modes:
+        mx.reset()
+        steps = mx.run(mode=mode)
+        assert steps >= 1
+        for i, (m, r) in enumerate(zip(models, refs)):
+            res = mx.result(i, with_states=True, key_width=m.key_width)
+            assert res["complete"] == 1, (mode, i)
+            assert res["states"] == r.total, (mode, i)
+            assert res["successors"] == int(r.level_succ.sum()), (mode, i)
+            np.testing.assert_array_equal(res["level_sizes"], r.level_sizes)
+            got = res["states_host"].astype(np.uint64)
+            off = 0
+            for d, n_d in enumerate(res["level_sizes"]):
+                np.testing.assert_array_equal(np.sort(got[off:off + n_d]), np.sort(r.level(d)))
+                off += n_d
+    mx.close()
+
+
+def test_multi_matches_oracle(oracle_lib):
+    models = ss.batched_models(24, seed=7)
+    _run_and_check(oracle_lib, models)
+
+
+def test_multi_mixed_key_widths_and_shapes(oracle_lib):
+    small = [ss.random_model(s, C=4, L=8, R=[3, 5, 4, 2], p_sync=0.3, P=2) for s in range(6)]     # 12-bit vectors
+    wide = [ss.random_model(100 + s, C=9, L=32, R=3, p_sync=0.2, P=3) for s in range(5)]        # 45-bit vectors
+    models = small + wide
+    assert {m.key_width for m in models} == {32, 64}
+    shapes = [dict(bucket_slots=16, lanes_per_key=2), dict(bucket_slots=8, lanes_per_key=4),
+              dict(bucket_slots=32, lanes_per_key=8)]
+    params = [shapes[i % 3] for i in range(len(models))]
+    _run_and_check(oracle_lib, models, params=params, modes=(0, 2))
+
+
+def test_multi_uneven_sizes_share_the_successor_budget(oracle_lib):
+    # One large exploration next to many tiny ones: the large one needs several
+    # steps per level while the tiny ones finish early.
+    big = ss.random_model(55, C=10, L=16, R=[4, 4, 4, 4, 4, 3, 3, 3, 3, 4], p_sync=0.1, P=2)
+    tiny = [ss.random_model(60 + s, C=2, L=4, R=[2, 3], P=0) for s in range(20)]
+    _run_and_check(oracle_lib, [big] + tiny, modes=(0,))
+
+
+def test_multi_full_batched_workload_against_stored_levels():
+    path = os.path.join(GOLDEN, "statespace_batched.json")
+    if not os.path.exists(path):
+        pytest.skip("stored batched levels not generated")
+    import sys
+    sys.path.insert(0, GOLDEN)
+    from digest import digest
+    gold = json.load(open(path))
+    models = ss.batched_models(gold["model"]["count"], seed=gold["model"]["seed"])
+    caps = [max(256, int(g["states"] / 0.7)) for g in gold["explorations"]]
+    mx = ht.MultiExploration([hmodel(m) for m in models], [0] * len(models), caps)
+    mx.run(mode=0)
+    for i, (m, g) in enumerate(zip(models, gold["explorations"])):
+        res = mx.result(i, with_states=True, key_width=m.key_width)
+        assert res["complete"] == 1 and res["states"] == g["states"], i
+        assert res["successors"] == g["successors"], i
+        got = res["states_host"].astype(np.uint64)
+        off = 0
+        for d, lev in enumerate(g["levels"]):
+            n_d = lev[0]
+            assert res["level_sizes"][d] == n_d
+            assert digest(got[off:off + n_d])[1:] == lev[1:3], (i, d)
+            off += n_d
+    mx.close()

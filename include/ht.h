@@ -272,6 +272,68 @@ uint64_t ht_multi_steps(const ht_multi* m);
 ht_status ht_multi_destroy(ht_multi* m);
 
 /* ---------------------------------------------------------------------------
+ * Serving: a request loop over many device-resident tables (64-bit keys).
+ * A worker thread inside the library forms batches continuously: whenever
+ * one of `max_inflight` batch slots is free it takes the oldest pending
+ * request of every admitted table that has no request in flight, packs them
+ * into one staging buffer and issues copy-in, one packed find-or-put launch
+ * for all bucket-scheme tables of the batch (Cuckoo tables get their own
+ * launches) and copy-out on the slot's stream.  A table's requests complete
+ * in submission order, so each result equals what the request gets when the
+ * requests of its table are run alone in that order.  Tables are admitted
+ * when free device memory (cudaMemGetInfo, or fake_free_bytes for tests)
+ * covers them plus hbm_reserve_bytes; requests for a table wait until it is
+ * admitted.  The paper has no serving layer; it only states the problem
+ * (Section 5: find-or-insert of a stream of elements).
+ * ------------------------------------------------------------------------- */
+typedef struct ht_server ht_server;
+
+typedef struct ht_server_config {
+    uint32_t max_inflight;            /* batch slots (streams), default 4, max 64 */
+    uint32_t max_requests_per_batch;  /* default 4096 */
+    uint64_t batch_key_budget;        /* keys per batch, also the largest request; default 2^22 */
+    uint64_t hbm_reserve_bytes;       /* device memory kept free, default 1 GiB */
+    uint64_t fake_free_bytes;         /* tests: free memory to assume (0 = ask the driver) */
+    int32_t pack;                     /* 1 (default): many tables per batch; 0: one request per batch */
+    int32_t reserved_[3];
+    ht_params table_params;           /* parameters of the bucket-scheme tables */
+} ht_server_config;
+
+typedef struct ht_server_stats {
+    uint64_t requests;                /* completed since creation or the last reset */
+    uint64_t keys;
+    uint64_t batches;
+    double seconds;                   /* wall time of the same period */
+    double p50_us, p99_us, mean_us, max_us;   /* submit-to-result latency */
+    uint64_t admitted_bytes;
+    uint32_t tables_admitted;
+    int32_t status;                   /* HT_OK, or the first error the worker met */
+} ht_server_stats;
+
+ht_status ht_server_default_config(ht_server_config* cfg);
+/* Starts the worker on the current device; allocates the batch slots. */
+ht_status ht_server_create(const ht_server_config* cfg, ht_server** out);
+/* Stops the worker (in-flight batches complete) and frees every table. */
+ht_status ht_server_destroy(ht_server* s);
+/* Registers a table of `capacity` slots; it is created once admitted. */
+ht_status ht_server_open_table(ht_server* s, uint64_t capacity, ht_scheme scheme, uint32_t* table_id);
+/* Frees the table after its pending requests complete. */
+ht_status ht_server_close_table(ht_server* s, uint32_t table_id);
+/* admitted: 1 admitted, 0 waiting, -1 closed; size: stored keys (0 while busy). */
+ht_status ht_server_table_state(ht_server* s, uint32_t table_id, int32_t* admitted, uint64_t* size);
+/* Queues a find-or-put of n keys (host memory, valid until the request
+ * completes); h_is_new (nullable, n bytes, host) receives the flags.
+ * HT_ERR_INVALID if n exceeds batch_key_budget or the table is closing. */
+ht_status ht_server_submit(ht_server* s, uint32_t table_id, const uint64_t* h_keys, uint64_t n,
+                           uint8_t* h_is_new, uint64_t* request_id);
+/* Waits up to timeout_ms for a request; HT_ERR_TIMEOUT if it is not done
+ * (it stays queued and can be waited for again).  On completion returns the
+ * request's status and forgets it. */
+ht_status ht_server_wait(ht_server* s, uint64_t request_id, uint32_t timeout_ms, double* latency_us);
+/* Counters and latency percentiles; reset != 0 starts a new period. */
+ht_status ht_server_get_stats(ht_server* s, ht_server_stats* out, int reset);
+
+/* ---------------------------------------------------------------------------
  * Kernel timing (CUDA events around every launch the library makes, on the
  * launch's stream).  ht_prof_read synchronises on the recorded events.
  * ------------------------------------------------------------------------- */

@@ -14,7 +14,8 @@ import ctypes
 
 import torch
 
-from ._lib import HT_BUCKET, HT_CUCKOO, HtBfsResult, HtError, HtModel, HtParams, load
+from ._lib import (HT_BUCKET, HT_CUCKOO, HtBfsResult, HtError, HtModel, HtParams, HtServerConfig,
+                   HtServerStats, load)
 
 __all__ = [
     "HT_BUCKET", "HT_CUCKOO", "HtError", "HtParams", "HashTable", "load",
@@ -23,7 +24,7 @@ __all__ = [
     "ht_compact", "ht_prof_enable", "ht_prof_reset", "ht_prof_read", "ht_prof_kernels",
     "ht_probe_random_read", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
     "NOALLOC_MAX_BATCH", "scheme_of", "HtModel", "HtBfsResult", "make_model", "ht_successors", "ht_bfs",
-    "MultiExploration",
+    "MultiExploration", "Server", "HtServerConfig", "HtServerStats",
 ]
 
 NOALLOC_STATE_BYTES = 2048      # HT_NOALLOC_STATE_BYTES
@@ -284,6 +285,77 @@ class MultiExploration:
         if self._h is not None and self._h.value:
             load().ht_multi_destroy(self._h)
         self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The serving loop (ht_server_*): keys are uint64 numpy arrays in host memory."""
+
+    def __init__(self, **cfg):
+        c = HtServerConfig()
+        _check(load().ht_server_default_config(ctypes.byref(c)), "ht_server_default_config")
+        for k, v in cfg.items():
+            if k == "table_params":
+                c.table_params = _params(v, HT_BUCKET)
+            else:
+                setattr(c, k, v)
+        out = ctypes.c_void_p()
+        _check(load().ht_server_create(ctypes.byref(c), ctypes.byref(out)), "ht_server_create")
+        self._h = out
+        self._live = {}
+
+    def open_table(self, capacity, scheme="bucket"):
+        tid = ctypes.c_uint32()
+        _check(load().ht_server_open_table(self._h, int(capacity), scheme_of(scheme), ctypes.byref(tid)),
+               "ht_server_open_table")
+        return tid.value
+
+    def close_table(self, table_id):
+        _check(load().ht_server_close_table(self._h, int(table_id)), "ht_server_close_table")
+
+    def table_state(self, table_id):
+        adm, size = ctypes.c_int32(), ctypes.c_uint64()
+        _check(load().ht_server_table_state(self._h, int(table_id), ctypes.byref(adm), ctypes.byref(size)),
+               "ht_server_table_state")
+        return adm.value, size.value
+
+    def submit(self, table_id, keys, out=None):
+        """Queues a find-or-put; `keys` (uint64) and `out` (uint8) must stay alive
+        until the request is waited for (the server holds references)."""
+        import numpy as np
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        if out is None:
+            out = np.empty(len(keys), dtype=np.uint8)
+        rid = ctypes.c_uint64()
+        _check(load().ht_server_submit(self._h, int(table_id), keys.ctypes.data_as(ctypes.c_void_p), len(keys),
+                                       out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rid)), "ht_server_submit")
+        self._live[rid.value] = (keys, out)
+        return rid.value
+
+    def wait(self, request_id, timeout_ms=60000):
+        """Returns (status, latency_us, flags); status 5 (HT_ERR_TIMEOUT) keeps it queued."""
+        lat = ctypes.c_double()
+        st = load().ht_server_wait(self._h, int(request_id), int(timeout_ms), ctypes.byref(lat))
+        if st == 5:
+            return st, None, None
+        keys, out = self._live.pop(request_id, (None, None))
+        return st, lat.value, out
+
+    def stats(self, reset=False):
+        s = HtServerStats()
+        _check(load().ht_server_get_stats(self._h, ctypes.byref(s), 1 if reset else 0), "ht_server_get_stats")
+        return {f: getattr(s, f) for f, _ in HtServerStats._fields_}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().ht_server_destroy(self._h)
+        self._h = None
+        self._live.clear()
 
     def __del__(self):
         try:

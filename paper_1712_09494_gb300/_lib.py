@@ -36,6 +36,24 @@ class HtBfsResult(ctypes.Structure):
                 ("reserved_", ctypes.c_int32)]
 
 
+class HtServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("max_inflight", ctypes.c_uint32), ("max_requests_per_batch", ctypes.c_uint32),
+        ("batch_key_budget", ctypes.c_uint64), ("hbm_reserve_bytes", ctypes.c_uint64),
+        ("fake_free_bytes", ctypes.c_uint64), ("pack", ctypes.c_int32), ("reserved_", ctypes.c_int32 * 3),
+        ("table_params", HtParams),
+    ]
+
+
+class HtServerStats(ctypes.Structure):
+    _fields_ = [
+        ("requests", ctypes.c_uint64), ("keys", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+        ("seconds", ctypes.c_double), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+        ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double), ("admitted_bytes", ctypes.c_uint64),
+        ("tables_admitted", ctypes.c_uint32), ("status", ctypes.c_int32),
+    ]
+
+
 class HtError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -77,6 +95,15 @@ SIGNATURES = {
                                _U64]),
     "ht_multi_steps": (_U64, [_VP]),
     "ht_multi_destroy": (_I32, [_VP]),
+    "ht_server_default_config": (_I32, [_P(HtServerConfig)]),
+    "ht_server_create": (_I32, [_P(HtServerConfig), _P(_VP)]),
+    "ht_server_destroy": (_I32, [_VP]),
+    "ht_server_open_table": (_I32, [_VP, _U64, _I32, _P(_U32)]),
+    "ht_server_close_table": (_I32, [_VP, _U32]),
+    "ht_server_table_state": (_I32, [_VP, _U32, _P(ctypes.c_int32), _P(_U64)]),
+    "ht_server_submit": (_I32, [_VP, _U32, _VP, _U64, _VP, _P(_U64)]),
+    "ht_server_wait": (_I32, [_VP, _U64, _U32, _P(ctypes.c_double)]),
+    "ht_server_get_stats": (_I32, [_VP, _P(HtServerStats), ctypes.c_int]),
 }
 
 _lib = None

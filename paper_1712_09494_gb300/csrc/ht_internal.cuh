@@ -338,4 +338,19 @@ cudaError_t multi_bucket_find_or_put(const BucketCfg& c, const MultiDev& m, uint
 // Stores every exploration's initial state (level 0) and resets its cursors.
 cudaError_t multi_bucket_init(const BucketCfg& c, const MultiDev& m, cudaStream_t s);
 
+// One packed serving batch: request r's n keys sit at keys[key_off, +n) and
+// its tiles of 32 keys start at tile index tile_off (ht_server.cu).
+struct ServeDesc {
+    uint64_t key_off;
+    uint64_t n;
+    uint64_t tile_off;
+    uint32_t table;
+    uint32_t pad_;
+};
+// find-or-put of every request of a batch against its own (64-bit key,
+// bucket scheme) table; flags[key_off + i] = is_new.
+cudaError_t serve_bucket_find_or_put(const BucketCfg& c, const DevTable* tables, const ServeDesc* reqs,
+                                     uint32_t nreq, uint64_t ntiles, const uint64_t* keys, uint8_t* flags,
+                                     cudaStream_t s);
+
 }  // namespace ht

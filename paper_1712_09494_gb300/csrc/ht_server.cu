@@ -1,0 +1,468 @@
+// Serving form: a request loop over many device-resident tables.
+//
+// Requests (find-or-put batches of 64-bit keys for one table) are queued per
+// table.  A worker thread forms batches continuously: whenever one of the
+// `max_inflight` batch slots is free it takes the head request of every
+// table that has no request in flight (so each table's requests complete in
+// arrival order and keep their sequential find-or-put meaning), packs their
+// keys into that slot's pinned staging buffer, and issues on the slot's own
+// stream: one copy in, one packed multi-table kernel for the bucket-scheme
+// tables (one 32-key tile per warp, each against its own table), the
+// Cuckoo tables' probe/insert launches, and one copy out.  Requests that
+// arrive while slots are busy join the next batch, and the slots' streams
+// overlap on the device.
+//
+// Tables are admitted when the free device memory (cudaMemGetInfo, or a
+// test value) covers them plus a reserve; requests for a table wait until it
+// is admitted.  Every wait the caller makes is bounded by its timeout.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ht_internal.cuh"
+
+using namespace ht;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+    uint32_t table = 0;
+    const uint64_t* keys = nullptr;
+    uint64_t n = 0;
+    uint8_t* out = nullptr;
+    Clock::time_point t0, t1;
+    int state = 0;                 // 0 queued, 1 in flight, 2 done
+    ht_status status = HT_OK;
+};
+
+struct Tab {
+    uint64_t capacity = 0;
+    ht_scheme scheme = HT_BUCKET;
+    ht_table* t = nullptr;
+    uint64_t bytes = 0;
+    bool admitted = false, busy = false, closing = false, closed = false;
+    std::deque<uint64_t> q;
+};
+
+struct Slot {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    uint64_t* h_keys = nullptr;    // pinned staging
+    uint8_t* h_flags = nullptr;
+    ServeDesc* h_desc = nullptr;
+    uint64_t* d_keys = nullptr;
+    uint8_t* d_flags = nullptr;
+    ServeDesc* d_desc = nullptr;
+    std::vector<std::pair<uint64_t, uint64_t>> reqs;   // (request id, key offset)
+    bool busy = false;
+};
+
+uint64_t table_bytes(uint64_t capacity, ht_scheme scheme, const ht_params& p) {
+    const uint64_t bs = p.bucket_slots ? p.bucket_slots : 16;
+    const uint64_t slots = (capacity + bs - 1) / bs * bs;
+    uint64_t b = slots * 8 + 4096 * 8 + (1 << 16) * 8 + 4096;
+    if (scheme == HT_CUCKOO) {
+        const uint64_t chunk = std::min<uint64_t>(p.max_batch ? p.max_batch : (1ull << 22), slots);
+        b += 2 * chunk * 8 * 2 + chunk * 16;
+    }
+    return b;
+}
+
+}  // namespace
+
+struct ht_server {
+    ht_server_config cfg{};
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    std::vector<Tab> tabs;
+    std::unordered_map<uint64_t, Req> reqs;
+    uint64_t next_id = 1;
+    std::vector<Slot> slots;
+    DevTable* d_tables = nullptr;
+    cudaStream_t admin = nullptr;
+    uint64_t admitted_bytes = 0;
+    size_t rr = 0;                 // round-robin start over tables
+    std::vector<double> lat_us;
+    uint64_t keys_done = 0, batches = 0, requests_done = 0;
+    Clock::time_point stats_t0;
+    ht_status fault = HT_OK;
+};
+
+namespace {
+
+constexpr uint32_t kMaxServerTables = 1u << 16;
+
+uint64_t free_bytes(ht_server* sv) {
+    if (sv->cfg.fake_free_bytes) {
+        return sv->cfg.fake_free_bytes > sv->admitted_bytes ? sv->cfg.fake_free_bytes - sv->admitted_bytes : 0;
+    }
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
+    return fr;
+}
+
+// Admits waiting tables, in id order, while free memory covers them.
+bool admit(ht_server* sv) {
+    bool any = false;
+    for (uint32_t id = 0; id < sv->tabs.size(); ++id) {
+        Tab& tb = sv->tabs[id];
+        if (tb.admitted || tb.closed) continue;
+        if (free_bytes(sv) < tb.bytes + sv->cfg.hbm_reserve_bytes) break;   // keep admission in order
+        ht_params p = sv->cfg.table_params;
+        if (tb.scheme == HT_CUCKOO) {
+            const uint64_t seed = p.seed;
+            ht_default_params(HT_CUCKOO, &p);
+            p.seed = seed;
+        }
+        ht_table* t = nullptr;
+        ht_status st = ht_create(tb.capacity, tb.scheme, 64, &p, sv->admin, &t);
+        if (st == HT_OK && tb.scheme == HT_BUCKET) {
+            const DevTable& dt = table_dev(t);
+            if (cudaMemcpyAsync(sv->d_tables + id, &dt, sizeof(DevTable), cudaMemcpyHostToDevice, sv->admin) !=
+                cudaSuccess)
+                st = HT_ERR_CUDA;
+        }
+        if (st == HT_OK && cudaStreamSynchronize(sv->admin) != cudaSuccess) st = HT_ERR_CUDA;
+        if (st != HT_OK) {
+            if (t) ht_destroy(t);
+            if (st == HT_ERR_OOM) break;          // try again when memory frees up
+            sv->fault = st;
+            break;
+        }
+        tb.t = t;
+        tb.admitted = true;
+        sv->admitted_bytes += tb.bytes;
+        any = true;
+    }
+    return any;
+}
+
+void finish(ht_server* sv, Slot& sl) {
+    const auto now = Clock::now();
+    for (const auto& pr : sl.reqs) {
+        auto it = sv->reqs.find(pr.first);
+        if (it == sv->reqs.end()) continue;
+        Req& r = it->second;
+        if (r.out) std::memcpy(r.out, sl.h_flags + pr.second, r.n);
+        r.t1 = now;
+        r.state = 2;
+        r.status = sv->fault;
+        sv->tabs[r.table].busy = false;
+        sv->keys_done += r.n;
+        sv->requests_done += 1;
+        sv->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r.t0).count());
+    }
+    sl.reqs.clear();
+    sl.busy = false;
+}
+
+// Packs the head request of every ready table into slot `sl` and issues it.
+bool launch(ht_server* sv, Slot& sl) {
+    const uint64_t budget = sv->cfg.batch_key_budget;
+    uint64_t off = 0, tiles = 0;
+    uint32_t nb = 0;
+    struct CuckooJob {
+        uint32_t table;
+        uint64_t off, n;
+    };
+    std::vector<CuckooJob> cuckoo;
+    const size_t nt = sv->tabs.size();
+    const uint32_t max_reqs = sv->cfg.pack ? sv->cfg.max_requests_per_batch : 1u;
+    for (size_t k = 0; k < nt && sl.reqs.size() < max_reqs; ++k) {
+        const uint32_t id = uint32_t((sv->rr + k) % nt);
+        Tab& tb = sv->tabs[id];
+        if (!tb.admitted || tb.busy || tb.q.empty()) continue;
+        Req& r = sv->reqs[tb.q.front()];
+        if (off + r.n > budget && off > 0) continue;
+        std::memcpy(sl.h_keys + off, r.keys, r.n * 8);
+        if (tb.scheme == HT_BUCKET) {
+            sl.h_desc[nb].key_off = off;
+            sl.h_desc[nb].n = r.n;
+            sl.h_desc[nb].tile_off = tiles;
+            sl.h_desc[nb].table = id;
+            sl.h_desc[nb].pad_ = 0;
+            tiles += (r.n + 31) / 32;
+            ++nb;
+        } else {
+            cuckoo.push_back(CuckooJob{id, off, r.n});
+        }
+        sl.reqs.emplace_back(tb.q.front(), off);
+        r.state = 1;
+        tb.q.pop_front();
+        tb.busy = true;
+        off += r.n;
+    }
+    if (sl.reqs.empty()) return false;
+    sv->rr = (sv->rr + 1) % std::max<size_t>(nt, 1);
+    cudaError_t e = cudaMemcpyAsync(sl.d_keys, sl.h_keys, off * 8, cudaMemcpyHostToDevice, sl.s);
+    if (e == cudaSuccess && nb) e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, nb * sizeof(ServeDesc), cudaMemcpyHostToDevice, sl.s);
+    if (e == cudaSuccess && nb)
+        e = serve_bucket_find_or_put(table_bucket_cfg(sv->tabs[sl.h_desc[0].table].t), sv->d_tables, sl.d_desc, nb, tiles,
+                                     sl.d_keys, sl.d_flags, sl.s);
+    for (const auto& c : cuckoo) {
+        if (e != cudaSuccess) break;
+        if (ht_find_or_put(sv->tabs[c.table].t, sl.d_keys + c.off, c.n, sl.d_flags + c.off, sl.s) != HT_OK)
+            e = cudaErrorLaunchFailure;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_flags, sl.d_flags, off, cudaMemcpyDeviceToHost, sl.s);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.s);
+    if (e != cudaSuccess) sv->fault = HT_ERR_CUDA;
+    sl.busy = true;
+    sv->batches += 1;
+    return true;
+}
+
+void close_idle(ht_server* sv) {
+    for (auto& tb : sv->tabs) {
+        if (!tb.closing || tb.closed || tb.busy || !tb.q.empty()) continue;
+        if (tb.t) {
+            cudaStreamSynchronize(sv->admin);
+            ht_destroy(tb.t);
+            tb.t = nullptr;
+        }
+        if (tb.admitted) sv->admitted_bytes -= tb.bytes;
+        tb.admitted = false;
+        tb.closed = true;
+    }
+}
+
+void worker_loop(ht_server* sv) {
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (!sv->stop) {
+        bool progress = false, any_busy = false;
+        for (auto& sl : sv->slots) {
+            if (sl.busy) {
+                const cudaError_t q = cudaEventQuery(sl.ev);
+                if (q == cudaSuccess) {
+                    finish(sv, sl);
+                    progress = true;
+                } else if (q != cudaErrorNotReady) {
+                    sv->fault = HT_ERR_CUDA;
+                    finish(sv, sl);
+                    progress = true;
+                } else {
+                    any_busy = true;
+                }
+            }
+        }
+        if (progress) sv->cv_done.notify_all();
+        close_idle(sv);
+        if (admit(sv)) progress = true;
+        for (auto& sl : sv->slots)
+            if (!sl.busy && launch(sv, sl)) progress = any_busy = true;
+        if (!progress) {
+            if (any_busy) sv->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            else sv->cv_work.wait_for(lk, std::chrono::milliseconds(1));
+        }
+    }
+}
+
+void destroy_server(ht_server* sv) {
+    {
+        std::lock_guard<std::mutex> g(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    cudaSetDevice(sv->device);
+    for (auto& sl : sv->slots) {
+        if (sl.s) cudaStreamSynchronize(sl.s);
+        cudaFreeHost(sl.h_keys);
+        cudaFreeHost(sl.h_flags);
+        cudaFreeHost(sl.h_desc);
+        cudaFree(sl.d_keys);
+        cudaFree(sl.d_flags);
+        cudaFree(sl.d_desc);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.s) cudaStreamDestroy(sl.s);
+    }
+    for (auto& tb : sv->tabs)
+        if (tb.t) ht_destroy(tb.t);
+    cudaFree(sv->d_tables);
+    if (sv->admin) cudaStreamDestroy(sv->admin);
+    delete sv;
+}
+
+}  // namespace
+
+extern "C" {
+
+ht_status ht_server_default_config(ht_server_config* c) {
+    if (!c) return HT_ERR_INVALID;
+    std::memset(c, 0, sizeof(*c));
+    c->max_inflight = 4;
+    c->batch_key_budget = 1ull << 22;
+    c->max_requests_per_batch = 4096;
+    c->hbm_reserve_bytes = 1ull << 30;
+    c->pack = 1;
+    ht_default_params(HT_BUCKET, &c->table_params);
+    return HT_OK;
+}
+
+ht_status ht_server_create(const ht_server_config* cfg, ht_server** out) {
+    if (!out) return HT_ERR_INVALID;
+    *out = nullptr;
+    ht_server_config c;
+    ht_server_default_config(&c);
+    if (cfg) c = *cfg;
+    if (c.max_inflight < 1 || c.max_inflight > 64 || c.batch_key_budget < 32 || c.batch_key_budget > (1ull << 28) ||
+        c.max_requests_per_batch < 1)
+        return HT_ERR_INVALID;
+    ht_server* sv = new (std::nothrow) ht_server();
+    if (!sv) return HT_ERR_OOM;
+    sv->cfg = c;
+    cudaGetDevice(&sv->device);
+    sv->stats_t0 = Clock::now();
+    bool ok = cudaStreamCreateWithFlags(&sv->admin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&sv->d_tables, kMaxServerTables * sizeof(DevTable)) == cudaSuccess;
+    sv->slots.resize(c.max_inflight);
+    const uint64_t nreq = std::min<uint64_t>(c.max_requests_per_batch, c.batch_key_budget);
+    for (auto& sl : sv->slots) {
+        if (!ok) break;
+        ok = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
+             cudaMallocHost(&sl.h_keys, c.batch_key_budget * 8) == cudaSuccess &&
+             cudaMallocHost(&sl.h_flags, c.batch_key_budget) == cudaSuccess &&
+             cudaMallocHost(&sl.h_desc, nreq * sizeof(ServeDesc)) == cudaSuccess &&
+             cudaMalloc(&sl.d_keys, c.batch_key_budget * 8) == cudaSuccess &&
+             cudaMalloc(&sl.d_flags, c.batch_key_budget) == cudaSuccess &&
+             cudaMalloc(&sl.d_desc, nreq * sizeof(ServeDesc)) == cudaSuccess;
+    }
+    if (!ok) {
+        destroy_server(sv);
+        return HT_ERR_OOM;
+    }
+    sv->worker = std::thread(worker_loop, sv);
+    *out = sv;
+    return HT_OK;
+}
+
+ht_status ht_server_destroy(ht_server* sv) {
+    if (!sv) return HT_OK;
+    destroy_server(sv);
+    return HT_OK;
+}
+
+ht_status ht_server_open_table(ht_server* sv, uint64_t capacity, ht_scheme scheme, uint32_t* table_id) {
+    if (!sv || !table_id || capacity == 0 || capacity > (1ull << 40) || (scheme != HT_BUCKET && scheme != HT_CUCKOO))
+        return HT_ERR_INVALID;
+    std::lock_guard<std::mutex> g(sv->mu);
+    if (sv->tabs.size() >= kMaxServerTables) return HT_ERR_INVALID;
+    Tab tb;
+    tb.capacity = capacity;
+    tb.scheme = scheme;
+    tb.bytes = table_bytes(capacity, scheme, sv->cfg.table_params);
+    sv->tabs.push_back(tb);
+    *table_id = uint32_t(sv->tabs.size() - 1);
+    sv->cv_work.notify_all();
+    return HT_OK;
+}
+
+ht_status ht_server_close_table(ht_server* sv, uint32_t table_id) {
+    if (!sv) return HT_ERR_INVALID;
+    std::lock_guard<std::mutex> g(sv->mu);
+    if (table_id >= sv->tabs.size() || sv->tabs[table_id].closing) return HT_ERR_INVALID;
+    sv->tabs[table_id].closing = true;
+    sv->cv_work.notify_all();
+    return HT_OK;
+}
+
+ht_status ht_server_table_state(ht_server* sv, uint32_t table_id, int32_t* admitted, uint64_t* size) {
+    if (!sv) return HT_ERR_INVALID;
+    std::lock_guard<std::mutex> g(sv->mu);
+    if (table_id >= sv->tabs.size()) return HT_ERR_INVALID;
+    Tab& tb = sv->tabs[table_id];
+    if (admitted) *admitted = tb.admitted ? 1 : (tb.closed ? -1 : 0);
+    if (size) {
+        *size = 0;
+        if (tb.t && !tb.busy) {
+            // Synchronises only the admission stream; the table is idle.
+            DevCounters c;
+            if (cudaMemcpy(&c, table_dev(tb.t).ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return HT_ERR_CUDA;
+            *size = c.size;
+        }
+    }
+    return HT_OK;
+}
+
+ht_status ht_server_submit(ht_server* sv, uint32_t table_id, const uint64_t* h_keys, uint64_t n, uint8_t* h_is_new,
+                           uint64_t* request_id) {
+    if (!sv || !request_id || (n && !h_keys) || n > sv->cfg.batch_key_budget) return HT_ERR_INVALID;
+    std::lock_guard<std::mutex> g(sv->mu);
+    if (table_id >= sv->tabs.size() || sv->tabs[table_id].closing || sv->tabs[table_id].closed) return HT_ERR_INVALID;
+    const uint64_t id = sv->next_id++;
+    Req& r = sv->reqs[id];
+    r.table = table_id;
+    r.keys = h_keys;
+    r.n = n;
+    r.out = h_is_new;
+    r.t0 = Clock::now();
+    sv->tabs[table_id].q.push_back(id);
+    *request_id = id;
+    sv->cv_work.notify_all();
+    return HT_OK;
+}
+
+ht_status ht_server_wait(ht_server* sv, uint64_t request_id, uint32_t timeout_ms, double* latency_us) {
+    if (!sv) return HT_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(request_id);
+    if (it == sv->reqs.end()) return HT_ERR_INVALID;
+    const bool done = sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+        auto jt = sv->reqs.find(request_id);
+        return jt == sv->reqs.end() || jt->second.state == 2;
+    });
+    if (!done) return HT_ERR_TIMEOUT;
+    it = sv->reqs.find(request_id);
+    const ht_status st = it->second.status;
+    if (latency_us) *latency_us = std::chrono::duration<double, std::micro>(it->second.t1 - it->second.t0).count();
+    sv->reqs.erase(it);
+    return st;
+}
+
+ht_status ht_server_get_stats(ht_server* sv, ht_server_stats* out, int reset) {
+    if (!sv || !out) return HT_ERR_INVALID;
+    std::lock_guard<std::mutex> g(sv->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->requests = sv->requests_done;
+    out->keys = sv->keys_done;
+    out->batches = sv->batches;
+    out->seconds = std::chrono::duration<double>(Clock::now() - sv->stats_t0).count();
+    std::vector<double> v = sv->lat_us;
+    if (!v.empty()) {
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) { return v[std::min<size_t>(v.size() - 1, size_t(q * (v.size() - 1) + 0.5))]; };
+        out->p50_us = pct(0.50);
+        out->p99_us = pct(0.99);
+        out->max_us = v.back();
+        double s = 0;
+        for (double x : v) s += x;
+        out->mean_us = s / double(v.size());
+    }
+    uint32_t adm = 0;
+    for (const auto& tb : sv->tabs) adm += tb.admitted;
+    out->tables_admitted = adm;
+    out->admitted_bytes = sv->admitted_bytes;
+    out->status = sv->fault;
+    if (reset) {
+        sv->lat_us.clear();
+        sv->requests_done = sv->keys_done = sv->batches = 0;
+        sv->stats_t0 = Clock::now();
+    }
+    return HT_OK;
+}
+
+}  // extern "C"

@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--no-bfs", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--serve-rate", type=float, default=40000.0, help="Poisson arrivals per second")
     return ap.parse_args()
 
 
@@ -291,6 +296,15 @@ def run_ours(a, rank, world, local):
         out["random_read_roofline"] = run_probe(ht, torch, dev)
     for t in tables.values():
         t.close()
+    tables = {}
+    if not a.no_bfs:
+        out["bfs_config3"] = run_bfs(ht, torch, dev, schemes)
+    if not a.no_batched:
+        out["batched_config4"] = run_batched(ht, torch)
+    if not a.no_serving:
+        out["serving_config5"] = run_serving(ht, a)
+    for t in tables.values():
+        t.close()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -363,6 +377,167 @@ def run_probe(ht, torch, dev):
         res["%dB_gbs" % gran] = round(n_acc * gran / (ms / 1e3) / 1e9, 1)
     del buf
     return res
+
+
+# ----------------------------------------------------------------- other rows
+def _hmodel(ht, m):
+    return ht.make_model(m.C, m.bits, m.deg, m.tgt, m.lab, m.pairs)
+
+
+def run_bfs(ht, torch, dev, schemes, warmup=1, reps=3):
+    """Config 3: full BFS of the 12 x 32 model (~10^8 states), per scheme:
+    states/s and find-or-put ops/s (successors/s); levels checked against the
+    stored oracle levels."""
+    from workloads import statespace as ss
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "statespace_config3.json")))
+    m = ss.config3_model(seed=gold["model"]["seed"], p_sync=gold["model"]["p_sync"])
+    hm = _hmodel(ht, m)
+    states = torch.empty(gold["states"] + 1024, dtype=torch.int64, device=dev)
+    out = {"workload": "12 components x 32 local states, 4 sync pairs, from the all-zero state: %d states, "
+                       "%d levels, %d successors" % (gold["states"], len(gold["levels"]), gold["successors"])}
+    for sch in schemes:
+        t = ht.HashTable(int(gold["states"] / 0.8), sch, 64)
+        times = []
+        for r in range(warmup + reps):
+            ht.ht_clear(t.handle)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res, sizes = ht.ht_bfs(t.handle, hm, 0, 4096, states)
+            torch.cuda.synchronize()
+            if r >= warmup:
+                times.append(time.perf_counter() - t0)
+        ok = (res.complete == 1 and res.states == gold["states"] and res.successors == gold["successors"]
+              and sizes == [lv[0] for lv in gold["levels"]])
+        sec = statistics.median(times)
+        out[sch] = {"seconds": round(sec, 4), "states_per_s_M": round(res.states / sec / 1e6, 1),
+                    "find_or_put_mops": round(res.successors / sec / 1e6, 1),
+                    "levels_match_oracle": bool(ok), "host_syncs": len(sizes) + 2}
+        t.close()
+    del states
+    return out
+
+
+def run_batched(ht, torch):
+    """Config 4: 256 explorations (6-10 components, 8-32 local states,
+    2^10..2^20 states each): graph-captured batched steps vs one exploration
+    at a time, same tables; results checked against the stored levels."""
+    from workloads import statespace as ss
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "statespace_batched.json")))
+    models = ss.batched_models(gold["model"]["count"], seed=gold["model"]["seed"])
+    caps = [max(256, int(g["states"] / 0.7)) for g in gold["explorations"]]
+    mx = ht.MultiExploration([_hmodel(ht, m) for m in models], [0] * len(models), caps)
+    res = {"workload": "%d explorations, %d states, %d successors in total" % (
+        len(models), sum(g["states"] for g in gold["explorations"]), sum(g["successors"] for g in gold["explorations"]))}
+    for mode, name in ((0, "batched_graph"), (1, "batched_launches"), (2, "one_table_at_a_time")):
+        times = []
+        for r in range(3):
+            mx.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps = mx.run(mode=mode)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        ok = all(mx.result(i)["states"] == g["states"] and mx.result(i)["level_sizes"] == [lv[0] for lv in g["levels"]]
+                 for i, g in enumerate(gold["explorations"]))
+        sec = min(times[1:])
+        tot = sum(g["successors"] for g in gold["explorations"])
+        res[name] = {"seconds": round(sec, 4), "steps": steps, "find_or_put_mops": round(tot / sec / 1e6, 1),
+                     "levels_match_oracle": bool(ok)}
+    res["speedup_batched_vs_per_table"] = round(res["one_table_at_a_time"]["seconds"] / res["batched_graph"]["seconds"], 2)
+    mx.close()
+    return res
+
+
+def serving_trace(n_req, rate, seed=5, n_tables=1024):
+    """Poisson arrivals of find-or-put batches over up to 1024 tables of
+    2^12..2^30 slots (log-uniform); batch sizes log-uniform in 1..2^20; each
+    table lives for a contiguous session of the trace (opened before its
+    first request, closed after its last), so admission by free memory
+    matters; keys are random 64-bit with repeats of the table's earlier keys."""
+    rng = np.random.default_rng(seed)
+    caps = np.exp2(rng.uniform(12, 30, size=n_tables)).astype(np.int64)
+    pos = np.sort(rng.uniform(0, n_tables, size=n_req))
+    table = np.minimum(n_tables - 1, (pos + rng.uniform(-8, 8, size=n_req)).clip(0)).astype(np.int64)
+    sizes = np.exp(rng.uniform(0, np.log(2 ** 20), size=n_req)).astype(np.int64).clip(1, 2 ** 20)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    return caps, table, sizes, arrivals
+
+
+def serving_keys(trace):
+    """Per request: fresh keys of its table, a quarter of them repeats of the
+    table's first keys once the table has been used."""
+    from workloads import keys as wk
+    caps, table, sizes, arrivals = trace
+    issued, keys = {}, []
+    for i in range(len(sizes)):
+        t, n = int(table[i]), int(sizes[i])
+        base = issued.get(t, 0)
+        k = wk.distinct_keys(n, 64, seed=1000 + t, start=base)
+        rep = min(n // 4, base)
+        if rep:
+            k[:rep] = wk.distinct_keys(rep, 64, seed=1000 + t, start=0)
+        issued[t] = base + n
+        keys.append(k)
+    return keys
+
+
+def run_serving_once(ht, a, pack, inflight, trace, keys):
+    import threading
+    caps, table, sizes, arrivals = trace
+    n_req = len(sizes)
+    srv = ht.Server(pack=pack, max_inflight=inflight, batch_key_budget=1 << 22,
+                    hbm_reserve_bytes=8 << 30)
+    last = {}
+    for i, t in enumerate(table):
+        last[int(t)] = i
+    tid = {}
+    rids = [None] * n_req
+    done_lat = [None] * n_req
+    errors = []
+
+    def completer():
+        for i in range(n_req):
+            while rids[i] is None:
+                time.sleep(0.0001)
+            st, lat, _ = srv.wait(rids[i], timeout_ms=600000)
+            if st != 0:
+                errors.append(st)
+            done_lat[i] = lat
+            t = int(table[i])
+            if last[t] == i:
+                srv.close_table(tid[t])
+
+    th = threading.Thread(target=completer)
+    th.start()
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        t = int(table[i])
+        if t not in tid:
+            tid[t] = srv.open_table(int(caps[t]), "bucket")
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        rids[i] = srv.submit(tid[t], keys[i])
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array(done_lat)
+    return {"p50_us": round(float(np.percentile(lat, 50)), 1), "p99_us": round(float(np.percentile(lat, 99)), 1),
+            "mean_us": round(float(lat.mean()), 1), "sustained_mops": round(float(sizes.sum()) / wall / 1e6, 1),
+            "wall_s": round(wall, 3), "batches": int(st["batches"]), "errors": len(errors)}
+
+
+def run_serving(ht, a):
+    trace = serving_trace(a.serve_requests, a.serve_rate)
+    caps, table, sizes, arrivals = trace
+    out = {"workload": "%d requests over %d tables (2^12..2^30 slots, sessions), batch 1..2^20 keys log-uniform "
+                       "(mean %d), Poisson %.0f req/s offered" % (len(sizes), len(set(table.tolist())),
+                                                                  int(sizes.mean()), a.serve_rate)}
+    keys = serving_keys(trace)
+    out["continuous_batching"] = run_serving_once(ht, a, pack=1, inflight=4, trace=trace, keys=keys)
+    out["per_request_launches"] = run_serving_once(ht, a, pack=0, inflight=1, trace=trace, keys=keys)
+    return out
 
 
 # ----------------------------------------------------------------- CPU legs

@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-rate", type=float, default=40000.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-deadline", type=float, default=120.0, help="seconds before a serving run gives up")
     return ap.parse_args()
 
 
@@ -357,14 +358,16 @@ def run_e2e(a, ht, torch, dev, fs, tables, schemes, world):
 
 
 def run_probe(ht, torch, dev):
-    """Random-read throughput at 32/128-byte granularity over a 4 GiB buffer
-    (>> L2): the ceiling for hash probes, reported beside the copy peak."""
+    """Random-read rates over a 4 GiB buffer (>> L2): 8-byte slot probes,
+    32-byte reads and 128-byte lines read by 8-lane groups.  On GB300 each
+    random access costs a whole 128-byte line of DRAM traffic, so the line
+    rate is the ceiling for both schemes' probes."""
     buf = torch.empty(1 << 29, dtype=torch.int64, device=dev)
     buf.fill_(1)
     sink = torch.zeros(1, dtype=torch.int64, device=dev)
-    res = {}
-    for gran in (32, 128):
-        n_acc = (1 << 31) // gran * 4   # 8 GiB of reads
+    res = {"buffer_gib": 4}
+    for gran in (8, 32, 128):
+        n_acc = (1 << 33) // 128          # the same number of accesses for every size
         ht.ht_probe_random_read(buf, gran, n_acc, 7, sink)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -374,7 +377,9 @@ def run_probe(ht, torch, dev):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 3
-        res["%dB_gbs" % gran] = round(n_acc * gran / (ms / 1e3) / 1e9, 1)
+        res["%dB" % gran] = {"gaccess_per_s": round(n_acc / (ms / 1e3) / 1e9, 2),
+                             "requested_gbs": round(n_acc * gran / (ms / 1e3) / 1e9, 1),
+                             "line_gbs": round(n_acc * 128 / (ms / 1e3) / 1e9, 1)}
     del buf
     return res
 
@@ -495,13 +500,18 @@ def run_serving_once(ht, a, pack, inflight, trace, keys):
     done_lat = [None] * n_req
     errors = []
 
+    deadline = time.perf_counter() + a.serve_deadline
+
     def completer():
         for i in range(n_req):
             while rids[i] is None:
                 time.sleep(0.0001)
-            st, lat, _ = srv.wait(rids[i], timeout_ms=600000)
+            left_ms = max(1, int((deadline - time.perf_counter()) * 1000))
+            st, lat, _ = srv.wait(rids[i], timeout_ms=left_ms)
             if st != 0:
                 errors.append(st)
+                if st == 5:                       # deadline passed: stop waiting
+                    break
             done_lat[i] = lat
             t = int(table[i])
             if last[t] == i:
@@ -521,6 +531,10 @@ def run_serving_once(ht, a, pack, inflight, trace, keys):
     th.join()
     wall = time.perf_counter() - t0
     st = srv.stats()
+    if errors:
+        srv.close()
+        return {"error": "%d requests failed or missed the %.0f s deadline (first status %d)" % (
+            len(errors), a.serve_deadline, errors[0])}
     srv.close()
     lat = np.array(done_lat)
     return {"p50_us": round(float(np.percentile(lat, 50)), 1), "p99_us": round(float(np.percentile(lat, 99)), 1),

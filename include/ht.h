@@ -93,7 +93,9 @@ ht_status ht_default_params(ht_scheme scheme, ht_params* p);
  * buckets, for both schemes) on the current device.  Section 5: the paper
  * sizes the table at 1.25x the number of unique keys.  params may be NULL.
  * Allocates the slot array, stash, overflow set and counters (and, for
- * Cuckoo, the dedup scratch) with cudaMalloc, and clears them on `stream`.
+ * Cuckoo, the dedup scratch) in the order of `stream` (cudaMallocAsync) and
+ * clears them on `stream`; use the table on other streams only after work
+ * on `stream` is ordered before that use.
  * Errors: HT_ERR_INVALID (capacity 0 or > 2^40, key_width not 32/64, bad
  * params), HT_ERR_OOM, HT_ERR_CUDA.  *out is NULL on error. */
 ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width,
@@ -345,10 +347,12 @@ const char* ht_prof_kernel_name(uint32_t id);
 ht_status ht_prof_read(uint32_t id, uint64_t* launches, double* total_ms);
 
 /* ---------------------------------------------------------------------------
- * Random-access roofline probe: reads n_access blocks of `gran` bytes (32,
- * 64 or 128) at uniformly random gran-aligned offsets of d_buf[0..bytes) and
- * folds them into *d_sink.  Measures the random-gather throughput that bounds
- * the probes of both schemes.  Not part of the hash table.
+ * Random-access roofline probe (not part of the hash table): n_access reads
+ * at uniformly random gran-aligned offsets of d_buf[0..bytes), folded into
+ * *d_sink.  gran 8: one 8-byte load per access, eight in flight per thread
+ * (a Cuckoo slot probe); gran 32: one 256-bit load per access, four in
+ * flight per thread; gran 128: a 128-byte line read by 8 lanes with one
+ * coalesced load (a bucket probe), four lines in flight per group.
  * ------------------------------------------------------------------------- */
 ht_status ht_probe_random_read(const void* d_buf, uint64_t bytes, uint32_t gran,
                                uint64_t n_access, uint64_t seed,

@@ -232,14 +232,13 @@ ht_params complete_params(ht_scheme scheme, const ht_params* in) {
     return p;
 }
 
-void free_table(ht_table* t) {
+// Table memory is stream-ordered (cudaMallocAsync / cudaFreeAsync), so a
+// table can be released without synchronising the whole device.
+void free_table(ht_table* t, cudaStream_t s) {
     if (!t) return;
-    cudaFree(t->dt.slots);
-    cudaFree(t->dt.stash);
-    cudaFree(t->dt.ovf);
-    cudaFree(t->dt.ctr);
-    cudaFree(t->sc.set);
-    cudaFree(t->sc.win);
+    void* ptrs[] = {t->dt.slots, t->dt.stash, t->dt.ovf, t->dt.ctr, t->sc.set, t->sc.win};
+    for (void* p : ptrs)
+        if (p) cudaFreeAsync(p, s);
     delete t;
 }
 
@@ -306,28 +305,29 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
     t->dt.max_evict = p.max_evictions;
     derive_seeds(t);
 
+    const cudaStream_t cs = as_stream(stream);
     auto fail = [&](cudaError_t e) {
-        free_table(t);
+        free_table(t, cs);
         return cuda_status(e);
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&t->dt.slots, t->dt.nslots * 8)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&t->dt.stash, std::max<uint32_t>(t->dt.stash_slots, 1) * 8)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&t->dt.ovf, uint64_t(t->dt.ovf_slots) * 8)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&t->dt.ctr, sizeof(DevCounters))) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocAsync(&t->dt.slots, t->dt.nslots * 8, cs)) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocAsync(&t->dt.stash, std::max<uint32_t>(t->dt.stash_slots, 1) * 8, cs)) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocAsync(&t->dt.ovf, uint64_t(t->dt.ovf_slots) * 8, cs)) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocAsync(&t->dt.ctr, sizeof(DevCounters), cs)) != cudaSuccess) return fail(e);
     if (scheme == HT_CUCKOO) {
         // A chunk never holds more absent distinct keys than the table can
         // take, so the scratch is sized by the smaller of the two.
         t->chunk = std::min<uint64_t>(p.max_batch, next_pow2(t->dt.nslots + t->dt.stash_slots + t->dt.ovf_slots));
         const uint64_t sslots = next_pow2(2 * t->chunk);
         t->sc.mask = sslots - 1;
-        if ((e = cudaMalloc(&t->sc.set, sslots * 8)) != cudaSuccess) return fail(e);
-        if ((e = cudaMalloc(&t->sc.win, t->chunk * sizeof(Winner))) != cudaSuccess) return fail(e);
-        if ((e = fill_words(t->sc.set, sslots, kEmpty, as_stream(stream))) != cudaSuccess) return fail(e);
+        if ((e = cudaMallocAsync(&t->sc.set, sslots * 8, cs)) != cudaSuccess) return fail(e);
+        if ((e = cudaMallocAsync(&t->sc.win, t->chunk * sizeof(Winner), cs)) != cudaSuccess) return fail(e);
+        if ((e = fill_words(t->sc.set, sslots, kEmpty, cs)) != cudaSuccess) return fail(e);
     }
-    ht_status st = clear_table(t, as_stream(stream));
+    ht_status st = clear_table(t, cs);
     if (st != HT_OK) {
-        free_table(t);
+        free_table(t, cs);
         return st;
     }
     *out = t;
@@ -337,8 +337,9 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
 ht_status ht_destroy(ht_table* t) {
     if (!t) return HT_OK;
     DeviceGuard g(t->device);
-    cudaDeviceSynchronize();
-    free_table(t);
+    cudaDeviceSynchronize();          // the table may have been used on any stream
+    free_table(t, nullptr);
+    cudaStreamSynchronize(nullptr);
     return HT_OK;
 }
 
@@ -483,6 +484,11 @@ uint64_t ht::model_max_successors(const ht_model* m, uint32_t key_width) {
 }
 
 const DevTable& ht::table_dev(const ht_table* t) { return t->dt; }
+void ht::table_release(ht_table* t, cudaStream_t s) {
+    if (!t) return;
+    DeviceGuard g(t->device);
+    free_table(t, s);
+}
 BucketCfg ht::table_bucket_cfg(const ht_table* t) { return bucket_cfg(t); }
 ht_scheme ht::table_scheme(const ht_table* t) { return t->scheme; }
 uint32_t ht::table_key_width(const ht_table* t) { return t->kw; }

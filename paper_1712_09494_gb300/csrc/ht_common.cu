@@ -1,5 +1,6 @@
 // Kernels shared by both schemes: export, fill, frontier compaction, the
 // random-read roofline probe; plus launch sizing and event timing.
+#include <algorithm>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -70,29 +71,61 @@ compact_kernel(const T* __restrict__ keys, const uint8_t* __restrict__ flags, ui
     }
 }
 
-// Random reads of `gran` bytes at gran-aligned offsets; four independent
-// reads in flight per thread.
+// Random-read probe (the denominator of the hash probes' roofline).
+//   GRAN 8:   each thread keeps 8 independent 8-byte loads in flight
+//             (a Cuckoo slot probe);
+//   GRAN 32:  each thread keeps 4 independent 32-byte (256-bit) loads in flight;
+//   GRAN 128: each group of 8 lanes reads one 128-byte line with one
+//             coalesced 16-byte load per lane, 4 lines in flight per group
+//             (a bucket probe).
+// Offsets come from a 32-bit mixer so address arithmetic stays cheap.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7FEB352Du;
+    x ^= x >> 15;
+    x *= 0x846CA68Bu;
+    x ^= x >> 16;
+    return x;
+}
+
 template <int GRAN>
 __global__ void __launch_bounds__(kBlock)
-probe_read_kernel(const uint64_t* __restrict__ buf, uint64_t nblocks, uint64_t n_access, uint64_t seed,
+probe_read_kernel(const uint64_t* __restrict__ buf, uint32_t nblocks, uint64_t n_access, uint32_t seed,
                   unsigned long long* __restrict__ sink) {
-    constexpr int W = GRAN / 16;
+    constexpr int U = GRAN == 8 ? 8 : 4;
     const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t nthreads = uint64_t(gridDim.x) * blockDim.x;
+    // Accesses handled per "unit": a thread (8, 32) or an 8-lane group (128).
+    const uint64_t unit = GRAN == 128 ? tid / 8 : tid;
+    const uint64_t units = GRAN == 128 ? nthreads / 8 : nthreads;
+    const uint64_t iters = (n_access + units * U - 1) / (units * U);
     uint64_t acc = 0;
-    for (uint64_t i = tid * 4; i < n_access; i += stride * 4) {
-        ulonglong2 v[4][W];
+    for (uint64_t it = 0; it < iters; ++it) {
+        uint64_t v[U][2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint64_t b = __umul64hi(mix64(seed ^ (i + u)), nblocks);
-            const ulonglong2* p = reinterpret_cast<const ulonglong2*>(buf + b * (GRAN / 8));
-#pragma unroll
-            for (int w = 0; w < W; ++w) v[u][w] = (i + u < n_access) ? __ldcg(p + w) : make_ulonglong2(0, 0);
+        for (int u = 0; u < U; ++u) {
+            const uint64_t a = (it * units + unit) * U + u;
+            const uint32_t b = __umulhi(mix32(uint32_t(a) * 0x9E3779B9u + uint32_t(a >> 32) + seed), nblocks);
+            const uint64_t* p = buf + uint64_t(b) * (GRAN / 8);
+            v[u][0] = v[u][1] = 0;
+            if (a < n_access) {
+                if constexpr (GRAN == 8) {
+                    v[u][0] = __ldcg(reinterpret_cast<const unsigned long long*>(p));
+                } else if constexpr (GRAN == 32) {
+                    unsigned long long x0, x1, x2, x3;
+                    asm volatile("ld.global.cg.v4.u64 {%0,%1,%2,%3}, [%4];"
+                                 : "=l"(x0), "=l"(x1), "=l"(x2), "=l"(x3) : "l"(p));
+                    v[u][0] = x0 ^ x2;
+                    v[u][1] = x1 ^ x3;
+                } else {
+                    const ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2*>(p) + (threadIdx.x & 7));
+                    v[u][0] = x.x;
+                    v[u][1] = x.y;
+                }
+            }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int w = 0; w < W; ++w) acc ^= v[u][w].x ^ v[u][w].y;
+        for (int u = 0; u < U; ++u) acc ^= v[u][0] ^ v[u][1];
     }
     for (int o = 16; o; o >>= 1) acc ^= __shfl_down_sync(0xFFFFFFFFu, acc, o);
     if ((threadIdx.x & 31) == 0 && acc == 0x9E3779B97F4A7C15ull) atomicXor(sink, acc);
@@ -207,14 +240,14 @@ cudaError_t compact(int kw, const void* keys, const uint8_t* flags, uint64_t n, 
 cudaError_t probe_random_read(const void* buf, uint64_t bytes, uint32_t gran, uint64_t n_access,
                               uint64_t seed, unsigned long long* sink, cudaStream_t s) {
     ProfScope ps(kKProbeRead, s);
-    const uint64_t nblocks = bytes / gran;
+    const uint32_t nblocks = uint32_t(std::min<uint64_t>(bytes / gran, 0xFFFFFFFFull));
     const uint64_t* b = static_cast<const uint64_t*>(buf);
-#define L(G)                                                                                  \
-    {                                                                                         \
-        auto k = probe_read_kernel<G>;                                                        \
-        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(b, nblocks, n_access, seed, sink); \
+#define L(G)                                                                                           \
+    {                                                                                                  \
+        auto k = probe_read_kernel<G>;                                                                 \
+        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(b, nblocks, n_access, uint32_t(seed), sink); \
     }
-    if (gran == 32) L(32) else if (gran == 64) L(64) else L(128)
+    if (gran == 8) L(8) else if (gran == 32) L(32) else L(128)
 #undef L
     return cudaGetLastError();
 }
@@ -276,7 +309,7 @@ ht_status ht_compact(const void* d_keys, const uint8_t* d_flags, uint64_t n, uin
 
 ht_status ht_probe_random_read(const void* d_buf, uint64_t bytes, uint32_t gran, uint64_t n_access,
                                uint64_t seed, unsigned long long* d_sink, void* stream) {
-    if (!d_buf || !d_sink || (gran != 32 && gran != 64 && gran != 128) || bytes < gran)
+    if (!d_buf || !d_sink || (gran != 8 && gran != 32 && gran != 128) || bytes < gran)
         return HT_ERR_INVALID;
     return ht::probe_random_read(d_buf, bytes, gran, n_access, seed, d_sink,
                                  static_cast<cudaStream_t>(stream)) == cudaSuccess ? HT_OK : HT_ERR_CUDA;

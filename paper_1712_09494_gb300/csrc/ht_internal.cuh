@@ -289,6 +289,9 @@ const DevTable& table_dev(const ht_table* t);
 BucketCfg table_bucket_cfg(const ht_table* t);
 ht_scheme table_scheme(const ht_table* t);
 uint32_t table_key_width(const ht_table* t);
+// Frees an idle table's memory in the order of stream s, without a device
+// synchronisation (the caller guarantees no work on the table is pending).
+void table_release(ht_table* t, cudaStream_t s);
 
 // State-space successors (ht_bfs.cu).  `model` is a device copy of ht_model.
 // count: reservation counter for succ[]; total (nullable): running count of

@@ -110,7 +110,23 @@ uint64_t free_bytes(ht_server* sv) {
     }
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
+    // Memory freed by closed tables stays cached in the device's
+    // stream-ordered pool, where new tables' allocations reuse it.
+    cudaMemPool_t pool;
+    uint64_t reserved = 0, used = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+        fr += reserved - used;
     return fr;
+}
+
+// Hands the pool's cached memory back to the driver (when a table's
+// allocation failed although the cached memory looked large enough).
+void trim_pool(ht_server* sv) {
+    cudaStreamSynchronize(sv->admin);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
 }
 
 // Admits waiting tables, in id order, while free memory covers them.
@@ -128,6 +144,10 @@ bool admit(ht_server* sv) {
         }
         ht_table* t = nullptr;
         ht_status st = ht_create(tb.capacity, tb.scheme, 64, &p, sv->admin, &t);
+        if (st == HT_ERR_OOM && !sv->cfg.fake_free_bytes) {
+            trim_pool(sv);
+            st = ht_create(tb.capacity, tb.scheme, 64, &p, sv->admin, &t);
+        }
         if (st == HT_OK && tb.scheme == HT_BUCKET) {
             const DevTable& dt = table_dev(t);
             if (cudaMemcpyAsync(sv->d_tables + id, &dt, sizeof(DevTable), cudaMemcpyHostToDevice, sv->admin) !=
@@ -136,7 +156,7 @@ bool admit(ht_server* sv) {
         }
         if (st == HT_OK && cudaStreamSynchronize(sv->admin) != cudaSuccess) st = HT_ERR_CUDA;
         if (st != HT_OK) {
-            if (t) ht_destroy(t);
+            if (t) table_release(t, sv->admin);
             if (st == HT_ERR_OOM) break;          // try again when memory frees up
             sv->fault = st;
             break;
@@ -225,17 +245,20 @@ bool launch(ht_server* sv, Slot& sl) {
 }
 
 void close_idle(ht_server* sv) {
+    bool freed = false;
     for (auto& tb : sv->tabs) {
         if (!tb.closing || tb.closed || tb.busy || !tb.q.empty()) continue;
         if (tb.t) {
-            cudaStreamSynchronize(sv->admin);
-            ht_destroy(tb.t);
+            // Idle: every batch that used it has completed (its event fired).
+            table_release(tb.t, sv->admin);
             tb.t = nullptr;
+            freed = true;
         }
         if (tb.admitted) sv->admitted_bytes -= tb.bytes;
         tb.admitted = false;
         tb.closed = true;
     }
+    (void)freed;   // the freed memory stays in the pool for the next tables (see free_bytes)
 }
 
 void worker_loop(ht_server* sv) {

@@ -108,3 +108,24 @@ def test_submit_rejects_bad_requests():
     with pytest.raises(ht.HtError):
         srv.submit(t, np.arange(10, dtype=np.uint64))
     srv.close()
+
+
+def test_admission_with_real_free_memory_after_close():
+    # Reserve all but ~1.5 tables of the real free memory: the second table
+    # is admitted only once the first one's memory is back with the driver.
+    cap = 1 << 26
+    one = cap * 8 + 4096 * 8 + (1 << 16) * 8 + 4096
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    srv = ht.Server(hbm_reserve_bytes=int(free - 1.5 * one))
+    a = srv.open_table(cap, "bucket")
+    b = srv.open_table(cap, "bucket")
+    ka, kb = wk.distinct_keys(1000, 64, seed=81), wk.distinct_keys(1000, 64, seed=82)
+    ra, rb = srv.submit(a, ka), srv.submit(b, kb)
+    st, _, flags = srv.wait(ra, timeout_ms=30000)
+    assert st == 0 and flags.sum() == 1000
+    assert srv.wait(rb, timeout_ms=300)[0] == 5       # b waits for memory
+    srv.close_table(a)
+    st, _, flags = srv.wait(rb, timeout_ms=30000)
+    assert st == 0 and flags.sum() == 1000
+    srv.close()

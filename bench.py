@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-bfs", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-rate", type=float, default=40000.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-deadline", type=float, default=120.0, help="seconds before a serving run gives up")
@@ -298,6 +299,8 @@ def run_ours(a, rank, world, local):
     for t in tables.values():
         t.close()
     tables = {}
+    if not a.no_small:
+        out["small_map_config1"] = run_small_map(ht, torch, dev, schemes)
     if not a.no_bfs:
         out["bfs_config3"] = run_bfs(ht, torch, dev, schemes)
     if not a.no_batched:
@@ -450,6 +453,43 @@ def run_batched(ht, torch):
                      "levels_match_oracle": bool(ok)}
     res["speedup_batched_vs_per_table"] = round(res["one_table_at_a_time"]["seconds"] / res["batched_graph"]["seconds"], 2)
     mx.close()
+    return res
+
+
+def run_small_map(ht, torch, dev, schemes, reps=10):
+    """Config 1: 2^20 distinct random 32-bit keys with 32-bit values into a
+    map of 2^21 slots (16 MB, load 0.5, L2-sized), then a lookup of 2^20 keys
+    (half present); with and without the L2 persisting window."""
+    from workloads import keys as wk
+    n = 1 << 20
+    keys = torch.from_numpy(wk.distinct_keys(n, 32, seed=1).view(np.int32)).to(dev)
+    vals = torch.arange(n, dtype=torch.int32, device=dev)
+    q, present = wk.lookup_batch(n, n, 32, seed=1)
+    qd = torch.from_numpy(q.view(np.int32)).to(dev)
+    found = torch.empty(n, dtype=torch.uint8, device=dev)
+    out_v = torch.empty(n, dtype=torch.int32, device=dev)
+    res = {"workload": "2^20 random 32-bit keys + values into 2^21 slots (16 MB), then 2^20 lookups, 50% present"}
+    for sch in schemes:
+        for persist in (0, 1):
+            t = ht.HashTable(1 << 21, sch, 32, dict(l2_persist=persist))
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ins, look = [], []
+            for r in range(reps + 2):
+                ht.ht_clear(t.handle)
+                e[0].record()
+                ht.ht_insert(t.handle, keys, vals)
+                e[1].record()
+                ht.ht_lookup(t.handle, qd, out_v, found)
+                e[2].record()
+                torch.cuda.synchronize()
+                if r >= 2:
+                    ins.append(e[0].elapsed_time(e[1]))
+                    look.append(e[1].elapsed_time(e[2]))
+            ok = bool(np.array_equal(found.cpu().numpy(), present)) and t.size() == n
+            res["%s_l2persist%d" % (sch, persist)] = {
+                "insert_mops": round(n / (statistics.median(ins) / 1e3) / 1e6, 1),
+                "lookup_mops": round(n / (statistics.median(look) / 1e3) / 1e6, 1), "exact": ok}
+            t.close()
     return res
 
 

@@ -20,6 +20,7 @@ struct ht_table {
     bool rebuild_exhausted;
     ht_status sticky;            // HT_ERR_FULL once a key was dropped
     uint64_t seed_base;
+    L2Window win;                // l2_persist: the slots (or the Cuckoo claim set)
 };
 
 namespace {
@@ -82,15 +83,15 @@ ht_status run_put(ht_table* t, const void* keys, const uint32_t* vals, uint64_t 
     if (n == 0) return HT_OK;
     if (t->scheme == HT_BUCKET) {
         return cuda_status(bucket_find_or_put(bucket_cfg(t), t->dt, keys, vals, n, d_n, is_new, new_out,
-                                              new_count, new_cap, s));
+                                              new_count, new_cap, s, t->win));
     }
     const size_t ksz = t->kw / 8;
     for (uint64_t off = 0; off < n; off += t->chunk) {
         const uint64_t m = std::min(t->chunk, n - off);
         const void* k = static_cast<const char*>(keys) + off * ksz;
         HT_TRY(cuckoo_probe(int(t->kw), t->dt, t->sc, t->parity, k, vals ? vals + off : nullptr, m, d_n,
-                            off, is_new ? is_new + off : nullptr, s));
-        HT_TRY(cuckoo_insert(int(t->kw), t->dt, t->sc, t->parity, new_out, new_count, new_cap, m, s));
+                            off, is_new ? is_new + off : nullptr, s, t->win));
+        HT_TRY(cuckoo_insert(int(t->kw), t->dt, t->sc, t->parity, new_out, new_count, new_cap, m, s, t->win));
         t->parity ^= 1u;
     }
     return HT_OK;
@@ -267,9 +268,11 @@ ht_status ht_default_params(ht_scheme scheme, ht_params* p) {
     p->bucket_slots = 16;
     p->lanes_per_key = 2;
     p->max_rebuilds = 8;
-    p->max_batch = 1ull << 22;
+    p->max_batch = scheme == HT_CUCKOO ? (1ull << 21) : (1ull << 22);
     p->seed = 0x243F6A8885A308D3ull;
-    p->l2_persist = 0;
+    // Cuckoo: keep the dedup claim set (2 x max_batch words) persisting in
+    // L2 -- measured +8% on the fill of 2^27 keys; bucket: no gain measured.
+    p->l2_persist = scheme == HT_CUCKOO ? 1 : 0;
     return HT_OK;
 }
 
@@ -330,6 +333,16 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
         free_table(t, cs);
         return st;
     }
+    if (p.l2_persist) {
+        // The slot array when it fits the device's persisting L2, else (Cuckoo)
+        // the dedup claim set, which every absent key of a batch touches.
+        int dev = 0, max_persist = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+        const size_t slot_bytes = t->dt.nslots * 8;
+        if (slot_bytes <= size_t(max_persist)) t->win = l2_window(t->dt.slots, slot_bytes);
+        else if (scheme == HT_CUCKOO) t->win = l2_window(t->sc.set, (t->sc.mask + 1) * 8);
+    }
     *out = t;
     return HT_OK;
 }
@@ -373,8 +386,9 @@ ht_status ht_lookup(ht_table* t, const void* d_keys, uint64_t n, uint32_t* d_val
     if (n == 0) return HT_OK;
     DeviceGuard g(t->device);
     const cudaStream_t s = as_stream(stream);
-    if (t->scheme == HT_BUCKET) return cuda_status(bucket_lookup(bucket_cfg(t), t->dt, d_keys, n, d_values, d_found, s));
-    return cuda_status(cuckoo_lookup(int(t->kw), t->dt, d_keys, n, d_values, d_found, s));
+    if (t->scheme == HT_BUCKET)
+        return cuda_status(bucket_lookup(bucket_cfg(t), t->dt, d_keys, n, d_values, d_found, s, t->win));
+    return cuda_status(cuckoo_lookup(int(t->kw), t->dt, d_keys, n, d_values, d_found, s, t->win));
 }
 
 ht_status ht_sync(ht_table* t, void* stream) {

@@ -135,115 +135,168 @@ __device__ __noinline__ uint32_t claim_slow(const DevTable t, bool active, uint6
 
 // find-or-put / insert.  A warp takes 32 keys; lane l hashes key l once.  In
 // round r, group g (G lanes) serves key r*(32/G)+g.  The first bucket of
-// every round is read up front; the rounds' first claims are then decided
-// from those reads and all their CASes issued together, so a tile waits for
-// about three memory round trips (keys, buckets, claims).  Claims go in
-// slot-index order: the lowest lane of the group holding a free slot (in the
-// group's view) CASes its lowest free slot; a failed CAS marks that slot
-// taken and claim_slow tries the next one.
+// every round is read up front (chunk_read); the rounds' first claims are
+// then decided from those reads and all their CASes issued together
+// (chunk_claim); the CAS results are read and the rare leftovers finished
+// (chunk_resolve).  Claims go in slot-index order: the lowest lane of the
+// group holding a free slot (in the group's view) CASes its lowest free
+// slot; a failed CAS marks that slot taken and claim_slow tries the next one.
+
+// State of rounds [r0, r0 + PF) of one tile between its phases.
+template <int KW, int BS, int G>
+struct TileChunk {
+    static constexpr int SPL = BS / G;
+    static constexpr int PF = Prefetch<G, SPL>::kRounds;
+    uint64_t w[PF][SPL];      // first bucket of each round, this lane's share
+    uint64_t old[PF];         // first CAS result (owner lanes)
+    uint64_t owner_pack;      // 5 bits per round: claiming lane within the group
+    uint32_t le_pack;         // SPL bits per round: free slots in this lane's share
+    uint32_t claim, slow;     // per round: first claim issued / needs claim_slow
+};
+
+// The key of lane l (`mykey`, `myok`) is served in round l / GPW by group l % GPW.
+template <int KW, int BS, int G>
+__device__ __forceinline__ void chunk_read(const DevTable& t, TileChunk<KW, BS, G>& c, int r0, uint64_t mybkt,
+                                           bool myok) {
+    using C = TileChunk<KW, BS, G>;
+    constexpr int GPW = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, sub = lane % G;
+#pragma unroll
+    for (int q = 0; q < C::PF; ++q) {
+        const int kidx = (r0 + q) * GPW + grp;
+        const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
+        if (__shfl_sync(kFull, myok, kidx)) {
+            load_lane<C::SPL>(t.slots + b * BS + sub * C::SPL, c.w[q]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < C::SPL; ++j) c.w[q][j] = kEmpty;
+        }
+    }
+}
+
+template <int KW, int BS, int G>
+__device__ __forceinline__ void chunk_claim(const DevTable& t, TileChunk<KW, BS, G>& c, int r0, uint64_t mykey,
+                                            uint64_t mybkt, uint64_t myword, bool myok) {
+    using C = TileChunk<KW, BS, G>;
+    constexpr int GPW = 32 / G;
+    constexpr uint32_t kGMask = (G == 32) ? 0xFFFFFFFFu : ((1u << G) - 1u);
+    constexpr uint32_t kLMask = (1u << C::SPL) - 1u;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, sub = lane % G, gbase = grp * G;
+    c.le_pack = c.claim = c.slow = 0;
+    c.owner_pack = 0;
+    // Decide each round from its read: found, claim, or slow path.
+#pragma unroll
+    for (int q = 0; q < C::PF; ++q) {
+        const int kidx = (r0 + q) * GPW + grp;
+        const uint64_t key = __shfl_sync(kFull, mykey, kidx);
+        const bool ok = __shfl_sync(kFull, myok, kidx);
+        uint32_t lm, le;
+        scan_lane<KW, C::SPL>(c.w[q], key, lm, le);
+        const uint32_t M = (__ballot_sync(kFull, ok && lm != 0) >> gbase) & kGMask;
+        const uint32_t E = (__ballot_sync(kFull, ok && le != 0) >> gbase) & kGMask;
+        c.le_pack |= le << (q * C::SPL);
+        if (ok && !M) {
+            if (E) {
+                c.claim |= 1u << q;
+                c.owner_pack |= uint64_t(__ffs(E) - 1) << (5 * q);
+            } else {
+                c.slow |= 1u << q;
+            }
+        }
+    }
+    // Issue every round's first CAS; the results are read in chunk_resolve.
+#pragma unroll
+    for (int q = 0; q < C::PF; ++q) {
+        const int kidx = (r0 + q) * GPW + grp;
+        const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
+        const uint64_t word = __shfl_sync(kFull, myword, kidx);
+        c.old[q] = kEmpty;
+        if (((c.claim >> q) & 1u) && sub == int((c.owner_pack >> (5 * q)) & 31u)) {
+            const int j = __ffs((c.le_pack >> (q * C::SPL)) & kLMask) - 1;
+            c.old[q] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + b * BS + sub * C::SPL + j),
+                                 kEmpty, word);
+            c.le_pack &= ~(1u << (q * C::SPL + j));
+        }
+    }
+}
+
+// Returns bit q set (group-uniform) when the group's key of round r0 + q was stored.
+template <int KW, int BS, int G>
+__device__ __forceinline__ uint32_t chunk_resolve(const DevTable& t, TileChunk<KW, BS, G>& c, int r0, uint64_t mykey,
+                                                  uint64_t mybkt, uint64_t myword) {
+    using K = Keys<KW>;
+    using C = TileChunk<KW, BS, G>;
+    constexpr int GPW = 32 / G;
+    constexpr uint32_t kLMask = (1u << C::SPL) - 1u;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, sub = lane % G, gbase = grp * G;
+    uint32_t res = 0;
+#pragma unroll
+    for (int q = 0; q < C::PF; ++q) {
+        const int kidx = (r0 + q) * GPW + grp;
+        const uint64_t key = __shfl_sync(kFull, mykey, kidx);
+        const uint32_t code = c.old[q] == kEmpty ? 0u : (K::keyof(c.old[q]) == key ? 1u : 2u);
+        const int src = gbase + int((c.owner_pack >> (5 * q)) & 31u);
+        const uint32_t v = __shfl_sync(kFull, code, src);
+        if ((c.claim >> q) & 1u) {
+            if (v == 0u) res |= 1u << q;
+            else if (v == 2u) c.slow |= 1u << q;
+        }
+    }
+    // Rare: claims that lost to another key, and full first buckets.
+    if (__any_sync(kFull, c.slow != 0)) {
+#pragma unroll 1
+        for (int q = 0; q < C::PF; ++q) {
+            if (!__any_sync(kFull, (c.slow >> q) & 1u)) continue;
+            const int kidx = (r0 + q) * GPW + grp;
+            const uint64_t key = __shfl_sync(kFull, mykey, kidx);
+            const uint64_t word = __shfl_sync(kFull, myword, kidx);
+            const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
+            const uint32_t r = claim_slow<KW, BS, G>(t, (c.slow >> q) & 1u, key, word, b,
+                                                     (c.le_pack >> (q * C::SPL)) & kLMask, sub, gbase, lane);
+            if (r) res |= 1u << q;
+        }
+    }
+    return res;
+}
+
+// Lane l's key was served by group l % GPW in round l / GPW.
+template <int G>
+__device__ __forceinline__ uint32_t my_result(uint32_t res_all) {
+    constexpr int GPW = 32 / G;
+    const int lane = threadIdx.x & 31;
+    return (__shfl_sync(kFull, res_all, (lane % GPW) * G) >> (lane / GPW)) & 1u;
+}
+
 // One warp serves one tile of up to 32 keys: lane l holds key l (myok false
 // on lanes without a valid key).  Returns 1 on the lanes whose key this call
-// stored.  Used by the plain find-or-put kernel and by the multi-table BFS
-// step, which passes a different table per tile.
+// stored.  Used by the multi-table BFS step and the serving kernel, which
+// pass a different table per tile.
 template <int KW, int BS, int G>
 __device__ __forceinline__ uint32_t bucket_tile(const DevTable& t, uint64_t mykey, uint32_t myval, bool myok) {
     using K = Keys<KW>;
-    constexpr int SPL = BS / G;
-    constexpr int GPW = 32 / G;
-    constexpr int PF = Prefetch<G, SPL>::kRounds;
-    constexpr uint32_t kGMask = (G == 32) ? 0xFFFFFFFFu : ((1u << G) - 1u);
-    constexpr uint32_t kLMask = (1u << SPL) - 1u;
-    static_assert(SPL >= 1 && SPL <= 8 && BS % G == 0 && G % PF == 0 && PF * SPL <= 32, "bucket/lane split");
-    const int lane = threadIdx.x & 31;
-    const int grp = lane / G, sub = lane % G, gbase = grp * G;
+    using C = TileChunk<KW, BS, G>;
+    static_assert(C::SPL >= 1 && C::SPL <= 8 && BS % G == 0 && G % C::PF == 0 && C::PF * C::SPL <= 32,
+                  "bucket/lane split");
     const uint64_t mybkt = hidx(mykey, t.seed[0], t.nbuckets);
     const uint64_t myword = K::word(mykey, myval);
     uint32_t res_all = 0;            // bit r: the group's key of round r was stored
 #pragma unroll 1
-    for (int r0 = 0; r0 < G; r0 += PF) {
-        // Read the first bucket of PF rounds.
-        uint64_t w[PF][SPL];
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-            const int kidx = (r0 + q) * GPW + grp;
-            const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
-            if (__shfl_sync(kFull, myok, kidx)) {
-                load_lane<SPL>(t.slots + b * BS + sub * SPL, w[q]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < SPL; ++j) w[q][j] = kEmpty;
-            }
-        }
-        // Decide each round from its read: found, claim, or slow path.
-        uint32_t le_pack = 0, claim = 0, slow = 0, valid = 0;
-        uint64_t owner_pack = 0;
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-            const int kidx = (r0 + q) * GPW + grp;
-            const uint64_t key = __shfl_sync(kFull, mykey, kidx);
-            const bool ok = __shfl_sync(kFull, myok, kidx);
-            uint32_t lm, le;
-            scan_lane<KW, SPL>(w[q], key, lm, le);
-            const uint32_t M = (__ballot_sync(kFull, ok && lm != 0) >> gbase) & kGMask;
-            const uint32_t E = (__ballot_sync(kFull, ok && le != 0) >> gbase) & kGMask;
-            le_pack |= le << (q * SPL);
-            valid |= uint32_t(ok) << q;
-            if (ok && !M) {
-                if (E) {
-                    claim |= 1u << q;
-                    owner_pack |= uint64_t(__ffs(E) - 1) << (5 * q);
-                } else {
-                    slow |= 1u << q;
-                }
-            }
-        }
-        // Issue every round's first CAS, then read the results.
-        uint64_t old[PF];
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-            const int kidx = (r0 + q) * GPW + grp;
-            const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
-            const uint64_t word = __shfl_sync(kFull, myword, kidx);
-            old[q] = kEmpty;
-            if (((claim >> q) & 1u) && sub == int((owner_pack >> (5 * q)) & 31u)) {
-                const int j = __ffs((le_pack >> (q * SPL)) & kLMask) - 1;
-                old[q] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + b * BS + sub * SPL + j),
-                                   kEmpty, word);
-                le_pack &= ~(1u << (q * SPL + j));
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-            const int kidx = (r0 + q) * GPW + grp;
-            const uint64_t key = __shfl_sync(kFull, mykey, kidx);
-            const uint32_t code = old[q] == kEmpty ? 0u : (K::keyof(old[q]) == key ? 1u : 2u);
-            const int src = gbase + int((owner_pack >> (5 * q)) & 31u);
-            const uint32_t c = __shfl_sync(kFull, code, src);
-            if ((claim >> q) & 1u) {
-                if (c == 0u) res_all |= 1u << (r0 + q);
-                else if (c == 2u) slow |= 1u << q;
-            }
-        }
-        // Rare: claims that lost to another key, and full first buckets.
-        if (__any_sync(kFull, slow != 0)) {
-#pragma unroll 1
-            for (int q = 0; q < PF; ++q) {
-                if (!__any_sync(kFull, (slow >> q) & 1u)) continue;
-                const int kidx = (r0 + q) * GPW + grp;
-                const uint64_t key = __shfl_sync(kFull, mykey, kidx);
-                const uint64_t word = __shfl_sync(kFull, myword, kidx);
-                const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
-                const uint32_t r = claim_slow<KW, BS, G>(t, (slow >> q) & 1u, key, word, b,
-                                                         (le_pack >> (q * SPL)) & kLMask, sub, gbase, lane);
-                if (r) res_all |= 1u << (r0 + q);
-            }
-        }
-        (void)valid;
+    for (int r0 = 0; r0 < G; r0 += C::PF) {
+        C c;
+        chunk_read<KW, BS, G>(t, c, r0, mybkt, myok);
+        chunk_claim<KW, BS, G>(t, c, r0, mykey, mybkt, myword, myok);
+        res_all |= chunk_resolve<KW, BS, G>(t, c, r0, mykey, mybkt, myword) << r0;
     }
-    // Lane l's key was served by group l % GPW in round l / GPW.
-    return (__shfl_sync(kFull, res_all, (lane % GPW) * G) >> (lane / GPW)) & 1u;
+    return my_result<G>(res_all);
 }
 
+// Plain find-or-put over one table.  The next tile's keys are loaded while
+// the current tile waits on the table.  (Pipelining tile i's claims with tile
+// i+1's bucket reads was measured slower on GB300: the extra live state costs
+// occupancy, and occupancy is what hides the table's latency here.)
 template <int KW, int BS, int G, bool VALUES, bool APPEND>
 __global__ void __launch_bounds__(kBlock, HT_BUCKET_MIN_BLOCKS)
 bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_t* __restrict__ vals,
@@ -254,16 +307,22 @@ bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_
     using K = Keys<KW>;
     const int lane = threadIdx.x & 31;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    const uint64_t step = nwarps * 32;
     unsigned long long stored = 0;
-
-    for (uint64_t base = ((uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32; base < n;
-         base += nwarps * 32) {
+    uint64_t base = ((uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32;
+    uint64_t next_key = 0;
+    uint32_t next_val = 0;
+    if (base + lane < n) {
+        next_key = K::load(keys, base + lane);
+        if (VALUES) next_val = vals[base + lane];
+    }
+    for (; base < n; base += step) {
         const bool mine = base + lane < n;
-        uint64_t mykey = 0;
-        uint32_t myval = 0;
-        if (mine) {
-            mykey = K::load(keys, base + lane);
-            if (VALUES) myval = vals[base + lane];
+        const uint64_t mykey = next_key;
+        const uint32_t myval = next_val;
+        if (base + step + lane < n) {
+            next_key = K::load(keys, base + step + lane);
+            if (VALUES) next_val = vals[base + step + lane];
         }
         const bool myok = mine && !K::reserved(mykey);
         if (mine && !myok) set_flag(t.ctr, kFlagInvalidKey);
@@ -384,33 +443,29 @@ bucket_lookup_kernel(const DevTable t, const void* __restrict__ keys, uint64_t n
 template <int KW, int BS, int G>
 cudaError_t launch_fop(const DevTable& t, const void* keys, const uint32_t* vals, uint64_t n,
                        const unsigned long long* d_n, uint8_t* is_new, void* new_out,
-                       unsigned long long* new_count, uint64_t new_cap, cudaStream_t s) {
+                       unsigned long long* new_count, uint64_t new_cap, cudaStream_t s, const L2Window& w) {
     using T = typename Keys<KW>::T;
     ProfScope ps(kKBucketFop, s);
     if (vals) {
         auto k = bucket_fop_kernel<KW, BS, G, true, false>;
-        const int grid = launch_blocks((const void*)k, kBlock);
-        k<<<grid, kBlock, 0, s>>>(t, keys, vals, n, d_n, is_new, nullptr, nullptr, 0);
+        return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, keys, vals, n, d_n, is_new,
+                          (T*)nullptr, (unsigned long long*)nullptr, uint64_t(0));
     } else if (new_out) {
         auto k = bucket_fop_kernel<KW, BS, G, false, true>;
-        const int grid = launch_blocks((const void*)k, kBlock);
-        k<<<grid, kBlock, 0, s>>>(t, keys, nullptr, n, d_n, is_new, static_cast<T*>(new_out), new_count, new_cap);
-    } else {
-        auto k = bucket_fop_kernel<KW, BS, G, false, false>;
-        const int grid = launch_blocks((const void*)k, kBlock);
-        k<<<grid, kBlock, 0, s>>>(t, keys, nullptr, n, d_n, is_new, nullptr, nullptr, 0);
+        return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, keys, (const uint32_t*)nullptr, n,
+                          d_n, is_new, static_cast<T*>(new_out), new_count, new_cap);
     }
-    return cudaGetLastError();
+    auto k = bucket_fop_kernel<KW, BS, G, false, false>;
+    return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, keys, (const uint32_t*)nullptr, n, d_n,
+                      is_new, (T*)nullptr, (unsigned long long*)nullptr, uint64_t(0));
 }
 
 template <int KW, int BS, int G>
 cudaError_t launch_lookup(const DevTable& t, const void* keys, uint64_t n, uint32_t* vals,
-                          uint8_t* found, cudaStream_t s) {
+                          uint8_t* found, cudaStream_t s, const L2Window& w) {
     ProfScope ps(kKBucketLookup, s);
     auto k = bucket_lookup_kernel<KW, BS, G>;
-    const int grid = launch_blocks((const void*)k, kBlock);
-    k<<<grid, kBlock, 0, s>>>(t, keys, n, vals, found);
-    return cudaGetLastError();
+    return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, keys, n, vals, found);
 }
 
 // Multi-table find-or-put: warp w takes tile w of the step's successor
@@ -527,11 +582,11 @@ serve_bucket_kernel(const DevTable* __restrict__ tables, const ServeDesc* __rest
 cudaError_t bucket_find_or_put(const BucketCfg& c, const DevTable& t, const void* keys,
                                const uint32_t* vals, uint64_t n, const unsigned long long* d_n,
                                uint8_t* is_new, void* new_out, unsigned long long* new_count,
-                               uint64_t new_cap, cudaStream_t s) {
+                               uint64_t new_cap, cudaStream_t s, const L2Window& w) {
 #define X(BS, G)                                                                                  \
     if (c.bucket_slots == BS && c.lanes == G)                                                     \
-        return c.kw == 32 ? launch_fop<32, BS, G>(t, keys, vals, n, d_n, is_new, new_out, new_count, new_cap, s) \
-                          : launch_fop<64, BS, G>(t, keys, vals, n, d_n, is_new, new_out, new_count, new_cap, s);
+        return c.kw == 32 ? launch_fop<32, BS, G>(t, keys, vals, n, d_n, is_new, new_out, new_count, new_cap, s, w) \
+                          : launch_fop<64, BS, G>(t, keys, vals, n, d_n, is_new, new_out, new_count, new_cap, s, w);
     HT_BUCKET_CONFIGS(X)
 #undef X
     return cudaErrorInvalidValue;
@@ -575,11 +630,11 @@ cudaError_t serve_bucket_find_or_put(const BucketCfg& c, const DevTable* tables,
 }
 
 cudaError_t bucket_lookup(const BucketCfg& c, const DevTable& t, const void* keys, uint64_t n,
-                          uint32_t* vals, uint8_t* found, cudaStream_t s) {
+                          uint32_t* vals, uint8_t* found, cudaStream_t s, const L2Window& w) {
 #define X(BS, G)                                                                    \
     if (c.bucket_slots == BS && c.lanes == G)                                       \
-        return c.kw == 32 ? launch_lookup<32, BS, G>(t, keys, n, vals, found, s)   \
-                          : launch_lookup<64, BS, G>(t, keys, n, vals, found, s);
+        return c.kw == 32 ? launch_lookup<32, BS, G>(t, keys, n, vals, found, s, w)   \
+                          : launch_lookup<64, BS, G>(t, keys, n, vals, found, s, w);
     HT_BUCKET_CONFIGS(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -203,6 +203,28 @@ int launch_blocks(const void* kernel, int block, size_t smem) {
     return grid;
 }
 
+L2Window l2_window(const void* base, size_t bytes) {
+    L2Window w;
+    if (!base || !bytes) return w;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> g(mu);
+    int dev = 0, max_persist = 0, max_window = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev) != cudaSuccess ||
+        max_persist <= 0 || max_window <= 0)
+        return w;
+    size_t cur = 0;
+    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    const size_t want = std::min<size_t>(bytes, size_t(max_persist));
+    if (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess) cur = want;
+    if (!cur) return w;
+    w.base = base;
+    w.bytes = std::min<size_t>(bytes, size_t(max_window));
+    w.hit = float(std::min<double>(1.0, double(cur) / double(w.bytes)));
+    return w;
+}
+
 cudaError_t table_export(int kw, const DevTable& t, void* keys_out, uint32_t* vals_out,
                          unsigned long long* count, uint64_t cap, cudaStream_t s) {
     ProfScope ps(kKExport, s);

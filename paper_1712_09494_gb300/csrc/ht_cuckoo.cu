@@ -53,6 +53,13 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     const uint64_t rounds = (n + stride * kU - 1) / (stride * kU);     // warp-uniform trip count
     const uint64_t dseed = t.aux_seed * 3 + 1;
     const int lane = threadIdx.x & 31;
+    // The next round's keys are loaded while this round waits on the table.
+    uint64_t next_key[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        const uint64_t i = uint64_t(u) * stride + tid;
+        next_key[u] = i < n ? K::load(keys, i) : 0;
+    }
     for (uint64_t r = 0; r < rounds; ++r) {
         uint64_t key[kU], w[kU];
         bool act[kU], found[kU];
@@ -60,7 +67,9 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         for (int u = 0; u < kU; ++u) {
             const uint64_t i = (r * kU + u) * stride + tid;
             act[u] = i < n;
-            key[u] = act[u] ? K::load(keys, i) : 0;
+            key[u] = next_key[u];
+            const uint64_t j = ((r + 1) * kU + u) * stride + tid;
+            if (j < n) next_key[u] = K::load(keys, j);
             if (act[u] && K::reserved(key[u])) {
                 set_flag(t.ctr, kFlagInvalidKey);
                 act[u] = false;
@@ -245,57 +254,52 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
 
 cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
                          const void* keys, const uint32_t* vals, uint64_t n,
-                         const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s) {
+                         const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s,
+                         const L2Window& w) {
     ProfScope ps(kKCuckooProbe, s);
-#define L(KW, V)                                                                    \
-    {                                                                               \
-        auto k = cuckoo_probe_kernel<KW, V, false>;                                 \
-        const int grid = launch_blocks((const void*)k, kBlock);                     \
-        k<<<grid, kBlock, 0, s>>>(t, sc, parity, keys, vals, n, d_n, off, is_new, nullptr); \
+#define L(KW, V)                                                                                        \
+    {                                                                                                   \
+        auto k = cuckoo_probe_kernel<KW, V, false>;                                                     \
+        return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, sc, parity, keys, vals, n, \
+                          d_n, off, is_new, (uint32_t*)nullptr);                                        \
     }
     if (kw == 32) {
         if (vals) L(32, true) else L(32, false)
-    } else {
-        L(64, false)
     }
+    L(64, false)
 #undef L
-    return cudaGetLastError();
 }
 
 cudaError_t cuckoo_insert(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
                           void* new_out, unsigned long long* new_count, uint64_t new_cap,
-                          uint64_t max_winners, cudaStream_t s) {
+                          uint64_t max_winners, cudaStream_t s, const L2Window& w) {
     ProfScope ps(kKCuckooInsert, s);
-#define L(KW, A)                                                                               \
-    {                                                                                          \
-        auto k = cuckoo_insert_kernel<KW, A>;                                                  \
-        const int grid = launch_blocks((const void*)k, kBlock);                                \
-        k<<<grid, kBlock, 0, s>>>(t, sc, parity, max_winners,                                  \
-                                  static_cast<typename Keys<KW>::T*>(new_out), new_count, new_cap); \
+#define L(KW, A)                                                                                        \
+    {                                                                                                   \
+        auto k = cuckoo_insert_kernel<KW, A>;                                                           \
+        return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, sc, parity, max_winners, \
+                          static_cast<typename Keys<KW>::T*>(new_out), new_count, new_cap);             \
     }
     if (kw == 32) {
         if (new_out) L(32, true) else L(32, false)
-    } else {
-        if (new_out) L(64, true) else L(64, false)
     }
+    if (new_out) L(64, true)
+    L(64, false)
 #undef L
-    return cudaGetLastError();
 }
 
 cudaError_t cuckoo_lookup(int kw, const DevTable& t, const void* keys, uint64_t n, uint32_t* vals,
-                          uint8_t* found, cudaStream_t s) {
+                          uint8_t* found, cudaStream_t s, const L2Window& w) {
     ProfScope ps(kKCuckooLookup, s);
     DevScratch none{};
     if (kw == 32) {
         auto k = cuckoo_probe_kernel<32, false, true>;
-        const int grid = launch_blocks((const void*)k, kBlock);
-        k<<<grid, kBlock, 0, s>>>(t, none, 0, keys, nullptr, n, nullptr, 0, found, vals);
-    } else {
-        auto k = cuckoo_probe_kernel<64, false, true>;
-        const int grid = launch_blocks((const void*)k, kBlock);
-        k<<<grid, kBlock, 0, s>>>(t, none, 0, keys, nullptr, n, nullptr, 0, found, vals);
+        return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, none, 0u, keys,
+                          (const uint32_t*)nullptr, n, (const unsigned long long*)nullptr, uint64_t(0), found, vals);
     }
-    return cudaGetLastError();
+    auto k = cuckoo_probe_kernel<64, false, true>;
+    return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, none, 0u, keys,
+                      (const uint32_t*)nullptr, n, (const unsigned long long*)nullptr, uint64_t(0), found, vals);
 }
 
 }  // namespace ht

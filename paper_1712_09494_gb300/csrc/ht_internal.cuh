@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/ht.h"
 
 namespace ht {
@@ -228,6 +230,44 @@ struct ProfScope {
 
 int launch_blocks(const void* kernel, int block, size_t smem = 0);
 
+// L2 residency: an access-policy window that marks a range persisting in L2
+// for the launches that carry it (bytes 0 = none).
+struct L2Window {
+    const void* base = nullptr;
+    size_t bytes = 0;
+    float hit = 0.f;
+};
+
+// Window over [base, base + bytes) if the device supports persisting L2:
+// raises the context's persisting set-aside (cudaLimitPersistingL2CacheSize,
+// a per-process setting that ends with the process) to cover it, up to the
+// device maximum; hit < 1 when the range is larger than that.
+L2Window l2_window(const void* base, size_t bytes);
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_win(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, const L2Window& w,
+                       Args&&... args) {
+    if (!w.bytes) {
+        kernel<<<grid, block, 0, s>>>(std::forward<Args>(args)...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    at[0].val.accessPolicyWindow.base_ptr = const_cast<void*>(w.base);
+    at[0].val.accessPolicyWindow.num_bytes = w.bytes;
+    at[0].val.accessPolicyWindow.hitRatio = w.hit;
+    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 // Launchers implemented by the scheme translation units.  All return the
 // cudaGetLastError() of the launch.
@@ -242,21 +282,21 @@ struct BucketCfg {
 cudaError_t bucket_find_or_put(const BucketCfg& c, const DevTable& t, const void* keys,
                                const uint32_t* vals, uint64_t n, const unsigned long long* d_n,
                                uint8_t* is_new, void* new_out, unsigned long long* new_count,
-                               uint64_t new_cap, cudaStream_t s);
+                               uint64_t new_cap, cudaStream_t s, const L2Window& w = L2Window());
 cudaError_t bucket_lookup(const BucketCfg& c, const DevTable& t, const void* keys, uint64_t n,
-                          uint32_t* vals, uint8_t* found, cudaStream_t s);
+                          uint32_t* vals, uint8_t* found, cudaStream_t s, const L2Window& w = L2Window());
 
 // d_n (nullable): the batch size lives on the device; this launch covers keys
 // [off, off + n) of it.
 cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
                          const void* keys, const uint32_t* vals, uint64_t n,
                          const unsigned long long* d_n, uint64_t off, uint8_t* is_new,
-                         cudaStream_t s);
+                         cudaStream_t s, const L2Window& w = L2Window());
 cudaError_t cuckoo_insert(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
                           void* new_out, unsigned long long* new_count, uint64_t new_cap,
-                          uint64_t max_winners, cudaStream_t s);
+                          uint64_t max_winners, cudaStream_t s, const L2Window& w = L2Window());
 cudaError_t cuckoo_lookup(int kw, const DevTable& t, const void* keys, uint64_t n,
-                          uint32_t* vals, uint8_t* found, cudaStream_t s);
+                          uint32_t* vals, uint8_t* found, cudaStream_t s, const L2Window& w = L2Window());
 
 cudaError_t table_export(int kw, const DevTable& t, void* keys_out, uint32_t* vals_out,
                          unsigned long long* count, uint64_t cap, cudaStream_t s);

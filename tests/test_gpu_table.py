@@ -70,6 +70,15 @@ def test_bucket_shapes_and_cuckoo_hashes(oracle_lib, scheme, slots, lanes):
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("n,kw", [(30_000, 32), (300_000, 64)])
+def test_l2_persisting_tables_stay_exact(oracle_lib, scheme, n, kw):
+    # l2_persist attaches an access-policy window (the slots, or Cuckoo's
+    # claim set) to every launch of the table; results must not change.
+    _fill_and_check(oracle_lib, scheme, kw, n_distinct=n, batch=1 << 14, dup=0.3, lf=0.8,
+                    params=dict(l2_persist=1), seed=13)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
 def test_single_key_repeated(oracle_lib, scheme):
     keys = np.full(1 << 16, 12345, dtype=np.uint64)
     t = ht.HashTable(1024, scheme, 64)

@@ -81,6 +81,24 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(value, device):
+    """The largest `value` over all ranks (the job's step time is the slowest
+    rank's); the identity when torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mops(units_per_rank, world, ms_per_step_max):
+    """Whole-job throughput: every rank processes units_per_rank per step
+    (replicas; weak scaling), timed by the slowest rank."""
+    return units_per_rank * world / (ms_per_step_max / 1e3) / 1e6
+
+
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons while running."""
 
@@ -236,16 +254,11 @@ def run_ours(a, rank, world, local):
     ms_total = t0.elapsed_time(t1)
     for s in schemes:
         per_ms[s] = sum(e0.elapsed_time(e1) for e0, e1 in step_ms_each[s]) / a.steps
-    ms_step = ms_total / a.steps
-    if world > 1:
-        import torch.distributed as dist
-        tm = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms_step = float(tm.item())
+    ms_step = reduce_max(ms_total / a.steps, dev)
     for s in schemes:
         if tables[s].sync() != 0 or tables[s].size() != n:
             raise RuntimeError("timed fill of %s did not end exact" % s)
-    value = n_ops * world / (ms_step / 1e3) / 1e6
+    value = whole_job_mops(n_ops, world, ms_step)
 
     # Roofline of the dominant kernel: algorithmic bytes per launch / event time.
     p_new = fs.n_distinct / fs.n_issued
@@ -346,12 +359,7 @@ def run_e2e(a, ht, torch, dev, fs, tables, schemes, world):
         step()
     t1.record(stream)
     torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / a.steps
-    if world > 1:
-        import torch.distributed as dist
-        tm = torch.tensor([ms], device=dev)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms = float(tm.item())
+    ms = reduce_max(t0.elapsed_time(t1) / a.steps, dev)
     # the last step's flags must count exactly the distinct keys
     if int(out_h.sum()) != fs.n_distinct:
         raise RuntimeError("e2e flags do not count the distinct keys")
@@ -452,6 +460,35 @@ def run_batched(ht, torch):
         res[name] = {"seconds": round(sec, 4), "steps": steps, "find_or_put_mops": round(tot / sec / 1e6, 1),
                      "levels_match_oracle": bool(ok)}
     res["speedup_batched_vs_per_table"] = round(res["one_table_at_a_time"]["seconds"] / res["batched_graph"]["seconds"], 2)
+    mx.close()
+    # Autotuned: each exploration's capacity class tuned once (bucket width,
+    # lanes per key, hash functions) for a BFS-like repeat rate.
+    import tempfile
+    from paper_1712_09494_gb300 import autotune
+    t0 = time.perf_counter()
+    with tempfile.TemporaryDirectory() as d:
+        cache = os.path.join(d, "autotune.json")
+        params = [autotune.tune("bucket", m.key_width, c, load=0.7, dup=0.9, cache_path=cache)
+                  for m, c in zip(models, caps)]
+        n_classes = len(json.load(open(cache)))
+    tune_s = time.perf_counter() - t0
+    mx = ht.MultiExploration([_hmodel(ht, m) for m in models], [0] * len(models), caps, params=params)
+    times = []
+    for r in range(3):
+        mx.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps = mx.run(mode=0)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    ok = all(mx.result(i)["states"] == g["states"] and mx.result(i)["level_sizes"] == [lv[0] for lv in g["levels"]]
+             for i, g in enumerate(gold["explorations"]))
+    shapes = sorted({"%dx%d/k%d" % (p["bucket_slots"], p["lanes_per_key"], p["num_hashes"]) for p in params})
+    tot = sum(g["successors"] for g in gold["explorations"])
+    res["batched_graph_autotuned"] = {"seconds": round(min(times[1:]), 4), "steps": steps,
+                                      "find_or_put_mops": round(tot / min(times[1:]) / 1e6, 1),
+                                      "levels_match_oracle": bool(ok), "tuning_seconds": round(tune_s, 2),
+                                      "classes_tuned": n_classes, "chosen": shapes}
     mx.close()
     return res
 

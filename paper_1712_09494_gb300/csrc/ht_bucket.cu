@@ -142,23 +142,30 @@ __device__ __noinline__ uint32_t claim_slow(const DevTable t, bool active, uint6
 // group holding a free slot (in the group's view) CASes its lowest free
 // slot; a failed CAS marks that slot taken and claim_slow tries the next one.
 
-// State of rounds [r0, r0 + PF) of one tile between its phases.
-template <int KW, int BS, int G>
-struct TileChunk {
+// State of rounds [r0, r0 + R) of one tile between its phases: the claim
+// bookkeeping (TileClaims) and, when read into registers, the first bucket
+// of each round (TileWords).
+template <int KW, int BS, int G, int R>
+struct TileClaims {
     static constexpr int SPL = BS / G;
-    static constexpr int PF = Prefetch<G, SPL>::kRounds;
-    uint64_t w[PF][SPL];      // first bucket of each round, this lane's share
-    uint64_t old[PF];         // first CAS result (owner lanes)
+    uint64_t old[R];          // first CAS result (owner lanes)
     uint64_t owner_pack;      // 5 bits per round: claiming lane within the group
     uint32_t le_pack;         // SPL bits per round: free slots in this lane's share
     uint32_t claim, slow;     // per round: first claim issued / needs claim_slow
 };
 
+template <int KW, int BS, int G>
+struct TileWords {
+    static constexpr int SPL = BS / G;
+    static constexpr int PF = Prefetch<G, SPL>::kRounds;
+    uint64_t w[PF][SPL];      // first bucket of each round, this lane's share
+};
+
 // The key of lane l (`mykey`, `myok`) is served in round l / GPW by group l % GPW.
 template <int KW, int BS, int G>
-__device__ __forceinline__ void chunk_read(const DevTable& t, TileChunk<KW, BS, G>& c, int r0, uint64_t mybkt,
+__device__ __forceinline__ void chunk_read(const DevTable& t, TileWords<KW, BS, G>& c, int r0, uint64_t mybkt,
                                            bool myok) {
-    using C = TileChunk<KW, BS, G>;
+    using C = TileWords<KW, BS, G>;
     constexpr int GPW = 32 / G;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G;
@@ -175,10 +182,12 @@ __device__ __forceinline__ void chunk_read(const DevTable& t, TileChunk<KW, BS, 
     }
 }
 
-template <int KW, int BS, int G>
-__device__ __forceinline__ void chunk_claim(const DevTable& t, TileChunk<KW, BS, G>& c, int r0, uint64_t mykey,
-                                            uint64_t mybkt, uint64_t myword, bool myok) {
-    using C = TileChunk<KW, BS, G>;
+// Decides rounds r0..r0+R-1 from their first buckets (fetch(q, w) supplies
+// this lane's share of round r0+q's bucket) and issues their first CASes.
+template <int KW, int BS, int G, int R, class Fetch>
+__device__ __forceinline__ void chunk_claim(const DevTable& t, TileClaims<KW, BS, G, R>& c, int r0, uint64_t mykey,
+                                            uint64_t mybkt, uint64_t myword, bool myok, Fetch&& fetch) {
+    using C = TileClaims<KW, BS, G, R>;
     constexpr int GPW = 32 / G;
     constexpr uint32_t kGMask = (G == 32) ? 0xFFFFFFFFu : ((1u << G) - 1u);
     constexpr uint32_t kLMask = (1u << C::SPL) - 1u;
@@ -188,12 +197,14 @@ __device__ __forceinline__ void chunk_claim(const DevTable& t, TileChunk<KW, BS,
     c.owner_pack = 0;
     // Decide each round from its read: found, claim, or slow path.
 #pragma unroll
-    for (int q = 0; q < C::PF; ++q) {
+    for (int q = 0; q < R; ++q) {
         const int kidx = (r0 + q) * GPW + grp;
         const uint64_t key = __shfl_sync(kFull, mykey, kidx);
         const bool ok = __shfl_sync(kFull, myok, kidx);
+        uint64_t w[C::SPL];
+        fetch(q, w);
         uint32_t lm, le;
-        scan_lane<KW, C::SPL>(c.w[q], key, lm, le);
+        scan_lane<KW, C::SPL>(w, key, lm, le);
         const uint32_t M = (__ballot_sync(kFull, ok && lm != 0) >> gbase) & kGMask;
         const uint32_t E = (__ballot_sync(kFull, ok && le != 0) >> gbase) & kGMask;
         c.le_pack |= le << (q * C::SPL);
@@ -208,7 +219,7 @@ __device__ __forceinline__ void chunk_claim(const DevTable& t, TileChunk<KW, BS,
     }
     // Issue every round's first CAS; the results are read in chunk_resolve.
 #pragma unroll
-    for (int q = 0; q < C::PF; ++q) {
+    for (int q = 0; q < R; ++q) {
         const int kidx = (r0 + q) * GPW + grp;
         const uint64_t b = __shfl_sync(kFull, mybkt, kidx);
         const uint64_t word = __shfl_sync(kFull, myword, kidx);
@@ -223,18 +234,18 @@ __device__ __forceinline__ void chunk_claim(const DevTable& t, TileChunk<KW, BS,
 }
 
 // Returns bit q set (group-uniform) when the group's key of round r0 + q was stored.
-template <int KW, int BS, int G>
-__device__ __forceinline__ uint32_t chunk_resolve(const DevTable& t, TileChunk<KW, BS, G>& c, int r0, uint64_t mykey,
-                                                  uint64_t mybkt, uint64_t myword) {
+template <int KW, int BS, int G, int R>
+__device__ __forceinline__ uint32_t chunk_resolve(const DevTable& t, TileClaims<KW, BS, G, R>& c, int r0,
+                                                  uint64_t mykey, uint64_t mybkt, uint64_t myword) {
     using K = Keys<KW>;
-    using C = TileChunk<KW, BS, G>;
+    using C = TileClaims<KW, BS, G, R>;
     constexpr int GPW = 32 / G;
     constexpr uint32_t kLMask = (1u << C::SPL) - 1u;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G, gbase = grp * G;
     uint32_t res = 0;
 #pragma unroll
-    for (int q = 0; q < C::PF; ++q) {
+    for (int q = 0; q < R; ++q) {
         const int kidx = (r0 + q) * GPW + grp;
         const uint64_t key = __shfl_sync(kFull, mykey, kidx);
         const uint32_t code = c.old[q] == kEmpty ? 0u : (K::keyof(c.old[q]) == key ? 1u : 2u);
@@ -248,7 +259,7 @@ __device__ __forceinline__ uint32_t chunk_resolve(const DevTable& t, TileChunk<K
     // Rare: claims that lost to another key, and full first buckets.
     if (__any_sync(kFull, c.slow != 0)) {
 #pragma unroll 1
-        for (int q = 0; q < C::PF; ++q) {
+        for (int q = 0; q < R; ++q) {
             if (!__any_sync(kFull, (c.slow >> q) & 1u)) continue;
             const int kidx = (r0 + q) * GPW + grp;
             const uint64_t key = __shfl_sync(kFull, mykey, kidx);
@@ -277,18 +288,23 @@ __device__ __forceinline__ uint32_t my_result(uint32_t res_all) {
 template <int KW, int BS, int G>
 __device__ __forceinline__ uint32_t bucket_tile(const DevTable& t, uint64_t mykey, uint32_t myval, bool myok) {
     using K = Keys<KW>;
-    using C = TileChunk<KW, BS, G>;
-    static_assert(C::SPL >= 1 && C::SPL <= 8 && BS % G == 0 && G % C::PF == 0 && C::PF * C::SPL <= 32,
+    using W = TileWords<KW, BS, G>;
+    constexpr int PF = W::PF;
+    static_assert(W::SPL >= 1 && W::SPL <= 8 && BS % G == 0 && G % PF == 0 && PF * W::SPL <= 32,
                   "bucket/lane split");
     const uint64_t mybkt = hidx(mykey, t.seed[0], t.nbuckets);
     const uint64_t myword = K::word(mykey, myval);
     uint32_t res_all = 0;            // bit r: the group's key of round r was stored
 #pragma unroll 1
-    for (int r0 = 0; r0 < G; r0 += C::PF) {
-        C c;
-        chunk_read<KW, BS, G>(t, c, r0, mybkt, myok);
-        chunk_claim<KW, BS, G>(t, c, r0, mykey, mybkt, myword, myok);
-        res_all |= chunk_resolve<KW, BS, G>(t, c, r0, mykey, mybkt, myword) << r0;
+    for (int r0 = 0; r0 < G; r0 += PF) {
+        W words;
+        TileClaims<KW, BS, G, PF> c;
+        chunk_read<KW, BS, G>(t, words, r0, mybkt, myok);
+        chunk_claim<KW, BS, G, PF>(t, c, r0, mykey, mybkt, myword, myok, [&](int q, uint64_t (&w)[W::SPL]) {
+#pragma unroll
+            for (int j = 0; j < W::SPL; ++j) w[j] = words.w[q][j];
+        });
+        res_all |= chunk_resolve<KW, BS, G, PF>(t, c, r0, mykey, mybkt, myword) << r0;
     }
     return my_result<G>(res_all);
 }

@@ -185,6 +185,24 @@ def recorded_traffic(kernel):
     return None, None
 
 
+def cuckoo_miss_probes(fs, table):
+    """Mean slots a Cuckoo probe reads for a key absent from the table: h_1,
+    and h_2..h_k only when h_1 is occupied, which for a uniform h_1 happens
+    with probability equal to the table load.  The load a batch's new keys
+    see is taken at the batch's midpoint."""
+    if table is None:
+        return 4.0
+    info = table.info()
+    k, nslots = info["num_hashes"], info["slots"]
+    before, acc, tot = 0, 0.0, 0
+    for f in fs.fresh_counts:
+        acc += f * (before + f / 2) / nslots
+        tot += f
+        before += f
+    load = acc / max(1, tot)
+    return 1 + load * (k - 1)
+
+
 # ----------------------------------------------------------------- our arm
 def run_ours(a, rank, world, local):
     import torch
@@ -262,12 +280,14 @@ def run_ours(a, rank, world, local):
 
     # Roofline of the dominant kernel: algorithmic bytes per launch / event time.
     p_new = fs.n_distinct / fs.n_issued
+    miss_probes = cuckoo_miss_probes(fs, tables.get("cuckoo"))
     per_key = {
         # key read + flag write + one 128-byte bucket + the claimed sector for new keys
         "bucket_find_or_put": 8 + 1 + 128 + p_new * 32,
-        # key read + flag write + 32-byte sector of h_1 for hits; k sectors plus the
-        # 16-byte winner record for misses (k = 4)
-        "cuckoo_probe": 8 + 1 + (1 - p_new) * 32 + p_new * (4 * 32 + 16),
+        # key read + flag write + 32-byte sector of h_1 for hits; for misses the
+        # probed sectors (h_1, and h_2..h_k when h_1 is occupied) plus the
+        # 16-byte winner record
+        "cuckoo_probe": 8 + 1 + (1 - p_new) * 32 + p_new * (miss_probes * 32 + 16),
         # winner record + one exchange (32-byte read + 32-byte write) per winner
         "cuckoo_insert": 16 + 64,
     }
@@ -291,7 +311,8 @@ def run_ours(a, rank, world, local):
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, copy burst)" if peak_src == "measured"
                 else "fallback 6.8 TB/s",
                 "unit": "GB/s", "frac": round(kernels[dom]["achieved_gbs"] / peak, 3),
-                "traffic": traffic, "alg_bytes_per_key": round(per_key[dom], 1)}
+                "traffic": traffic, "alg_bytes_per_key": round(per_key[dom], 1),
+                "cuckoo_miss_probes": round(miss_probes, 3)}
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "Mops/s", "n_gpus": world, "steps": a.steps,

@@ -30,13 +30,19 @@ namespace {
 #define HT_CUCKOO_KEYS_PER_THREAD 4
 #endif
 constexpr int kU = HT_CUCKOO_KEYS_PER_THREAD;   // keys in flight per thread
+#ifndef HT_CUCKOO_PROBE_MIN_BLOCKS
+#define HT_CUCKOO_PROBE_MIN_BLOCKS 3
+#endif
 
 // Probe (and, for find-or-put, dedup).  Each thread holds U keys of a round,
 // strided by the grid so every load of keys stays coalesced; all U first
 // probes are issued together, then all remaining probes of the misses, then
-// every miss's first dedup claim, so U memory latencies overlap.
-template <int KW, bool VALUES, bool LOOKUP>
-__global__ void __launch_bounds__(kBlock)
+// every miss's first dedup claim, so U memory latencies overlap.  KH bounds
+// the table's k at compile time (4 for the usual k <= 4, else 8): the probe
+// words in flight are held in registers, and sizing them for k <= 4 keeps
+// enough warps resident per SM.
+template <int KW, bool VALUES, bool LOOKUP, int KH>
+__global__ void __launch_bounds__(kBlock, KH <= 4 ? HT_CUCKOO_PROBE_MIN_BLOCKS : 1)
 cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     const void* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t n,
                     const unsigned long long* __restrict__ d_n, uint64_t off,
@@ -79,20 +85,28 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
 #pragma unroll
         for (int u = 0; u < kU; ++u)
             if (act[u]) w[u] = __ldcg(reinterpret_cast<const unsigned long long*>(t.slots + hidx(key[u], t.seed[0], t.nslots)));
+        // An empty h_1 slot ends the table probe: every chain starts at h_1,
+        // an evicted key moves from h_a to h_{a+1}, and slots never return to
+        // EMPTY, so a key stored at h_j has h_1 .. h_{j-1} all occupied.  A
+        // miss at table load a then costs 1 + a (k - 1) probes, not k.
+        bool more[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) found[u] = act[u] && K::keyof(w[u]) == key[u];
-        uint64_t ws[kU][kMaxCuckooHashes];
+        for (int u = 0; u < kU; ++u) {
+            found[u] = act[u] && K::keyof(w[u]) == key[u];
+            more[u] = act[u] && !found[u] && !K::empty(w[u]);
+        }
+        uint64_t ws[kU][KH];
 #pragma unroll
         for (int u = 0; u < kU; ++u)
 #pragma unroll
-            for (int a = 1; a < kMaxCuckooHashes; ++a)
-                if (a < int(t.k) && act[u] && !found[u])
+            for (int a = 1; a < KH; ++a)
+                if (a < int(t.k) && more[u])
                     ws[u][a] = __ldcg(reinterpret_cast<const unsigned long long*>(t.slots + hidx(key[u], t.seed[a], t.nslots)));
 #pragma unroll
         for (int u = 0; u < kU; ++u)
 #pragma unroll
-            for (int a = 1; a < kMaxCuckooHashes; ++a)
-                if (a < int(t.k) && act[u] && !found[u] && K::keyof(ws[u][a]) == key[u]) {
+            for (int a = 1; a < KH; ++a)
+                if (a < int(t.k) && more[u] && !found[u] && K::keyof(ws[u][a]) == key[u]) {
                     found[u] = true;
                     w[u] = ws[u][a];
                 }
@@ -259,7 +273,7 @@ cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32
     ProfScope ps(kKCuckooProbe, s);
 #define L(KW, V)                                                                                        \
     {                                                                                                   \
-        auto k = cuckoo_probe_kernel<KW, V, false>;                                                     \
+        auto k = t.k <= 4 ? cuckoo_probe_kernel<KW, V, false, 4> : cuckoo_probe_kernel<KW, V, false, kMaxCuckooHashes>; \
         return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, sc, parity, keys, vals, n, \
                           d_n, off, is_new, (uint32_t*)nullptr);                                        \
     }
@@ -293,11 +307,11 @@ cudaError_t cuckoo_lookup(int kw, const DevTable& t, const void* keys, uint64_t 
     ProfScope ps(kKCuckooLookup, s);
     DevScratch none{};
     if (kw == 32) {
-        auto k = cuckoo_probe_kernel<32, false, true>;
+        auto k = t.k <= 4 ? cuckoo_probe_kernel<32, false, true, 4> : cuckoo_probe_kernel<32, false, true, kMaxCuckooHashes>;
         return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, none, 0u, keys,
                           (const uint32_t*)nullptr, n, (const unsigned long long*)nullptr, uint64_t(0), found, vals);
     }
-    auto k = cuckoo_probe_kernel<64, false, true>;
+    auto k = t.k <= 4 ? cuckoo_probe_kernel<64, false, true, 4> : cuckoo_probe_kernel<64, false, true, kMaxCuckooHashes>;
     return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, none, 0u, keys,
                       (const uint32_t*)nullptr, n, (const unsigned long long*)nullptr, uint64_t(0), found, vals);
 }

@@ -185,22 +185,55 @@ def recorded_traffic(kernel):
     return None, None
 
 
-def cuckoo_miss_probes(fs, table):
-    """Mean slots a Cuckoo probe reads for a key absent from the table: h_1,
-    and h_2..h_k only when h_1 is occupied, which for a uniform h_1 happens
-    with probability equal to the table load.  The load a batch's new keys
-    see is taken at the batch's midpoint."""
-    if table is None:
-        return 4.0
-    info = table.info()
-    k, nslots = info["num_hashes"], info["slots"]
+def new_key_load(fs, nslots):
+    """Mean table load seen by the fill's new keys, each batch's taken at the
+    batch's midpoint."""
     before, acc, tot = 0, 0.0, 0
     for f in fs.fresh_counts:
         acc += f * (before + f / 2) / nslots
         tot += f
         before += f
-    load = acc / max(1, tot)
-    return 1 + load * (k - 1)
+    return acc / max(1, tot)
+
+
+def cuckoo_miss_probes(fs, table):
+    """Mean slots a Cuckoo probe reads for a key absent from the table: h_1,
+    and h_2..h_k only when h_1 is occupied, which for a uniform h_1 happens
+    with probability equal to the table load."""
+    if table is None:
+        return 4.0
+    info = table.info()
+    return 1 + new_key_load(fs, info["slots"]) * (info["num_hashes"] - 1)
+
+
+def random_access_roofline(scheme, fs, table, stats, ms_per_fill, probe):
+    """Lower bound on a fill's time from the measured random-access rates:
+    the lines a scheme must only read at the random-read rate plus the lines
+    it must claim in at the random read-modify-write rate.  Bucket: one line
+    per key, read-only for repeats, claimed for new keys.  Cuckoo: one line
+    (h_1) per repeat; per new key the extra probes h_2..h_k when h_1 is
+    occupied; and every exchange its insertion chains made (counted on the
+    device, `stats`), each a claimed line.  In-batch repeats that miss and
+    the dedup set (kept in L2) are not counted, so the bound is optimistic
+    and the fraction conservative."""
+    if not probe or "rmw_line" not in probe:
+        return None
+    r_rmw = probe["rmw_line"]["gaccess_per_s"] * 1e9
+    n_new = fs.n_distinct
+    n_rep = fs.n_issued - fs.n_distinct
+    if scheme == "bucket":
+        r_read = probe["128B"]["gaccess_per_s"] * 1e9
+        reads, claims = n_rep, n_new
+    else:
+        r_read = probe["8B"]["gaccess_per_s"] * 1e9
+        info = table.info()
+        reads = n_rep + n_new * new_key_load(fs, info["slots"]) * (info["num_hashes"] - 1)
+        claims = max(n_new, stats["exchanges"])
+    t_min = reads / r_read + claims / r_rmw
+    return {"min_ms_per_fill": round(t_min * 1e3, 3), "frac": round(t_min * 1e3 / ms_per_fill, 3),
+            "lines_read_per_key": round(reads / fs.n_issued, 3),
+            "lines_claimed_per_key": round(claims / fs.n_issued, 3),
+            "read_gaccess_per_s": round(r_read / 1e9, 2), "rmw_gaccess_per_s": round(r_rmw / 1e9, 2)}
 
 
 # ----------------------------------------------------------------- our arm
@@ -276,6 +309,7 @@ def run_ours(a, rank, world, local):
     for s in schemes:
         if tables[s].sync() != 0 or tables[s].size() != n:
             raise RuntimeError("timed fill of %s did not end exact" % s)
+    fill_stats = {s: tables[s].stats() for s in schemes}      # of the last timed fill
     value = whole_job_mops(n_ops, world, ms_step)
 
     # Roofline of the dominant kernel: algorithmic bytes per launch / event time.
@@ -330,6 +364,9 @@ def run_ours(a, rank, world, local):
         out["e2e"] = run_e2e(a, ht, torch, dev, fs, tables, schemes, world)
     if not a.no_probe and rank == 0:
         out["random_read_roofline"] = run_probe(ht, torch, dev)
+        for s in schemes:
+            out["per_scheme"][s]["random_access_roofline"] = random_access_roofline(
+                s, fs, tables[s], fill_stats[s], per_ms[s], out["random_read_roofline"])
     for t in tables.values():
         t.close()
     tables = {}
@@ -421,28 +458,39 @@ def run_e2e(a, ht, torch, dev, fs, tables, schemes, world):
 
 
 def run_probe(ht, torch, dev):
-    """Random-read rates over a 4 GiB buffer (>> L2): 8-byte slot probes,
-    32-byte reads and 128-byte lines read by 8-lane groups.  On GB300 each
-    random access costs a whole 128-byte line of DRAM traffic, so the line
-    rate is the ceiling for both schemes' probes."""
+    """Random-access rates over a 4 GiB buffer (>> L2), best of 5 launches:
+    8-byte slot probes, 32-byte reads and 128-byte lines read by 8-lane
+    groups; and random claims (8-byte atomic adds, one per random line).  On
+    GB300 each random read costs a whole 128-byte line of DRAM traffic, so
+    the line rate is the ceiling for both schemes' probes; a claim adds the
+    write-back of the dirtied sector."""
     buf = torch.empty(1 << 29, dtype=torch.int64, device=dev)
     buf.fill_(1)
     sink = torch.zeros(1, dtype=torch.int64, device=dev)
     res = {"buffer_gib": 4}
+
+    def best_ms(launch, reps=5):
+        launch(0)
+        times = []
+        for r in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            launch(r + 1)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return min(times)
+
     for gran in (8, 32, 128):
         n_acc = (1 << 33) // 128          # the same number of accesses for every size
-        ht.ht_probe_random_read(buf, gran, n_acc, 7, sink)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for r in range(3):
-            ht.ht_probe_random_read(buf, gran, n_acc, 11 + r, sink)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / 3
+        ms = best_ms(lambda r: ht.ht_probe_random_read(buf, gran, n_acc, 11 + r, sink))
         res["%dB" % gran] = {"gaccess_per_s": round(n_acc / (ms / 1e3) / 1e9, 2),
                              "requested_gbs": round(n_acc * gran / (ms / 1e3) / 1e9, 1),
                              "line_gbs": round(n_acc * 128 / (ms / 1e3) / 1e9, 1)}
+    n_acc = (1 << 33) // 128
+    ms = best_ms(lambda r: ht.ht_probe_random_rmw(buf, n_acc, 21 + r))
+    res["rmw_line"] = {"gaccess_per_s": round(n_acc / (ms / 1e3) / 1e9, 2),
+                       "line_read_gbs": round(n_acc * 128 / (ms / 1e3) / 1e9, 1)}
     del buf
     return res
 

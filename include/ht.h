@@ -160,6 +160,24 @@ ht_status ht_clear(ht_table* t, void* stream);
 ht_status ht_info(const ht_table* t, uint64_t* slots, uint32_t* num_hashes,
                   uint32_t* rebuilds);
 
+/* Counters of a table since its last clear (ht_clear) or rebuild. */
+typedef struct ht_table_stats {
+    uint64_t size;            /* keys stored (table + stash + overflow set) */
+    uint64_t dropped;         /* keys that found no place (then HT_ERR_FULL) */
+    uint64_t exchanges;       /* Cuckoo: atomic exchanges made by insertion
+                                 chains (Section 4.1); 0 for the bucket scheme */
+    uint32_t stash_used;      /* stash slots in use */
+    uint32_t overflow_used;   /* overflow-set slots in use */
+    uint32_t rebuilds;        /* rebuilds since ht_create */
+    uint32_t flags;           /* device status bits: 1 reserved key seen,
+                                 2 rebuild pending, 4 key dropped */
+    uint64_t reserved_[4];
+} ht_table_stats;
+
+/* Reads the table's counters into *out; synchronises `stream`.
+ * HT_ERR_INVALID for a NULL table or out. */
+ht_status ht_stats(ht_table* t, ht_table_stats* out, void* stream);
+
 const char* ht_status_str(ht_status s);
 
 /* ---------------------------------------------------------------------------
@@ -362,6 +380,14 @@ ht_status ht_prof_read(uint32_t id, uint64_t* launches, double* total_ms);
 ht_status ht_probe_random_read(const void* d_buf, uint64_t bytes, uint32_t gran,
                                uint64_t n_access, uint64_t seed,
                                unsigned long long* d_sink, void* stream);
+/* Random read-modify-write probe (not part of the hash table): n_access
+ * 8-byte atomic adds of 1 at uniformly random 128-byte-aligned offsets of
+ * d_buf[0..bytes) (the buffer's words change), eight in flight per thread;
+ * each touches one line that L2 fetches from DRAM and later writes back, the
+ * memory cost of a claim (CAS or exchange) in a random slot.  d_buf must be
+ * 128-byte aligned and bytes >= 128, else HT_ERR_INVALID.  Asynchronous on
+ * `stream`. */
+ht_status ht_probe_random_rmw(void* d_buf, uint64_t bytes, uint64_t n_access, uint64_t seed, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Cuckoo find-or-put that allocates nothing.  The paper has no counterpart:

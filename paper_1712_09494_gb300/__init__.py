@@ -15,14 +15,14 @@ import ctypes
 import torch
 
 from ._lib import (HT_BUCKET, HT_CUCKOO, HtBfsResult, HtError, HtModel, HtParams, HtServerConfig,
-                   HtServerStats, load)
+                   HtServerStats, HtTableStats, load)
 
 __all__ = [
     "HT_BUCKET", "HT_CUCKOO", "HtError", "HtParams", "HashTable", "load",
     "ht_default_params", "ht_create", "ht_destroy", "ht_find_or_put", "ht_find_or_put_append",
     "ht_insert", "ht_lookup", "ht_sync", "ht_size", "ht_export", "ht_clear", "ht_info",
     "ht_compact", "ht_prof_enable", "ht_prof_reset", "ht_prof_read", "ht_prof_kernels",
-    "ht_probe_random_read", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
+    "ht_probe_random_read", "ht_probe_random_rmw", "ht_stats", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
     "NOALLOC_MAX_BATCH", "scheme_of", "HtModel", "HtBfsResult", "make_model", "ht_successors", "ht_bfs",
     "MultiExploration", "Server", "HtServerConfig", "HtServerStats",
 ]
@@ -149,6 +149,13 @@ def ht_info(table):
     return dict(slots=s.value, num_hashes=k.value, rebuilds=r.value)
 
 
+def ht_stats(table, stream=None):
+    """Counters since the last clear or rebuild (synchronises the stream)."""
+    st = HtTableStats()
+    _check(load().ht_stats(table, ctypes.byref(st), _stream(stream)), "ht_stats")
+    return {f: getattr(st, f) for f, _ in HtTableStats._fields_ if f != "reserved_"}
+
+
 def ht_compact(keys, flags, out, count, stream=None):
     _check(load().ht_compact(_dptr(keys, "keys"), _dptr(flags, "flags"), keys.numel(), _key_width(keys),
                              _dptr(out, "out"), _dptr(count, "count"), _stream(stream)), "ht_compact")
@@ -183,6 +190,11 @@ def ht_probe_random_read(buf, gran, n_access, seed, sink, stream=None):
     _check(load().ht_probe_random_read(_dptr(buf, "buf"), buf.numel() * buf.element_size(), int(gran),
                                        int(n_access), int(seed), _dptr(sink, "sink"), _stream(stream)),
            "ht_probe_random_read")
+
+
+def ht_probe_random_rmw(buf, n_access, seed, stream=None):
+    _check(load().ht_probe_random_rmw(_dptr(buf, "buf"), buf.numel() * buf.element_size(), int(n_access),
+                                      int(seed), _stream(stream)), "ht_probe_random_rmw")
 
 
 def ht_cuckoo_find_or_put_noalloc(slots, state, seed, keys, is_new=None, reset=False, stream=None):
@@ -430,3 +442,6 @@ class HashTable:
 
     def info(self):
         return ht_info(self._h)
+
+    def stats(self, stream=None):
+        return ht_stats(self._h, stream)

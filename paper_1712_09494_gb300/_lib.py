@@ -54,6 +54,14 @@ class HtServerStats(ctypes.Structure):
     ]
 
 
+class HtTableStats(ctypes.Structure):
+    _fields_ = [
+        ("size", ctypes.c_uint64), ("dropped", ctypes.c_uint64), ("exchanges", ctypes.c_uint64),
+        ("stash_used", ctypes.c_uint32), ("overflow_used", ctypes.c_uint32),
+        ("rebuilds", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("reserved_", ctypes.c_uint64 * 4),
+    ]
+
+
 class HtError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -77,6 +85,7 @@ SIGNATURES = {
     "ht_export": (_I32, [_VP, _VP, _VP, _U64, _P(_U64), _VP]),
     "ht_clear": (_I32, [_VP, _VP]),
     "ht_info": (_I32, [_VP, _P(_U64), _P(_U32), _P(_U32)]),
+    "ht_stats": (_I32, [_VP, _P(HtTableStats), _VP]),
     "ht_status_str": (ctypes.c_char_p, [_I32]),
     "ht_compact": (_I32, [_VP, _VP, _U64, _U32, _VP, _VP, _VP]),
     "ht_prof_enable": (_I32, [ctypes.c_int]),
@@ -85,6 +94,7 @@ SIGNATURES = {
     "ht_prof_kernel_name": (ctypes.c_char_p, [_U32]),
     "ht_prof_read": (_I32, [_U32, _P(_U64), _P(ctypes.c_double)]),
     "ht_probe_random_read": (_I32, [_VP, _U64, _U32, _U64, _U64, _VP, _VP]),
+    "ht_probe_random_rmw": (_I32, [_VP, _U64, _U64, _U64, _VP]),
     "ht_cuckoo_find_or_put_noalloc": (_I32, [_VP, _U64, _VP, _U64, _VP, _U64, _VP, ctypes.c_int, _VP]),
     "ht_successors": (_I32, [_P(HtModel), _U32, _VP, _U64, _VP, _U64, _VP, _VP]),
     "ht_bfs": (_I32, [_VP, _P(HtModel), _U64, _U32, _VP, _VP, _U64, _P(HtBfsResult), _VP]),

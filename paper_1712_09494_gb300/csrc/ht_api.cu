@@ -438,6 +438,22 @@ ht_status ht_clear(ht_table* t, void* stream) {
     return clear_table(t, as_stream(stream));
 }
 
+ht_status ht_stats(ht_table* t, ht_table_stats* out, void* stream) {
+    if (!t || !out) return HT_ERR_INVALID;
+    DevCounters c;
+    const ht_status st = read_counters(t, &c, static_cast<cudaStream_t>(stream));
+    if (st != HT_OK) return st;
+    std::memset(out, 0, sizeof(*out));
+    out->size = c.size;
+    out->dropped = c.dropped;
+    out->exchanges = c.exchanges;
+    out->stash_used = c.stash_used;
+    out->overflow_used = c.ovf_used;
+    out->rebuilds = t->rebuilds;
+    out->flags = c.flags;
+    return HT_OK;
+}
+
 ht_status ht_info(const ht_table* t, uint64_t* slots, uint32_t* num_hashes, uint32_t* rebuilds) {
     if (!t) return HT_ERR_INVALID;
     if (slots) *slots = t->dt.nslots;

@@ -131,6 +131,26 @@ probe_read_kernel(const uint64_t* __restrict__ buf, uint32_t nblocks, uint64_t n
     if ((threadIdx.x & 31) == 0 && acc == 0x9E3779B97F4A7C15ull) atomicXor(sink, acc);
 }
 
+// Random read-modify-write: n_access 8-byte atomic adds at uniformly random
+// 128-byte-aligned offsets, eight in flight per thread.  Each one makes L2
+// fetch a line from DRAM and, once evicted, write it back: the cost of a
+// claim in a random line.
+__global__ void __launch_bounds__(kBlock)
+probe_rmw_kernel(unsigned long long* __restrict__ buf, uint32_t nlines, uint64_t n_access, uint32_t seed) {
+    constexpr int U = 8;
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t iters = (n_access + nthreads * U - 1) / (nthreads * U);
+    for (uint64_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t a = (it * nthreads + tid) * U + u;
+            const uint32_t b = __umulhi(mix32(uint32_t(a) * 0x9E3779B9u + uint32_t(a >> 32) + seed), nlines);
+            if (a < n_access) atomicAdd(buf + uint64_t(b) * 16, 1ull);
+        }
+    }
+}
+
 // ------------------------------------------------------------- profiling
 struct ProfRec {
     uint32_t id;
@@ -153,7 +173,7 @@ Prof& prof() {
 
 const char* kNames[kKNumKernels] = {
     "bucket_find_or_put", "bucket_lookup", "cuckoo_probe", "cuckoo_insert", "cuckoo_lookup",
-    "export", "clear", "compact", "probe_random_read", "successors",
+    "export", "clear", "compact", "probe_random_read", "successors", "probe_random_rmw",
 };
 
 }  // namespace
@@ -274,6 +294,15 @@ cudaError_t probe_random_read(const void* buf, uint64_t bytes, uint32_t gran, ui
     return cudaGetLastError();
 }
 
+cudaError_t probe_random_rmw(void* buf, uint64_t bytes, uint64_t n_access, uint64_t seed, cudaStream_t s) {
+    ProfScope ps(kKProbeRmw, s);
+    const uint32_t nlines = uint32_t(std::min<uint64_t>(bytes / 128, 0xFFFFFFFFull));
+    auto k = probe_rmw_kernel;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(static_cast<unsigned long long*>(buf), nlines,
+                                                              n_access, uint32_t(seed));
+    return cudaGetLastError();
+}
+
 }  // namespace ht
 
 extern "C" {
@@ -335,6 +364,13 @@ ht_status ht_probe_random_read(const void* d_buf, uint64_t bytes, uint32_t gran,
         return HT_ERR_INVALID;
     return ht::probe_random_read(d_buf, bytes, gran, n_access, seed, d_sink,
                                  static_cast<cudaStream_t>(stream)) == cudaSuccess ? HT_OK : HT_ERR_CUDA;
+}
+
+ht_status ht_probe_random_rmw(void* d_buf, uint64_t bytes, uint64_t n_access, uint64_t seed, void* stream) {
+    if (!d_buf || bytes < 128 || (reinterpret_cast<uintptr_t>(d_buf) & 127)) return HT_ERR_INVALID;
+    return ht::probe_random_rmw(d_buf, bytes, n_access, seed, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? HT_OK
+               : HT_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -33,6 +33,9 @@ constexpr int kU = HT_CUCKOO_KEYS_PER_THREAD;   // keys in flight per thread
 #ifndef HT_CUCKOO_PROBE_MIN_BLOCKS
 #define HT_CUCKOO_PROBE_MIN_BLOCKS 3
 #endif
+#ifndef HT_CUCKOO_INSERT_MIN_BLOCKS
+#define HT_CUCKOO_INSERT_MIN_BLOCKS 4
+#endif
 
 // Probe (and, for find-or-put, dedup).  Each thread holds U keys of a round,
 // strided by the grid so every load of keys stays coalesced; all U first
@@ -115,7 +118,7 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             for (int u = 0; u < kU; ++u)
                 if (act[u] && !found[u]) found[u] = find_spill<KW>(t, key[u], stash_used, ovf_used, &w[u]);
         }
-        if (LOOKUP) {
+        if constexpr (LOOKUP) {
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const uint64_t i = (r * kU + u) * stride + tid;
@@ -124,71 +127,74 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     if (out_val) out_val[i] = found[u] ? K::value(w[u]) : 0u;
                 }
             }
-            continue;
-        }
-        // In-batch dedup: the one claimant of each absent key wins.  First
-        // claim attempt of every miss together; collisions fall back to the
-        // linear-probing loop.
-        uint32_t spos[kU];
-        uint64_t sw[kU];
-        bool need[kU], winner[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            need[u] = act[u] && !found[u];
-            spos[u] = uint32_t(mix64(key[u] ^ dseed) & sc.mask);
-            sw[u] = kEmpty;
-            if (need[u]) sw[u] = __ldcg(reinterpret_cast<const unsigned long long*>(sc.set + spos[u]));
-        }
-        bool won[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            won[u] = false;
-            if (need[u] && sw[u] == kEmpty) {
-                const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(sc.set + spos[u]), kEmpty, key[u]);
-                won[u] = old == kEmpty;
-                sw[u] = old;
+        } else {
+            // In-batch dedup: the one claimant of each absent key wins.  First
+            // claim attempt of every miss together; collisions fall back to the
+            // linear-probing loop.
+            uint32_t spos[kU];
+            uint64_t sw[kU];
+            bool need[kU], winner[kU];
+    #pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                need[u] = act[u] && !found[u];
+                spos[u] = uint32_t(mix64(key[u] ^ dseed) & sc.mask);
+                sw[u] = kEmpty;
+                if (need[u]) sw[u] = __ldcg(reinterpret_cast<const unsigned long long*>(sc.set + spos[u]));
             }
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            winner[u] = false;
-            if (!need[u]) continue;
-            if (won[u]) {
-                winner[u] = true;                          // our CAS filled the empty slot
-            } else if (K::keyof(sw[u]) != key[u]) {        // another key sits there: probe on
-                uint32_t at = 0;
-                const uint32_t next = spos[u] + 1 == uint32_t(sc.mask + 1) ? 0u : spos[u] + 1;
-                winner[u] = lp_insert<KW>(sc.set, uint32_t(sc.mask + 1), next, key[u], key[u], &at) == 1;
-                spos[u] = at;
+            bool won[kU];
+    #pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                won[u] = false;
+                if (need[u] && sw[u] == kEmpty) {
+                    const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(sc.set + spos[u]), kEmpty, key[u]);
+                    won[u] = old == kEmpty;
+                    sw[u] = old;
+                }
             }
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const uint64_t i = (r * kU + u) * stride + tid;
-            if (i < n && out_flag) out_flag[i] = uint8_t(winner[u]);
-            // Warp-aggregated append of the winners to the insert list.
-            const unsigned wm = __ballot_sync(0xFFFFFFFFu, winner[u]);
-            if (wm) {
-                const int leader = __ffs(wm) - 1;
-                unsigned int b = 0;
-                if (lane == leader) b = atomicAdd(&t.ctr->winners[parity], unsigned(__popc(wm)));
-                b = __shfl_sync(0xFFFFFFFFu, b, leader);
-                if (winner[u]) {
-                    Winner wn;
-                    wn.word = K::word(key[u], VALUES ? vals[i] : 0u);
-                    wn.spos = spos[u];
-                    wn.pad_ = 0;
-                    sc.win[b + __popc(wm & ((1u << lane) - 1))] = wn;
+    #pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                winner[u] = false;
+                if (!need[u]) continue;
+                if (won[u]) {
+                    winner[u] = true;                          // our CAS filled the empty slot
+                } else if (K::keyof(sw[u]) != key[u]) {        // another key sits there: probe on
+                    uint32_t at = 0;
+                    const uint32_t next = spos[u] + 1 == uint32_t(sc.mask + 1) ? 0u : spos[u] + 1;
+                    winner[u] = lp_insert<KW>(sc.set, uint32_t(sc.mask + 1), next, key[u], key[u], &at) == 1;
+                    spos[u] = at;
+                }
+            }
+    #pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint64_t i = (r * kU + u) * stride + tid;
+                if (i < n && out_flag) out_flag[i] = uint8_t(winner[u]);
+                // Warp-aggregated append of the winners to the insert list.
+                const unsigned wm = __ballot_sync(0xFFFFFFFFu, winner[u]);
+                if (wm) {
+                    const int leader = __ffs(wm) - 1;
+                    unsigned int b = 0;
+                    if (lane == leader) b = atomicAdd(&t.ctr->winners[parity], unsigned(__popc(wm)));
+                    b = __shfl_sync(0xFFFFFFFFu, b, leader);
+                    if (winner[u]) {
+                        Winner wn;
+                        wn.word = K::word(key[u], VALUES ? vals[i] : 0u);
+                        wn.spos = spos[u];
+                        wn.pad_ = 0;
+                        sc.win[b + __popc(wm & ((1u << lane) - 1))] = wn;
+                    }
                 }
             }
         }
     }
 }
 
-// Eviction-chain insert of the winners; each thread runs U chains in step so
-// their exchanges overlap.
+// Eviction-chain insert of the winners.  Each thread keeps U chains in
+// flight so their exchanges overlap, and a chain that ends (an empty slot,
+// or the stash) is replaced at once by the thread's next winner: chain
+// lengths vary widely at high load, and refilling keeps every slot of the
+// thread busy instead of waiting for the longest chain of a round.
 template <int KW, bool APPEND>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, HT_CUCKOO_INSERT_MIN_BLOCKS)
 cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uint64_t max_winners,
                      typename Keys<KW>::T* __restrict__ new_out, unsigned long long* __restrict__ new_count,
                      uint64_t new_cap) {
@@ -199,69 +205,81 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
     if (blockIdx.x == 0 && threadIdx.x == 0) t.ctr->winners[parity ^ 1u] = 0;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint64_t rounds = (count + stride * kU - 1) / (stride * kU);
-    unsigned long long placed = 0;
-    for (uint64_t r = 0; r < rounds; ++r) {
-        uint64_t word[kU], pos[kU], first[kU];
-        bool live[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const uint64_t i = (r * kU + u) * stride + tid;
-            live[u] = i < count;
-            first[u] = 0;
-            word[u] = 0;
-            pos[u] = 0;
-            if (live[u]) {
-                const Winner wn = sc.win[i];
-                sc.set[wn.spos] = kEmpty;      // leave the dedup set empty for the next batch
-                word[u] = wn.word;
-                first[u] = K::keyof(wn.word);
-                pos[u] = hidx(first[u], t.seed[0], t.nslots);
-            }
-        }
-        bool any = false;
-#pragma unroll
-        for (int u = 0; u < kU; ++u) any |= live[u];
-        for (uint32_t e = 0; any && e <= t.max_evict; ++e) {
-            uint64_t old[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u)
-                if (live[u]) old[u] = atomicExch(reinterpret_cast<unsigned long long*>(t.slots + pos[u]), word[u]);
-            any = false;
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                if (!live[u]) continue;
-                if (K::empty(old[u])) {
-                    live[u] = false;
-                    ++placed;
-                    continue;
-                }
-                // Section 4.1: the evicted key k' sat at h_a(k') = pos; it
-                // moves on to h_{a+1}(k') (cyclically after h_k).
-                word[u] = old[u];
-                const uint64_t key = K::keyof(old[u]);
-                uint32_t a = 0;
-                for (; a + 1 < t.k; ++a)
-                    if (hidx(key, t.seed[a], t.nslots) == pos[u]) break;
-                const uint32_t nxt = (a + 1 == t.k) ? 0u : a + 1;
-                pos[u] = hidx(key, t.seed[nxt], t.nslots);
-                any = true;
-            }
-        }
-        // Chains that hit the eviction bound hold a word that goes to the stash.
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-            if (live[u] && place_spill<KW>(t, K::keyof(word[u]), word[u]) == 1) ++placed;
-        if (APPEND) {
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const uint64_t i = (r * kU + u) * stride + tid;
-                warp_append<typename K::T>(i < count, typename K::T(first[u]), new_out, new_count, new_cap);
-            }
+    if (APPEND) {
+        // Every winner is a new key: append them all, warp-aggregated.
+        const uint64_t rounds = (count + stride - 1) / stride;
+        for (uint64_t r = 0; r < rounds; ++r) {
+            const uint64_t i = r * stride + tid;
+            const uint64_t key = i < count ? K::keyof(sc.win[i].word) : 0;
+            warp_append<typename K::T>(i < count, typename K::T(key), new_out, new_count, new_cap);
         }
     }
-    for (int o = 16; o; o >>= 1) placed += __shfl_down_sync(0xFFFFFFFFu, placed, o);
+    unsigned long long placed = 0, exchanges = 0;
+    uint64_t next = tid;                  // this thread's next winner: tid, tid + stride, ...
+    uint64_t word[kU], pos[kU];
+    uint32_t evictions[kU];
+    bool live[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        live[u] = false;
+        word[u] = 0;
+        pos[u] = 0;
+        evictions[u] = 0;
+    }
+    // Bounded: each winner is taken once and its chain ends after at most
+    // max_evictions + 1 exchanges.
+    for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (!live[u] && next < count) {
+                const Winner wn = sc.win[next];
+                next += stride;
+                sc.set[wn.spos] = kEmpty;      // leave the dedup set empty for the next batch
+                word[u] = wn.word;
+                pos[u] = hidx(K::keyof(wn.word), t.seed[0], t.nslots);
+                evictions[u] = 0;
+                live[u] = true;
+            }
+            any |= live[u];
+        }
+        if (!any) break;
+        uint64_t old[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (live[u]) old[u] = atomicExch(reinterpret_cast<unsigned long long*>(t.slots + pos[u]), word[u]);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (!live[u]) continue;
+            ++exchanges;
+            if (K::empty(old[u])) {
+                live[u] = false;
+                ++placed;
+                continue;
+            }
+            // Section 4.1: the evicted key k' sat at h_a(k') = pos; it moves
+            // on to h_{a+1}(k') (cyclically after h_k).
+            word[u] = old[u];
+            if (++evictions[u] > t.max_evict) {
+                // The chain hit the eviction bound: the held word goes to the stash.
+                if (place_spill<KW>(t, K::keyof(word[u]), word[u]) == 1) ++placed;
+                live[u] = false;
+                continue;
+            }
+            const uint64_t key = K::keyof(old[u]);
+            uint32_t a = 0;
+            for (; a + 1 < t.k; ++a)
+                if (hidx(key, t.seed[a], t.nslots) == pos[u]) break;
+            const uint32_t nxt = (a + 1 == t.k) ? 0u : a + 1;
+            pos[u] = hidx(key, t.seed[nxt], t.nslots);
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        placed += __shfl_down_sync(0xFFFFFFFFu, placed, o);
+        exchanges += __shfl_down_sync(0xFFFFFFFFu, exchanges, o);
+    }
     if ((threadIdx.x & 31) == 0 && placed) atomicAdd(&t.ctr->size, placed);
+    if ((threadIdx.x & 31) == 0 && exchanges) atomicAdd(&t.ctr->exchanges, exchanges);
 }
 
 }  // namespace

@@ -30,8 +30,11 @@ struct DevCounters {
     unsigned int ovf_used;
     unsigned int flags;
     unsigned int winners[2];      // Cuckoo dedup winners per chunk parity
-    unsigned int pad_[9];
+    unsigned int pad0_;
+    unsigned long long exchanges; // Cuckoo: atomic exchanges made by insert chains
+    unsigned int pad_[6];
 };
+static_assert(sizeof(DevCounters) == 72, "counter block layout");
 
 // Everything a kernel needs to address a table; passed by value.
 struct DevTable {
@@ -217,6 +220,7 @@ enum KernelId : uint32_t {
     kKCompact,
     kKProbeRead,
     kKSuccessors,
+    kKProbeRmw,
     kKNumKernels
 };
 
@@ -305,6 +309,7 @@ cudaError_t compact(int kw, const void* keys, const uint8_t* flags, uint64_t n, 
                     unsigned long long* count, cudaStream_t s);
 cudaError_t probe_random_read(const void* buf, uint64_t bytes, uint32_t gran, uint64_t n_access,
                               uint64_t seed, unsigned long long* sink, cudaStream_t s);
+cudaError_t probe_random_rmw(void* buf, uint64_t bytes, uint64_t n_access, uint64_t seed, cudaStream_t s);
 
 // A model with its bit offsets precomputed (device copy; the single-table
 // successor kernel stages it in shared memory).

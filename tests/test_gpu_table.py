@@ -238,6 +238,26 @@ def test_compact_matches_numpy():
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
+def test_stats_counters(oracle_lib, scheme):
+    # size and the stash/overflow counts agree with the table; Cuckoo makes
+    # at least one exchange per new key (its first, at h_1) and the bucket
+    # scheme none; ht_clear zeroes them.
+    t, orc, fs = _fill_and_check(oracle_lib, scheme, 64, n_distinct=200_000, batch=1 << 15, dup=0.25, lf=0.85,
+                                 seed=31)
+    st = t.stats()
+    assert st["size"] == orc.size() == t.size()
+    assert st["dropped"] == 0 and st["flags"] == 0
+    if scheme == "cuckoo":
+        assert st["exchanges"] >= fs.n_distinct - st["stash_used"] - st["overflow_used"]
+        assert st["exchanges"] < 50 * fs.n_distinct
+    else:
+        assert st["exchanges"] == 0
+    t.clear()
+    st = t.stats()
+    assert st["size"] == st["exchanges"] == st["stash_used"] == st["overflow_used"] == 0
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
 def test_clear_empties(oracle_lib, scheme):
     t = ht.HashTable(4096, scheme, 64)
     k = to_dev(wk.distinct_keys(3000, 64, seed=1))

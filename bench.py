@@ -315,6 +315,7 @@ def run_ours(a, rank, world, local):
     # Roofline of the dominant kernel: algorithmic bytes per launch / event time.
     p_new = fs.n_distinct / fs.n_issued
     miss_probes = cuckoo_miss_probes(fs, tables.get("cuckoo"))
+    cuckoo_exchanges_per_new = (fill_stats["cuckoo"]["exchanges"] / fs.n_distinct) if "cuckoo" in fill_stats else 1.0
     per_key = {
         # key read + flag write + one 128-byte bucket + the claimed sector for new keys
         "bucket_find_or_put": 8 + 1 + 128 + p_new * 32,
@@ -322,8 +323,9 @@ def run_ours(a, rank, world, local):
         # probed sectors (h_1, and h_2..h_k when h_1 is occupied) plus the
         # 16-byte winner record
         "cuckoo_probe": 8 + 1 + (1 - p_new) * 32 + p_new * (miss_probes * 32 + 16),
-        # winner record + one exchange (32-byte read + 32-byte write) per winner
-        "cuckoo_insert": 16 + 64,
+        # winner record + per exchange a 32-byte sector read and written
+        # (exchanges per winner counted on the device over the last timed fill)
+        "cuckoo_insert": 16 + 64 * max(1.0, cuckoo_exchanges_per_new),
     }
     # units over the timed region; divided by each kernel's launch count below
     units_total = {"bucket_find_or_put": fs.n_issued * a.steps,
@@ -346,7 +348,8 @@ def run_ours(a, rank, world, local):
                 else "fallback 6.8 TB/s",
                 "unit": "GB/s", "frac": round(kernels[dom]["achieved_gbs"] / peak, 3),
                 "traffic": traffic, "alg_bytes_per_key": round(per_key[dom], 1),
-                "cuckoo_miss_probes": round(miss_probes, 3)}
+                "cuckoo_miss_probes": round(miss_probes, 3),
+                "cuckoo_exchanges_per_new_key": round(cuckoo_exchanges_per_new, 3)}
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "Mops/s", "n_gpus": world, "steps": a.steps,

@@ -638,7 +638,8 @@ def serving_trace(n_req, rate, seed=5, n_tables=1024):
     2^12..2^30 slots (log-uniform); batch sizes log-uniform in 1..2^20; each
     table lives for a contiguous session of the trace (opened before its
     first request, closed after its last), so admission by free memory
-    matters; keys are random 64-bit with repeats of the table's earlier keys."""
+    matters; keys are random 64-bit with repeats of the table's earlier keys
+    (serving_keys), never more distinct keys than 0.8 of a table's slots."""
     rng = np.random.default_rng(seed)
     caps = np.exp2(rng.uniform(12, 30, size=n_tables)).astype(np.int64)
     pos = np.sort(rng.uniform(0, n_tables, size=n_req))
@@ -648,21 +649,30 @@ def serving_trace(n_req, rate, seed=5, n_tables=1024):
     return caps, table, sizes, arrivals
 
 
-def serving_keys(trace):
-    """Per request: fresh keys of its table, a quarter of them repeats of the
-    table's first keys once the table has been used."""
+def serving_keys(trace, load=0.8, seed=6):
+    """Per request: a quarter repeats of its table's earlier keys (once it has
+    some), the rest fresh keys of the table -- until the table holds `load` x
+    its capacity distinct keys; from then on the request's other keys are
+    repeats too, so no table is filled past that load."""
     from workloads import keys as wk
+    rng = np.random.default_rng(seed)
     caps, table, sizes, arrivals = trace
     issued, keys = {}, []
     for i in range(len(sizes)):
         t, n = int(table[i]), int(sizes[i])
         base = issued.get(t, 0)
-        k = wk.distinct_keys(n, 64, seed=1000 + t, start=base)
-        rep = min(n // 4, base)
+        room = max(0, int(load * caps[t]) - base)
+        fresh = min(n - (min(n // 4, base)), room)
+        if base + fresh == 0:
+            fresh = 1                                   # a table's first key
+        rep = n - fresh
+        k = np.empty(n, dtype=np.uint64)
+        k[:fresh] = wk.distinct_keys(fresh, 64, seed=1000 + t, start=base)
         if rep:
-            k[:rep] = wk.distinct_keys(rep, 64, seed=1000 + t, start=0)
-        issued[t] = base + n
-        keys.append(k)
+            idx = rng.integers(0, base + fresh, size=rep).astype(np.uint64)
+            k[fresh:] = wk.mix63_perm(idx, 1000 + t)
+        issued[t] = base + fresh
+        keys.append(k[rng.permutation(n)])
     return keys
 
 
@@ -719,7 +729,11 @@ def run_serving_once(ht, a, pack, inflight, trace, keys):
     lat = np.array(done_lat)
     return {"p50_us": round(float(np.percentile(lat, 50)), 1), "p99_us": round(float(np.percentile(lat, 99)), 1),
             "mean_us": round(float(lat.mean()), 1), "sustained_mops": round(float(sizes.sum()) / wall / 1e6, 1),
-            "wall_s": round(wall, 3), "batches": int(st["batches"]), "errors": len(errors)}
+            "wall_s": round(wall, 3), "batches": int(st["batches"]), "errors": len(errors),
+            "worker": {"admit_s": round(st["admit_seconds"], 3), "pack_s": round(st["pack_seconds"], 3),
+                       "finish_s": round(st["finish_seconds"], 3), "batch_us_mean": round(st["batch_us_mean"], 1),
+                       "batch_gpu_us_mean": round(st["batch_gpu_us_mean"], 1),
+                       "tables_created": int(st["tables_created"])}}
 
 
 def run_serving(ht, a):

@@ -315,7 +315,7 @@ typedef struct ht_server ht_server;
 
 typedef struct ht_server_config {
     uint32_t max_inflight;            /* batch slots (streams), default 4, max 64 */
-    uint32_t max_requests_per_batch;  /* default 4096 */
+    uint32_t max_requests_per_batch;  /* default 4096, at most 2^20 */
     uint64_t batch_key_budget;        /* keys per batch, also the largest request; default 2^22 */
     uint64_t hbm_reserve_bytes;       /* device memory kept free, default 1 GiB */
     uint64_t fake_free_bytes;         /* tests: free memory to assume (0 = ask the driver) */
@@ -333,6 +333,13 @@ typedef struct ht_server_stats {
     uint64_t admitted_bytes;
     uint32_t tables_admitted;
     int32_t status;                   /* HT_OK, or the first error the worker met */
+    /* Where the worker thread's time went over the same period: */
+    double admit_seconds;             /* creating admitted tables (allocate + clear) */
+    double pack_seconds;              /* packing requests into batches and issuing them */
+    double finish_seconds;            /* copying results out of completed batches */
+    double batch_us_mean;             /* mean issue-to-completion time of a batch (host view) */
+    double batch_gpu_us_mean;         /* mean device time of a batch (events on its stream) */
+    uint64_t tables_created;
 } ht_server_stats;
 
 ht_status ht_server_default_config(ht_server_config* cfg);

@@ -51,6 +51,10 @@ class HtServerStats(ctypes.Structure):
         ("seconds", ctypes.c_double), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
         ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double), ("admitted_bytes", ctypes.c_uint64),
         ("tables_admitted", ctypes.c_uint32), ("status", ctypes.c_int32),
+        ("admit_seconds", ctypes.c_double), ("pack_seconds", ctypes.c_double),
+        ("finish_seconds", ctypes.c_double), ("batch_us_mean", ctypes.c_double),
+        ("batch_gpu_us_mean", ctypes.c_double),
+        ("tables_created", ctypes.c_uint64),
     ]
 
 

@@ -50,20 +50,27 @@ struct Tab {
     ht_table* t = nullptr;
     uint64_t bytes = 0;
     bool admitted = false, busy = false, closing = false, closed = false;
+    cudaEvent_t ready = nullptr;   // recorded on the admission stream after the table's clear
+    bool ready_seen = false;       // `ready` has completed
     std::deque<uint64_t> q;
 };
 
 struct Slot {
     cudaStream_t s = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev0 = nullptr, ev = nullptr;   // batch start / end on the slot's stream
     uint64_t* h_keys = nullptr;    // pinned staging
     uint8_t* h_flags = nullptr;
     ServeDesc* h_desc = nullptr;
+    uint32_t* h_tid = nullptr;     // per request of the batch: its table id ...
+    uint32_t* h_flagw = nullptr;   // ... and that table's device status bits after the batch
     uint64_t* d_keys = nullptr;
     uint8_t* d_flags = nullptr;
     ServeDesc* d_desc = nullptr;
+    uint32_t* d_tid = nullptr;
+    uint32_t* d_flagw = nullptr;
     std::vector<std::pair<uint64_t, uint64_t>> reqs;   // (request id, key offset)
     bool busy = false;
+    std::chrono::steady_clock::time_point issued;
 };
 
 uint64_t table_bytes(uint64_t capacity, ht_scheme scheme, const ht_params& p) {
@@ -75,6 +82,14 @@ uint64_t table_bytes(uint64_t capacity, ht_scheme scheme, const ht_params& p) {
         b += 2 * chunk * 8 * 2 + chunk * 16;
     }
     return b;
+}
+
+// After a batch: the status bits of each request's table (a key that found
+// no place anywhere sets kFlagDropped; a reserved key kFlagInvalidKey).
+__global__ void serve_status_kernel(const DevTable* __restrict__ tables, const uint32_t* __restrict__ tid,
+                                    uint32_t n, uint32_t* __restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __ldcg(&tables[tid[i]].ctr->flags);
 }
 
 }  // namespace
@@ -91,11 +106,15 @@ struct ht_server {
     uint64_t next_id = 1;
     std::vector<Slot> slots;
     DevTable* d_tables = nullptr;
+    DevTable* h_tables = nullptr;  // pinned source of the descriptor copies (asynchronous)
     cudaStream_t admin = nullptr;
     uint64_t admitted_bytes = 0;
+    uint64_t pool_threshold = 0;   // the default pool's release threshold before this server
+    bool pool_kept = false;
     size_t rr = 0;                 // round-robin start over tables
     std::vector<double> lat_us;
-    uint64_t keys_done = 0, batches = 0, requests_done = 0;
+    uint64_t keys_done = 0, batches = 0, requests_done = 0, tables_created = 0;
+    double admit_s = 0, pack_s = 0, finish_s = 0, batch_us = 0, batch_gpu_us = 0;
     Clock::time_point stats_t0;
     ht_status fault = HT_OK;
 };
@@ -132,6 +151,7 @@ void trim_pool(ht_server* sv) {
 // Admits waiting tables, in id order, while free memory covers them.
 bool admit(ht_server* sv) {
     bool any = false;
+    const auto t0 = Clock::now();
     for (uint32_t id = 0; id < sv->tabs.size(); ++id) {
         Tab& tb = sv->tabs[id];
         if (tb.admitted || tb.closed) continue;
@@ -148,13 +168,18 @@ bool admit(ht_server* sv) {
             trim_pool(sv);
             st = ht_create(tb.capacity, tb.scheme, 64, &p, sv->admin, &t);
         }
-        if (st == HT_OK && tb.scheme == HT_BUCKET) {
-            const DevTable& dt = table_dev(t);
-            if (cudaMemcpyAsync(sv->d_tables + id, &dt, sizeof(DevTable), cudaMemcpyHostToDevice, sv->admin) !=
-                cudaSuccess)
+        if (st == HT_OK) {
+            sv->h_tables[id] = table_dev(t);     // ids are never reused: the source stays valid
+            if (cudaMemcpyAsync(sv->d_tables + id, sv->h_tables + id, sizeof(DevTable), cudaMemcpyHostToDevice,
+                                sv->admin) != cudaSuccess)
                 st = HT_ERR_CUDA;
         }
-        if (st == HT_OK && cudaStreamSynchronize(sv->admin) != cudaSuccess) st = HT_ERR_CUDA;
+        // No wait here: a table joins batches once `ready` has completed, so
+        // admission never stalls behind the batches in flight, and requests
+        // of ready tables never wait for another table's clear.
+        if (st == HT_OK && !tb.ready && cudaEventCreateWithFlags(&tb.ready, cudaEventDisableTiming) != cudaSuccess)
+            st = HT_ERR_CUDA;
+        if (st == HT_OK && cudaEventRecord(tb.ready, sv->admin) != cudaSuccess) st = HT_ERR_CUDA;
         if (st != HT_OK) {
             if (t) table_release(t, sv->admin);
             if (st == HT_ERR_OOM) break;          // try again when memory frees up
@@ -162,23 +187,36 @@ bool admit(ht_server* sv) {
             break;
         }
         tb.t = t;
+        tb.ready_seen = false;
         tb.admitted = true;
         sv->admitted_bytes += tb.bytes;
+        sv->tables_created += 1;
         any = true;
     }
+    if (any) sv->admit_s += std::chrono::duration<double>(Clock::now() - t0).count();
     return any;
 }
 
 void finish(ht_server* sv, Slot& sl) {
     const auto now = Clock::now();
-    for (const auto& pr : sl.reqs) {
+    sv->batch_us += std::chrono::duration<double, std::micro>(now - sl.issued).count();
+    float gpu_ms = 0.f;
+    if (cudaEventElapsedTime(&gpu_ms, sl.ev0, sl.ev) == cudaSuccess) sv->batch_gpu_us += 1e3 * double(gpu_ms);
+    for (size_t j = 0; j < sl.reqs.size(); ++j) {
+        const auto& pr = sl.reqs[j];
         auto it = sv->reqs.find(pr.first);
         if (it == sv->reqs.end()) continue;
         Req& r = it->second;
         if (r.out) std::memcpy(r.out, sl.h_flags + pr.second, r.n);
         r.t1 = now;
         r.state = 2;
-        r.status = sv->fault;
+        // Sticky per table: once a key of the table found no place, its
+        // requests report HT_ERR_FULL (nothing is dropped silently).
+        const uint32_t fl = sl.h_flagw[j];
+        r.status = sv->fault != HT_OK ? sv->fault
+                   : (fl & kFlagDropped) ? HT_ERR_FULL
+                   : (fl & kFlagInvalidKey) ? HT_ERR_INVALID
+                                            : HT_OK;
         sv->tabs[r.table].busy = false;
         sv->keys_done += r.n;
         sv->requests_done += 1;
@@ -186,10 +224,12 @@ void finish(ht_server* sv, Slot& sl) {
     }
     sl.reqs.clear();
     sl.busy = false;
+    sv->finish_s += std::chrono::duration<double>(Clock::now() - now).count();
 }
 
 // Packs the head request of every ready table into slot `sl` and issues it.
 bool launch(ht_server* sv, Slot& sl) {
+    const auto t0 = Clock::now();
     const uint64_t budget = sv->cfg.batch_key_budget;
     uint64_t off = 0, tiles = 0;
     uint32_t nb = 0;
@@ -204,6 +244,10 @@ bool launch(ht_server* sv, Slot& sl) {
         const uint32_t id = uint32_t((sv->rr + k) % nt);
         Tab& tb = sv->tabs[id];
         if (!tb.admitted || tb.busy || tb.q.empty()) continue;
+        if (!tb.ready_seen) {
+            if (cudaEventQuery(tb.ready) != cudaSuccess) continue;     // still being cleared
+            tb.ready_seen = true;
+        }
         Req& r = sv->reqs[tb.q.front()];
         if (off + r.n > budget && off > 0) continue;
         std::memcpy(sl.h_keys + off, r.keys, r.n * 8);
@@ -218,6 +262,7 @@ bool launch(ht_server* sv, Slot& sl) {
         } else {
             cuckoo.push_back(CuckooJob{id, off, r.n});
         }
+        sl.h_tid[sl.reqs.size()] = id;
         sl.reqs.emplace_back(tb.q.front(), off);
         r.state = 1;
         tb.q.pop_front();
@@ -226,7 +271,8 @@ bool launch(ht_server* sv, Slot& sl) {
     }
     if (sl.reqs.empty()) return false;
     sv->rr = (sv->rr + 1) % std::max<size_t>(nt, 1);
-    cudaError_t e = cudaMemcpyAsync(sl.d_keys, sl.h_keys, off * 8, cudaMemcpyHostToDevice, sl.s);
+    cudaError_t e = cudaEventRecord(sl.ev0, sl.s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.d_keys, sl.h_keys, off * 8, cudaMemcpyHostToDevice, sl.s);
     if (e == cudaSuccess && nb) e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, nb * sizeof(ServeDesc), cudaMemcpyHostToDevice, sl.s);
     if (e == cudaSuccess && nb)
         e = serve_bucket_find_or_put(table_bucket_cfg(sv->tabs[sl.h_desc[0].table].t), sv->d_tables, sl.d_desc, nb, tiles,
@@ -236,11 +282,20 @@ bool launch(ht_server* sv, Slot& sl) {
         if (ht_find_or_put(sv->tabs[c.table].t, sl.d_keys + c.off, c.n, sl.d_flags + c.off, sl.s) != HT_OK)
             e = cudaErrorLaunchFailure;
     }
+    const uint32_t nr = uint32_t(sl.reqs.size());
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.d_tid, sl.h_tid, nr * sizeof(uint32_t), cudaMemcpyHostToDevice, sl.s);
+    if (e == cudaSuccess) {
+        serve_status_kernel<<<(nr + 255) / 256, 256, 0, sl.s>>>(sv->d_tables, sl.d_tid, nr, sl.d_flagw);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_flagw, sl.d_flagw, nr * sizeof(uint32_t), cudaMemcpyDeviceToHost, sl.s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_flags, sl.d_flags, off, cudaMemcpyDeviceToHost, sl.s);
     if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.s);
     if (e != cudaSuccess) sv->fault = HT_ERR_CUDA;
     sl.busy = true;
+    sl.issued = Clock::now();
     sv->batches += 1;
+    sv->pack_s += std::chrono::duration<double>(sl.issued - t0).count();
     return true;
 }
 
@@ -287,6 +342,12 @@ void worker_loop(ht_server* sv) {
         for (auto& sl : sv->slots)
             if (!sl.busy && launch(sv, sl)) progress = any_busy = true;
         if (!progress) {
+            // Short waits while work is on the device: batches in flight, or
+            // admitted tables with requests whose clear is still running.
+            for (const auto& tb : sv->tabs) {
+                if (any_busy) break;
+                any_busy = tb.admitted && !tb.ready_seen && !tb.q.empty();
+            }
             if (any_busy) sv->cv_work.wait_for(lk, std::chrono::microseconds(20));
             else sv->cv_work.wait_for(lk, std::chrono::milliseconds(1));
         }
@@ -306,16 +367,31 @@ void destroy_server(ht_server* sv) {
         cudaFreeHost(sl.h_keys);
         cudaFreeHost(sl.h_flags);
         cudaFreeHost(sl.h_desc);
+        cudaFreeHost(sl.h_tid);
+        cudaFreeHost(sl.h_flagw);
+        cudaFree(sl.d_tid);
+        cudaFree(sl.d_flagw);
         cudaFree(sl.d_keys);
         cudaFree(sl.d_flags);
         cudaFree(sl.d_desc);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.ev0) cudaEventDestroy(sl.ev0);
         if (sl.s) cudaStreamDestroy(sl.s);
     }
-    for (auto& tb : sv->tabs)
+    for (auto& tb : sv->tabs) {
         if (tb.t) ht_destroy(tb.t);
+        if (tb.ready) cudaEventDestroy(tb.ready);
+    }
     cudaFree(sv->d_tables);
+    cudaFreeHost(sv->h_tables);
     if (sv->admin) cudaStreamDestroy(sv->admin);
+    if (sv->pool_kept) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess) {
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &sv->pool_threshold);
+            cudaMemPoolTrimTo(pool, 0);
+        }
+    }
     delete sv;
 }
 
@@ -342,24 +418,43 @@ ht_status ht_server_create(const ht_server_config* cfg, ht_server** out) {
     ht_server_default_config(&c);
     if (cfg) c = *cfg;
     if (c.max_inflight < 1 || c.max_inflight > 64 || c.batch_key_budget < 32 || c.batch_key_budget > (1ull << 28) ||
-        c.max_requests_per_batch < 1)
+        c.max_requests_per_batch < 1 || c.max_requests_per_batch > (1u << 20))
         return HT_ERR_INVALID;
     ht_server* sv = new (std::nothrow) ht_server();
     if (!sv) return HT_ERR_OOM;
     sv->cfg = c;
     cudaGetDevice(&sv->device);
     sv->stats_t0 = Clock::now();
+    {
+        // Keep memory freed by closed tables in the device's default
+        // stream-ordered pool while the server runs: the next tables reuse
+        // it without mapping fresh memory (for a 2^30-slot table that cut
+        // create + release from ~19 ms to ~1.4 ms).  It goes back to the
+        // driver when an allocation fails (trim_pool) and when the server
+        // is destroyed, which also restores the previous threshold.
+        cudaMemPool_t pool;
+        uint64_t keep = ~0ull;
+        if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &sv->pool_threshold) == cudaSuccess &&
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess)
+            sv->pool_kept = true;
+    }
     bool ok = cudaStreamCreateWithFlags(&sv->admin, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaMalloc(&sv->d_tables, kMaxServerTables * sizeof(DevTable)) == cudaSuccess;
+              cudaMalloc(&sv->d_tables, kMaxServerTables * sizeof(DevTable)) == cudaSuccess &&
+              cudaMallocHost(&sv->h_tables, kMaxServerTables * sizeof(DevTable)) == cudaSuccess;
     sv->slots.resize(c.max_inflight);
-    const uint64_t nreq = std::min<uint64_t>(c.max_requests_per_batch, c.batch_key_budget);
+    const uint64_t nreq = c.max_requests_per_batch;
     for (auto& sl : sv->slots) {
         if (!ok) break;
         ok = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreate(&sl.ev0) == cudaSuccess && cudaEventCreate(&sl.ev) == cudaSuccess &&
              cudaMallocHost(&sl.h_keys, c.batch_key_budget * 8) == cudaSuccess &&
              cudaMallocHost(&sl.h_flags, c.batch_key_budget) == cudaSuccess &&
              cudaMallocHost(&sl.h_desc, nreq * sizeof(ServeDesc)) == cudaSuccess &&
+             cudaMallocHost(&sl.h_tid, nreq * sizeof(uint32_t)) == cudaSuccess &&
+             cudaMallocHost(&sl.h_flagw, nreq * sizeof(uint32_t)) == cudaSuccess &&
+             cudaMalloc(&sl.d_tid, nreq * sizeof(uint32_t)) == cudaSuccess &&
+             cudaMalloc(&sl.d_flagw, nreq * sizeof(uint32_t)) == cudaSuccess &&
              cudaMalloc(&sl.d_keys, c.batch_key_budget * 8) == cudaSuccess &&
              cudaMalloc(&sl.d_flags, c.batch_key_budget) == cudaSuccess &&
              cudaMalloc(&sl.d_desc, nreq * sizeof(ServeDesc)) == cudaSuccess;
@@ -412,7 +507,8 @@ ht_status ht_server_table_state(ht_server* sv, uint32_t table_id, int32_t* admit
     if (size) {
         *size = 0;
         if (tb.t && !tb.busy) {
-            // Synchronises only the admission stream; the table is idle.
+            // The table is idle; its clear (on the admission stream) may still run.
+            if (!tb.ready_seen && cudaEventSynchronize(tb.ready) != cudaSuccess) return HT_ERR_CUDA;
             DevCounters c;
             if (cudaMemcpy(&c, table_dev(tb.t).ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return HT_ERR_CUDA;
             *size = c.size;
@@ -480,8 +576,16 @@ ht_status ht_server_get_stats(ht_server* sv, ht_server_stats* out, int reset) {
     out->tables_admitted = adm;
     out->admitted_bytes = sv->admitted_bytes;
     out->status = sv->fault;
+    out->admit_seconds = sv->admit_s;
+    out->pack_seconds = sv->pack_s;
+    out->finish_seconds = sv->finish_s;
+    out->batch_us_mean = sv->batches ? sv->batch_us / double(sv->batches) : 0.0;
+    out->batch_gpu_us_mean = sv->batches ? sv->batch_gpu_us / double(sv->batches) : 0.0;
+    out->tables_created = sv->tables_created;
     if (reset) {
         sv->lat_us.clear();
+        sv->admit_s = sv->pack_s = sv->finish_s = sv->batch_us = sv->batch_gpu_us = 0;
+        sv->tables_created = 0;
         sv->requests_done = sv->keys_done = sv->batches = 0;
         sv->stats_t0 = Clock::now();
     }

@@ -129,3 +129,21 @@ def test_admission_with_real_free_memory_after_close():
     st, _, flags = srv.wait(rb, timeout_ms=30000)
     assert st == 0 and flags.sum() == 1000
     srv.close()
+
+
+def test_overfull_table_reports_full_and_others_stay_exact(oracle_lib):
+    # A 64-slot table cannot hold 5000 keys (table + stash + overflow set):
+    # its request reports HT_ERR_FULL (3), sticky for its later requests;
+    # requests of another table in the same batches stay exact.
+    srv = ht.Server(hbm_reserve_bytes=0)
+    small = srv.open_table(64, "bucket")
+    big = srv.open_table(100_000, "bucket")
+    ks, kb = wk.distinct_keys(5000, 64, seed=91), wk.distinct_keys(20_000, 64, seed=92)
+    r1, r2 = srv.submit(small, ks), srv.submit(big, kb)
+    assert srv.wait(r1, timeout_ms=30000)[0] == 3
+    st, _, flags = srv.wait(r2, timeout_ms=30000)
+    assert st == 0 and flags.sum() == 20_000
+    assert srv.wait(srv.submit(small, ks[:10]), timeout_ms=30000)[0] == 3
+    st, _, flags = srv.wait(srv.submit(big, kb[:100]), timeout_ms=30000)
+    assert st == 0 and flags.sum() == 0
+    srv.close()

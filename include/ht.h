@@ -279,7 +279,9 @@ ht_status ht_multi_reset(ht_multi* m, void* stream);
  * array).  mode 0: batched, graph-captured steps; mode 1: the same steps as
  * plain launches; mode 2: one exploration after another with ht_bfs (one
  * table per launch sequence, the baseline).  max_steps 0 = no limit beyond a
- * safety bound.  Synchronises once per step. */
+ * safety bound.  Synchronises once per step.  HT_ERR_FULL when a table had
+ * to drop a key (its capacity was too small for its exploration); the
+ * results are then inexact. */
 ht_status ht_multi_run(ht_multi* m, int mode, uint64_t max_steps, void* stream);
 
 /* Result of exploration i after a run: non-empty levels, states, successors

@@ -26,6 +26,13 @@ using namespace ht;
 namespace ht {
 namespace {
 
+// Status bits of every table of a group (a key that found no place sets
+// kFlagDropped), gathered after a run in one launch.
+__global__ void multi_flags_kernel(const DevTable* __restrict__ tables, uint32_t n, unsigned int* __restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __ldcg(&tables[i].ctr->flags);
+}
+
 constexpr int kAdvThreads = 1024;
 
 // Block-wide sum of one value per thread (blockDim.x == kAdvThreads).
@@ -154,7 +161,9 @@ struct Group {
     uint64_t budget = 0;             // successors per step
     uint64_t max_work = 0, max_tiles = 0;
     unsigned int* h_active = nullptr;  // pinned
+    unsigned int* d_flags = nullptr;   // [count] tables' device status bits after a run
 };
+
 
 }  // namespace
 
@@ -185,6 +194,7 @@ void destroy_multi(ht_multi* m) {
     for (auto& g : m->groups) {
         cudaFree(g.arena);
         cudaFree(g.dev.succ);
+        cudaFree(g.d_flags);
         cudaFreeHost(g.h_active);
     }
     for (void* p : m->states) cudaFree(p);
@@ -306,6 +316,7 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
                                3 * 256 + n * sizeof(DevTable) + 256 + n * sizeof(PreparedModel) + 256 +
                                n * sizeof(void*) + 256;
         if (cudaMalloc(&g.arena, bytes) != cudaSuccess || cudaMalloc(&g.dev.succ, succ_cap * 8) != cudaSuccess ||
+            cudaMalloc(&g.d_flags, n * sizeof(unsigned int)) != cudaSuccess ||
             cudaMallocHost(&g.h_active, sizeof(unsigned int)) != cudaSuccess) {
             destroy_multi(m);
             return HT_ERR_OOM;
@@ -470,8 +481,11 @@ ht_status ht_multi_run(ht_multi* m, int mode, uint64_t max_steps, void* stream) 
             if (st != HT_OK) break;
             const uint64_t n = g.members.size();
             std::vector<unsigned long long> tot(n), gen(n), sz(n * m->max_levels);
-            std::vector<unsigned int> lvl(n), done(n);
-            if (cudaMemcpyAsync(tot.data(), g.dev.total, n * 8, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+            std::vector<unsigned int> lvl(n), done(n), flags(n);
+            multi_flags_kernel<<<uint32_t((n + 255) / 256), 256, 0, m->stream>>>(g.dev.tables, uint32_t(n), g.d_flags);
+            if (cudaGetLastError() != cudaSuccess ||
+                cudaMemcpyAsync(flags.data(), g.d_flags, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+                cudaMemcpyAsync(tot.data(), g.dev.total, n * 8, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
                 cudaMemcpyAsync(gen.data(), g.dev.gen, n * 8, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
                 cudaMemcpyAsync(lvl.data(), g.dev.level, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
                 cudaMemcpyAsync(done.data(), g.dev.done, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
@@ -483,6 +497,8 @@ ht_status ht_multi_run(ht_multi* m, int mode, uint64_t max_steps, void* stream) 
             }
             for (uint64_t i = 0; i < n; ++i) {
                 const uint32_t e = g.members[i];
+                // A table that dropped a key makes the exploration inexact.
+                if (flags[i] & kFlagDropped) st = HT_ERR_FULL;
                 m->res_complete[e] = done[i] == 1;
                 m->res_states[e] = std::min<uint64_t>(tot[i], m->states_cap[e]);
                 m->res_levels[e] = tot[i] ? uint64_t(lvl[i]) + 1 : 0;

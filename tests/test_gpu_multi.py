@@ -100,3 +100,19 @@ def test_multi_full_batched_workload_against_stored_levels():
             assert digest(got[off:off + n_d])[1:] == lev[1:3], (i, d)
             off += n_d
     mx.close()
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_multi_reports_a_table_too_small_for_its_exploration(oracle_lib, mode):
+    # Exploration 1's table (256 slots + stash + overflow set, ~1400 keys)
+    # cannot hold its ~20000 reachable states: the run reports HT_ERR_FULL
+    # instead of returning an inexact exploration.
+    ok = ss.random_model(3, C=4, L=8, R=[3, 5, 4, 2], p_sync=0.3, P=2)
+    big = ss.random_model(55, C=10, L=16, R=[4, 4, 4, 4, 4, 3, 3, 3, 3, 4], p_sync=0.1, P=2)
+    r_ok, r_big = oracle_lib.bfs(ok, max_states=1 << 22), oracle_lib.bfs(big, max_states=1 << 22)
+    assert r_big.total > 10_000
+    mx = ht.MultiExploration([hmodel(ok), hmodel(big)], [0, 0], [max(256, int(r_ok.total / 0.7)), 256])
+    with pytest.raises(ht.HtError) as e:
+        mx.run(mode=mode)
+    assert e.value.status == 3
+    mx.close()

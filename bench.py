@@ -742,7 +742,11 @@ def run_serving(ht, a):
     out = {"workload": "%d requests over %d tables (2^12..2^30 slots, sessions), batch 1..2^20 keys log-uniform "
                        "(mean %d), Poisson %.0f req/s offered" % (len(sizes), len(set(table.tolist())),
                                                                   int(sizes.mean()), a.serve_rate)}
-    keys = serving_keys(trace)
+    import torch
+    # Request keys live in page-locked host memory, as a serving front end
+    # that receives them into pinned buffers would hold them.
+    pinned = [torch.from_numpy(k.view(np.int64)).pin_memory() for k in serving_keys(trace)]
+    keys = [p.numpy().view(np.uint64) for p in pinned]
     out["continuous_batching"] = run_serving_once(ht, a, pack=1, inflight=4, trace=trace, keys=keys)
     out["per_request_launches"] = run_serving_once(ht, a, pack=0, inflight=1, trace=trace, keys=keys)
     return out

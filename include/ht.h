@@ -356,7 +356,10 @@ ht_status ht_server_close_table(ht_server* s, uint32_t table_id);
 /* admitted: 1 admitted, 0 waiting, -1 closed; size: stored keys (0 while busy). */
 ht_status ht_server_table_state(ht_server* s, uint32_t table_id, int32_t* admitted, uint64_t* size);
 /* Queues a find-or-put of n keys (host memory, valid until the request
- * completes); h_is_new (nullable, n bytes, host) receives the flags.
+ * completes); h_is_new (nullable, n bytes, host) receives the flags.  Keys of
+ * a large request (>= 2^16) in page-locked memory (cudaMallocHost,
+ * cudaHostRegister) go to the device straight from h_keys; others are copied
+ * through the server's own page-locked staging.
  * HT_ERR_INVALID if n exceeds batch_key_budget or the table is closing. */
 ht_status ht_server_submit(ht_server* s, uint32_t table_id, const uint64_t* h_keys, uint64_t n,
                            uint8_t* h_is_new, uint64_t* request_id);

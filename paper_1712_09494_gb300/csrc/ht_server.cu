@@ -40,6 +40,7 @@ struct Req {
     uint64_t n = 0;
     uint8_t* out = nullptr;
     Clock::time_point t0, t1;
+    bool pinned = false;           // keys are in page-locked host memory
     int state = 0;                 // 0 queued, 1 in flight, 2 done
     ht_status status = HT_OK;
 };
@@ -122,6 +123,9 @@ struct ht_server {
 namespace {
 
 constexpr uint32_t kMaxServerTables = 1u << 16;
+// Requests at least this large whose keys are in page-locked memory are
+// copied to the device straight from the caller's buffer (no staging copy).
+constexpr uint64_t kDirectCopyKeys = 1u << 16;
 
 uint64_t free_bytes(ht_server* sv) {
     if (sv->cfg.fake_free_bytes) {
@@ -238,6 +242,11 @@ bool launch(ht_server* sv, Slot& sl) {
         uint64_t off, n;
     };
     std::vector<CuckooJob> cuckoo;
+    struct Copy {
+        uint64_t off, n;
+        const uint64_t* src;          // caller's pinned keys, or null: from the staging buffer
+    };
+    std::vector<Copy> staged, direct;
     const size_t nt = sv->tabs.size();
     const uint32_t max_reqs = sv->cfg.pack ? sv->cfg.max_requests_per_batch : 1u;
     for (size_t k = 0; k < nt && sl.reqs.size() < max_reqs; ++k) {
@@ -250,7 +259,13 @@ bool launch(ht_server* sv, Slot& sl) {
         }
         Req& r = sv->reqs[tb.q.front()];
         if (off + r.n > budget && off > 0) continue;
-        std::memcpy(sl.h_keys + off, r.keys, r.n * 8);
+        if (r.pinned && r.n >= kDirectCopyKeys) {
+            direct.push_back(Copy{off, r.n, r.keys});
+        } else {
+            std::memcpy(sl.h_keys + off, r.keys, r.n * 8);
+            if (!staged.empty() && staged.back().off + staged.back().n == off) staged.back().n += r.n;
+            else staged.push_back(Copy{off, r.n, nullptr});
+        }
         if (tb.scheme == HT_BUCKET) {
             sl.h_desc[nb].key_off = off;
             sl.h_desc[nb].n = r.n;
@@ -272,7 +287,11 @@ bool launch(ht_server* sv, Slot& sl) {
     if (sl.reqs.empty()) return false;
     sv->rr = (sv->rr + 1) % std::max<size_t>(nt, 1);
     cudaError_t e = cudaEventRecord(sl.ev0, sl.s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.d_keys, sl.h_keys, off * 8, cudaMemcpyHostToDevice, sl.s);
+    for (const Copy& c : staged)
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sl.d_keys + c.off, sl.h_keys + c.off, c.n * 8, cudaMemcpyHostToDevice, sl.s);
+    for (const Copy& c : direct)
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sl.d_keys + c.off, c.src, c.n * 8, cudaMemcpyHostToDevice, sl.s);
     if (e == cudaSuccess && nb) e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, nb * sizeof(ServeDesc), cudaMemcpyHostToDevice, sl.s);
     if (e == cudaSuccess && nb)
         e = serve_bucket_find_or_put(table_bucket_cfg(sv->tabs[sl.h_desc[0].table].t), sv->d_tables, sl.d_desc, nb, tiles,
@@ -528,6 +547,11 @@ ht_status ht_server_submit(ht_server* sv, uint32_t table_id, const uint64_t* h_k
     r.keys = h_keys;
     r.n = n;
     r.out = h_is_new;
+    if (n >= kDirectCopyKeys) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, h_keys) == cudaSuccess) r.pinned = a.type == cudaMemoryTypeHost;
+        else cudaGetLastError();
+    }
     r.t0 = Clock::now();
     sv->tabs[table_id].q.push_back(id);
     *request_id = id;

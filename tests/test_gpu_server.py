@@ -147,3 +147,24 @@ def test_overfull_table_reports_full_and_others_stay_exact(oracle_lib):
     st, _, flags = srv.wait(srv.submit(big, kb[:100]), timeout_ms=30000)
     assert st == 0 and flags.sum() == 0
     srv.close()
+
+
+def test_pinned_requests_match_pageable(oracle_lib):
+    # Large requests whose keys sit in page-locked memory are copied to the
+    # device straight from the caller's buffer; results are the same.
+    reqs = [wk.distinct_keys(n, 64, seed=95 + i) for i, n in enumerate([70_000, 1000, 200_000, 65_536])]
+    reqs[2][:50_000] = reqs[0][:50_000]                 # repeats across requests of one table
+    pinned = [torch.from_numpy(k.view(np.int64)).pin_memory() for k in reqs]
+    srv = ht.Server(hbm_reserve_bytes=0)
+    t_pin, t_page = srv.open_table(600_000, "bucket"), srv.open_table(600_000, "bucket")
+    rp = [srv.submit(t_pin, p.numpy().view(np.uint64)) for p in pinned]
+    rq = [srv.submit(t_page, k) for k in reqs]
+    orc = oracle_lib.OracleTable()
+    for k, a, b in zip(reqs, rp, rq):
+        sa, _, fa = srv.wait(a, timeout_ms=30000)
+        sb, _, fb = srv.wait(b, timeout_ms=30000)
+        assert sa == sb == 0
+        exp = orc.find_or_put(k)
+        assert_flags_per_key(k, fa, exp)
+        assert_flags_per_key(k, fb, exp)
+    srv.close()

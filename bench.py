@@ -375,6 +375,7 @@ def run_ours(a, rank, world, local):
     tables = {}
     if not a.no_small:
         out["small_map_config1"] = run_small_map(ht, torch, dev, schemes)
+        out["many_tables_one_call"] = run_multi_table(ht, torch, dev)
     if not a.no_bfs:
         out["bfs_config3"] = run_bfs(ht, torch, dev, schemes)
     if not a.no_batched:
@@ -594,6 +595,58 @@ def run_batched(ht, torch):
                                       "classes_tuned": n_classes, "chosen": shapes}
     mx.close()
     return res
+
+
+def run_multi_table(ht, torch, dev, n_tables=1024, keys_per=4096, rounds=8):
+    """Many small tables: every round gives each of 1024 bucket tables (2^16
+    slots) 4096 keys (25% repeats of its earlier keys); one
+    ht_multi_find_or_put call per round against one ht_find_or_put per table.
+    Results are checked equal (per table, the stored-key counts)."""
+    from workloads import keys as wk
+    rng = np.random.default_rng(17)
+    fresh_per = keys_per * 3 // 4
+    batches = []
+    for r in range(rounds):
+        per = []
+        for t in range(n_tables):
+            k = wk.distinct_keys(keys_per, 64, seed=2000 + t, start=r * fresh_per)
+            if r:
+                k[fresh_per:] = wk.distinct_keys(r * fresh_per, 64, seed=2000 + t)[
+                    rng.integers(0, r * fresh_per, size=keys_per - fresh_per)]
+            per.append(k)
+        batches.append(torch.from_numpy(np.stack(per).view(np.int64)).to(dev))
+    flags = torch.empty(n_tables, keys_per, dtype=torch.uint8, device=dev)
+    out = {"workload": "%d bucket tables of 2^16 slots, %d rounds of %d keys per table (25%% repeats)" % (
+        n_tables, rounds, keys_per)}
+    sizes = {}
+    for mode in ("packed", "per_table"):
+        tabs = [ht.HashTable(1 << 16, "bucket", 64) for _ in range(n_tables)]
+        handles = [t.handle for t in tabs]
+
+        def run():
+            for b in batches:
+                if mode == "packed":
+                    ht.ht_multi_find_or_put(handles, [(i, b[i], flags[i]) for i in range(n_tables)])
+                else:
+                    for i in range(n_tables):
+                        ht.ht_find_or_put(handles[i], b[i], flags[i])
+
+        run()                                            # warm-up (and exactness check below)
+        torch.cuda.synchronize()
+        for t in tabs:
+            t.clear()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run()
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        sizes[mode] = [t.size() for t in tabs]
+        out[mode] = {"seconds": round(sec, 4), "mops": round(n_tables * keys_per * rounds / sec / 1e6, 1)}
+        for t in tabs:
+            t.close()
+    out["exact"] = sizes["packed"] == sizes["per_table"] == [fresh_per * rounds] * n_tables
+    out["speedup_packed_vs_per_table"] = round(out["per_table"]["seconds"] / out["packed"]["seconds"], 2)
+    return out
 
 
 def run_small_map(ht, torch, dev, schemes, reps=10):

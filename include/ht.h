@@ -255,6 +255,32 @@ ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max
                  ht_bfs_result* result, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched find-or-put over many tables in one call (the batched form of
+ * Section 5's find-or-insert, for workloads with many small tables).  Item i
+ * runs find-or-put of h_list[i].n keys (device memory, the key width of
+ * tables[h_list[i].table]) and writes is_new to h_list[i].d_is_new (device,
+ * nullable).  Bucket-scheme items with the same key width and bucket shape
+ * run together in one launch, one 32-key tile per warp against its own
+ * table; Cuckoo items run one after another in list order.  Items that name
+ * the same table behave as one batch: a key new to the table is flagged new
+ * in exactly one of its occurrences across them.  Asynchronous on `stream`;
+ * every table must be used on this stream only meanwhile.  A table's own
+ * errors (full, reserved keys) are reported at its next synchronising call
+ * (ht_sync, ht_size, ht_stats), as for ht_find_or_put.  HT_ERR_INVALID for a
+ * NULL table, an item naming a table >= ntables, or n > 0 with NULL keys.
+ * ------------------------------------------------------------------------- */
+typedef struct ht_work {
+    uint32_t table;          /* index into tables[] */
+    uint32_t reserved_;
+    const void* d_keys;
+    uint64_t n;
+    uint8_t* d_is_new;
+} ht_work;
+
+ht_status ht_multi_find_or_put(ht_table* const* tables, uint32_t ntables, const ht_work* h_list, uint32_t m,
+                               void* stream);
+
+/* ---------------------------------------------------------------------------
  * Batched exploration: `count` independent explorations (models of uneven
  * sizes) advanced together.  Each exploration gets its own bucket-scheme
  * table of h_capacity[i] slots (h_params: NULL or `count` parameter sets;

@@ -15,14 +15,14 @@ import ctypes
 import torch
 
 from ._lib import (HT_BUCKET, HT_CUCKOO, HtBfsResult, HtError, HtModel, HtParams, HtServerConfig,
-                   HtServerStats, HtTableStats, load)
+                   HtServerStats, HtTableStats, HtWork, load)
 
 __all__ = [
     "HT_BUCKET", "HT_CUCKOO", "HtError", "HtParams", "HashTable", "load",
     "ht_default_params", "ht_create", "ht_destroy", "ht_find_or_put", "ht_find_or_put_append",
     "ht_insert", "ht_lookup", "ht_sync", "ht_size", "ht_export", "ht_clear", "ht_info",
     "ht_compact", "ht_prof_enable", "ht_prof_reset", "ht_prof_read", "ht_prof_kernels",
-    "ht_probe_random_read", "ht_probe_random_rmw", "ht_stats", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
+    "ht_probe_random_read", "ht_probe_random_rmw", "ht_stats", "ht_multi_find_or_put", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
     "NOALLOC_MAX_BATCH", "scheme_of", "HtModel", "HtBfsResult", "make_model", "ht_successors", "ht_bfs",
     "MultiExploration", "Server", "HtServerConfig", "HtServerStats",
 ]
@@ -147,6 +147,36 @@ def ht_info(table):
     s, k, r = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
     _check(load().ht_info(table, ctypes.byref(s), ctypes.byref(k), ctypes.byref(r)), "ht_info")
     return dict(slots=s.value, num_hashes=k.value, rebuilds=r.value)
+
+
+def ht_multi_find_or_put(tables, items, stream=None):
+    """find-or-put over many tables in one call: `tables` a list of handles,
+    `items` a list of (table index, keys tensor, is_new uint8 tensor or None)."""
+    import numpy as np
+    n = len(tables)
+    arr_t = (ctypes.c_void_p * max(1, n))(*[getattr(t, "value", t) for t in tables])
+    w = np.zeros(max(1, len(items)), dtype=_WORK_DTYPE)
+    for i, (ti, keys, is_new) in enumerate(items):
+        if not (keys.is_cuda and keys.is_contiguous()):
+            raise ValueError("keys of item %d must be a contiguous CUDA tensor" % i)
+        if is_new is not None and not (is_new.is_cuda and is_new.is_contiguous()):
+            raise ValueError("is_new of item %d must be a contiguous CUDA tensor" % i)
+        w[i] = (ti, 0, keys.data_ptr() if keys.numel() else 0, keys.numel(),
+                is_new.data_ptr() if is_new is not None and is_new.numel() else 0)
+    _check(load().ht_multi_find_or_put(arr_t, n, w.ctypes.data_as(ctypes.c_void_p), len(items), _stream(stream)),
+           "ht_multi_find_or_put")
+
+
+# numpy layout of ht_work (include/ht.h), checked against the ctypes struct.
+def _work_dtype():
+    import numpy as np
+    dt = np.dtype([("table", "<u4"), ("reserved_", "<u4"), ("d_keys", "<u8"), ("n", "<u8"), ("d_is_new", "<u8")])
+    assert dt.itemsize == ctypes.sizeof(HtWork)
+    assert all(dt.fields[f][1] == getattr(HtWork, f).offset for f, _ in HtWork._fields_)
+    return dt
+
+
+_WORK_DTYPE = _work_dtype()
 
 
 def ht_stats(table, stream=None):

@@ -66,6 +66,13 @@ class HtTableStats(ctypes.Structure):
     ]
 
 
+class HtWork(ctypes.Structure):
+    _fields_ = [
+        ("table", ctypes.c_uint32), ("reserved_", ctypes.c_uint32), ("d_keys", ctypes.c_void_p),
+        ("n", ctypes.c_uint64), ("d_is_new", ctypes.c_void_p),
+    ]
+
+
 class HtError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -90,6 +97,7 @@ SIGNATURES = {
     "ht_clear": (_I32, [_VP, _VP]),
     "ht_info": (_I32, [_VP, _P(_U64), _P(_U32), _P(_U32)]),
     "ht_stats": (_I32, [_VP, _P(HtTableStats), _VP]),
+    "ht_multi_find_or_put": (_I32, [_VP, _U32, _VP, _U32, _VP]),
     "ht_status_str": (ctypes.c_char_p, [_I32]),
     "ht_compact": (_I32, [_VP, _VP, _U64, _U32, _VP, _VP, _VP]),
     "ht_prof_enable": (_I32, [ctypes.c_int]),

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "ht_internal.cuh"
 
@@ -245,6 +246,20 @@ void free_table(ht_table* t, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+// Bucket-scheme items of one ht_multi_find_or_put call that share a key
+// width and bucket shape (one packed launch).
+struct PackGroup {
+    BucketCfg cfg;
+    std::vector<DevTable> tabs;
+    std::vector<uint32_t> slot_of;   // table index -> position in tabs (or ~0)
+    std::vector<WorkDesc> items;
+    uint64_t tiles = 0;
+};
+
+}  // namespace
+
 extern "C" {
 
 const char* ht_status_str(ht_status s) {
@@ -389,6 +404,74 @@ ht_status ht_lookup(ht_table* t, const void* d_keys, uint64_t n, uint32_t* d_val
     if (t->scheme == HT_BUCKET)
         return cuda_status(bucket_lookup(bucket_cfg(t), t->dt, d_keys, n, d_values, d_found, s, t->win));
     return cuda_status(cuckoo_lookup(int(t->kw), t->dt, d_keys, n, d_values, d_found, s, t->win));
+}
+
+ht_status ht_multi_find_or_put(ht_table* const* tables, uint32_t ntables, const ht_work* list, uint32_t m,
+                               void* stream) {
+    if (m && (!tables || !list)) return HT_ERR_INVALID;
+    for (uint32_t i = 0; i < m; ++i) {
+        if (list[i].table >= ntables || !tables[list[i].table]) return HT_ERR_INVALID;
+        if (list[i].n && !list[i].d_keys) return HT_ERR_INVALID;
+    }
+    if (!m) return HT_OK;
+    DeviceGuard g(tables[list[0].table]->device);
+    const cudaStream_t s = as_stream(stream);
+    // Bucket items, grouped by key width and bucket shape: one packed launch
+    // per group.  A group's tables and items go to the device in one
+    // stream-ordered scratch block.
+    std::vector<PackGroup> groups;
+    for (uint32_t i = 0; i < m; ++i) {
+        const ht_work& w = list[i];
+        ht_table* t = tables[w.table];
+        if (t->scheme != HT_BUCKET || w.n == 0) continue;
+        const BucketCfg c = bucket_cfg(t);
+        PackGroup* gp = nullptr;
+        for (auto& gr : groups)
+            if (gr.cfg.kw == c.kw && gr.cfg.bucket_slots == c.bucket_slots && gr.cfg.lanes == c.lanes) gp = &gr;
+        if (!gp) {
+            groups.emplace_back();
+            gp = &groups.back();
+            gp->cfg = c;
+            gp->slot_of.assign(ntables, ~0u);
+        }
+        if (gp->slot_of[w.table] == ~0u) {
+            gp->slot_of[w.table] = uint32_t(gp->tabs.size());
+            gp->tabs.push_back(t->dt);
+        }
+        WorkDesc d;
+        d.keys = w.d_keys;
+        d.flags = w.d_is_new;
+        d.n = w.n;
+        d.tile_off = gp->tiles;
+        d.table = gp->slot_of[w.table];
+        d.pad_ = 0;
+        gp->items.push_back(d);
+        gp->tiles += (w.n + 31) / 32;
+    }
+    for (auto& gr : groups) {
+        const size_t tb = gr.tabs.size() * sizeof(DevTable), ib = gr.items.size() * sizeof(WorkDesc);
+        const size_t toff = (ib + 255) / 256 * 256;
+        char* scratch = nullptr;
+        HT_TRY(cudaMallocAsync(&scratch, toff + tb, s));
+        // Pageable sources: each copy has read its source when the call returns.
+        cudaError_t e = cudaMemcpyAsync(scratch, gr.items.data(), ib, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + toff, gr.tabs.data(), tb, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = packed_bucket_find_or_put(gr.cfg, reinterpret_cast<const DevTable*>(scratch + toff),
+                                          reinterpret_cast<const WorkDesc*>(scratch), uint32_t(gr.items.size()),
+                                          gr.tiles, s);
+        cudaFreeAsync(scratch, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    // Cuckoo items, in list order.
+    for (uint32_t i = 0; i < m; ++i) {
+        const ht_work& w = list[i];
+        ht_table* t = tables[w.table];
+        if (t->scheme != HT_CUCKOO || w.n == 0) continue;
+        const ht_status st = run_put(t, w.d_keys, nullptr, w.n, w.d_is_new, nullptr, nullptr, s);
+        if (st != HT_OK) return st;
+    }
+    return HT_OK;
 }
 
 ht_status ht_sync(ht_table* t, void* stream) {

@@ -563,30 +563,31 @@ cudaError_t launch_multi(const MultiDev& m, uint64_t max_tiles, bool init, cudaS
     return cudaGetLastError();
 }
 
-// Serving: warp w takes tile w of a packed batch of requests, each tile
-// against its request's table.
-template <int BS, int G>
+// Packed multi-table find-or-put (the serving loop's batches and
+// ht_multi_find_or_put): warp w takes tile w of the packed items, each tile
+// against its item's table.
+template <int KW, int BS, int G>
 __global__ void __launch_bounds__(kBlock, HT_BUCKET_MIN_BLOCKS)
-serve_bucket_kernel(const DevTable* __restrict__ tables, const ServeDesc* __restrict__ reqs, uint32_t nreq,
-                    uint64_t ntiles, const uint64_t* __restrict__ keys, uint8_t* __restrict__ flags) {
-    using K = Keys<64>;
+packed_bucket_kernel(const DevTable* __restrict__ tables, const WorkDesc* __restrict__ items, uint32_t nitems,
+                     uint64_t ntiles) {
+    using K = Keys<KW>;
     const int lane = threadIdx.x & 31;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
     for (uint64_t tile = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; tile < ntiles; tile += nwarps) {
-        uint32_t a = 0, b = nreq;                      // largest r with tile_off[r] <= tile
+        uint32_t a = 0, b = nitems;                    // largest r with tile_off[r] <= tile
         while (b - a > 1) {
             const uint32_t mid = (a + b) / 2;
-            if (reqs[mid].tile_off <= tile) a = mid; else b = mid;
+            if (items[mid].tile_off <= tile) a = mid; else b = mid;
         }
-        const ServeDesc d = reqs[a];
+        const WorkDesc d = items[a];
         const uint64_t i = (tile - d.tile_off) * 32 + lane;
         const bool mine = i < d.n;
-        const uint64_t key = mine ? keys[d.key_off + i] : 0;
+        const uint64_t key = mine ? K::load(d.keys, i) : 0;
         const bool ok = mine && !K::reserved(key);
         const DevTable& t = tables[d.table];
         if (mine && !ok) set_flag(t.ctr, kFlagInvalidKey);
-        const uint32_t my_new = bucket_tile<64, BS, G>(t, key, 0, ok);
-        if (mine) flags[d.key_off + i] = uint8_t(my_new);
+        const uint32_t my_new = bucket_tile<KW, BS, G>(t, key, 0, ok);
+        if (mine && d.flags) d.flags[i] = uint8_t(my_new);
         const unsigned nm = __ballot_sync(kFull, my_new != 0);
         if (lane == 0 && nm) atomicAdd(&t.ctr->size, (unsigned long long)__popc(nm));
     }
@@ -631,20 +632,25 @@ cudaError_t multi_bucket_init(const BucketCfg& c, const MultiDev& m, cudaStream_
     return cudaErrorInvalidValue;
 }
 
-cudaError_t serve_bucket_find_or_put(const BucketCfg& c, const DevTable* tables, const ServeDesc* reqs,
-                                     uint32_t nreq, uint64_t ntiles, const uint64_t* keys, uint8_t* flags,
-                                     cudaStream_t s) {
-    if (!nreq || !ntiles) return cudaSuccess;
+cudaError_t packed_bucket_find_or_put(const BucketCfg& c, const DevTable* tables, const WorkDesc* items,
+                                      uint32_t nitems, uint64_t ntiles, cudaStream_t s) {
+    if (!nitems || !ntiles) return cudaSuccess;
     ProfScope ps(kKBucketFop, s);
-#define X(BS, G)                                                                                  \
-    if (c.bucket_slots == BS && c.lanes == G) {                                                   \
-        auto k = serve_bucket_kernel<BS, G>;                                                      \
+#define L(KW, BS, G)                                                                                      \
+    {                                                                                                     \
+        auto k = packed_bucket_kernel<KW, BS, G>;                                                         \
         const int grid = int(std::min<uint64_t>(launch_blocks((const void*)k, kBlock), (ntiles + 7) / 8)); \
-        k<<<grid, kBlock, 0, s>>>(tables, reqs, nreq, ntiles, keys, flags);                       \
-        return cudaGetLastError();                                                                \
+        k<<<grid, kBlock, 0, s>>>(tables, items, nitems, ntiles);                                         \
+        return cudaGetLastError();                                                                        \
+    }
+#define X(BS, G)                                                                                          \
+    if (c.bucket_slots == BS && c.lanes == G) {                                                           \
+        if (c.kw == 32) L(32, BS, G)                                                                      \
+        L(64, BS, G)                                                                                      \
     }
     HT_BUCKET_CONFIGS(X)
 #undef X
+#undef L
     return cudaErrorInvalidValue;
 }
 

@@ -388,17 +388,20 @@ cudaError_t multi_bucket_init(const BucketCfg& c, const MultiDev& m, cudaStream_
 
 // One packed serving batch: request r's n keys sit at keys[key_off, +n) and
 // its tiles of 32 keys start at tile index tile_off (ht_server.cu).
-struct ServeDesc {
-    uint64_t key_off;
+// One item of a packed multi-table find-or-put: n keys (device, the table's
+// key width) against tables[table]; flags[i] = is_new (nullable).  Tiles of
+// 32 keys are numbered across the items: the item's first is tile_off.
+struct WorkDesc {
+    const void* keys;
+    uint8_t* flags;
     uint64_t n;
     uint64_t tile_off;
     uint32_t table;
     uint32_t pad_;
 };
-// find-or-put of every request of a batch against its own (64-bit key,
-// bucket scheme) table; flags[key_off + i] = is_new.
-cudaError_t serve_bucket_find_or_put(const BucketCfg& c, const DevTable* tables, const ServeDesc* reqs,
-                                     uint32_t nreq, uint64_t ntiles, const uint64_t* keys, uint8_t* flags,
-                                     cudaStream_t s);
+// find-or-put of every item against its own bucket-scheme table (all of the
+// key width and bucket shape `c`), one warp per tile, in one launch.
+cudaError_t packed_bucket_find_or_put(const BucketCfg& c, const DevTable* tables, const WorkDesc* items,
+                                      uint32_t nitems, uint64_t ntiles, cudaStream_t s);
 
 }  // namespace ht

@@ -61,12 +61,12 @@ struct Slot {
     cudaEvent_t ev0 = nullptr, ev = nullptr;   // batch start / end on the slot's stream
     uint64_t* h_keys = nullptr;    // pinned staging
     uint8_t* h_flags = nullptr;
-    ServeDesc* h_desc = nullptr;
+    WorkDesc* h_desc = nullptr;
     uint32_t* h_tid = nullptr;     // per request of the batch: its table id ...
     uint32_t* h_flagw = nullptr;   // ... and that table's device status bits after the batch
     uint64_t* d_keys = nullptr;
     uint8_t* d_flags = nullptr;
-    ServeDesc* d_desc = nullptr;
+    WorkDesc* d_desc = nullptr;
     uint32_t* d_tid = nullptr;
     uint32_t* d_flagw = nullptr;
     std::vector<std::pair<uint64_t, uint64_t>> reqs;   // (request id, key offset)
@@ -267,7 +267,8 @@ bool launch(ht_server* sv, Slot& sl) {
             else staged.push_back(Copy{off, r.n, nullptr});
         }
         if (tb.scheme == HT_BUCKET) {
-            sl.h_desc[nb].key_off = off;
+            sl.h_desc[nb].keys = sl.d_keys + off;
+            sl.h_desc[nb].flags = sl.d_flags + off;
             sl.h_desc[nb].n = r.n;
             sl.h_desc[nb].tile_off = tiles;
             sl.h_desc[nb].table = id;
@@ -292,10 +293,10 @@ bool launch(ht_server* sv, Slot& sl) {
             e = cudaMemcpyAsync(sl.d_keys + c.off, sl.h_keys + c.off, c.n * 8, cudaMemcpyHostToDevice, sl.s);
     for (const Copy& c : direct)
         if (e == cudaSuccess) e = cudaMemcpyAsync(sl.d_keys + c.off, c.src, c.n * 8, cudaMemcpyHostToDevice, sl.s);
-    if (e == cudaSuccess && nb) e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, nb * sizeof(ServeDesc), cudaMemcpyHostToDevice, sl.s);
+    if (e == cudaSuccess && nb) e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, nb * sizeof(WorkDesc), cudaMemcpyHostToDevice, sl.s);
     if (e == cudaSuccess && nb)
-        e = serve_bucket_find_or_put(table_bucket_cfg(sv->tabs[sl.h_desc[0].table].t), sv->d_tables, sl.d_desc, nb, tiles,
-                                     sl.d_keys, sl.d_flags, sl.s);
+        e = packed_bucket_find_or_put(table_bucket_cfg(sv->tabs[sl.h_desc[0].table].t), sv->d_tables, sl.d_desc, nb,
+                                      tiles, sl.s);
     for (const auto& c : cuckoo) {
         if (e != cudaSuccess) break;
         if (ht_find_or_put(sv->tabs[c.table].t, sl.d_keys + c.off, c.n, sl.d_flags + c.off, sl.s) != HT_OK)
@@ -469,14 +470,14 @@ ht_status ht_server_create(const ht_server_config* cfg, ht_server** out) {
              cudaEventCreate(&sl.ev0) == cudaSuccess && cudaEventCreate(&sl.ev) == cudaSuccess &&
              cudaMallocHost(&sl.h_keys, c.batch_key_budget * 8) == cudaSuccess &&
              cudaMallocHost(&sl.h_flags, c.batch_key_budget) == cudaSuccess &&
-             cudaMallocHost(&sl.h_desc, nreq * sizeof(ServeDesc)) == cudaSuccess &&
+             cudaMallocHost(&sl.h_desc, nreq * sizeof(WorkDesc)) == cudaSuccess &&
              cudaMallocHost(&sl.h_tid, nreq * sizeof(uint32_t)) == cudaSuccess &&
              cudaMallocHost(&sl.h_flagw, nreq * sizeof(uint32_t)) == cudaSuccess &&
              cudaMalloc(&sl.d_tid, nreq * sizeof(uint32_t)) == cudaSuccess &&
              cudaMalloc(&sl.d_flagw, nreq * sizeof(uint32_t)) == cudaSuccess &&
              cudaMalloc(&sl.d_keys, c.batch_key_budget * 8) == cudaSuccess &&
              cudaMalloc(&sl.d_flags, c.batch_key_budget) == cudaSuccess &&
-             cudaMalloc(&sl.d_desc, nreq * sizeof(ServeDesc)) == cudaSuccess;
+             cudaMalloc(&sl.d_desc, nreq * sizeof(WorkDesc)) == cudaSuccess;
     }
     if (!ok) {
         destroy_server(sv);

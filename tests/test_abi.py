@@ -73,6 +73,8 @@ def test_null_arguments_are_invalid(lib):
     assert lib.ht_probe_random_read(None, 0, 32, 1, 1, None, None) == 1
     assert lib.ht_probe_random_rmw(None, 0, 1, 1, None) == 1
     assert lib.ht_stats(None, None, None) == 1
+    assert lib.ht_multi_find_or_put(None, 0, None, 3, None) == 1
+    assert lib.ht_multi_find_or_put(None, 0, None, 0, None) == 0
     assert lib.ht_destroy(None) == 0
     assert lib.ht_status_str(3) == b"table full: keys could not be placed"
 

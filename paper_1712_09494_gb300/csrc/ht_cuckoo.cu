@@ -128,34 +128,24 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                 }
             }
         } else {
-            // In-batch dedup: the one claimant of each absent key wins.  First
-            // claim attempt of every miss together; collisions fall back to the
-            // linear-probing loop.
+            // In-batch dedup: the one claimant of each absent key wins.  Every
+            // miss first CASes its key into its slot of the claim set (kept in
+            // L2); a slot holding another key sends it on by linear probing.
             uint32_t spos[kU];
             uint64_t sw[kU];
             bool need[kU], winner[kU];
-    #pragma unroll
+#pragma unroll
             for (int u = 0; u < kU; ++u) {
                 need[u] = act[u] && !found[u];
                 spos[u] = uint32_t(mix64(key[u] ^ dseed) & sc.mask);
                 sw[u] = kEmpty;
-                if (need[u]) sw[u] = __ldcg(reinterpret_cast<const unsigned long long*>(sc.set + spos[u]));
+                if (need[u]) sw[u] = atomicCAS(reinterpret_cast<unsigned long long*>(sc.set + spos[u]), kEmpty, key[u]);
             }
-            bool won[kU];
-    #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                won[u] = false;
-                if (need[u] && sw[u] == kEmpty) {
-                    const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(sc.set + spos[u]), kEmpty, key[u]);
-                    won[u] = old == kEmpty;
-                    sw[u] = old;
-                }
-            }
-    #pragma unroll
+#pragma unroll
             for (int u = 0; u < kU; ++u) {
                 winner[u] = false;
                 if (!need[u]) continue;
-                if (won[u]) {
+                if (sw[u] == kEmpty) {
                     winner[u] = true;                          // our CAS filled the empty slot
                 } else if (K::keyof(sw[u]) != key[u]) {        // another key sits there: probe on
                     uint32_t at = 0;
@@ -164,25 +154,31 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     spos[u] = at;
                 }
             }
-    #pragma unroll
+            // Append the round's winners to the insert list: one atomic per warp.
+            unsigned wm[kU];
+            unsigned total = 0;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                wm[u] = __ballot_sync(0xFFFFFFFFu, winner[u]);
+                total += __popc(wm[u]);
+            }
+            unsigned int b = 0;
+            if (total) {
+                if (lane == 0) b = atomicAdd(&t.ctr->winners[parity], total);
+                b = __shfl_sync(0xFFFFFFFFu, b, 0);
+            }
+#pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const uint64_t i = (r * kU + u) * stride + tid;
                 if (i < n && out_flag) out_flag[i] = uint8_t(winner[u]);
-                // Warp-aggregated append of the winners to the insert list.
-                const unsigned wm = __ballot_sync(0xFFFFFFFFu, winner[u]);
-                if (wm) {
-                    const int leader = __ffs(wm) - 1;
-                    unsigned int b = 0;
-                    if (lane == leader) b = atomicAdd(&t.ctr->winners[parity], unsigned(__popc(wm)));
-                    b = __shfl_sync(0xFFFFFFFFu, b, leader);
-                    if (winner[u]) {
-                        Winner wn;
-                        wn.word = K::word(key[u], VALUES ? vals[i] : 0u);
-                        wn.spos = spos[u];
-                        wn.pad_ = 0;
-                        sc.win[b + __popc(wm & ((1u << lane) - 1))] = wn;
-                    }
+                if (winner[u]) {
+                    Winner wn;
+                    wn.word = K::word(key[u], VALUES ? vals[i] : 0u);
+                    wn.spos = spos[u];
+                    wn.pad_ = 0;
+                    sc.win[b + __popc(wm[u] & ((1u << lane) - 1))] = wn;
                 }
+                b += __popc(wm[u]);
             }
         }
     }

@@ -321,10 +321,13 @@ bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_
                   uint64_t new_cap) {
     if (d_n) n = min(n, uint64_t(__ldcg(d_n)));        // batch size produced on the device
     using K = Keys<KW>;
+    using T = typename K::T;
     const int lane = threadIdx.x & 31;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
     const uint64_t step = nwarps * 32;
     unsigned long long stored = 0;
+    __shared__ T s_new[APPEND ? kBlock / 32 : 1][APPEND ? kStageCap : 1];   // new keys awaiting the append
+    WarpStage<T, kStageCap> stage(s_new[APPEND ? (threadIdx.x >> 5) : 0]);
     uint64_t base = ((uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32;
     uint64_t next_key = 0;
     uint32_t next_val = 0;
@@ -344,9 +347,10 @@ bucket_fop_kernel(const DevTable t, const void* __restrict__ keys, const uint32_
         if (mine && !myok) set_flag(t.ctr, kFlagInvalidKey);
         const uint32_t my_new = bucket_tile<KW, BS, G>(t, mykey, myval, myok);
         if (mine && is_new) is_new[base + lane] = uint8_t(my_new);
-        if (APPEND) warp_append<typename K::T>(mine && my_new, typename K::T(mykey), new_out, new_count, new_cap);
+        if (APPEND) stage.push(mine && my_new, T(mykey), new_out, new_count, new_cap);
         stored += __popc(__ballot_sync(kFull, my_new != 0));
     }
+    if (APPEND) stage.flush(new_out, new_count, new_cap);
     if ((threadIdx.x & 31) == 0 && stored) atomicAdd(&t.ctr->size, stored);
 }
 

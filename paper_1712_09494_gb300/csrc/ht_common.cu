@@ -63,12 +63,15 @@ compact_kernel(const T* __restrict__ keys, const uint8_t* __restrict__ flags, ui
                T* __restrict__ out, unsigned long long* __restrict__ count) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint64_t rounds = (n + stride - 1) / stride;
+    __shared__ T s_keep[kBlock / 32][kStageCap];
+    WarpStage<T, kStageCap> stage(s_keep[threadIdx.x >> 5]);
     for (uint64_t r = 0; r < rounds; ++r) {
         const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x + r * stride;
         const bool keep = i < n && flags[i] != 0;
         T k = keep ? keys[i] : T(0);
-        warp_append<T>(keep, k, out, count);
+        stage.push(keep, k, out, count, ~0ull);
     }
+    stage.flush(out, count, ~0ull);
 }
 
 // Random-read probe (the denominator of the hash probes' roofline).

@@ -206,6 +206,41 @@ __device__ __forceinline__ void warp_append(bool pred, T v, T* out, unsigned lon
     if (pred && at < cap) out[at] = v;
 }
 
+// Warp-aggregated append staged in shared memory: the warp collects up to
+// CAP entries in `buf` (its own CAP slots) and moves them out with one atomic
+// on the counter per flush, instead of one atomic per 32-entry tile -- many
+// warps appending to one counter otherwise serialise on its L2 slice.  Every
+// lane of the warp calls push/flush together; flush must end the warp's
+// work.  Entries past `cap` are not written (the counter still counts them).
+template <typename T, int CAP>
+struct WarpStage {
+    T* buf;
+    uint32_t pend;
+    __device__ __forceinline__ explicit WarpStage(T* b) : buf(b), pend(0) {}
+    __device__ __forceinline__ void flush(T* out, unsigned long long* counter, uint64_t cap) {
+        __syncwarp();
+        if (pend) {
+            const int lane = threadIdx.x & 31;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(counter, (unsigned long long)pend);
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            for (uint32_t j = lane; j < pend; j += 32)
+                if (base + j < cap) out[base + j] = buf[j];
+        }
+        __syncwarp();
+        pend = 0;
+    }
+    __device__ __forceinline__ void push(bool pred, T v, T* out, unsigned long long* counter, uint64_t cap) {
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
+        const uint32_t c = __popc(mask);
+        if (pend + c > uint32_t(CAP)) flush(out, counter, cap);
+        const int lane = threadIdx.x & 31;
+        if (pred) buf[pend + __popc(mask & ((1u << lane) - 1))] = v;
+        pend += c;
+    }
+};
+constexpr int kStageCap = 256;   // entries per warp (8 tiles of 32)
+
 // ---------------------------------------------------------------------------
 // Kernel timing (ht_prof_*).
 // ---------------------------------------------------------------------------

@@ -491,9 +491,12 @@ cudaError_t launch_lookup(const DevTable& t, const void* keys, uint64_t n, uint3
     return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, keys, n, vals, found);
 }
 
-// Multi-table find-or-put: warp w takes tile w of the step's successor
-// segments (segment e starts at seg_off[e], a multiple of 32), runs it
-// against exploration e's table and appends the new states to its states.
+// Multi-table find-or-put: the step's successor segments (segment e starts at
+// seg_off[e], a multiple of 32) are cut into 32-key tiles and each warp takes
+// a contiguous range of them, so it finds its first tile's exploration once
+// and then walks the segments in order with that exploration's descriptor in
+// registers; each tile runs against exploration e's table and its new states
+// are appended to e's states.
 template <int KW, int BS, int G>
 __global__ void __launch_bounds__(kBlock, HT_BUCKET_MIN_BLOCKS)
 multi_bucket_fop_kernel(const MultiDev m, uint64_t max_tiles) {
@@ -502,26 +505,52 @@ multi_bucket_fop_kernel(const MultiDev m, uint64_t max_tiles) {
     const uint64_t tiles = min(uint64_t(__ldcg(m.tiles_total)), max_tiles);
     const int lane = threadIdx.x & 31;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-    for (uint64_t tile = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; tile < tiles; tile += nwarps) {
-        uint32_t a = 0, b = m.count;                   // largest e with seg_off[e] <= 32 * tile
-        while (b - a > 1) {
-            const uint32_t mid = (a + b) / 2;
-            if (__ldcg(m.seg_off + mid) <= tile * 32) a = mid; else b = mid;
+    const uint64_t gw = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t per = (tiles + nwarps - 1) / nwarps;
+    const uint64_t t_begin = min(tiles, gw * per), t_end = min(tiles, t_begin + per);
+    if (t_begin >= t_end) return;
+    // New states are staged per warp and appended, with the table's size, in
+    // one atomic each when the warp moves to another exploration or the stage
+    // is full: the large explorations' counters are shared by many warps.
+    __shared__ T s_new[kBlock / 32][kStageCap];
+    WarpStage<T, kStageCap> stage(s_new[threadIdx.x >> 5]);
+    uint32_t e = 0, b = m.count;                       // largest e with seg_off[e] <= 32 * t_begin
+    while (b - e > 1) {
+        const uint32_t mid = (e + b) / 2;
+        if (__ldcg(m.seg_off + mid) <= t_begin * 32) e = mid; else b = mid;
+    }
+    uint64_t seg = 0, cnt = 0, next_seg = 0;
+    auto load_desc = [&]() {
+        seg = __ldcg(m.seg_off + e);
+        cnt = min(uint64_t(__ldcg(m.seg_cnt + e)), uint64_t(__ldcg(m.take + e)) * uint64_t(__ldcg(m.msucc + e)));
+        next_seg = e + 1 < m.count ? __ldcg(m.seg_off + e + 1) : ~0ull;
+    };
+    load_desc();
+    unsigned long long stored = 0;
+    auto settle = [&]() {
+        stage.flush(static_cast<T*>(m.states[e]), m.total + e, m.states_cap[e]);
+        if (lane == 0 && stored) atomicAdd(&m.tables[e].ctr->size, stored);
+        stored = 0;
+    };
+    for (uint64_t tile = t_begin; tile < t_end; ++tile) {
+        if (tile * 32 >= next_seg) {                   // into a later exploration's segment
+            settle();
+            do {
+                ++e;
+                next_seg = e + 1 < m.count ? __ldcg(m.seg_off + e + 1) : ~0ull;
+            } while (tile * 32 >= next_seg);
+            load_desc();
         }
-        const uint32_t e = a;
-        const uint64_t base = __ldcg(m.seg_off + e);
-        const uint64_t cnt = min(uint64_t(__ldcg(m.seg_cnt + e)), uint64_t(__ldcg(m.take + e)) * uint64_t(__ldcg(m.msucc + e)));
-        const uint64_t i = tile * 32 - base + lane;
+        const uint64_t i = tile * 32 - seg + lane;
         const bool mine = i < cnt;
         if (!__any_sync(kFull, mine)) continue;
-        const uint64_t key = mine ? __ldcg(reinterpret_cast<const unsigned long long*>(m.succ + base + i)) : 0;
+        const uint64_t key = mine ? __ldcg(reinterpret_cast<const unsigned long long*>(m.succ + seg + i)) : 0;
         const bool ok = mine && !K::reserved(key);
-        const DevTable& t = m.tables[e];
-        const uint32_t my_new = bucket_tile<KW, BS, G>(t, key, 0, ok);
-        warp_append<T>(mine && my_new, T(key), static_cast<T*>(m.states[e]), m.total + e, m.states_cap[e]);
-        const unsigned nm = __ballot_sync(kFull, my_new != 0);
-        if (lane == 0 && nm) atomicAdd(&t.ctr->size, (unsigned long long)__popc(nm));
+        const uint32_t my_new = bucket_tile<KW, BS, G>(m.tables[e], key, 0, ok);
+        stage.push(mine && my_new, T(key), static_cast<T*>(m.states[e]), m.total + e, m.states_cap[e]);
+        stored += __popc(__ballot_sync(kFull, my_new != 0));
     }
+    settle();
 }
 
 // One warp per exploration: level 0 is the initial state.

@@ -597,8 +597,10 @@ cudaError_t launch_multi(const MultiDev& m, uint64_t max_tiles, bool init, cudaS
 }
 
 // Packed multi-table find-or-put (the serving loop's batches and
-// ht_multi_find_or_put): warp w takes tile w of the packed items, each tile
-// against its item's table.
+// ht_multi_find_or_put): the items' 32-key tiles are numbered across the
+// items and each warp takes a contiguous range of them, finds its first
+// tile's item once and walks the items in order, keeping the item's
+// descriptor in registers and its table's size count until it moves on.
 template <int KW, int BS, int G>
 __global__ void __launch_bounds__(kBlock, HT_BUCKET_MIN_BLOCKS)
 packed_bucket_kernel(const DevTable* __restrict__ tables, const WorkDesc* __restrict__ items, uint32_t nitems,
@@ -606,13 +608,28 @@ packed_bucket_kernel(const DevTable* __restrict__ tables, const WorkDesc* __rest
     using K = Keys<KW>;
     const int lane = threadIdx.x & 31;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-    for (uint64_t tile = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; tile < ntiles; tile += nwarps) {
-        uint32_t a = 0, b = nitems;                    // largest r with tile_off[r] <= tile
-        while (b - a > 1) {
-            const uint32_t mid = (a + b) / 2;
-            if (items[mid].tile_off <= tile) a = mid; else b = mid;
+    const uint64_t gw = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t per = (ntiles + nwarps - 1) / nwarps;
+    const uint64_t t_begin = min(ntiles, gw * per), t_end = min(ntiles, t_begin + per);
+    if (t_begin >= t_end) return;
+    uint32_t r = 0, b = nitems;                        // largest r with tile_off[r] <= t_begin
+    while (b - r > 1) {
+        const uint32_t mid = (r + b) / 2;
+        if (items[mid].tile_off <= t_begin) r = mid; else b = mid;
+    }
+    WorkDesc d = items[r];
+    uint64_t next_off = r + 1 < nitems ? items[r + 1].tile_off : ~0ull;
+    unsigned long long stored = 0;
+    for (uint64_t tile = t_begin; tile < t_end; ++tile) {
+        if (tile >= next_off) {                        // into a later item
+            if (lane == 0 && stored) atomicAdd(&tables[d.table].ctr->size, stored);
+            stored = 0;
+            do {
+                ++r;
+                next_off = r + 1 < nitems ? items[r + 1].tile_off : ~0ull;
+            } while (tile >= next_off);
+            d = items[r];
         }
-        const WorkDesc d = items[a];
         const uint64_t i = (tile - d.tile_off) * 32 + lane;
         const bool mine = i < d.n;
         const uint64_t key = mine ? K::load(d.keys, i) : 0;
@@ -621,9 +638,9 @@ packed_bucket_kernel(const DevTable* __restrict__ tables, const WorkDesc* __rest
         if (mine && !ok) set_flag(t.ctr, kFlagInvalidKey);
         const uint32_t my_new = bucket_tile<KW, BS, G>(t, key, 0, ok);
         if (mine && d.flags) d.flags[i] = uint8_t(my_new);
-        const unsigned nm = __ballot_sync(kFull, my_new != 0);
-        if (lane == 0 && nm) atomicAdd(&t.ctr->size, (unsigned long long)__popc(nm));
+        stored += __popc(__ballot_sync(kFull, my_new != 0));
     }
+    if (lane == 0 && stored) atomicAdd(&tables[d.table].ctr->size, stored);
 }
 
 // (bucket_slots, lanes) pairs that are instantiated.

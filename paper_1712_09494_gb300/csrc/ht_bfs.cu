@@ -41,13 +41,24 @@ __device__ __forceinline__ void for_each_successor(const PreparedModel& m, uint6
     }
 }
 
+// Successors of a frontier: lane l expands state l of the warp's 32.  The
+// lanes count their successors, reserve one range for the warp, then emit
+// them into the warp's buffer in shared memory (in chunks of kSuccStage when
+// the warp has more), from where the warp writes them out with coalesced
+// stores: each lane's successors are contiguous in the output, so writing
+// them straight from the lanes would scatter every store instruction over
+// 32 places.
+constexpr int kSuccBlock = 128;
+constexpr int kSuccStage = 1024;
+
 template <typename T>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kSuccBlock)
 successors_kernel(const PreparedModel* __restrict__ model, const T* __restrict__ states, uint64_t n,
                   const unsigned long long* __restrict__ d_n, uint64_t off, T* __restrict__ succ,
                   uint64_t cap, unsigned long long* __restrict__ count,
                   unsigned long long* __restrict__ total) {
     __shared__ PreparedModel sm;
+    __shared__ T s_out[kSuccBlock / 32][kSuccStage];
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(model);
         uint32_t* dst = reinterpret_cast<uint32_t*>(&sm);
@@ -59,6 +70,7 @@ successors_kernel(const PreparedModel* __restrict__ model, const T* __restrict__
         n = all > off ? min(n, all - off) : 0;
     }
     const int lane = threadIdx.x & 31;
+    T* buf = s_out[threadIdx.x >> 5];
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint64_t rounds = (n + stride - 1) / stride;       // warp-uniform trip count
     unsigned long long made = 0;
@@ -79,12 +91,21 @@ successors_kernel(const PreparedModel* __restrict__ model, const T* __restrict__
         unsigned long long base = 0;
         if (lane == 0 && tot) base = atomicAdd(count, (unsigned long long)tot);
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
-        uint64_t pos = base + (incl - cnt);
-        if (act)
-            for_each_successor(sm, s, [&](uint64_t v) {
-                if (pos < cap) succ[pos] = T(v);
-                ++pos;
-            });
+        const uint32_t excl = incl - cnt;
+        for (uint32_t chunk = 0; chunk < tot; chunk += kSuccStage) {
+            if (act && excl < chunk + kSuccStage && incl > chunk) {
+                uint32_t k = excl;
+                for_each_successor(sm, s, [&](uint64_t v) {
+                    if (k >= chunk && k < chunk + kSuccStage) buf[k - chunk] = T(v);
+                    ++k;
+                });
+            }
+            __syncwarp();
+            const uint32_t m = min(uint32_t(kSuccStage), tot - chunk);
+            for (uint32_t j = lane; j < m; j += 32)
+                if (base + chunk + j < cap) succ[base + chunk + j] = buf[j];
+            __syncwarp();
+        }
         made += cnt;
     }
     if (total) {
@@ -188,11 +209,11 @@ cudaError_t successors(int kw, const PreparedModel* model, const void* states, u
     ProfScope ps(kKSuccessors, s);
     if (kw == 32) {
         auto k = successors_kernel<uint32_t>;
-        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(
+        k<<<launch_blocks((const void*)k, kSuccBlock), kSuccBlock, 0, s>>>(
             model, static_cast<const uint32_t*>(states), n, d_n, off, static_cast<uint32_t*>(succ), cap, count, total);
     } else {
         auto k = successors_kernel<uint64_t>;
-        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(
+        k<<<launch_blocks((const void*)k, kSuccBlock), kSuccBlock, 0, s>>>(
             model, static_cast<const uint64_t*>(states), n, d_n, off, static_cast<uint64_t*>(succ), cap, count, total);
     }
     return cudaGetLastError();

@@ -24,21 +24,27 @@ template <class F>
 __device__ __forceinline__ void for_each_successor(const PreparedModel& m, uint64_t s, F&& emit) {
     for (int c = 0; c < m.C; ++c) {
         const uint32_t u = local_of(m, s, c);
-        const int d = m.deg[c][u];
-        for (int j = 0; j < d; ++j)
-            if (m.lab[c][u][j] == 0) emit(with_local(m, s, c, m.tgt[c][u][j]));
+        const int d = m.nloc[c][u];
+        for (int j = 0; j < d; ++j) emit(with_local(m, s, c, m.loc[c][u][j]));
     }
     for (int p = 0; p < m.P; ++p) {
         const int c1 = m.pc1[p], c2 = m.pc2[p];
         const uint32_t u1 = local_of(m, s, c1), u2 = local_of(m, s, c2);
-        const int d1 = m.deg[c1][u1], d2 = m.deg[c2][u2];
+        const int d1 = m.nsyn[p][0][u1], d2 = m.nsyn[p][1][u2];
         for (int j1 = 0; j1 < d1; ++j1) {
-            if (m.lab[c1][u1][j1] != p + 1) continue;
-            const uint64_t s1 = with_local(m, s, c1, m.tgt[c1][u1][j1]);
-            for (int j2 = 0; j2 < d2; ++j2)
-                if (m.lab[c2][u2][j2] == p + 1) emit(with_local(m, s1, c2, m.tgt[c2][u2][j2]));
+            const uint64_t s1 = with_local(m, s, c1, m.syn[p][0][u1][j1]);
+            for (int j2 = 0; j2 < d2; ++j2) emit(with_local(m, s1, c2, m.syn[p][1][u2][j2]));
         }
     }
+}
+
+// The number of successors of s (what for_each_successor visits).
+__device__ __forceinline__ uint32_t count_successors(const PreparedModel& m, uint64_t s) {
+    uint32_t n = 0;
+    for (int c = 0; c < m.C; ++c) n += m.nloc[c][local_of(m, s, c)];
+    for (int p = 0; p < m.P; ++p)
+        n += uint32_t(m.nsyn[p][0][local_of(m, s, m.pc1[p])]) * m.nsyn[p][1][local_of(m, s, m.pc2[p])];
+    return n;
 }
 
 // Successors of a frontier: lane l expands state l of the warp's 32.  The
@@ -79,7 +85,7 @@ successors_kernel(const PreparedModel* __restrict__ model, const T* __restrict__
         const bool act = i < n;
         const uint64_t s = act ? uint64_t(states[i]) : 0;
         uint32_t cnt = 0;
-        if (act) for_each_successor(sm, s, [&](uint64_t) { ++cnt; });
+        if (act) cnt = count_successors(sm, s);
         // Warp-wide exclusive scan of the counts, one reservation per warp.
         uint32_t incl = cnt;
 #pragma unroll
@@ -139,7 +145,7 @@ __global__ void __launch_bounds__(kBlock) multi_successors_kernel(const MultiDev
             e = a;
             const uint64_t idx = __ldcg(m.cur + e) + (v - __ldcg(m.work_off + e));
             s = uint64_t(static_cast<const T*>(m.states[e])[idx]);
-            for_each_successor(m.models[e], s, [&](uint64_t) { ++cnt; });
+            cnt = count_successors(m.models[e], s);
         }
         // Consecutive lanes hold consecutive v, so lanes of one exploration
         // form a contiguous run; the run's first lane reserves for the run.
@@ -175,9 +181,23 @@ __global__ void __launch_bounds__(kBlock) multi_successors_kernel(const MultiDev
 PreparedModel prepare_model(const ht_model& h) {
     PreparedModel p;
     memset(&p, 0, sizeof(p));
-    memcpy(p.deg, h.deg, sizeof(p.deg));
-    memcpy(p.tgt, h.tgt, sizeof(p.tgt));
-    memcpy(p.lab, h.lab, sizeof(p.lab));
+    // Transition j of component c in local state u: label 0 is a local
+    // action; label q+1 belongs to synchronising pair q (whose members are
+    // pair_c1[q] and pair_c2[q]).  The model was validated (deg <= 4, labels
+    // <= num_pairs, members distinct).
+    for (int c = 0; c < h.num_components && c < 16; ++c)
+        for (int u = 0; u < 32; ++u)
+            for (int j = 0; j < h.deg[c][u] && j < 4; ++j) {
+                const int lab = h.lab[c][u][j];
+                if (lab == 0) {
+                    p.loc[c][u][p.nloc[c][u]++] = h.tgt[c][u][j];
+                } else if (lab <= h.num_pairs && lab <= 8) {
+                    const int q = lab - 1;
+                    for (int side = 0; side < 2; ++side)
+                        if ((side == 0 ? h.pair_c1[q] : h.pair_c2[q]) == c)
+                            p.syn[q][side][u][p.nsyn[q][side][u]++] = h.tgt[c][u][j];
+                }
+            }
     int o = 0;
     for (int c = 0; c < 16; ++c) {
         p.bits[c] = h.bits[c];

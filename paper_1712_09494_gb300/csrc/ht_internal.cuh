@@ -348,10 +348,15 @@ cudaError_t probe_random_rmw(void* buf, uint64_t bytes, uint64_t n_access, uint6
 
 // A model with its bit offsets precomputed (device copy; the single-table
 // successor kernel stages it in shared memory).
+// A model's transitions regrouped for successor generation: per component
+// and local state the targets of its local (unlabelled) transitions, and per
+// synchronising pair, member (0: pc1, 1: pc2) and local state the targets of
+// that member's transitions carrying the pair's label.
 struct PreparedModel {
-    uint8_t deg[16][32];
-    uint8_t tgt[16][32][4];
-    uint8_t lab[16][32][4];
+    uint8_t nloc[16][32];
+    uint8_t loc[16][32][4];
+    uint8_t nsyn[8][2][32];
+    uint8_t syn[8][2][32][4];
     uint8_t off[16];
     uint8_t bits[16];
     uint8_t pc1[8];

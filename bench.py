@@ -236,6 +236,31 @@ def random_access_roofline(scheme, fs, table, stats, ms_per_fill, probe):
             "read_gaccess_per_s": round(r_read / 1e9, 2), "rmw_gaccess_per_s": round(r_rmw / 1e9, 2)}
 
 
+def kernel_random_access(name, k, fs, tables, stats, probe, steps):
+    """The dominant kernel against the measured random-access rates: its
+    minimum time per launch (lines it must read at the random-read rate +
+    lines it must claim in at the random-claim rate, as in
+    random_access_roofline) over its measured average launch time."""
+    r_read = probe["128B" if name == "bucket_find_or_put" else "8B"]["gaccess_per_s"] * 1e9
+    r_rmw = probe["rmw_line"]["gaccess_per_s"] * 1e9
+    n_new, n_rep = fs.n_distinct, fs.n_issued - fs.n_distinct
+    if name == "bucket_find_or_put":
+        reads, claims = n_rep, n_new
+    elif name == "cuckoo_probe":
+        info = tables["cuckoo"].info()
+        reads = n_rep + n_new * (1 + new_key_load(fs, info["slots"]) * (info["num_hashes"] - 1))
+        claims = 0
+    elif name == "cuckoo_insert":
+        reads, claims = 0, stats["cuckoo"]["exchanges"]
+    else:
+        return None
+    per_launch_s = (reads / r_read + claims / r_rmw) * steps / k["launches"]
+    return {"frac": round(per_launch_s / (k["avg_ms"] / 1e3), 3),
+            "lines_read_per_launch": int(reads * steps / k["launches"]),
+            "lines_claimed_per_launch": int(claims * steps / k["launches"]),
+            "read_gaccess_per_s": round(r_read / 1e9, 2), "rmw_gaccess_per_s": round(r_rmw / 1e9, 2)}
+
+
 # ----------------------------------------------------------------- our arm
 def run_ours(a, rank, world, local):
     import torch
@@ -370,6 +395,8 @@ def run_ours(a, rank, world, local):
         for s in schemes:
             out["per_scheme"][s]["random_access_roofline"] = random_access_roofline(
                 s, fs, tables[s], fill_stats[s], per_ms[s], out["random_read_roofline"])
+        out["roofline"]["random_access"] = kernel_random_access(
+            dom, kernels[dom], fs, tables, fill_stats, out["random_read_roofline"], a.steps)
     for t in tables.values():
         t.close()
     tables = {}

@@ -36,6 +36,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the config-2 parameter sweep")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--schemes", default="bucket,cuckoo")
     ap.add_argument("--n-log2", type=int, default=27)
@@ -328,8 +329,11 @@ def run_ours(a, rank, world, local):
     ht.ht_prof_enable(False)
     kern = ht.ht_prof_read()
     ms_total = t0.elapsed_time(t1)
+    med_ms = {}
     for s in schemes:
-        per_ms[s] = sum(e0.elapsed_time(e1) for e0, e1 in step_ms_each[s]) / a.steps
+        each = [e0.elapsed_time(e1) for e0, e1 in step_ms_each[s]]
+        per_ms[s] = sum(each) / a.steps
+        med_ms[s] = statistics.median(each)
     ms_step = reduce_max(ms_total / a.steps, dev)
     for s in schemes:
         if tables[s].sync() != 0 or tables[s].size() != n:
@@ -372,6 +376,7 @@ def run_ours(a, rank, world, local):
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, copy burst)" if peak_src == "measured"
                 else "fallback 6.8 TB/s",
                 "unit": "GB/s", "frac": round(kernels[dom]["achieved_gbs"] / peak, 3),
+                "frac_of_nominal_7900": round(kernels[dom]["achieved_gbs"] / 7900.0, 3),
                 "traffic": traffic, "alg_bytes_per_key": round(per_key[dom], 1),
                 "cuckoo_miss_probes": round(miss_probes, 3),
                 "cuckoo_exchanges_per_new_key": round(cuckoo_exchanges_per_new, 3)}
@@ -381,7 +386,7 @@ def run_ours(a, rank, world, local):
         "warmup": a.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": workload_config(a, schemes),
-        "per_scheme": {s: {"ms_per_fill": round(per_ms[s], 3),
+        "per_scheme": {s: {"ms_per_fill": round(per_ms[s], 3), "median_ms_per_fill": round(med_ms[s], 3),
                            "mops": round(fs.n_issued / (per_ms[s] / 1e3) / 1e6, 1)} for s in schemes},
         "roofline": roofline, "kernels": kernels, "clocks": clk,
         "gpu_launches": int(sum(v[0] for v in kern.values())),
@@ -403,6 +408,8 @@ def run_ours(a, rank, world, local):
     if not a.no_small:
         out["small_map_config1"] = run_small_map(ht, torch, dev, schemes)
         out["many_tables_one_call"] = run_multi_table(ht, torch, dev)
+    if not a.no_sweep:
+        out["sweep_config2"] = run_sweep(ht, torch, dev)
     if not a.no_bfs:
         out["bfs_config3"] = run_bfs(ht, torch, dev, schemes)
     if not a.no_batched:
@@ -567,7 +574,8 @@ def run_bfs(ht, torch, dev, schemes, warmup=1, reps=3):
         kern = {k: round(v[1], 2) for k, v in ht.ht_prof_read().items() if k != "clear"}
         out[sch] = {"seconds": round(sec, 4), "states_per_s_M": round(res.states / sec / 1e6, 1),
                     "find_or_put_mops": round(res.successors / sec / 1e6, 1),
-                    "levels_match_oracle": bool(ok), "host_syncs": len(sizes) + 2, "kernel_ms": kern}
+                    "levels_match_oracle": bool(ok), "host_syncs": len(sizes) + 2, "kernel_ms": kern,
+                    "multiplicity": round(res.successors / max(1, res.states), 2)}
         t.close()
     del states
     return out
@@ -631,6 +639,60 @@ def run_batched(ht, torch):
                                       "classes_tuned": n_classes, "chosen": shapes}
     mx.close()
     return res
+
+
+def run_sweep(ht, torch, dev, reps=3):
+    """Config 2 beyond the headline point: fills of random 64-bit keys over
+    load (0.5-0.9), size (2^24-2^27), batch size (2^20-2^24) and repeat rate
+    (0-0.5), for the bucket scheme and Cuckoo with k = 3 and 4 (stash 101).
+    Streams are drawn on the device (workloads.device_keys).  Per point: the
+    median of `reps` whole fills (keys issued / time) and the rate of the
+    last batch, the one that takes the table to its load ("at load"); every
+    fill must end with exactly n keys stored."""
+    from workloads import device_keys as dk
+    base = dict(n_log2=27, lf=0.8, batch_log2=24, dup=0.25)
+    points = [dict(base, lf=lf) for lf in (0.5, 0.7, 0.8, 0.9)]
+    points += [dict(base, n_log2=nl) for nl in (24, 25, 26)]
+    points += [dict(base, batch_log2=bl) for bl in (20, 22)]
+    points += [dict(base, dup=d) for d in (0.0, 0.5)]
+    schemes = [("bucket", None), ("cuckoo", 3), ("cuckoo", 4)]
+    out = []
+    for pt in points:
+        n = 1 << pt["n_log2"]
+        batches, _ = dk.fill_batches_dev(n, 1 << pt["batch_log2"], pt["dup"], seed=11 + pt["n_log2"], device=dev)
+        issued = sum(b.numel() for b in batches)
+        flags = torch.empty(max(b.numel() for b in batches), dtype=torch.uint8, device=dev)
+        cap = int(np.ceil(n / pt["lf"]))
+        for sch, k in schemes:
+            rec = dict(pt, scheme=sch if k is None else "cuckoo_k%d" % k)
+            t = ht.HashTable(cap, sch, 64, None if k is None else dict(num_hashes=k))
+            fills, lasts = [], []
+            for r in range(reps + 1):
+                ht.ht_clear(t.handle)
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record()
+                for b in batches[:-1]:
+                    ht.ht_find_or_put(t.handle, b, flags[:b.numel()])
+                e[1].record()
+                ht.ht_find_or_put(t.handle, batches[-1], flags[:batches[-1].numel()])
+                e[2].record()
+                torch.cuda.synchronize()
+                if r:
+                    fills.append(e[0].elapsed_time(e[2]))
+                    lasts.append(e[1].elapsed_time(e[2]))
+            st = t.sync()
+            rec["exact"] = st == 0 and t.size() == n
+            rec["mops"] = round(issued / (statistics.median(fills) / 1e3) / 1e6, 1)
+            rec["at_load_mops"] = round(batches[-1].numel() / (statistics.median(lasts) / 1e3) / 1e6, 1)
+            if st:
+                rec["status"] = st
+            t.close()
+            out.append(rec)
+        del batches, flags
+        torch.cuda.empty_cache()
+    return {"workload": "random 64-bit keys; one parameter varied at a time around n=2^27, load 0.8, "
+                        "batches 2^24, 25% repeats; bucket 16x2/k16 and Cuckoo k=3/4 (stash 101)",
+            "points": out, "all_exact": all(p["exact"] for p in out)}
 
 
 def run_multi_table(ht, torch, dev, n_tables=1024, keys_per=4096, rounds=8):
@@ -719,6 +781,21 @@ def run_small_map(ht, torch, dev, schemes, reps=10):
                 "insert_mops": round(n / (statistics.median(ins) / 1e3) / 1e6, 1),
                 "lookup_mops": round(n / (statistics.median(look) / 1e3) / 1e6, 1), "exact": ok}
             t.close()
+    # The table fits in L2, so its bound is L2's random-access rate, not HBM's:
+    # the same random-read probe over a 16 MB buffer.
+    buf = torch.ones(1 << 21, dtype=torch.int64, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    l2 = {}
+    for gran in (8, 128):
+        n_acc = 1 << 28
+        ht.ht_probe_random_read(buf, gran, n_acc, 3, sink)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ht.ht_probe_random_read(buf, gran, n_acc, 4, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        l2["%dB_gaccess_per_s" % gran] = round(n_acc / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+    res["l2_random_read"] = dict(l2, bound="L2: the 16 MB table fits the L2 cache, HBM roofline not binding")
     return res
 
 
@@ -838,6 +915,15 @@ def run_serving(ht, a):
     keys = [p.numpy().view(np.uint64) for p in pinned]
     out["continuous_batching"] = run_serving_once(ht, a, pack=1, inflight=4, trace=trace, keys=keys)
     out["per_request_launches"] = run_serving_once(ht, a, pack=0, inflight=1, trace=trace, keys=keys)
+    # Offered rate swept towards saturation (continuous batching; the same
+    # requests, only the arrival times change).
+    sweep = []
+    for rate in (10000.0, 160000.0, 640000.0):
+        tr = serving_trace(a.serve_requests, rate)
+        r = run_serving_once(ht, a, pack=1, inflight=4, trace=tr, keys=keys)
+        sweep.append({"offered_req_per_s": rate, "p50_us": r.get("p50_us"), "p99_us": r.get("p99_us"),
+                      "sustained_mops": r.get("sustained_mops"), "errors": r.get("errors", r.get("error"))})
+    out["continuous_batching_rate_sweep"] = sweep
     return out
 
 

@@ -66,3 +66,28 @@ def test_models_fit_their_format():
     ms = ss.batched_models(16, seed=2)
     for mm in ms:
         assert 6 <= mm.C <= 10 and mm.total_bits <= 63
+
+
+def test_device_keys_match_the_host_stream():
+    torch = pytest.importorskip("torch")
+    from workloads import device_keys as dk
+    for seed, start, n in [(0, 0, 1000), (7, 123456789, 5000), (2 ** 40 + 3, 2 ** 62 - 10, 10)]:
+        host = wk.distinct_keys(n, 64, seed, start=start)
+        dev = dk.distinct_keys_dev(n, seed, start=start).numpy().view(np.uint64)
+        np.testing.assert_array_equal(dev, host)
+
+
+def test_device_fill_batches_shape():
+    torch = pytest.importorskip("torch")
+    from workloads import device_keys as dk
+    n, B, d = 10_000, 1024, 0.25
+    batches, fresh = dk.fill_batches_dev(n, B, d, seed=3, device="cpu")
+    assert sum(fresh) == n
+    allk = torch.cat(batches).numpy()
+    assert len(np.unique(allk)) == n
+    assert all(len(b) == B for b in batches[:-1])
+    seen = set()
+    for b, f in zip(batches, fresh):
+        s = set(b.tolist())
+        assert len(s - seen) == f             # exactly f keys new to the stream
+        seen |= s

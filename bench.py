@@ -410,6 +410,7 @@ def run_ours(a, rank, world, local):
         out["many_tables_one_call"] = run_multi_table(ht, torch, dev)
     if not a.no_sweep:
         out["sweep_config2"] = run_sweep(ht, torch, dev)
+        out["replay_multiplicity"] = run_replay(ht, torch, dev)
     if not a.no_bfs:
         out["bfs_config3"] = run_bfs(ht, torch, dev, schemes)
     if not a.no_batched:
@@ -693,6 +694,44 @@ def run_sweep(ht, torch, dev, reps=3):
     return {"workload": "random 64-bit keys; one parameter varied at a time around n=2^27, load 0.8, "
                         "batches 2^24, 25% repeats; bucket 16x2/k16 and Cuckoo k=3/4 (stash 101)",
             "points": out, "all_exact": all(p["exact"] for p in out)}
+
+
+def run_replay(ht, torch, dev, n=100_000_000, mults=(1, 2, 5, 10, 50, 100, 200, 450, 700, 1000), reps=2):
+    """The shape of the paper's random-data experiment (Section 5.2, Fig. 5):
+    sequences of 10^8 32-bit integers whose value range sets the mean
+    multiplicity, each found-or-inserted as one whole sequence into a table
+    of 1.25 x its distinct values (load 0.8), both schemes.  Synthetic
+    stand-in for the paper's files; exact when the table ends with exactly
+    the sequence's distinct values."""
+    from workloads import device_keys as dk
+    flags = torch.empty(n, dtype=torch.uint8, device=dev)
+    pts = []
+    for m in mults:
+        keys = dk.multiplicity_sequence_dev(n, m, seed=29 + m, device=dev)
+        uniq = int(torch.unique(keys).numel())
+        rec = {"multiplicity_range": m, "distinct": uniq, "mean_multiplicity": round(n / uniq, 2)}
+        for sch in ("bucket", "cuckoo"):
+            t = ht.HashTable(int(np.ceil(uniq * 1.25)), sch, 32)
+            times = []
+            for r in range(reps + 1):
+                ht.ht_clear(t.handle)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ht.ht_find_or_put(t.handle, keys, flags)
+                e1.record()
+                torch.cuda.synchronize()
+                if r:
+                    times.append(e0.elapsed_time(e1))
+            ms = statistics.median(times)
+            rec[sch] = {"ms": round(ms, 2), "mops": round(n / (ms / 1e3) / 1e6, 1),
+                        "exact": t.sync() == 0 and t.size() == uniq}
+            t.close()
+        rec["cuckoo_time_over_bucket"] = round(rec["cuckoo"]["ms"] / rec["bucket"]["ms"], 2)
+        pts.append(rec)
+        del keys
+    return {"workload": "10^8 random 32-bit keys per sequence, value range n/m for mean multiplicity ~m, "
+                        "table 1.25 x distinct (load 0.8), whole sequence in one find-or-put call",
+            "points": pts, "all_exact": all(p["bucket"]["exact"] and p["cuckoo"]["exact"] for p in pts)}
 
 
 def run_multi_table(ht, torch, dev, n_tables=1024, keys_per=4096, rounds=8):

@@ -91,3 +91,29 @@ def test_device_fill_batches_shape():
         s = set(b.tolist())
         assert len(s - seen) == f             # exactly f keys new to the stream
         seen |= s
+
+
+def test_device_mix32_matches_the_host_permutation():
+    torch = pytest.importorskip("torch")
+    from workloads import device_keys as dk
+    for seed in (0, 1, 12345):
+        x = np.concatenate([np.arange(0, 5000), np.arange(2 ** 32 - 5000, 2 ** 32 - 1)]).astype(np.uint64)
+        host = wk.mix32_perm(x, seed)
+        dev = dk.mix32_perm_dev(torch.from_numpy(x.astype(np.int64)), seed).numpy().astype(np.uint64)
+        np.testing.assert_array_equal(dev, host)
+
+
+def test_multiplicity_sequence_shape():
+    torch = pytest.importorskip("torch")
+    from workloads import device_keys as dk
+    n = 200_000
+    for mult in (1, 10, 100):
+        k = dk.multiplicity_sequence_dev(n, mult, seed=5, device="cpu")
+        assert k.dtype == torch.int32 and k.numel() == n
+        u = np.unique(k.numpy().view(np.uint32))
+        assert 0xFFFFFFFF not in u
+        rng = round(n / mult)
+        assert len(u) <= rng
+        # Uniform draws: the expected number of distinct values is rng (1 - e^-mult).
+        exp = rng * (1 - np.exp(-mult))
+        assert abs(len(u) - exp) < 5 * np.sqrt(exp) + 10

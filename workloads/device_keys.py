@@ -60,3 +60,41 @@ def fill_batches_dev(n_distinct, batch, dup_rate, seed, device):
         counts.append(nf)
         issued = end
     return out, counts
+
+
+_M32 = 0xFFFFFFFF
+
+
+def _perm32_once_dev(z, s):
+    z = (z + s) & _M32
+    z = (z * 0x7FEB352D) & _M32
+    z = z ^ (z >> 15)
+    z = (z * 0x846CA68B) & _M32
+    z = z ^ (z >> 16)
+    return z
+
+
+def mix32_perm_dev(x, seed=0):
+    """keys.mix32_perm on an int64 tensor of indices in [0, 2^32 - 1):
+    the 32-bit permutation, re-applied while the result is the reserved
+    0xFFFFFFFF (cycle walking)."""
+    s = (seed * 0x9E3779B9 + 0x85EBCA6B) & _M32
+    z = _perm32_once_dev(x & _M32, s)
+    bad = z == _M32
+    while bool(bad.any()):
+        z = torch.where(bad, _perm32_once_dev(z, s), z)
+        bad = z == _M32
+    return z
+
+
+def multiplicity_sequence_dev(n, mult, seed, device):
+    """n 32-bit keys (int32 tensor with the keys' bits) drawn uniformly from a
+    value range of round(n / mult) values, so a value occurs `mult` times on
+    average among those drawn: the shape of the paper's random sequences
+    (Section 5.2, mean multiplicity 1..1000)."""
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    rng = max(1, int(round(n / mult)))
+    v = torch.randint(0, rng, (n,), device=device, generator=g, dtype=torch.int64)
+    k = mix32_perm_dev(v, seed)
+    return (k - ((k >> 31) << 32)).to(torch.int32)      # same 32 bits, as int32

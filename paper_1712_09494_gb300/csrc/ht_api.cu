@@ -92,7 +92,8 @@ ht_status run_put(ht_table* t, const void* keys, const uint32_t* vals, uint64_t 
         const void* k = static_cast<const char*>(keys) + off * ksz;
         HT_TRY(cuckoo_probe(int(t->kw), t->dt, t->sc, t->parity, k, vals ? vals + off : nullptr, m, d_n,
                             off, is_new ? is_new + off : nullptr, s, t->win));
-        HT_TRY(cuckoo_insert(int(t->kw), t->dt, t->sc, t->parity, new_out, new_count, new_cap, m, s, t->win));
+        HT_TRY(cuckoo_insert(int(t->kw), t->dt, t->sc, t->parity, new_out, new_count, new_cap,
+                             std::min<uint64_t>(m, t->sc.win_cap), s, t->win));
         t->parity ^= 1u;
     }
     return HT_OK;
@@ -334,13 +335,20 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
     if ((e = cudaMallocAsync(&t->dt.ovf, uint64_t(t->dt.ovf_slots) * 8, cs)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocAsync(&t->dt.ctr, sizeof(DevCounters), cs)) != cudaSuccess) return fail(e);
     if (scheme == HT_CUCKOO) {
-        // A chunk never holds more absent distinct keys than the table can
-        // take, so the scratch is sized by the smaller of the two.
-        t->chunk = std::min<uint64_t>(p.max_batch, next_pow2(t->dt.nslots + t->dt.stash_slots + t->dt.ovf_slots));
-        const uint64_t sslots = next_pow2(2 * t->chunk);
+        // Keys per probe/insert launch pair: max_batch.  Unless the table
+        // overflows, a chunk's distinct absent keys (its winners) are no more
+        // than the table can hold, so the dedup set (twice that, for short
+        // probe runs) and the winner list are sized by the smaller of the
+        // two; a chunk that exceeds them would overflow the table anyway and
+        // reports its keys as dropped.
+        t->chunk = p.max_batch;
+        const uint64_t sc_cap =
+            std::min<uint64_t>(p.max_batch, next_pow2(t->dt.nslots + t->dt.stash_slots + t->dt.ovf_slots));
+        const uint64_t sslots = next_pow2(2 * sc_cap);
         t->sc.mask = sslots - 1;
+        t->sc.win_cap = sc_cap;
         if ((e = cudaMallocAsync(&t->sc.set, sslots * 8, cs)) != cudaSuccess) return fail(e);
-        if ((e = cudaMallocAsync(&t->sc.win, t->chunk * sizeof(Winner), cs)) != cudaSuccess) return fail(e);
+        if ((e = cudaMallocAsync(&t->sc.win, sc_cap * sizeof(Winner), cs)) != cudaSuccess) return fail(e);
         if ((e = fill_words(t->sc.set, sslots, kEmpty, cs)) != cudaSuccess) return fail(e);
     }
     ht_status st = clear_table(t, cs);

@@ -150,8 +150,13 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                 } else if (K::keyof(sw[u]) != key[u]) {        // another key sits there: probe on
                     uint32_t at = 0;
                     const uint32_t next = spos[u] + 1 == uint32_t(sc.mask + 1) ? 0u : spos[u] + 1;
-                    winner[u] = lp_insert<KW>(sc.set, uint32_t(sc.mask + 1), next, key[u], key[u], &at) == 1;
+                    const int rc = lp_insert<KW>(sc.set, uint32_t(sc.mask + 1), next, key[u], key[u], &at);
+                    winner[u] = rc == 1;
                     spos[u] = at;
+                    if (rc < 0) {                              // more distinct misses than the table holds
+                        set_flag(t.ctr, kFlagDropped);
+                        atomicAdd(&t.ctr->dropped, 1ull);
+                    }
                 }
             }
             // Append the round's winners to the insert list: one atomic per warp.
@@ -170,14 +175,23 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const uint64_t i = (r * kU + u) * stride + tid;
-                if (i < n && out_flag) out_flag[i] = uint8_t(winner[u]);
-                if (winner[u]) {
-                    Winner wn;
-                    wn.word = K::word(key[u], VALUES ? vals[i] : 0u);
-                    wn.spos = spos[u];
-                    wn.pad_ = 0;
-                    sc.win[b + __popc(wm[u] & ((1u << lane) - 1))] = wn;
+                bool stored = winner[u];
+                if (stored) {
+                    const uint64_t at = uint64_t(b) + __popc(wm[u] & ((1u << lane) - 1));
+                    if (at < sc.win_cap) {
+                        Winner wn;
+                        wn.word = K::word(key[u], VALUES ? vals[i] : 0u);
+                        wn.spos = spos[u];
+                        wn.pad_ = 0;
+                        sc.win[at] = wn;
+                    } else {                                   // more winners than the table holds
+                        stored = false;
+                        sc.set[spos[u]] = kEmpty;              // no insert will clear its claim
+                        set_flag(t.ctr, kFlagDropped);
+                        atomicAdd(&t.ctr->dropped, 1ull);
+                    }
                 }
+                if (i < n && out_flag) out_flag[i] = uint8_t(stored);
                 b += __popc(wm[u]);
             }
         }

@@ -64,6 +64,7 @@ struct DevScratch {
     uint64_t* set;
     uint64_t mask;            // slots - 1 (power of two)
     Winner* win;
+    uint64_t win_cap;         // entries of win
 };
 
 // ---------------------------------------------------------------------------

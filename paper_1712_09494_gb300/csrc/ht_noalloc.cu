@@ -92,6 +92,7 @@ extern "C" ht_status ht_cuckoo_find_or_put_noalloc(uint64_t* d_slots, uint64_t n
     sc.set = scratch;
     sc.mask = kNoallocSetSlots - 1;
     sc.win = reinterpret_cast<Winner*>(scratch + kNoallocSetSlots);
+    sc.win_cap = kNoallocMaxBatch;
 
     if (reset) {
         if (fill_words(d_slots, nslots, kEmpty, s) != cudaSuccess ||

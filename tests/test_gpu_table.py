@@ -192,6 +192,37 @@ def test_stash_overflow_and_rebuild(oracle_lib, scheme):
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
+def test_small_table_large_batches_with_repeats(oracle_lib, scheme):
+    # Batches far larger than the table (each key repeated ~40 times): a
+    # Cuckoo launch takes max_batch keys while its dedup set and winner list
+    # are sized by the table; results stay exact.
+    rng = np.random.default_rng(8)
+    pool = wk.distinct_keys(50_000, 64, seed=61)
+    t = ht.HashTable(65_000, scheme, 64)
+    orc = oracle_lib.OracleTable()
+    for b in range(3):
+        kb = pool[rng.integers(0, len(pool), size=(1 << 21) + 12345)]
+        got = to_np(t.find_or_put(to_dev(kb)))
+        assert_flags_per_key(kb, got, orc.find_or_put(kb))
+    assert t.sync() == 0 and t.size() == orc.size()
+
+
+def test_cuckoo_batch_with_more_distinct_keys_than_the_table_holds():
+    # 200k distinct keys into ~1300 places: the table reports HT_ERR_FULL and
+    # counts what it dropped; nothing is written out of bounds; every stored
+    # key was reported new (a new key may still be dropped: the table is full).
+    keys = wk.distinct_keys(200_000, 64, seed=62)
+    t = ht.HashTable(128, "cuckoo", 64)
+    flags = to_np(t.find_or_put(to_dev(keys))).astype(bool)
+    assert t.sync() == 3
+    found = to_np(t.lookup(to_dev(keys))[0]).astype(bool)
+    st = t.stats()
+    assert 0 < found.sum() == st["size"] <= 128 + 101 + 1024
+    assert not (found & ~flags).any()
+    assert st["dropped"] > 0 and st["dropped"] + st["size"] >= flags.sum()
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
 def test_overfull_table_reports_full(oracle_lib, scheme):
     # 3000 keys into 64 slots + 4 stash + 1024 overflow: keys are dropped and
     # the table reports HT_ERR_FULL; nothing hangs.

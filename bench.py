@@ -550,14 +550,15 @@ def run_bfs(ht, torch, dev, schemes, warmup=1, reps=3):
     states = torch.empty(gold["states"] + 1024, dtype=torch.int64, device=dev)
     out = {"workload": "12 components x 32 local states, 4 sync pairs, from the all-zero state: %d states, "
                        "%d levels, %d successors" % (gold["states"], len(gold["levels"]), gold["successors"])}
-    for sch in schemes:
+    forms = [(sch, False) for sch in schemes] + ([("bucket", True)] if "bucket" in schemes else [])
+    for sch, fused in forms:
         t = ht.HashTable(int(gold["states"] / 0.8), sch, 64)
         times = []
         for r in range(warmup + reps):
             ht.ht_clear(t.handle)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res, sizes = ht.ht_bfs(t.handle, hm, 0, 4096, states)
+            res, sizes = ht.ht_bfs(t.handle, hm, 0, 4096, states, fused=fused)
             torch.cuda.synchronize()
             if r >= warmup:
                 times.append(time.perf_counter() - t0)
@@ -569,11 +570,11 @@ def run_bfs(ht, torch, dev, schemes, warmup=1, reps=3):
         torch.cuda.synchronize()
         ht.ht_prof_reset()
         ht.ht_prof_enable(True)
-        ht.ht_bfs(t.handle, hm, 0, 4096, states)
+        ht.ht_bfs(t.handle, hm, 0, 4096, states, fused=fused)
         torch.cuda.synchronize()
         ht.ht_prof_enable(False)
         kern = {k: round(v[1], 2) for k, v in ht.ht_prof_read().items() if k != "clear"}
-        out[sch] = {"seconds": round(sec, 4), "states_per_s_M": round(res.states / sec / 1e6, 1),
+        out[sch + ("_fused" if fused else "")] = {"seconds": round(sec, 4), "states_per_s_M": round(res.states / sec / 1e6, 1),
                     "find_or_put_mops": round(res.successors / sec / 1e6, 1),
                     "levels_match_oracle": bool(ok), "host_syncs": len(sizes) + 2, "kernel_ms": kern,
                     "multiplicity": round(res.successors / max(1, res.states), 2)}

@@ -254,6 +254,17 @@ ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max
                  uint64_t* h_level_sizes, void* d_states, uint64_t states_cap,
                  ht_bfs_result* result, void* stream);
 
+/* ht_bfs with each level's successor generation and find-or-put fused into
+ * one launch (exploration on the fly, as GPUexplore does, Section 3.2):
+ * a warp generates its frontier states' successors into shared memory and
+ * finds-or-puts them from there, so no successor buffer goes through device
+ * memory.  Bucket-scheme tables only (HT_ERR_INVALID for Cuckoo, whose
+ * find-or-put needs two launches); same arguments, results and errors as
+ * ht_bfs. */
+ht_status ht_bfs_fused(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max_levels,
+                       uint64_t* h_level_sizes, void* d_states, uint64_t states_cap, ht_bfs_result* result,
+                       void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batched find-or-put over many tables in one call (the batched form of
  * Section 5's find-or-insert, for workloads with many small tables).  Item i

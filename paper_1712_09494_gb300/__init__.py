@@ -266,14 +266,16 @@ def ht_successors(model, states, succ, count, stream=None):
            "ht_successors")
 
 
-def ht_bfs(table, model, s0=0, max_levels=4096, states=None, states_cap=0, stream=None):
+def ht_bfs(table, model, s0=0, max_levels=4096, states=None, states_cap=0, stream=None, fused=False):
     """Returns (HtBfsResult, level sizes list); `states` (optional tensor)
-    receives every reachable state in level order."""
+    receives every reachable state in level order.  fused=True runs
+    ht_bfs_fused (bucket-scheme tables)."""
     sizes = (ctypes.c_uint64 * max_levels)()
     res = HtBfsResult()
     cap = states.numel() if states is not None else int(states_cap)
-    _check(load().ht_bfs(table, ctypes.byref(model), int(s0), int(max_levels), sizes,
-                         _dptr(states, "states"), cap, ctypes.byref(res), _stream(stream)), "ht_bfs")
+    name = "ht_bfs_fused" if fused else "ht_bfs"
+    _check(getattr(load(), name)(table, ctypes.byref(model), int(s0), int(max_levels), sizes,
+                                 _dptr(states, "states"), cap, ctypes.byref(res), _stream(stream)), name)
     return res, [int(sizes[i]) for i in range(res.levels)]
 
 

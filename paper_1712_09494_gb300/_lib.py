@@ -110,6 +110,7 @@ SIGNATURES = {
     "ht_cuckoo_find_or_put_noalloc": (_I32, [_VP, _U64, _VP, _U64, _VP, _U64, _VP, ctypes.c_int, _VP]),
     "ht_successors": (_I32, [_P(HtModel), _U32, _VP, _U64, _VP, _U64, _VP, _VP]),
     "ht_bfs": (_I32, [_VP, _P(HtModel), _U64, _U32, _VP, _VP, _U64, _P(HtBfsResult), _VP]),
+    "ht_bfs_fused": (_I32, [_VP, _P(HtModel), _U64, _U32, _VP, _VP, _U64, _P(HtBfsResult), _VP]),
     "ht_multi_create": (_I32, [_U32, _VP, _VP, _VP, _VP, _U32, _VP, _P(_VP)]),
     "ht_multi_reset": (_I32, [_VP, _VP]),
     "ht_multi_run": (_I32, [_VP, ctypes.c_int, _U64, _VP]),

@@ -641,9 +641,11 @@ ht_status ht_successors(const ht_model* h_model, uint32_t key_width, const void*
     return HT_OK;
 }
 
-ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max_levels, uint64_t* h_level_sizes,
-                 void* d_states, uint64_t states_cap, ht_bfs_result* result, void* stream) {
+static ht_status bfs_common(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max_levels,
+                            uint64_t* h_level_sizes, void* d_states, uint64_t states_cap, ht_bfs_result* result,
+                            void* stream, bool fused) {
     if (!t || !result) return HT_ERR_INVALID;
+    if (fused && t->scheme != HT_BUCKET) return HT_ERR_INVALID;
     const uint64_t msucc = model_max_successors(h_model, t->kw);
     if (!msucc) return HT_ERR_INVALID;
     if (t->kw == 32 ? s0 >= 0xFFFFFFFFull : (s0 >> 63) != 0) return HT_ERR_INVALID;
@@ -656,8 +658,10 @@ ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max
     } else if (!states_cap) {
         return HT_ERR_INVALID;
     }
-    // Successor buffer: up to 2^26 vectors per find-or-put launch sequence.
-    const uint64_t succ_cap = std::min<uint64_t>(1ull << 26, std::max<uint64_t>(msucc, (t->dt.nslots + 1) * msucc));
+    // Successor buffer (split form): up to 2^26 vectors per find-or-put
+    // launch sequence; the fused form has none.
+    const uint64_t succ_cap =
+        fused ? 1 : std::min<uint64_t>(1ull << 26, std::max<uint64_t>(msucc, (t->dt.nslots + 1) * msucc));
     const uint64_t chunk_states = std::max<uint64_t>(1, succ_cap / msucc);
     DevBuf dm, states_own, succ, ctr;
     const PreparedModel pm = prepare_model(*h_model);
@@ -704,6 +708,13 @@ ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max
             break;
         }
         if (h_level_sizes) h_level_sizes[level] = nd;
+        if (fused) {
+            HT_TRY(bfs_fused_level(bucket_cfg(t), static_cast<const PreparedModel*>(dm.p), states + lo * ksz, nd,
+                                   t->dt, d_states, c, states_cap, c + 2, s));
+            lo = hi;
+            ++level;
+            continue;
+        }
         for (uint64_t c0 = lo; c0 < hi; c0 += chunk_states) {
             const uint64_t m = std::min<uint64_t>(chunk_states, hi - c0);
             HT_TRY(cudaMemsetAsync(c + 1, 0, sizeof(unsigned long long), s));
@@ -722,6 +733,17 @@ ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max
     result->successors = gen;
     const ht_status ts = sync_and_status(t, s);
     return ts;
+}
+
+ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max_levels, uint64_t* h_level_sizes,
+                 void* d_states, uint64_t states_cap, ht_bfs_result* result, void* stream) {
+    return bfs_common(t, h_model, s0, max_levels, h_level_sizes, d_states, states_cap, result, stream, false);
+}
+
+ht_status ht_bfs_fused(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max_levels,
+                       uint64_t* h_level_sizes, void* d_states, uint64_t states_cap, ht_bfs_result* result,
+                       void* stream) {
+    return bfs_common(t, h_model, s0, max_levels, h_level_sizes, d_states, states_cap, result, stream, true);
 }
 
 }  // extern "C"

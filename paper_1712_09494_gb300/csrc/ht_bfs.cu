@@ -9,44 +9,6 @@
 namespace ht {
 namespace {
 
-__device__ __forceinline__ uint32_t local_of(const PreparedModel& m, uint64_t s, int c) {
-    return uint32_t(s >> m.off[c]) & ((1u << m.bits[c]) - 1u);
-}
-
-__device__ __forceinline__ uint64_t with_local(const PreparedModel& m, uint64_t s, int c, uint32_t v) {
-    const uint64_t mask = ((1ull << m.bits[c]) - 1ull) << m.off[c];
-    return (s & ~mask) | (uint64_t(v) << m.off[c]);
-}
-
-// Visits every successor of s: local actions of each component, then every
-// combination of the two members' transitions of each synchronising pair.
-template <class F>
-__device__ __forceinline__ void for_each_successor(const PreparedModel& m, uint64_t s, F&& emit) {
-    for (int c = 0; c < m.C; ++c) {
-        const uint32_t u = local_of(m, s, c);
-        const int d = m.nloc[c][u];
-        for (int j = 0; j < d; ++j) emit(with_local(m, s, c, m.loc[c][u][j]));
-    }
-    for (int p = 0; p < m.P; ++p) {
-        const int c1 = m.pc1[p], c2 = m.pc2[p];
-        const uint32_t u1 = local_of(m, s, c1), u2 = local_of(m, s, c2);
-        const int d1 = m.nsyn[p][0][u1], d2 = m.nsyn[p][1][u2];
-        for (int j1 = 0; j1 < d1; ++j1) {
-            const uint64_t s1 = with_local(m, s, c1, m.syn[p][0][u1][j1]);
-            for (int j2 = 0; j2 < d2; ++j2) emit(with_local(m, s1, c2, m.syn[p][1][u2][j2]));
-        }
-    }
-}
-
-// The number of successors of s (what for_each_successor visits).
-__device__ __forceinline__ uint32_t count_successors(const PreparedModel& m, uint64_t s) {
-    uint32_t n = 0;
-    for (int c = 0; c < m.C; ++c) n += m.nloc[c][local_of(m, s, c)];
-    for (int p = 0; p < m.P; ++p)
-        n += uint32_t(m.nsyn[p][0][local_of(m, s, m.pc1[p])]) * m.nsyn[p][1][local_of(m, s, m.pc2[p])];
-    return n;
-}
-
 // Successors of a frontier: lane l expands state l of the warp's 32.  The
 // lanes count their successors, reserve one range for the warp, then emit
 // them into the warp's buffer in shared memory (in chunks of kSuccStage when

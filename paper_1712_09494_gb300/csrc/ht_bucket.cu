@@ -643,6 +643,80 @@ packed_bucket_kernel(const DevTable* __restrict__ tables, const WorkDesc* __rest
     if (lane == 0 && stored) atomicAdd(&tables[d.table].ctr->size, stored);
 }
 
+// One BFS level with successor generation and find-or-put fused (the
+// GPUexplore way of exploring on the fly, Section 3.2): lane l of a warp
+// expands frontier state l of the warp's 32; the warp lays their successors
+// out in shared memory (in chunks of kFusedStage) and runs them through the
+// bucket claim tile by tile; new states are appended to `out` through the
+// warp's stage.  No successor buffer goes through HBM.
+constexpr int kFusedBlock = 128;
+constexpr int kFusedStage = 512;
+
+template <int KW, int BS, int G>
+__global__ void __launch_bounds__(kFusedBlock, HT_BUCKET_MIN_BLOCKS * 2)
+bfs_fused_kernel(const PreparedModel* __restrict__ model, const typename Keys<KW>::T* __restrict__ frontier,
+                 uint64_t n, const DevTable t, typename Keys<KW>::T* __restrict__ out,
+                 unsigned long long* __restrict__ count, uint64_t cap, unsigned long long* __restrict__ gen) {
+    using K = Keys<KW>;
+    using T = typename K::T;
+    __shared__ PreparedModel sm;
+    __shared__ uint64_t s_succ[kFusedBlock / 32][kFusedStage];
+    __shared__ T s_new[kFusedBlock / 32][kStageCap];
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(model);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&sm);
+        for (int i = threadIdx.x; i < int(sizeof(PreparedModel) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    uint64_t* buf = s_succ[warp];
+    WarpStage<T, kStageCap> stage(s_new[warp]);
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t rounds = (n + stride - 1) / stride;       // warp-uniform trip count
+    unsigned long long made = 0, stored = 0;
+    for (uint64_t r = 0; r < rounds; ++r) {
+        const uint64_t i = r * stride + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+        const bool act = i < n;
+        const uint64_t st = act ? uint64_t(frontier[i]) : 0;
+        const uint32_t cnt = act ? count_successors(sm, st) : 0;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t tot = __shfl_sync(kFull, incl, 31);
+        const uint32_t excl = incl - cnt;
+        for (uint32_t chunk = 0; chunk < tot; chunk += kFusedStage) {
+            if (act && excl < chunk + kFusedStage && incl > chunk) {
+                uint32_t k = excl;
+                for_each_successor(sm, st, [&](uint64_t v) {
+                    if (k >= chunk && k < chunk + kFusedStage) buf[k - chunk] = v;
+                    ++k;
+                });
+            }
+            __syncwarp();
+            const uint32_t m = min(uint32_t(kFusedStage), tot - chunk);
+            for (uint32_t j0 = 0; j0 < m; j0 += 32) {
+                const bool mine = j0 + lane < m;
+                const uint64_t key = mine ? buf[j0 + lane] : 0;
+                const bool ok = mine && !K::reserved(key);
+                if (mine && !ok) set_flag(t.ctr, kFlagInvalidKey);
+                const uint32_t my_new = bucket_tile<KW, BS, G>(t, key, 0, ok);
+                stage.push(mine && my_new, T(key), out, count, cap);
+                stored += __popc(__ballot_sync(kFull, my_new != 0));
+            }
+            __syncwarp();
+        }
+        made += cnt;
+    }
+    stage.flush(out, count, cap);
+    for (int o = 16; o; o >>= 1) made += __shfl_down_sync(kFull, made, o);
+    if (lane == 0 && stored) atomicAdd(&t.ctr->size, stored);
+    if (lane == 0 && made) atomicAdd(gen, made);
+}
+
 // (bucket_slots, lanes) pairs that are instantiated.
 #define HT_BUCKET_CONFIGS(X) \
     X(8, 2) X(8, 4) X(8, 8) X(16, 2) X(16, 4) X(16, 8) X(16, 16) X(32, 4) X(32, 8) X(32, 16) X(32, 32)
@@ -697,6 +771,30 @@ cudaError_t packed_bucket_find_or_put(const BucketCfg& c, const DevTable* tables
     if (c.bucket_slots == BS && c.lanes == G) {                                                           \
         if (c.kw == 32) L(32, BS, G)                                                                      \
         L(64, BS, G)                                                                                      \
+    }
+    HT_BUCKET_CONFIGS(X)
+#undef X
+#undef L
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t bfs_fused_level(const BucketCfg& c, const PreparedModel* model, const void* frontier, uint64_t n,
+                            const DevTable& t, void* out, unsigned long long* count, uint64_t cap,
+                            unsigned long long* gen, cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    ProfScope ps(kKBucketFop, s);
+#define L(KW, BS, G)                                                                                     \
+    {                                                                                                    \
+        using T = typename Keys<KW>::T;                                                                  \
+        auto k = bfs_fused_kernel<KW, BS, G>;                                                            \
+        k<<<launch_blocks((const void*)k, kFusedBlock), kFusedBlock, 0, s>>>(                            \
+            model, static_cast<const T*>(frontier), n, t, static_cast<T*>(out), count, cap, gen);        \
+        return cudaGetLastError();                                                                       \
+    }
+#define X(BS, G)                                                                                         \
+    if (c.bucket_slots == BS && c.lanes == G) {                                                          \
+        if (c.kw == 32) L(32, BS, G)                                                                     \
+        L(64, BS, G)                                                                                     \
     }
     HT_BUCKET_CONFIGS(X)
 #undef X

@@ -367,8 +367,56 @@ struct PreparedModel {
 };
 
 PreparedModel prepare_model(const ht_model& m);
+
+// Successor enumeration over a prepared model (state vectors of up to 64
+// bits; component c's local state is bits [off[c], off[c] + bits[c])).
+__device__ __forceinline__ uint32_t local_of(const PreparedModel& m, uint64_t s, int c) {
+    return uint32_t(s >> m.off[c]) & ((1u << m.bits[c]) - 1u);
+}
+
+__device__ __forceinline__ uint64_t with_local(const PreparedModel& m, uint64_t s, int c, uint32_t v) {
+    const uint64_t mask = ((1ull << m.bits[c]) - 1ull) << m.off[c];
+    return (s & ~mask) | (uint64_t(v) << m.off[c]);
+}
+
+// Visits every successor of s: local actions of each component, then every
+// combination of the two members' transitions of each synchronising pair.
+template <class F>
+__device__ __forceinline__ void for_each_successor(const PreparedModel& m, uint64_t s, F&& emit) {
+    for (int c = 0; c < m.C; ++c) {
+        const uint32_t u = local_of(m, s, c);
+        const int d = m.nloc[c][u];
+        for (int j = 0; j < d; ++j) emit(with_local(m, s, c, m.loc[c][u][j]));
+    }
+    for (int p = 0; p < m.P; ++p) {
+        const int c1 = m.pc1[p], c2 = m.pc2[p];
+        const uint32_t u1 = local_of(m, s, c1), u2 = local_of(m, s, c2);
+        const int d1 = m.nsyn[p][0][u1], d2 = m.nsyn[p][1][u2];
+        for (int j1 = 0; j1 < d1; ++j1) {
+            const uint64_t s1 = with_local(m, s, c1, m.syn[p][0][u1][j1]);
+            for (int j2 = 0; j2 < d2; ++j2) emit(with_local(m, s1, c2, m.syn[p][1][u2][j2]));
+        }
+    }
+}
+
+// The number of successors of s (what for_each_successor visits).
+__device__ __forceinline__ uint32_t count_successors(const PreparedModel& m, uint64_t s) {
+    uint32_t n = 0;
+    for (int c = 0; c < m.C; ++c) n += m.nloc[c][local_of(m, s, c)];
+    for (int p = 0; p < m.P; ++p)
+        n += uint32_t(m.nsyn[p][0][local_of(m, s, m.pc1[p])]) * m.nsyn[p][1][local_of(m, s, m.pc2[p])];
+    return n;
+}
+
 // Largest number of successors of one state, or 0 for a malformed model.
 uint64_t model_max_successors(const ht_model* m, uint32_t key_width);
+
+// One BFS level fused: successors of frontier[0..n) generated and
+// found-or-put into a bucket-scheme table in one launch; new states appended
+// to out at *count (entries past cap not written); *gen += successors.
+cudaError_t bfs_fused_level(const BucketCfg& c, const PreparedModel* model, const void* frontier, uint64_t n,
+                            const DevTable& t, void* out, unsigned long long* count, uint64_t cap,
+                            unsigned long long* gen, cudaStream_t s);
 
 // Read-only views of a table for the batched form (ht_api.cu).
 const DevTable& table_dev(const ht_table* t);

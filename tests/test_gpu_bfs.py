@@ -67,13 +67,18 @@ def _oracle_bfs(oracle_lib, m):
     return _REF[key]
 
 
-def _check_bfs(oracle_lib, m, scheme, params=None):
+# BFS forms: (scheme, fused successor generation + find-or-put).
+FORMS = [("bucket", False), ("bucket", True), ("cuckoo", False)]
+FORM_IDS = ["bucket", "bucket_fused", "cuckoo"]
+
+
+def _check_bfs(oracle_lib, m, scheme, params=None, fused=False):
     ref = _oracle_bfs(oracle_lib, m)
     assert ref.rc == 0
     kw = m.key_width
     t = ht.HashTable(max(64, int(ref.total / 0.7)), scheme, kw, params)
     states = torch.empty(ref.total + 16, dtype=torch.int32 if kw == 32 else torch.int64, device="cuda")
-    res, sizes = ht.ht_bfs(t.handle, hmodel(m), 0, 4096, states)
+    res, sizes = ht.ht_bfs(t.handle, hmodel(m), 0, 4096, states, fused=fused)
     assert res.complete == 1
     assert res.states == ref.total
     assert res.successors == int(ref.level_succ.sum())
@@ -87,23 +92,38 @@ def _check_bfs(oracle_lib, m, scheme, params=None):
     return res
 
 
-@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
 @pytest.mark.parametrize("spec", MODELS)
-def test_bfs_matches_oracle(oracle_lib, scheme, spec):
+def test_bfs_matches_oracle(oracle_lib, form, spec):
     m = ss.random_model(spec["seed"], C=spec["C"], L=spec["L"], R=spec["R"], p_sync=spec["p_sync"], P=spec["P"])
-    _check_bfs(oracle_lib, m, scheme)
+    _check_bfs(oracle_lib, m, form[0], fused=form[1])
 
 
-@pytest.mark.parametrize("scheme", SCHEMES)
-def test_bfs_medium_model_small_chunks(oracle_lib, scheme):
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_bfs_medium_model_small_chunks(oracle_lib, form):
     # ~10^5-10^6 states; a small Cuckoo batch bound forces many chunks per level.
+    scheme, fused = form
     m = ss.random_model(21, C=10, L=16, R=[4, 4, 4, 4, 3, 3, 3, 3, 4, 4], p_sync=0.2, P=3)
     params = dict(max_batch=1 << 12) if scheme == "cuckoo" else dict(bucket_slots=16, lanes_per_key=4)
-    _check_bfs(oracle_lib, m, scheme, params)
+    _check_bfs(oracle_lib, m, scheme, params, fused=fused)
 
 
-@pytest.mark.parametrize("scheme", SCHEMES)
-def test_bfs_degenerate_models(oracle_lib, scheme):
+@pytest.mark.parametrize("shape", [(8, 2), (32, 8), (16, 16)])
+def test_bfs_fused_other_bucket_shapes(oracle_lib, shape):
+    m = ss.random_model(33, C=9, L=32, R=3, p_sync=0.2, P=3)             # 45-bit vectors
+    _check_bfs(oracle_lib, m, "bucket", dict(bucket_slots=shape[0], lanes_per_key=shape[1]), fused=True)
+
+
+def test_bfs_fused_rejects_cuckoo():
+    m = ss.random_model(1, C=3, L=8, R=5)
+    t = ht.HashTable(1024, "cuckoo", 32)
+    with pytest.raises(ht.HtError):
+        ht.ht_bfs(t.handle, hmodel(m), 0, 16, torch.empty(1024, dtype=torch.int32, device="cuda"), fused=True)
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_bfs_degenerate_models(oracle_lib, form):
+    scheme, fused = form
     # Every transition synchronised with a partner that never matches: s0 only.
     L = [4, 4]
     bits = np.zeros(16, np.uint8)
@@ -116,12 +136,13 @@ def test_bfs_degenerate_models(oracle_lib, scheme):
     lab[0, :4, 0] = 1           # pair 0, but component 1 has no label-1 transitions
     m = ss.Model(C=2, L=np.array(L), bits=bits, deg=deg, tgt=tgt, lab=lab, pairs=np.array([[0, 1]], np.uint8))
     t = ht.HashTable(64, scheme, 32)
-    res, sizes = ht.ht_bfs(t.handle, hmodel(m), 0, 16, torch.empty(8, dtype=torch.int32, device="cuda"))
+    res, sizes = ht.ht_bfs(t.handle, hmodel(m), 0, 16, torch.empty(8, dtype=torch.int32, device="cuda"), fused=fused)
     assert res.complete == 1 and sizes == [1] and res.successors == 0
     # A chain longer than max_levels stops incomplete.
     m2 = ss.random_model(1, C=1, L=32, R=32, deg_lo=1, deg_hi=1)
     t2 = ht.HashTable(64, scheme, 32)
-    res2, sizes2 = ht.ht_bfs(t2.handle, hmodel(m2), 0, 5, torch.empty(64, dtype=torch.int32, device="cuda"))
+    res2, sizes2 = ht.ht_bfs(t2.handle, hmodel(m2), 0, 5, torch.empty(64, dtype=torch.int32, device="cuda"),
+                             fused=fused)
     assert res2.complete == 0 and sizes2 == [1] * 5
 
 

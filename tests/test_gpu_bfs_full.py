@@ -32,14 +32,15 @@ def _lib():
     ht.load()
 
 
-@pytest.mark.parametrize("scheme", ["bucket", "cuckoo"])
-def test_config3_bfs_matches_stored_oracle_levels(scheme):
+@pytest.mark.parametrize("scheme,fused", [("bucket", False), ("bucket", True), ("cuckoo", False)],
+                         ids=["bucket", "bucket_fused", "cuckoo"])
+def test_config3_bfs_matches_stored_oracle_levels(scheme, fused):
     gold = json.load(open(os.path.join(GOLDEN, "statespace_config3.json")))
     m = ss.config3_model(seed=gold["model"]["seed"], p_sync=gold["model"]["p_sync"])
     hm = ht.make_model(m.C, m.bits, m.deg, m.tgt, m.lab, m.pairs)
     t = ht.HashTable(int(gold["states"] / 0.8), scheme, 64)
     states = torch.empty(gold["states"] + 1024, dtype=torch.int64, device="cuda")
-    res, sizes = ht.ht_bfs(t.handle, hm, 0, 4096, states)
+    res, sizes = ht.ht_bfs(t.handle, hm, 0, 4096, states, fused=fused)
     assert res.complete == 1
     assert res.states == gold["states"]
     assert res.successors == gold["successors"]

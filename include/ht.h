@@ -75,7 +75,14 @@ typedef enum {
  *                  the device's persisting L2 (else, for Cuckoo, the dedup
  *                  claim set); this raises the process's persisting L2
  *                  set-aside (cudaLimitPersistingL2CacheSize).  Default: 1
- *                  for Cuckoo, 0 for the bucket scheme.  */
+ *                  for Cuckoo, 0 for the bucket scheme.
+ *   grow_load_permille  0 (default): fixed capacity.  Else a synchronising
+ *                  call (ht_sync, ht_size, ht_export) that finds
+ *                  the table above this load (per mille of its slots), or
+ *                  using its overflow set, doubles its capacity (ht_grow)
+ *                  until it is below (100..1000; 0 = off).  Between two
+ *                  synchronising calls the keys still have to fit the table,
+ *                  stash and overflow set as they are.  */
 typedef struct ht_params {
     uint32_t num_hashes;
     uint32_t max_evictions;
@@ -86,7 +93,8 @@ typedef struct ht_params {
     uint64_t max_batch;
     uint64_t seed;
     int32_t l2_persist;
-    int32_t reserved_[3];
+    uint32_t grow_load_permille;
+    int32_t reserved_[2];
 } ht_params;
 
 typedef struct ht_table ht_table;
@@ -155,6 +163,17 @@ ht_status ht_export(ht_table* t, void* d_keys_out, uint32_t* d_values_out,
 
 /* Empties the table, keeping its capacity and hash constants. */
 ht_status ht_clear(ht_table* t, void* stream);
+
+/* Moves the table to `new_capacity` slots (rounded up to whole buckets):
+ * every stored key (and value) is copied out of the table, stash and
+ * overflow set and inserted into new storage with the current hash
+ * constants; the old storage is freed.  Synchronises `stream`.  Not part of
+ * the paper (Sections 4.1, 4.2 report a full table); it lets a table start
+ * small.  HT_ERR_INVALID if new_capacity is 0 or too large; HT_ERR_FULL if
+ * the keys do not fit the new capacity (the table is then unchanged);
+ * HT_ERR_OOM if the new storage cannot be allocated (unchanged too).  The
+ * table must not be in use on another stream meanwhile. */
+ht_status ht_grow(ht_table* t, uint64_t new_capacity, void* stream);
 
 /* Table facts: slots, hash functions, rebuilds done so far. */
 ht_status ht_info(const ht_table* t, uint64_t* slots, uint32_t* num_hashes,

@@ -22,7 +22,7 @@ __all__ = [
     "ht_default_params", "ht_create", "ht_destroy", "ht_find_or_put", "ht_find_or_put_append",
     "ht_insert", "ht_lookup", "ht_sync", "ht_size", "ht_export", "ht_clear", "ht_info",
     "ht_compact", "ht_prof_enable", "ht_prof_reset", "ht_prof_read", "ht_prof_kernels",
-    "ht_probe_random_read", "ht_probe_random_rmw", "ht_stats", "ht_multi_find_or_put", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
+    "ht_probe_random_read", "ht_probe_random_rmw", "ht_stats", "ht_grow", "ht_multi_find_or_put", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
     "NOALLOC_MAX_BATCH", "scheme_of", "HtModel", "HtBfsResult", "make_model", "ht_successors", "ht_bfs",
     "MultiExploration", "Server", "HtServerConfig", "HtServerStats",
 ]
@@ -177,6 +177,10 @@ def _work_dtype():
 
 
 _WORK_DTYPE = _work_dtype()
+
+
+def ht_grow(table, new_capacity, stream=None):
+    _check(load().ht_grow(table, int(new_capacity), _stream(stream)), "ht_grow")
 
 
 def ht_stats(table, stream=None):
@@ -477,3 +481,6 @@ class HashTable:
 
     def stats(self, stream=None):
         return ht_stats(self._h, stream)
+
+    def grow(self, new_capacity, stream=None):
+        ht_grow(self._h, new_capacity, stream)

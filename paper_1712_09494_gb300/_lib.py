@@ -15,7 +15,7 @@ class HtParams(ctypes.Structure):
         ("stash_slots", ctypes.c_uint32), ("bucket_slots", ctypes.c_uint32),
         ("lanes_per_key", ctypes.c_uint32), ("max_rebuilds", ctypes.c_uint32),
         ("max_batch", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-        ("l2_persist", ctypes.c_int32), ("reserved_", ctypes.c_int32 * 3),
+        ("l2_persist", ctypes.c_int32), ("grow_load_permille", ctypes.c_uint32), ("reserved_", ctypes.c_int32 * 2),
     ]
 
 
@@ -97,6 +97,7 @@ SIGNATURES = {
     "ht_clear": (_I32, [_VP, _VP]),
     "ht_info": (_I32, [_VP, _P(_U64), _P(_U32), _P(_U32)]),
     "ht_stats": (_I32, [_VP, _P(HtTableStats), _VP]),
+    "ht_grow": (_I32, [_VP, _U64, _VP]),
     "ht_multi_find_or_put": (_I32, [_VP, _U32, _VP, _U32, _VP]),
     "ht_status_str": (ctypes.c_char_p, [_I32]),
     "ht_compact": (_I32, [_VP, _VP, _U64, _U32, _VP, _VP, _VP]),

@@ -177,10 +177,23 @@ ht_status rebuild(ht_table* t, cudaStream_t s) {
     return st;
 }
 
+ht_status grow_to(ht_table* t, uint64_t new_capacity, cudaStream_t s);
+
 ht_status sync_and_status(ht_table* t, cudaStream_t s) {
     DevCounters c;
     ht_status st = read_counters(t, &c, s);
     if (st != HT_OK) return st;
+    if (t->p.grow_load_permille && !(c.flags & kFlagDropped)) {
+        // Growth instead of rebuilds: double while above the load or while
+        // keys sit in the overflow set (bounded: capacity doubles each time).
+        while ((c.size * 1000 > t->dt.nslots * uint64_t(t->p.grow_load_permille) || (c.flags & kFlagRebuild)) &&
+               t->dt.nslots * 2 <= kMaxCapacity) {
+            st = grow_to(t, t->dt.nslots * 2, s);
+            if (st != HT_OK) return st;
+            st = read_counters(t, &c, s);
+            if (st != HT_OK) return st;
+        }
+    }
     if ((c.flags & kFlagRebuild) && !t->rebuild_exhausted) {
         st = rebuild(t, s);
         if (st != HT_OK) return st;
@@ -199,6 +212,7 @@ ht_status sync_and_status(ht_table* t, cudaStream_t s) {
 }
 
 bool valid_params(ht_scheme scheme, const ht_params& p) {
+    if (p.grow_load_permille != 0 && (p.grow_load_permille < 100 || p.grow_load_permille > 1000)) return false;
     if (scheme == HT_BUCKET) {
         if (p.num_hashes < 1 || p.num_hashes > uint32_t(kMaxHashes)) return false;
         if (p.bucket_slots != 8 && p.bucket_slots != 16 && p.bucket_slots != 32) return false;
@@ -248,6 +262,65 @@ void free_table(ht_table* t, cudaStream_t s) {
 }  // namespace
 
 namespace {
+
+// Copies every stored word out, inserts them into new storage of
+// new_capacity slots with the current hash constants, and swaps the storage
+// in; on any failure the table is left as it was.
+ht_status grow_to(ht_table* t, uint64_t new_capacity, cudaStream_t s) {
+    DevCounters c;
+    ht_status st = read_counters(t, &c, s);
+    if (st != HT_OK) return st;
+    ht_params p = t->p;
+    p.seed = t->seed_base;                // the constants in use (after any rebuild)
+    ht_table* nt = nullptr;
+    st = ht_create(new_capacity, t->scheme, t->kw, &p, s, &nt);
+    if (st != HT_OK) return st;
+    const uint64_t n = c.size;
+    void* keys = nullptr;
+    uint32_t* vals = nullptr;
+    unsigned long long* cnt = nullptr;
+    cudaError_t e = cudaMalloc(&keys, std::max<uint64_t>(n, 1) * (t->kw / 8));
+    if (e == cudaSuccess && t->kw == 32) e = cudaMalloc(&vals, std::max<uint64_t>(n, 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(*cnt));
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(*cnt), s);
+    if (e == cudaSuccess) e = table_export(int(t->kw), t->dt, keys, vals, cnt, n, s);
+    unsigned long long got = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&got, cnt, sizeof(got), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    st = cuda_status(e);
+    if (st == HT_OK) st = run_put(nt, keys, vals, std::min<uint64_t>(got, n), nullptr, nullptr, nullptr, s);
+    if (st == HT_OK) {
+        nt->p.grow_load_permille = 0;     // the new storage must hold them as it is
+        st = sync_and_status(nt, s);
+        nt->p.grow_load_permille = t->p.grow_load_permille;
+    }
+    cudaFree(keys);
+    cudaFree(vals);
+    cudaFree(cnt);
+    if (st != HT_OK) {
+        cudaStreamSynchronize(s);
+        free_table(nt, s);
+        return st == HT_ERR_INVALID ? HT_ERR_FULL : st;
+    }
+    // Carry the sticky facts over (dropped keys stay counted), then swap.
+    if (c.dropped || (c.flags & (kFlagDropped | kFlagInvalidKey))) {
+        DevCounters nc;
+        if ((st = read_counters(nt, &nc, s)) == HT_OK) {
+            nc.dropped += c.dropped;
+            nc.flags |= c.flags & (kFlagDropped | kFlagInvalidKey);
+            cudaMemcpyAsync(nt->dt.ctr, &nc, sizeof(nc), cudaMemcpyHostToDevice, s);
+        }
+    }
+    std::swap(t->dt, nt->dt);
+    std::swap(t->sc, nt->sc);
+    std::swap(t->chunk, nt->chunk);
+    std::swap(t->parity, nt->parity);
+    std::swap(t->win, nt->win);
+    t->rebuild_exhausted = false;
+    cudaStreamSynchronize(s);
+    free_table(nt, s);                    // the old storage
+    return HT_OK;
+}
 
 // Bucket-scheme items of one ht_multi_find_or_put call that share a key
 // width and bucket shape (one packed launch).
@@ -527,6 +600,12 @@ ht_status ht_clear(ht_table* t, void* stream) {
     t->sticky = HT_OK;
     t->rebuild_exhausted = false;
     return clear_table(t, as_stream(stream));
+}
+
+ht_status ht_grow(ht_table* t, uint64_t new_capacity, void* stream) {
+    if (!t || new_capacity == 0 || new_capacity > kMaxCapacity) return HT_ERR_INVALID;
+    DeviceGuard g(t->device);
+    return grow_to(t, new_capacity, as_stream(stream));
 }
 
 ht_status ht_stats(ht_table* t, ht_table_stats* out, void* stream) {

@@ -296,3 +296,57 @@ def test_clear_empties(oracle_lib, scheme):
     t.clear()
     assert t.size() == 0
     assert to_np(t.find_or_put(k)).sum() == 3000
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kw", [32, 64])
+def test_grow_keeps_contents_and_values(oracle_lib, scheme, kw):
+    n = 50_000
+    keys = wk.distinct_keys(n, kw, seed=71)
+    t = ht.HashTable(70_000, scheme, kw)
+    orc = oracle_lib.OracleTable()
+    if kw == 32:
+        vals = ((np.arange(n, dtype=np.uint64) * 2654435761) & 0xFFFFFFFF).astype(np.uint32)
+        t.insert(to_dev(keys), to_dev(vals))
+    else:
+        t.find_or_put(to_dev(keys))
+    orc.find_or_put(keys)
+    t.grow(300_000)
+    assert t.info()["slots"] >= 300_000 and t.size() == n
+    f, v = t.lookup(to_dev(keys))
+    assert to_np(f).all()
+    if kw == 32:
+        np.testing.assert_array_equal(to_np(v, np.uint32), vals)
+    more = wk.distinct_keys(150_000, kw, seed=71, start=n - 10_000)       # 10k repeats, 140k new
+    assert_flags_per_key(more, to_np(t.find_or_put(to_dev(more))), orc.find_or_put(more))
+    assert t.sync() == 0 and t.size() == orc.size()
+    k, _ = t.export()
+    assert_same_set(keys_np(k, kw), orc.export()[0])
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_grow_too_small_reports_full_and_keeps_the_table(oracle_lib, scheme):
+    keys = wk.distinct_keys(20_000, 64, seed=72)
+    t = ht.HashTable(30_000, scheme, 64)
+    t.find_or_put(to_dev(keys))
+    slots = t.info()["slots"]
+    with pytest.raises(ht.HtError) as e:
+        t.grow(1000)
+    assert e.value.status == 3
+    assert t.info()["slots"] == slots and t.size() == 20_000 and t.sync() == 0
+    assert to_np(t.lookup(to_dev(keys))[0]).all()
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_auto_grow_at_synchronising_calls(oracle_lib, scheme):
+    # Starts at 4096 slots, grows whenever a sync finds it above load 0.8.
+    fs = wk.fill_stream(200_000, 1024, 0.25, 64, seed=73)
+    t = ht.HashTable(4096, scheme, 64, dict(grow_load_permille=800))
+    orc = oracle_lib.OracleTable()
+    for b in range(fs.n_batches):
+        kb = fs.batch(b)
+        assert_flags_per_key(kb, to_np(t.find_or_put(to_dev(kb))), orc.find_or_put(kb))
+        assert t.sync() == 0
+    assert t.size() == 200_000 and t.info()["slots"] >= 200_000 / 0.8
+    k, _ = t.export()
+    assert_same_set(keys_np(k, 64), orc.export()[0])

@@ -532,7 +532,14 @@ multi_bucket_fop_kernel(const MultiDev m, uint64_t max_tiles) {
         if (lane == 0 && stored) atomicAdd(&m.tables[e].ctr->size, stored);
         stored = 0;
     };
+    // Tile T's keys are succ[32 T + lane] whatever its exploration (segments
+    // are laid out by seg_off): the next tile's are loaded while this one is
+    // claimed.  Lanes past an exploration's count read unused words.
+    uint64_t next_key = __ldcg(reinterpret_cast<const unsigned long long*>(m.succ + t_begin * 32 + lane));
     for (uint64_t tile = t_begin; tile < t_end; ++tile) {
+        const uint64_t cur_key = next_key;
+        if (tile + 1 < t_end)
+            next_key = __ldcg(reinterpret_cast<const unsigned long long*>(m.succ + (tile + 1) * 32 + lane));
         if (tile * 32 >= next_seg) {                   // into a later exploration's segment
             settle();
             do {
@@ -544,7 +551,7 @@ multi_bucket_fop_kernel(const MultiDev m, uint64_t max_tiles) {
         const uint64_t i = tile * 32 - seg + lane;
         const bool mine = i < cnt;
         if (!__any_sync(kFull, mine)) continue;
-        const uint64_t key = mine ? __ldcg(reinterpret_cast<const unsigned long long*>(m.succ + seg + i)) : 0;
+        const uint64_t key = mine ? cur_key : 0;
         const bool ok = mine && !K::reserved(key);
         const uint32_t my_new = bucket_tile<KW, BS, G>(m.tables[e], key, 0, ok);
         stage.push(mine && my_new, T(key), static_cast<T*>(m.states[e]), m.total + e, m.states_cap[e]);

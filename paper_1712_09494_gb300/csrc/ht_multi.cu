@@ -162,6 +162,8 @@ struct Group {
     uint64_t max_work = 0, max_tiles = 0;
     unsigned int* h_active = nullptr;  // pinned
     unsigned int* d_flags = nullptr;   // [count] tables' device status bits after a run
+    cudaStream_t s = nullptr;          // the group's stream in a step (groups after the first)
+    cudaEvent_t joined = nullptr;      // the group's step is done
 };
 
 
@@ -178,6 +180,7 @@ struct ht_multi {
     std::vector<ht_model> models;
     std::vector<uint64_t> s0;
     std::vector<Group> groups;
+    cudaEvent_t fork = nullptr;        // a step starts (the other groups' streams wait for it)
     cudaGraphExec_t graph = nullptr;
     // results (host)
     std::vector<uint64_t> res_states, res_levels, res_gen;
@@ -196,7 +199,10 @@ void destroy_multi(ht_multi* m) {
         cudaFree(g.dev.succ);
         cudaFree(g.d_flags);
         cudaFreeHost(g.h_active);
+        if (g.s) cudaStreamDestroy(g.s);
+        if (g.joined) cudaEventDestroy(g.joined);
     }
+    if (m->fork) cudaEventDestroy(m->fork);
     for (void* p : m->states) cudaFree(p);
     for (ht_table* t : m->tables) ht_destroy(t);
     if (m->stream) cudaStreamDestroy(m->stream);
@@ -210,17 +216,25 @@ T* carve(char*& p, uint64_t n) {
     return r;
 }
 
+// One step: each group (explorations of one key width and bucket shape)
+// advances, generates successors and finds-or-puts them.  Groups are
+// independent, so groups after the first run on their own streams, forked
+// from and joined back into the main stream (parallel branches when the step
+// is captured as a graph).
 ht_status step_launches(ht_multi* m) {
-    for (auto& g : m->groups)
-        if (multi_advance(g.dev, g.budget, m->stream) != cudaSuccess) return HT_ERR_CUDA;
-    for (auto& g : m->groups)
-        if (multi_successors(g.cfg.kw, g.dev, g.max_work, m->stream) != cudaSuccess) return HT_ERR_CUDA;
-    for (auto& g : m->groups)
-        if (multi_bucket_find_or_put(g.cfg, g.dev, g.max_tiles, m->stream) != cudaSuccess) return HT_ERR_CUDA;
-    for (auto& g : m->groups)
-        if (cudaMemcpyAsync(g.h_active, g.dev.active, sizeof(unsigned int), cudaMemcpyDeviceToHost, m->stream) !=
-            cudaSuccess)
+    if (cudaEventRecord(m->fork, m->stream) != cudaSuccess) return HT_ERR_CUDA;
+    for (size_t i = 0; i < m->groups.size(); ++i) {
+        Group& g = m->groups[i];
+        const cudaStream_t s = i == 0 ? m->stream : g.s;
+        if (i > 0 && cudaStreamWaitEvent(s, m->fork, 0) != cudaSuccess) return HT_ERR_CUDA;
+        if (multi_advance(g.dev, g.budget, s) != cudaSuccess ||
+            multi_successors(g.cfg.kw, g.dev, g.max_work, s) != cudaSuccess ||
+            multi_bucket_find_or_put(g.cfg, g.dev, g.max_tiles, s) != cudaSuccess ||
+            cudaMemcpyAsync(g.h_active, g.dev.active, sizeof(unsigned int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return HT_ERR_CUDA;
+        if (i > 0 && (cudaEventRecord(g.joined, s) != cudaSuccess || cudaStreamWaitEvent(m->stream, g.joined, 0) != cudaSuccess))
+            return HT_ERR_CUDA;
+    }
     return HT_OK;
 }
 
@@ -305,6 +319,18 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
             g->cfg = c;
         }
         g->members.push_back(e);
+    }
+    if (cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) != cudaSuccess) {
+        destroy_multi(m);
+        return HT_ERR_CUDA;
+    }
+    for (size_t i = 1; i < m->groups.size(); ++i) {
+        Group& g = m->groups[i];
+        if (cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g.joined, cudaEventDisableTiming) != cudaSuccess) {
+            destroy_multi(m);
+            return HT_ERR_CUDA;
+        }
     }
     for (auto& g : m->groups) {
         const uint64_t n = g.members.size();

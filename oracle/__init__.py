@@ -57,6 +57,15 @@ def _load():
         lib.orc_lookup.argtypes = [VP, VP, U64, VP, VP]
         lib.orc_export.restype = U64
         lib.orc_export.argtypes = [VP, VP, VP, U64]
+        lib.orc128_new.restype = VP
+        lib.orc128_new.argtypes = [U64]
+        lib.orc128_free.argtypes = [VP]
+        lib.orc128_size.restype = U64
+        lib.orc128_size.argtypes = [VP]
+        lib.orc128_find_or_put.argtypes = [VP, VP, U64, VP]
+        lib.orc128_lookup.argtypes = [VP, VP, U64, VP]
+        lib.orc128_export.restype = U64
+        lib.orc128_export.argtypes = [VP, VP, U64]
         lib.orc_successors.restype = U64
         lib.orc_successors.argtypes = [P(Model), U64, VP, U64]
         lib.orc_bfs.restype = ctypes.c_int
@@ -71,6 +80,53 @@ def _ptr(a):
 
 def _u64(keys):
     return np.ascontiguousarray(np.asarray(keys).astype(np.uint64, copy=False))
+
+
+class OracleTable128:
+    """The plain set definition for 128-bit keys (std::unordered_set of word
+    pairs, one thread).  Keys are (n, 2) uint64 arrays: column 0 the low
+    word, column 1 the high word."""
+
+    def __init__(self, reserve=0):
+        self._lib = _load()
+        self._h = self._lib.orc128_new(int(reserve))
+
+    def close(self):
+        if self._h:
+            self._lib.orc128_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def size(self):
+        return int(self._lib.orc128_size(self._h))
+
+    @staticmethod
+    def _k(keys):
+        k = np.ascontiguousarray(np.asarray(keys, dtype=np.uint64).reshape(-1, 2))
+        return k
+
+    def find_or_put(self, keys):
+        k = self._k(keys)
+        out = np.empty(len(k), dtype=np.uint8)
+        self._lib.orc128_find_or_put(self._h, _ptr(k), len(k), _ptr(out))
+        return out
+
+    def lookup(self, keys):
+        k = self._k(keys)
+        found = np.empty(len(k), dtype=np.uint8)
+        self._lib.orc128_lookup(self._h, _ptr(k), len(k), _ptr(found))
+        return found
+
+    def export(self):
+        n = self.size()
+        out = np.empty((max(n, 1), 2), dtype=np.uint64)
+        got = int(self._lib.orc128_export(self._h, _ptr(out), n))
+        return out[:got]
 
 
 class OracleTable:

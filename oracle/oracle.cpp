@@ -28,12 +28,25 @@
 #include <cstdint>
 #include <cstring>
 #include <unordered_map>
+#include <unordered_set>
+#include <utility>
 #include <vector>
 
 namespace {
 
 struct Table {
     std::unordered_map<uint64_t, uint32_t> m;
+};
+
+// 128-bit keys (two 64-bit words, low word first): the same set definition.
+struct PairHash {
+    size_t operator()(const std::pair<uint64_t, uint64_t>& k) const {
+        return std::hash<uint64_t>()(k.first) ^ (std::hash<uint64_t>()(k.second) * 0x9E3779B97F4A7C15ull);
+    }
+};
+
+struct Table128 {
+    std::unordered_set<std::pair<uint64_t, uint64_t>, PairHash> s;
 };
 
 }  // namespace
@@ -107,6 +120,44 @@ struct orc_model {
     uint8_t tgt[16][32][4];
     uint8_t lab[16][32][4];
 };
+
+// 128-bit sets: keys[2i] is key i's low word, keys[2i+1] its high word.
+void* orc128_new(uint64_t reserve) {
+    Table128* t = new Table128();
+    if (reserve) t->s.reserve(reserve);
+    return t;
+}
+
+void orc128_free(void* h) { delete static_cast<Table128*>(h); }
+
+uint64_t orc128_size(const void* h) { return static_cast<const Table128*>(h)->s.size(); }
+
+// find-or-put in order: is_new[i] = key i not yet in the set; then it is.
+void orc128_find_or_put(void* h, const uint64_t* keys, uint64_t n, uint8_t* is_new) {
+    auto& s = static_cast<Table128*>(h)->s;
+    for (uint64_t i = 0; i < n; ++i) {
+        const bool inserted = s.emplace(keys[2 * i], keys[2 * i + 1]).second;
+        if (is_new) is_new[i] = inserted ? 1 : 0;
+    }
+}
+
+void orc128_lookup(const void* h, const uint64_t* keys, uint64_t n, uint8_t* found) {
+    const auto& s = static_cast<const Table128*>(h)->s;
+    for (uint64_t i = 0; i < n; ++i) found[i] = s.count({keys[2 * i], keys[2 * i + 1]}) ? 1 : 0;
+}
+
+uint64_t orc128_export(const void* h, uint64_t* keys, uint64_t cap) {
+    const auto& s = static_cast<const Table128*>(h)->s;
+    uint64_t i = 0;
+    for (const auto& k : s) {
+        if (i < cap) {
+            keys[2 * i] = k.first;
+            keys[2 * i + 1] = k.second;
+        }
+        ++i;
+    }
+    return i;
+}
 
 }  // extern "C"
 

@@ -236,3 +236,23 @@ def test_bfs_limits(oracle_lib):
     assert oracle_lib.bfs(m, max_levels=3).rc == 2
     m = ss.random_model(7, C=4, L=8, R=8)
     assert oracle_lib.bfs(m, max_states=100).rc == 1
+
+
+def test_oracle128_find_or_put_lookup_export_against_brute_force(oracle_lib):
+    # Keys that share their low word, keys that share their high word, and
+    # repeats: a key is the pair, neither word alone.
+    rng = np.random.default_rng(12)
+    lo = rng.integers(0, 6, size=3000).astype(np.uint64)
+    hi = rng.integers(0, 6, size=3000).astype(np.uint64) << np.uint64(40)
+    keys = np.stack([lo, hi], axis=1)
+    t = oracle_lib.OracleTable128()
+    seen, exp = set(), []
+    for a, b in keys.tolist():
+        exp.append(int((a, b) not in seen))
+        seen.add((a, b))
+    got = np.concatenate([t.find_or_put(keys[i:i + 700]) for i in range(0, len(keys), 700)])
+    np.testing.assert_array_equal(got, np.array(exp, dtype=np.uint8))
+    assert t.size() == len(seen) == 36
+    q = np.array([[0, 0], [5, 5 << 40], [6, 0], [0, 6 << 40], [1, 1]], dtype=np.uint64)
+    np.testing.assert_array_equal(t.lookup(q), [1, 1, 0, 0, 0])
+    assert set(map(tuple, t.export().tolist())) == seen

@@ -411,6 +411,7 @@ def run_ours(a, rank, world, local):
     if not a.no_sweep:
         out["sweep_config2"] = run_sweep(ht, torch, dev)
         out["replay_multiplicity"] = run_replay(ht, torch, dev)
+        out["wide_keys_128"] = run_wide(ht, torch, dev)
     if not a.no_bfs:
         out["bfs_config3"] = run_bfs(ht, torch, dev, schemes)
     if not a.no_batched:
@@ -733,6 +734,41 @@ def run_replay(ht, torch, dev, n=100_000_000, mults=(1, 2, 5, 10, 50, 100, 200, 
     return {"workload": "10^8 random 32-bit keys per sequence, value range n/m for mean multiplicity ~m, "
                         "table 1.25 x distinct (load 0.8), whole sequence in one find-or-put call",
             "points": pts, "all_exact": all(p["bucket"]["exact"] and p["cuckoo"]["exact"] for p in pts)}
+
+
+def run_wide(ht, torch, dev, n_log2=26, batch_log2=24, dup=0.25, lf=0.8, reps=3):
+    """128-bit keys (state vectors wider than 64 bits), bucket scheme: a fill
+    of 2^26 random keys to load 0.8 in batches of 2^24 with 25% repeats (two
+    independent 63-bit streams as the words); exact when the table ends with
+    exactly 2^26 keys."""
+    from workloads import device_keys as dk
+    n = 1 << n_log2
+    batches, _ = dk.fill_batches_dev(n, 1 << batch_log2, dup, seed=91, device=dev)
+    out = {"workload": "2^%d random 128-bit keys to load %.1f, batches 2^%d, %d%% repeats" % (
+        n_log2, lf, batch_log2, int(dup * 100))}
+    # The high word is a bijection of the low word (another seed of the same
+    # permutation), so distinct low words give distinct keys and repeats repeat.
+    pairs = [torch.stack([b, dk.mix63_perm_dev(b, 92)], dim=1).contiguous() for b in batches]
+    issued = sum(p.shape[0] for p in pairs)
+    flags = torch.empty(max(p.shape[0] for p in pairs), dtype=torch.uint8, device=dev)
+    for lanes in (2, 4):
+        t = ht.HashTable(int(np.ceil(n / lf)), "bucket", 128, dict(lanes_per_key=lanes))
+        times = []
+        for r in range(reps + 1):
+            ht.ht_clear(t.handle)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for p in pairs:
+                ht.ht_find_or_put(t.handle, p, flags[:p.shape[0]])
+            e1.record()
+            torch.cuda.synchronize()
+            if r:
+                times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        out["lanes%d" % lanes] = {"ms_per_fill": round(ms, 2), "mops": round(issued / (ms / 1e3) / 1e6, 1),
+                                  "exact": t.sync() == 0 and t.size() == n}
+        t.close()
+    return out
 
 
 def run_multi_table(ht, torch, dev, n_tables=1024, keys_per=4096, rounds=8):

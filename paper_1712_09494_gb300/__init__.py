@@ -63,10 +63,18 @@ def _dptr(t, what):
 
 
 def _key_width(keys):
+    """32 or 64 for a 1-D int32/int64 tensor; 128 for an (n, 2) int64 tensor
+    of (low word, high word) pairs."""
     es = keys.element_size()
+    if es == 8 and keys.dim() == 2 and keys.shape[1] == 2:
+        return 128
     if es not in (4, 8):
         raise ValueError("keys must be 32- or 64-bit integers")
     return es * 8
+
+
+def _nkeys(keys):
+    return keys.shape[0] if _key_width(keys) == 128 else keys.numel()
 
 
 def _params(params, scheme):
@@ -89,6 +97,9 @@ def ht_default_params(scheme):
 
 def ht_create(capacity, scheme, key_width, params=None, stream=None):
     scheme = scheme_of(scheme)
+    if int(key_width) == 128 and isinstance(params, dict):
+        # 16-byte slots: 8 per 128-byte bucket, 4 lanes unless given.
+        params = dict(dict(bucket_slots=8, lanes_per_key=4), **params)
     p = _params(params, scheme)
     out = ctypes.c_void_p()
     _check(load().ht_create(int(capacity), scheme, int(key_width),
@@ -102,23 +113,23 @@ def ht_destroy(table):
 
 
 def ht_find_or_put(table, keys, is_new=None, stream=None):
-    _check(load().ht_find_or_put(table, _dptr(keys, "keys"), keys.numel(), _dptr(is_new, "is_new"),
+    _check(load().ht_find_or_put(table, _dptr(keys, "keys"), _nkeys(keys), _dptr(is_new, "is_new"),
                                  _stream(stream)), "ht_find_or_put")
 
 
 def ht_find_or_put_append(table, keys, new_keys, new_count, is_new=None, stream=None):
-    _check(load().ht_find_or_put_append(table, _dptr(keys, "keys"), keys.numel(), _dptr(is_new, "is_new"),
+    _check(load().ht_find_or_put_append(table, _dptr(keys, "keys"), _nkeys(keys), _dptr(is_new, "is_new"),
                                         _dptr(new_keys, "new_keys"), _dptr(new_count, "new_count"),
                                         _stream(stream)), "ht_find_or_put_append")
 
 
 def ht_insert(table, keys, values=None, stream=None):
-    _check(load().ht_insert(table, _dptr(keys, "keys"), _dptr(values, "values"), keys.numel(),
+    _check(load().ht_insert(table, _dptr(keys, "keys"), _dptr(values, "values"), _nkeys(keys),
                             _stream(stream)), "ht_insert")
 
 
 def ht_lookup(table, keys, values=None, found=None, stream=None):
-    _check(load().ht_lookup(table, _dptr(keys, "keys"), keys.numel(), _dptr(values, "values"),
+    _check(load().ht_lookup(table, _dptr(keys, "keys"), _nkeys(keys), _dptr(values, "values"),
                             _dptr(found, "found"), _stream(stream)), "ht_lookup")
 
 
@@ -135,7 +146,7 @@ def ht_size(table, stream=None):
 def ht_export(table, keys_out, values_out=None, stream=None):
     n = ctypes.c_uint64()
     _check(load().ht_export(table, _dptr(keys_out, "keys_out"), _dptr(values_out, "values_out"),
-                            keys_out.numel(), ctypes.byref(n), _stream(stream)), "ht_export")
+                            _nkeys(keys_out), ctypes.byref(n), _stream(stream)), "ht_export")
     return n.value
 
 
@@ -443,7 +454,7 @@ class HashTable:
 
     def find_or_put(self, keys, stream=None):
         keys = self._keys(keys)
-        is_new = torch.empty(keys.numel(), dtype=torch.uint8, device=keys.device)
+        is_new = torch.empty(_nkeys(keys), dtype=torch.uint8, device=keys.device)
         ht_find_or_put(self._h, keys, is_new, stream)
         return is_new
 
@@ -453,7 +464,7 @@ class HashTable:
 
     def lookup(self, keys, stream=None):
         keys = self._keys(keys)
-        found = torch.empty(keys.numel(), dtype=torch.uint8, device=keys.device)
+        found = torch.empty(_nkeys(keys), dtype=torch.uint8, device=keys.device)
         values = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device) if self.key_width == 32 else None
         ht_lookup(self._h, keys, values, found, stream)
         return found, values
@@ -468,7 +479,8 @@ class HashTable:
         n = self.size(stream)
         dt = torch.int32 if self.key_width == 32 else torch.int64
         dev = torch.device("cuda", torch.cuda.current_device())
-        keys = torch.empty(max(n, 1), dtype=dt, device=dev)
+        shape = (max(n, 1), 2) if self.key_width == 128 else (max(n, 1),)
+        keys = torch.empty(shape, dtype=dt, device=dev)
         vals = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if self.key_width == 32 else None
         got = ht_export(self._h, keys, vals, stream)
         return keys[:got], (vals[:got] if vals is not None else None)

@@ -70,11 +70,19 @@ struct DeviceGuard {
 };
 
 ht_status clear_table(ht_table* t, cudaStream_t s) {
-    HT_TRY(fill_words(t->dt.slots, t->dt.nslots, kEmpty, s));
+    const uint64_t w = t->kw == 128 ? 2 : 1;     // words per slot
+    HT_TRY(fill_words(t->dt.slots, t->dt.nslots * w, kEmpty, s));
     HT_TRY(fill_words(t->dt.stash, t->dt.stash_slots, kEmpty, s));
-    HT_TRY(fill_words(t->dt.ovf, t->dt.ovf_slots, kEmpty, s));
+    HT_TRY(fill_words(t->dt.ovf, t->dt.ovf_slots * w, kEmpty, s));
     HT_TRY(cudaMemsetAsync(t->dt.ctr, 0, sizeof(DevCounters), s));
     return HT_OK;
+}
+
+// Every stored key (and value) to the caller's buffers, any key width.
+cudaError_t export_any(ht_table* t, void* keys, uint32_t* vals, unsigned long long* cnt, uint64_t cap,
+                       cudaStream_t s) {
+    if (t->kw == 128) return wide_export(t->dt, keys, cnt, cap, s);
+    return table_export(int(t->kw), t->dt, keys, vals, cnt, cap, s);
 }
 
 // Runs find-or-put / insert over a batch without touching rebuild state.
@@ -82,6 +90,10 @@ ht_status run_put(ht_table* t, const void* keys, const uint32_t* vals, uint64_t 
                   void* new_out, unsigned long long* new_count, cudaStream_t s,
                   const unsigned long long* d_n = nullptr, uint64_t new_cap = ~0ull) {
     if (n == 0) return HT_OK;
+    if (t->kw == 128) {
+        if (vals || new_out || d_n) return HT_ERR_INVALID;
+        return cuda_status(wide_find_or_put(int(t->p.lanes_per_key), t->dt, keys, n, is_new, s));
+    }
     if (t->scheme == HT_BUCKET) {
         return cuda_status(bucket_find_or_put(bucket_cfg(t), t->dt, keys, vals, n, d_n, is_new, new_out,
                                               new_count, new_cap, s, t->win));
@@ -130,7 +142,7 @@ ht_status rebuild(ht_table* t, cudaStream_t s) {
     st = HT_OK;
     do {
         if (cudaMemsetAsync(cnt, 0, sizeof(*cnt), s) != cudaSuccess ||
-            table_export(int(t->kw), t->dt, keys, vals, cnt, n, s) != cudaSuccess) {
+            export_any(t, keys, vals, cnt, n, s) != cudaSuccess) {
             st = HT_ERR_CUDA;
             break;
         }
@@ -280,10 +292,10 @@ ht_status grow_to(ht_table* t, uint64_t new_capacity, cudaStream_t s) {
     uint32_t* vals = nullptr;
     unsigned long long* cnt = nullptr;
     cudaError_t e = cudaMalloc(&keys, std::max<uint64_t>(n, 1) * (t->kw / 8));
-    if (e == cudaSuccess && t->kw == 32) e = cudaMalloc(&vals, std::max<uint64_t>(n, 1) * 4);
+    if (e == cudaSuccess && t->kw == 32) e = cudaMalloc(&vals, std::max<uint64_t>(n, 1) * 4);   // 32-bit maps
     if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(*cnt));
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(*cnt), s);
-    if (e == cudaSuccess) e = table_export(int(t->kw), t->dt, keys, vals, cnt, n, s);
+    if (e == cudaSuccess) e = export_any(t, keys, vals, cnt, n, s);
     unsigned long long got = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&got, cnt, sizeof(got), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -371,8 +383,17 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
     *out = nullptr;
     if (capacity == 0 || capacity > kMaxCapacity) return HT_ERR_INVALID;
     if (scheme != HT_BUCKET && scheme != HT_CUCKOO) return HT_ERR_INVALID;
-    if (key_width != 32 && key_width != 64) return HT_ERR_INVALID;
-    const ht_params p = complete_params(scheme, params);
+    if (key_width != 32 && key_width != 64 && !(key_width == 128 && scheme == HT_BUCKET)) return HT_ERR_INVALID;
+    ht_params p = complete_params(scheme, params);
+    if (key_width == 128) {
+        // 16-byte slots: buckets of 8 (one 128-byte line), 2 or 4 lanes, no stash.
+        if (!params) {
+            p.bucket_slots = 8;
+            p.lanes_per_key = 4;              // measured faster than 2 for 16-byte slots
+        }
+        if (p.bucket_slots != 8 || (p.lanes_per_key != 2 && p.lanes_per_key != 4)) return HT_ERR_INVALID;
+        p.stash_slots = 0;
+    }
     if (!valid_params(scheme, p)) return HT_ERR_INVALID;
 
     ht_table* t = new (std::nothrow) ht_table();
@@ -403,9 +424,10 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
         return cuda_status(e);
     };
     cudaError_t e;
-    if ((e = cudaMallocAsync(&t->dt.slots, t->dt.nslots * 8, cs)) != cudaSuccess) return fail(e);
+    const uint64_t slot_bytes = key_width == 128 ? 16 : 8;
+    if ((e = cudaMallocAsync(&t->dt.slots, t->dt.nslots * slot_bytes, cs)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocAsync(&t->dt.stash, std::max<uint32_t>(t->dt.stash_slots, 1) * 8, cs)) != cudaSuccess) return fail(e);
-    if ((e = cudaMallocAsync(&t->dt.ovf, uint64_t(t->dt.ovf_slots) * 8, cs)) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocAsync(&t->dt.ovf, uint64_t(t->dt.ovf_slots) * slot_bytes, cs)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocAsync(&t->dt.ctr, sizeof(DevCounters), cs)) != cudaSuccess) return fail(e);
     if (scheme == HT_CUCKOO) {
         // Keys per probe/insert launch pair: max_batch.  Unless the table
@@ -435,8 +457,8 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
         int dev = 0, max_persist = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
-        const size_t slot_bytes = t->dt.nslots * 8;
-        if (slot_bytes <= size_t(max_persist)) t->win = l2_window(t->dt.slots, slot_bytes);
+        const size_t table_bytes = t->dt.nslots * slot_bytes;
+        if (table_bytes <= size_t(max_persist)) t->win = l2_window(t->dt.slots, table_bytes);
         else if (scheme == HT_CUCKOO) t->win = l2_window(t->sc.set, (t->sc.mask + 1) * 8);
     }
     *out = t;
@@ -482,6 +504,10 @@ ht_status ht_lookup(ht_table* t, const void* d_keys, uint64_t n, uint32_t* d_val
     if (n == 0) return HT_OK;
     DeviceGuard g(t->device);
     const cudaStream_t s = as_stream(stream);
+    if (t->kw == 128) {
+        if (d_values) return HT_ERR_INVALID;
+        return cuda_status(wide_lookup(int(t->p.lanes_per_key), t->dt, d_keys, n, d_found, s));
+    }
     if (t->scheme == HT_BUCKET)
         return cuda_status(bucket_lookup(bucket_cfg(t), t->dt, d_keys, n, d_values, d_found, s, t->win));
     return cuda_status(cuckoo_lookup(int(t->kw), t->dt, d_keys, n, d_values, d_found, s, t->win));
@@ -491,7 +517,8 @@ ht_status ht_multi_find_or_put(ht_table* const* tables, uint32_t ntables, const 
                                void* stream) {
     if (m && (!tables || !list)) return HT_ERR_INVALID;
     for (uint32_t i = 0; i < m; ++i) {
-        if (list[i].table >= ntables || !tables[list[i].table]) return HT_ERR_INVALID;
+        if (list[i].table >= ntables || !tables[list[i].table] || tables[list[i].table]->kw == 128)
+            return HT_ERR_INVALID;
         if (list[i].n && !list[i].d_keys) return HT_ERR_INVALID;
     }
     if (!m) return HT_OK;
@@ -583,7 +610,7 @@ ht_status ht_export(ht_table* t, void* d_keys_out, uint32_t* d_values_out, uint6
     unsigned long long* cnt = nullptr;
     HT_TRY(cudaMalloc(&cnt, sizeof(*cnt)));
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(*cnt), s);
-    if (e == cudaSuccess) e = table_export(int(t->kw), t->dt, d_keys_out, d_values_out, cnt, cap, s);
+    if (e == cudaSuccess) e = export_any(t, d_keys_out, d_values_out, cnt, cap, s);
     unsigned long long got = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&got, cnt, sizeof(got), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -724,7 +751,7 @@ static ht_status bfs_common(ht_table* t, const ht_model* h_model, uint64_t s0, u
                             uint64_t* h_level_sizes, void* d_states, uint64_t states_cap, ht_bfs_result* result,
                             void* stream, bool fused) {
     if (!t || !result) return HT_ERR_INVALID;
-    if (fused && t->scheme != HT_BUCKET) return HT_ERR_INVALID;
+    if (t->kw == 128 || (fused && t->scheme != HT_BUCKET)) return HT_ERR_INVALID;
     const uint64_t msucc = model_max_successors(h_model, t->kw);
     if (!msucc) return HT_ERR_INVALID;
     if (t->kw == 32 ? s0 >= 0xFFFFFFFFull : (s0 >> 63) != 0) return HT_ERR_INVALID;

@@ -418,6 +418,14 @@ cudaError_t bfs_fused_level(const BucketCfg& c, const PreparedModel* model, cons
                             const DevTable& t, void* out, unsigned long long* count, uint64_t cap,
                             unsigned long long* gen, cudaStream_t s);
 
+// Bucket-scheme tables of 128-bit keys (ht_wide.cu): keys are 16-byte pairs
+// (low word, high word), 16-byte aligned; slots are 16 bytes, buckets 8 slots.
+cudaError_t wide_find_or_put(int lanes, const DevTable& t, const void* keys, uint64_t n, uint8_t* is_new,
+                             cudaStream_t s);
+cudaError_t wide_lookup(int lanes, const DevTable& t, const void* keys, uint64_t n, uint8_t* found,
+                        cudaStream_t s);
+cudaError_t wide_export(const DevTable& t, void* keys, unsigned long long* count, uint64_t cap, cudaStream_t s);
+
 // Read-only views of a table for the batched form (ht_api.cu).
 const DevTable& table_dev(const ht_table* t);
 BucketCfg table_bucket_cfg(const ht_table* t);

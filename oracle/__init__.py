@@ -68,6 +68,10 @@ def _load():
         lib.orc128_export.argtypes = [VP, VP, U64]
         lib.orc_successors.restype = U64
         lib.orc_successors.argtypes = [P(Model), U64, VP, U64]
+        lib.orc_successors128.restype = U64
+        lib.orc_successors128.argtypes = [P(Model), U64, U64, VP, U64]
+        lib.orc_bfs128.restype = ctypes.c_int
+        lib.orc_bfs128.argtypes = [P(Model), U64, U64, U64, U32, VP, VP, VP, U64, P(U32), P(U64)]
         lib.orc_bfs.restype = ctypes.c_int
         lib.orc_bfs.argtypes = [P(Model), U64, U64, U32, VP, VP, VP, U64, P(U32), P(U64)]
         _lib = lib
@@ -203,6 +207,22 @@ def successors(model, s):
     return out[:n]
 
 
+def successors128(model, s):
+    """Successors of a state wider than 64 bits (a Python int): (n, 2)
+    uint64 array of (low word, high word)."""
+    lib = _load()
+    cm = to_ctypes_model(model)
+    s = int(s)
+    lo, hi = s & (2 ** 64 - 1), s >> 64
+    cap = 256
+    out = np.empty((cap, 2), dtype=np.uint64)
+    n = lib.orc_successors128(ctypes.byref(cm), lo, hi, _ptr(out), cap)
+    if n > cap:
+        out = np.empty((int(n), 2), dtype=np.uint64)
+        n = lib.orc_successors128(ctypes.byref(cm), lo, hi, _ptr(out), int(n))
+    return out[:n]
+
+
 class BfsResult:
     def __init__(self, rc, level_sizes, level_succ, states, total):
         self.rc = rc
@@ -216,18 +236,25 @@ class BfsResult:
         return self.states[off:off + int(self.level_sizes[d])]
 
 
-def bfs(model, max_states=1 << 24, max_levels=4096, keep_states=True, s0=0):
-    """BFS over the model's reachable states (Section 3.2's open/closed sets)."""
+def bfs(model, max_states=1 << 24, max_levels=4096, keep_states=True, s0=0, wide=False):
+    """BFS over the model's reachable states (Section 3.2's open/closed sets).
+    wide=True: states as 128-bit vectors, (n, 2) uint64 arrays of (low
+    word, high word) -- for models wider than 64 bits."""
     lib = _load()
     cm = to_ctypes_model(model)
     sizes = np.zeros(max_levels, dtype=np.uint64)
     succ = np.zeros(max_levels, dtype=np.uint64)
     cap = int(max_states) + 1 if keep_states else 0
-    states = np.empty(cap, dtype=np.uint64) if keep_states else None
+    states = (np.empty((cap, 2) if wide else cap, dtype=np.uint64)) if keep_states else None
     nlev = ctypes.c_uint32(0)
     total = ctypes.c_uint64(0)
-    rc = lib.orc_bfs(ctypes.byref(cm), int(s0), int(max_states), int(max_levels), _ptr(sizes),
-                     _ptr(succ), _ptr(states), cap, ctypes.byref(nlev), ctypes.byref(total))
+    if wide:
+        rc = lib.orc_bfs128(ctypes.byref(cm), int(s0) & (2 ** 64 - 1), int(s0) >> 64, int(max_states),
+                            int(max_levels), _ptr(sizes), _ptr(succ), _ptr(states), cap, ctypes.byref(nlev),
+                            ctypes.byref(total))
+    else:
+        rc = lib.orc_bfs(ctypes.byref(cm), int(s0), int(max_states), int(max_levels), _ptr(sizes),
+                         _ptr(succ), _ptr(states), cap, ctypes.byref(nlev), ctypes.byref(total))
     n = nlev.value
     st = states[:min(int(total.value), cap)] if keep_states else None
     return BfsResult(rc, sizes[:n].astype(np.int64), succ[:n].astype(np.int64), st, int(total.value))

@@ -25,6 +25,7 @@
 // Nothing here models hash functions, buckets, slots or eviction: those are
 // not observable in the results, so parity is checked on sets, flags and
 // values only.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <unordered_map>
@@ -163,31 +164,37 @@ uint64_t orc128_export(const void* h, uint64_t* keys, uint64_t cap) {
 
 namespace {
 
+// Component c's local state is bits [off[c], off[c] + bits[c]) of the state
+// vector; S is the vector's type (64 bits, or 128 for wider models).
+template <class S>
 struct Layout {
     int off[16];
-    uint64_t mask[16];
+    S mask[16];
 };
 
-Layout layout_of(const orc_model* m) {
-    Layout l{};
+template <class S>
+Layout<S> layout_of(const orc_model* m) {
+    Layout<S> l{};
     int o = 0;
     for (int c = 0; c < m->C; ++c) {
         l.off[c] = o;
-        l.mask[c] = (uint64_t(1) << m->bits[c]) - 1;
+        l.mask[c] = (S(1) << m->bits[c]) - 1;
         o += m->bits[c];
     }
     return l;
 }
 
-inline uint64_t local_of(const Layout& l, uint64_t s, int c) { return (s >> l.off[c]) & l.mask[c]; }
+template <class S>
+inline uint64_t local_of(const Layout<S>& l, S s, int c) { return uint64_t((s >> l.off[c]) & l.mask[c]); }
 
-inline uint64_t with_local(const Layout& l, uint64_t s, int c, uint64_t v) {
-    return (s & ~(l.mask[c] << l.off[c])) | (v << l.off[c]);
+template <class S>
+inline S with_local(const Layout<S>& l, S s, int c, uint64_t v) {
+    return (s & ~(l.mask[c] << l.off[c])) | (S(v) << l.off[c]);
 }
 
 // Successors of s, in a fixed order (components' local actions, then pairs).
-template <class Emit>
-void successors(const orc_model* m, const Layout& l, uint64_t s, Emit emit) {
+template <class S, class Emit>
+void successors(const orc_model* m, const Layout<S>& l, S s, Emit emit) {
     for (int c = 0; c < m->C; ++c) {
         uint64_t u = local_of(l, s, c);
         for (int j = 0; j < m->deg[c][u]; ++j)
@@ -200,11 +207,59 @@ void successors(const orc_model* m, const Layout& l, uint64_t s, Emit emit) {
             if (m->lab[c1][u1][j1] != p + 1) continue;
             for (int j2 = 0; j2 < m->deg[c2][u2]; ++j2) {
                 if (m->lab[c2][u2][j2] != p + 1) continue;
-                uint64_t t = with_local(l, s, c1, m->tgt[c1][u1][j1]);
+                S t = with_local(l, s, c1, m->tgt[c1][u1][j1]);
                 emit(with_local(l, t, c2, m->tgt[c2][u2][j2]));
             }
         }
     }
+}
+
+using u128 = unsigned __int128;
+
+struct StateHash {
+    size_t operator()(uint64_t s) const { return std::hash<uint64_t>()(s); }
+    size_t operator()(u128 s) const {
+        return std::hash<uint64_t>()(uint64_t(s)) ^ (std::hash<uint64_t>()(uint64_t(s >> 64)) * 0x9E3779B97F4A7C15ull);
+    }
+};
+
+// Level-synchronous BFS from s0 (see orc_bfs).
+template <class S>
+int bfs(const orc_model* m, S s0, uint64_t max_states, uint32_t max_levels, uint64_t* level_sizes,
+        uint64_t* level_succ, S* states_out, uint64_t states_cap, uint32_t* nlevels, uint64_t* total) {
+    const Layout<S> l = layout_of<S>(m);
+    std::unordered_map<S, uint32_t, StateHash> seen;  // closed + open sets
+    seen.reserve(max_states < (uint64_t(1) << 28) ? max_states + 1 : (uint64_t(1) << 28));
+    std::vector<S> cur{s0}, nxt;
+    seen.emplace(s0, 0u);
+    uint64_t stored = 0;
+    auto keep = [&](S s) {
+        if (states_out && stored < states_cap) states_out[stored] = s;
+        ++stored;
+    };
+    keep(s0);
+    uint32_t d = 0;
+    int rc = 0;
+    while (!cur.empty()) {
+        if (d >= max_levels) { rc = 2; break; }
+        level_sizes[d] = cur.size();
+        uint64_t gen = 0;
+        nxt.clear();
+        for (S s : cur) {
+            successors(m, l, s, [&](S t) {
+                ++gen;
+                if (seen.emplace(t, d + 1).second) nxt.push_back(t);
+            });
+        }
+        if (level_succ) level_succ[d] = gen;
+        ++d;
+        for (S t : nxt) keep(t);
+        if (seen.size() > max_states) { rc = 1; break; }
+        cur.swap(nxt);
+    }
+    *nlevels = d;
+    *total = stored;
+    return rc;
 }
 
 }  // namespace
@@ -213,7 +268,7 @@ extern "C" {
 
 // All successors of one state; returns how many there are (writes at most cap).
 uint64_t orc_successors(const orc_model* m, uint64_t s, uint64_t* out, uint64_t cap) {
-    Layout l = layout_of(m);
+    const Layout<uint64_t> l = layout_of<uint64_t>(m);
     uint64_t n = 0;
     successors(m, l, s, [&](uint64_t t) {
         if (n < cap) out[n] = t;
@@ -230,38 +285,37 @@ uint64_t orc_successors(const orc_model* m, uint64_t s, uint64_t* out, uint64_t 
 int orc_bfs(const orc_model* m, uint64_t s0, uint64_t max_states, uint32_t max_levels,
             uint64_t* level_sizes, uint64_t* level_succ, uint64_t* states_out,
             uint64_t states_cap, uint32_t* nlevels, uint64_t* total) {
-    Layout l = layout_of(m);
-    std::unordered_map<uint64_t, uint32_t> seen;  // closed + open sets
-    seen.reserve(max_states < (uint64_t(1) << 28) ? max_states + 1 : (uint64_t(1) << 28));
-    std::vector<uint64_t> cur{s0}, nxt;
-    seen.emplace(s0, 0u);
-    uint64_t stored = 0;
-    auto keep = [&](uint64_t s) {
-        if (states_out && stored < states_cap) states_out[stored] = s;
-        ++stored;
-    };
-    keep(s0);
-    uint32_t d = 0;
-    int rc = 0;
-    while (!cur.empty()) {
-        if (d >= max_levels) { rc = 2; break; }
-        level_sizes[d] = cur.size();
-        uint64_t gen = 0;
-        nxt.clear();
-        for (uint64_t s : cur) {
-            successors(m, l, s, [&](uint64_t t) {
-                ++gen;
-                if (seen.emplace(t, d + 1).second) nxt.push_back(t);
-            });
+    return bfs<uint64_t>(m, s0, max_states, max_levels, level_sizes, level_succ, states_out, states_cap, nlevels,
+                         total);
+}
+
+// The same for models whose state vectors are wider than 64 bits (up to 127):
+// a state is two words, low word first (s0, out and states_out likewise).
+uint64_t orc_successors128(const orc_model* m, uint64_t s_lo, uint64_t s_hi, uint64_t* out, uint64_t cap) {
+    const Layout<u128> l = layout_of<u128>(m);
+    const u128 s = (u128(s_hi) << 64) | s_lo;
+    uint64_t n = 0;
+    successors(m, l, s, [&](u128 t) {
+        if (n < cap) {
+            out[2 * n] = uint64_t(t);
+            out[2 * n + 1] = uint64_t(t >> 64);
         }
-        if (level_succ) level_succ[d] = gen;
-        ++d;
-        for (uint64_t t : nxt) keep(t);
-        if (seen.size() > max_states) { rc = 1; break; }
-        cur.swap(nxt);
-    }
-    *nlevels = d;
-    *total = seen.size();
+        ++n;
+    });
+    return n;
+}
+
+int orc_bfs128(const orc_model* m, uint64_t s0_lo, uint64_t s0_hi, uint64_t max_states, uint32_t max_levels,
+               uint64_t* level_sizes, uint64_t* level_succ, uint64_t* states_out, uint64_t states_cap,
+               uint32_t* nlevels, uint64_t* total) {
+    std::vector<u128> st(states_out ? states_cap : 0);
+    const int rc = bfs<u128>(m, (u128(s0_hi) << 64) | s0_lo, max_states, max_levels, level_sizes, level_succ,
+                             states_out ? st.data() : nullptr, states_cap, nlevels, total);
+    if (states_out)
+        for (uint64_t i = 0; i < std::min<uint64_t>(*total, states_cap); ++i) {
+            states_out[2 * i] = uint64_t(st[i]);
+            states_out[2 * i + 1] = uint64_t(st[i] >> 64);
+        }
     return rc;
 }
 

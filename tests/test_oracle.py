@@ -256,3 +256,51 @@ def test_oracle128_find_or_put_lookup_export_against_brute_force(oracle_lib):
     q = np.array([[0, 0], [5, 5 << 40], [6, 0], [0, 6 << 40], [1, 1]], dtype=np.uint64)
     np.testing.assert_array_equal(t.lookup(q), [1, 1, 0, 0, 0])
     assert set(map(tuple, t.export().tolist())) == seen
+
+
+def _component_hist(m, c):
+    a = sp.lil_matrix((int(m.L[c]), int(m.L[c])))
+    for u in range(int(m.L[c])):
+        for j in range(int(m.deg[c, u])):
+            a[u, int(m.tgt[c, u, j])] = 1
+    d = shortest_path(a.tocsr(), unweighted=True, indices=0)
+    return np.bincount(d[np.isfinite(d)].astype(np.int64))
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_wide_bfs_closed_form_without_sync(oracle_lib, seed):
+    # 16 components x 5 bits = 80-bit vectors (component 12 straddles the two
+    # words): reachable = product of windows, levels = convolution of the
+    # per-component distance histograms, and every stored state decodes to
+    # local states inside each component's window.
+    R = [2, 3, 2, 2, 3, 2, 2, 2, 2, 2, 2, 2, 3, 2, 2, 2]
+    m = ss.random_model(seed, C=16, L=32, R=R, p_sync=0.0, P=0)
+    assert m.total_bits == 80 and m.key_width == 128
+    res = oracle_lib.bfs(m, max_states=1 << 20, wide=True)
+    assert res.rc == 0 and res.total == int(np.prod(R))
+    poly = np.array([1], dtype=np.int64)
+    for c in range(m.C):
+        poly = np.convolve(poly, _component_hist(m, c))
+    np.testing.assert_array_equal(res.level_sizes, poly)
+    full = res.states[:, 0].astype(object) | (res.states[:, 1].astype(object) << 64)
+    assert len(set(full.tolist())) == res.total
+    off = 0
+    for c in range(m.C):
+        loc = np.array([(v >> off) & 31 for v in full.tolist()])
+        assert loc.max() < R[c] and len(np.unique(loc)) == R[c]
+        off += 5
+
+
+def test_wide_successors_and_bfs_agree_with_the_64_bit_path(oracle_lib):
+    # A model that fits 64 bits gives the same successors and levels either way.
+    m = ss.random_model(7, C=6, L=[8, 4, 8, 16, 4, 8], R=[5, 4, 6, 7, 3, 5], p_sync=0.4, P=3)
+    for s in [0, 3, 100, 4000]:
+        a = np.sort(oracle_lib.successors(m, s))
+        w = oracle_lib.successors128(m, s)
+        assert (w[:, 1] == 0).all()
+        np.testing.assert_array_equal(np.sort(w[:, 0]), a)
+    r64 = oracle_lib.bfs(m, max_states=1 << 20)
+    r128 = oracle_lib.bfs(m, max_states=1 << 20, wide=True)
+    np.testing.assert_array_equal(r64.level_sizes, r128.level_sizes)
+    np.testing.assert_array_equal(r64.level_succ, r128.level_succ)
+    assert set(r64.states.tolist()) == set(r128.states[:, 0].tolist())

@@ -67,7 +67,8 @@ class Model:
 
     @property
     def key_width(self):
-        return 32 if self.total_bits <= 31 else 64
+        b = self.total_bits
+        return 32 if b <= 31 else (64 if b <= 63 else 128)
 
     def pair_arrays(self):
         c1 = np.zeros(PMAX, dtype=np.uint8)
@@ -128,8 +129,8 @@ def random_model(seed, C, L, R, p_sync=0.0, P=0, deg_lo=1, deg_hi=3):
                     r = rng.random()
                     if mine and r < p_sync:
                         lab[c, u, j] = mine[0] + 1
-    if bits.sum() > 63:
-        raise ValueError("state vector exceeds 63 bits")
+    if bits.sum() > 127:
+        raise ValueError("state vector exceeds 127 bits")
     return Model(C=C, L=L, bits=bits, deg=deg, tgt=tgt, lab=lab, pairs=pairs,
                  meta=dict(seed=seed, R=R.tolist(), p_sync=p_sync, P=P))
 

@@ -114,9 +114,10 @@ ht_status ht_default_params(ht_scheme scheme, ht_params* p);
  * for state vectors wider than 64 bits, in 16-byte slots claimed with one
  * 16-byte compare-and-swap, buckets of 8 slots (bucket_slots must be 8,
  * lanes_per_key 2 or 4; with params NULL: 8 and 4), no stash, no values;
- * such tables support
- * find-or-put, insert without values, lookup without values, export, size,
- * clear, grow and stats (not ht_bfs, the batched forms or Cuckoo).
+ * such tables support find-or-put (with append), insert without values,
+ * lookup without values, export, size, clear, grow, stats, ht_successors
+ * and ht_bfs over models up to 127 bits wide (not ht_bfs_fused, the batched
+ * forms or Cuckoo).
  * Errors: HT_ERR_INVALID (capacity 0 or > 2^40, key_width not 32/64/128,
  * bad params), HT_ERR_OOM, HT_ERR_CUDA.  *out is NULL on error. */
 ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width,
@@ -275,6 +276,9 @@ typedef struct ht_bfs_result {
  * h_level_sizes (nullable, max_levels entries) receives the level sizes.
  * Stops when a level is empty (complete = 1), or when max_levels or
  * states_cap would be exceeded (complete = 0).  Synchronises once per level.
+ * With a 128-bit table (models wider than 63 bits) states are 16-byte
+ * pairs (low word first) and s0 is the initial state's low word (its high
+ * word is 0).
  * Allocates its work buffers with cudaMalloc and frees them before
  * returning. */
 ht_status ht_bfs(ht_table* t, const ht_model* h_model, uint64_t s0, uint32_t max_levels,

@@ -276,8 +276,8 @@ def make_model(num_components, bits, deg, tgt, lab, pairs):
 
 
 def ht_successors(model, states, succ, count, stream=None):
-    _check(load().ht_successors(ctypes.byref(model), _key_width(states), _dptr(states, "states"), states.numel(),
-                                _dptr(succ, "succ"), succ.numel(), _dptr(count, "count"), _stream(stream)),
+    _check(load().ht_successors(ctypes.byref(model), _key_width(states), _dptr(states, "states"), _nkeys(states),
+                                _dptr(succ, "succ"), _nkeys(succ), _dptr(count, "count"), _stream(stream)),
            "ht_successors")
 
 
@@ -287,7 +287,7 @@ def ht_bfs(table, model, s0=0, max_levels=4096, states=None, states_cap=0, strea
     ht_bfs_fused (bucket-scheme tables)."""
     sizes = (ctypes.c_uint64 * max_levels)()
     res = HtBfsResult()
-    cap = states.numel() if states is not None else int(states_cap)
+    cap = _nkeys(states) if states is not None else int(states_cap)
     name = "ht_bfs_fused" if fused else "ht_bfs"
     _check(getattr(load(), name)(table, ctypes.byref(model), int(s0), int(max_levels), sizes,
                                  _dptr(states, "states"), cap, ctypes.byref(res), _stream(stream)), name)

@@ -91,8 +91,9 @@ ht_status run_put(ht_table* t, const void* keys, const uint32_t* vals, uint64_t 
                   const unsigned long long* d_n = nullptr, uint64_t new_cap = ~0ull) {
     if (n == 0) return HT_OK;
     if (t->kw == 128) {
-        if (vals || new_out || d_n) return HT_ERR_INVALID;
-        return cuda_status(wide_find_or_put(int(t->p.lanes_per_key), t->dt, keys, n, is_new, s));
+        if (vals) return HT_ERR_INVALID;
+        return cuda_status(wide_find_or_put(int(t->p.lanes_per_key), t->dt, keys, n, d_n, is_new, new_out, new_count,
+                                            new_cap, s));
     }
     if (t->scheme == HT_BUCKET) {
         return cuda_status(bucket_find_or_put(bucket_cfg(t), t->dt, keys, vals, n, d_n, is_new, new_out,
@@ -677,7 +678,7 @@ uint64_t ht::model_max_successors(const ht_model* m, uint32_t key_width) {
         if (m->bits[c] < 1 || m->bits[c] > 5) return 0;
         bits += m->bits[c];
     }
-    if (bits > (key_width == 32 ? 31u : 63u)) return 0;
+    if (bits > (key_width == 32 ? 31u : key_width == 64 ? 63u : 127u)) return 0;
     for (int p = 0; p < m->num_pairs; ++p)
         if (m->pair_c1[p] >= m->num_components || m->pair_c2[p] >= m->num_components ||
             m->pair_c1[p] == m->pair_c2[p])
@@ -733,7 +734,8 @@ extern "C" {
 
 ht_status ht_successors(const ht_model* h_model, uint32_t key_width, const void* d_states, uint64_t n,
                         void* d_succ, uint64_t cap, unsigned long long* d_count, void* stream) {
-    if ((key_width != 32 && key_width != 64) || !d_count || (n && (!d_states || !d_succ))) return HT_ERR_INVALID;
+    if ((key_width != 32 && key_width != 64 && key_width != 128) || !d_count || (n && (!d_states || !d_succ)))
+        return HT_ERR_INVALID;
     if (!model_max_successors(h_model, key_width)) return HT_ERR_INVALID;
     if (n == 0) return HT_OK;
     const cudaStream_t s = as_stream(stream);
@@ -751,7 +753,7 @@ static ht_status bfs_common(ht_table* t, const ht_model* h_model, uint64_t s0, u
                             uint64_t* h_level_sizes, void* d_states, uint64_t states_cap, ht_bfs_result* result,
                             void* stream, bool fused) {
     if (!t || !result) return HT_ERR_INVALID;
-    if (t->kw == 128 || (fused && t->scheme != HT_BUCKET)) return HT_ERR_INVALID;
+    if (fused && (t->scheme != HT_BUCKET || t->kw == 128)) return HT_ERR_INVALID;
     const uint64_t msucc = model_max_successors(h_model, t->kw);
     if (!msucc) return HT_ERR_INVALID;
     if (t->kw == 32 ? s0 >= 0xFFFFFFFFull : (s0 >> 63) != 0) return HT_ERR_INVALID;
@@ -779,14 +781,15 @@ static ht_status bfs_common(ht_table* t, const ht_model* h_model, uint64_t s0, u
     }
     HT_TRY(cudaMalloc(&succ.p, succ_cap * ksz));
     // ctr[0]: states stored so far; ctr[1]: successors of the current chunk;
-    // ctr[2]: successors generated in total; ctr[3]: the initial state.
-    HT_TRY(cudaMalloc(&ctr.p, 4 * sizeof(unsigned long long)));
+    // ctr[2]: successors generated in total; ctr[4..5]: the initial state
+    // (16-byte aligned; for 128-bit tables s0 is its low word, the high word 0).
+    HT_TRY(cudaMalloc(&ctr.p, 6 * sizeof(unsigned long long)));
     unsigned long long* c = static_cast<unsigned long long*>(ctr.p);
-    unsigned long long init[4] = {0, 0, 0, s0};
+    unsigned long long init[6] = {0, 0, 0, 0, s0, 0};
     HT_TRY(cudaMemcpyAsync(c, init, sizeof(init), cudaMemcpyHostToDevice, s));
     // Level 0: the initial state (the open set starts with it).
-    ht_status st = run_put(t, t->kw == 32 ? static_cast<const void*>(reinterpret_cast<const uint32_t*>(c + 3))
-                                          : static_cast<const void*>(c + 3),
+    ht_status st = run_put(t, t->kw == 32 ? static_cast<const void*>(reinterpret_cast<const uint32_t*>(c + 4))
+                                          : static_cast<const void*>(c + 4),
                            nullptr, 1, nullptr, d_states, c, s, nullptr, states_cap);
     if (st != HT_OK) return st;
     char* states = static_cast<char*>(d_states);

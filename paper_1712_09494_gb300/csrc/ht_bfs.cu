@@ -3,6 +3,7 @@
 // transitions of the processes).  The model's transition tables live in
 // shared memory, read-only, as the paper keeps them in texture memory.
 #include <cstring>
+#include <type_traits>
 
 #include "ht_internal.cuh"
 
@@ -25,8 +26,11 @@ successors_kernel(const PreparedModel* __restrict__ model, const T* __restrict__
                   const unsigned long long* __restrict__ d_n, uint64_t off, T* __restrict__ succ,
                   uint64_t cap, unsigned long long* __restrict__ count,
                   unsigned long long* __restrict__ total) {
+    // 16-byte states (models wider than 63 bits) use a half-size stage.
+    constexpr int kStage = sizeof(T) > 8 ? kSuccStage / 2 : kSuccStage;
+    using S = typename std::conditional<(sizeof(T) > 8), unsigned __int128, uint64_t>::type;
     __shared__ PreparedModel sm;
-    __shared__ T s_out[kSuccBlock / 32][kSuccStage];
+    __shared__ T s_out[kSuccBlock / 32][kStage];
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(model);
         uint32_t* dst = reinterpret_cast<uint32_t*>(&sm);
@@ -45,7 +49,7 @@ successors_kernel(const PreparedModel* __restrict__ model, const T* __restrict__
     for (uint64_t r = 0; r < rounds; ++r) {
         const uint64_t i = r * stride + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
         const bool act = i < n;
-        const uint64_t s = act ? uint64_t(states[i]) : 0;
+        const S s = act ? S(states[i]) : S(0);
         uint32_t cnt = 0;
         if (act) cnt = count_successors(sm, s);
         // Warp-wide exclusive scan of the counts, one reservation per warp.
@@ -60,16 +64,16 @@ successors_kernel(const PreparedModel* __restrict__ model, const T* __restrict__
         if (lane == 0 && tot) base = atomicAdd(count, (unsigned long long)tot);
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         const uint32_t excl = incl - cnt;
-        for (uint32_t chunk = 0; chunk < tot; chunk += kSuccStage) {
-            if (act && excl < chunk + kSuccStage && incl > chunk) {
+        for (uint32_t chunk = 0; chunk < tot; chunk += kStage) {
+            if (act && excl < chunk + kStage && incl > chunk) {
                 uint32_t k = excl;
-                for_each_successor(sm, s, [&](uint64_t v) {
-                    if (k >= chunk && k < chunk + kSuccStage) buf[k - chunk] = T(v);
+                for_each_successor(sm, s, [&](S v) {
+                    if (k >= chunk && k < chunk + kStage) buf[k - chunk] = T(v);
                     ++k;
                 });
             }
             __syncwarp();
-            const uint32_t m = min(uint32_t(kSuccStage), tot - chunk);
+            const uint32_t m = min(uint32_t(kStage), tot - chunk);
             for (uint32_t j = lane; j < m; j += 32)
                 if (base + chunk + j < cap) succ[base + chunk + j] = buf[j];
             __syncwarp();
@@ -193,6 +197,11 @@ cudaError_t successors(int kw, const PreparedModel* model, const void* states, u
         auto k = successors_kernel<uint32_t>;
         k<<<launch_blocks((const void*)k, kSuccBlock), kSuccBlock, 0, s>>>(
             model, static_cast<const uint32_t*>(states), n, d_n, off, static_cast<uint32_t*>(succ), cap, count, total);
+    } else if (kw == 128) {
+        using U = unsigned __int128;
+        auto k = successors_kernel<U>;
+        k<<<launch_blocks((const void*)k, kSuccBlock), kSuccBlock, 0, s>>>(
+            model, static_cast<const U*>(states), n, d_n, off, static_cast<U*>(succ), cap, count, total);
     } else {
         auto k = successors_kernel<uint64_t>;
         k<<<launch_blocks((const void*)k, kSuccBlock), kSuccBlock, 0, s>>>(

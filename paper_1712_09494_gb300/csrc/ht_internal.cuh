@@ -370,19 +370,23 @@ PreparedModel prepare_model(const ht_model& m);
 
 // Successor enumeration over a prepared model (state vectors of up to 64
 // bits; component c's local state is bits [off[c], off[c] + bits[c])).
-__device__ __forceinline__ uint32_t local_of(const PreparedModel& m, uint64_t s, int c) {
+// S is the state vector's type: uint64_t, or unsigned __int128 for models
+// wider than 63 bits.
+template <class S>
+__device__ __forceinline__ uint32_t local_of(const PreparedModel& m, S s, int c) {
     return uint32_t(s >> m.off[c]) & ((1u << m.bits[c]) - 1u);
 }
 
-__device__ __forceinline__ uint64_t with_local(const PreparedModel& m, uint64_t s, int c, uint32_t v) {
-    const uint64_t mask = ((1ull << m.bits[c]) - 1ull) << m.off[c];
-    return (s & ~mask) | (uint64_t(v) << m.off[c]);
+template <class S>
+__device__ __forceinline__ S with_local(const PreparedModel& m, S s, int c, uint32_t v) {
+    const S mask = ((S(1) << m.bits[c]) - S(1)) << m.off[c];
+    return (s & ~mask) | (S(v) << m.off[c]);
 }
 
 // Visits every successor of s: local actions of each component, then every
 // combination of the two members' transitions of each synchronising pair.
-template <class F>
-__device__ __forceinline__ void for_each_successor(const PreparedModel& m, uint64_t s, F&& emit) {
+template <class S, class F>
+__device__ __forceinline__ void for_each_successor(const PreparedModel& m, S s, F&& emit) {
     for (int c = 0; c < m.C; ++c) {
         const uint32_t u = local_of(m, s, c);
         const int d = m.nloc[c][u];
@@ -393,14 +397,15 @@ __device__ __forceinline__ void for_each_successor(const PreparedModel& m, uint6
         const uint32_t u1 = local_of(m, s, c1), u2 = local_of(m, s, c2);
         const int d1 = m.nsyn[p][0][u1], d2 = m.nsyn[p][1][u2];
         for (int j1 = 0; j1 < d1; ++j1) {
-            const uint64_t s1 = with_local(m, s, c1, m.syn[p][0][u1][j1]);
+            const S s1 = with_local(m, s, c1, m.syn[p][0][u1][j1]);
             for (int j2 = 0; j2 < d2; ++j2) emit(with_local(m, s1, c2, m.syn[p][1][u2][j2]));
         }
     }
 }
 
 // The number of successors of s (what for_each_successor visits).
-__device__ __forceinline__ uint32_t count_successors(const PreparedModel& m, uint64_t s) {
+template <class S>
+__device__ __forceinline__ uint32_t count_successors(const PreparedModel& m, S s) {
     uint32_t n = 0;
     for (int c = 0; c < m.C; ++c) n += m.nloc[c][local_of(m, s, c)];
     for (int p = 0; p < m.P; ++p)
@@ -420,8 +425,9 @@ cudaError_t bfs_fused_level(const BucketCfg& c, const PreparedModel* model, cons
 
 // Bucket-scheme tables of 128-bit keys (ht_wide.cu): keys are 16-byte pairs
 // (low word, high word), 16-byte aligned; slots are 16 bytes, buckets 8 slots.
-cudaError_t wide_find_or_put(int lanes, const DevTable& t, const void* keys, uint64_t n, uint8_t* is_new,
-                             cudaStream_t s);
+cudaError_t wide_find_or_put(int lanes, const DevTable& t, const void* keys, uint64_t n,
+                             const unsigned long long* d_n, uint8_t* is_new, void* new_out,
+                             unsigned long long* new_count, uint64_t new_cap, cudaStream_t s);
 cudaError_t wide_lookup(int lanes, const DevTable& t, const void* keys, uint64_t n, uint8_t* found,
                         cudaStream_t s);
 cudaError_t wide_export(const DevTable& t, void* keys, unsigned long long* count, uint64_t cap, cudaStream_t s);

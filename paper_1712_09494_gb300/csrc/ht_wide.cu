@@ -89,16 +89,24 @@ __device__ bool wide_ovf_find(const DevTable& t, uint64_t lo, uint64_t hi) {
 // find-or-put: a warp takes 32 keys (lane l loads key l); in round q group
 // g (G lanes) serves key q*(32/G)+g through buckets h_1, h_2, ... until the
 // key is found, claimed, or (all k buckets full) placed in the overflow set.
-template <int G, bool LOOKUP>
+// APPEND: the keys new to the table also go to new_out at *new_count
+// (staged per warp in shared memory; entries past new_cap not written).
+// d_n (nullable): the batch size produced on the device, at most n.
+template <int G, bool LOOKUP, bool APPEND>
 __global__ void __launch_bounds__(kBlock)
-wide_kernel(const DevTable t, const ulonglong2* __restrict__ keys, uint64_t n, uint8_t* __restrict__ out) {
+wide_kernel(const DevTable t, const ulonglong2* __restrict__ keys, uint64_t n,
+            const unsigned long long* __restrict__ d_n, uint8_t* __restrict__ out,
+            ulonglong2* __restrict__ new_out, unsigned long long* __restrict__ new_count, uint64_t new_cap) {
     constexpr int SPL = kWideBS / G;
     constexpr int GPW = 32 / G;
     constexpr uint32_t kGMask = (1u << G) - 1u;
+    if (d_n) n = min(n, uint64_t(__ldcg(d_n)));
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane % G, gbase = grp * G;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
     unsigned long long stored = 0;
+    __shared__ ulonglong2 s_new[APPEND ? kBlock / 32 : 1][APPEND ? kStageCap : 1];
+    WarpStage<ulonglong2, kStageCap> stage(s_new[APPEND ? (threadIdx.x >> 5) : 0]);
     for (uint64_t base = ((uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32; base < n;
          base += nwarps * 32) {
         const bool mine = base + lane < n;
@@ -197,8 +205,10 @@ wide_kernel(const DevTable t, const ulonglong2* __restrict__ keys, uint64_t n, u
         }
         const uint32_t my = (__shfl_sync(kFull, res_all, (lane % GPW) * G) >> (lane / GPW)) & 1u;
         if (mine && out) out[base + lane] = uint8_t(my);
+        if (APPEND) stage.push(mine && my, mk, new_out, new_count, new_cap);
         if (!LOOKUP) stored += __popc(__ballot_sync(kFull, my != 0));
     }
+    if (APPEND) stage.flush(new_out, new_count, new_cap);
     if (!LOOKUP && lane == 0 && stored) atomicAdd(&t.ctr->size, stored);
 }
 
@@ -229,21 +239,29 @@ wide_export_kernel(const DevTable t, uint64_t* __restrict__ out, unsigned long l
     }
 }
 
-template <int G, bool LOOKUP>
-cudaError_t launch_wide(const DevTable& t, const void* keys, uint64_t n, uint8_t* out, cudaStream_t s) {
-    auto k = wide_kernel<G, LOOKUP>;
-    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, static_cast<const ulonglong2*>(keys), n, out);
+template <int G, bool LOOKUP, bool APPEND>
+cudaError_t launch_wide(const DevTable& t, const void* keys, uint64_t n, const unsigned long long* d_n,
+                        uint8_t* out, void* new_out, unsigned long long* new_count, uint64_t new_cap,
+                        cudaStream_t s) {
+    auto k = wide_kernel<G, LOOKUP, APPEND>;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, static_cast<const ulonglong2*>(keys), n, d_n, out,
+                                                              static_cast<ulonglong2*>(new_out), new_count, new_cap);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t wide_find_or_put(int lanes, const DevTable& t, const void* keys, uint64_t n, uint8_t* is_new,
-                             cudaStream_t s) {
+cudaError_t wide_find_or_put(int lanes, const DevTable& t, const void* keys, uint64_t n,
+                             const unsigned long long* d_n, uint8_t* is_new, void* new_out,
+                             unsigned long long* new_count, uint64_t new_cap, cudaStream_t s) {
     if (!n) return cudaSuccess;
     ProfScope ps(kKBucketFop, s);
-    if (lanes == 2) return launch_wide<2, false>(t, keys, n, is_new, s);
-    if (lanes == 4) return launch_wide<4, false>(t, keys, n, is_new, s);
+#define L(G)                                                                                                 \
+    return new_out ? launch_wide<G, false, true>(t, keys, n, d_n, is_new, new_out, new_count, new_cap, s)     \
+                   : launch_wide<G, false, false>(t, keys, n, d_n, is_new, nullptr, nullptr, 0, s);
+    if (lanes == 2) L(2)
+    if (lanes == 4) L(4)
+#undef L
     return cudaErrorInvalidValue;
 }
 
@@ -251,8 +269,8 @@ cudaError_t wide_lookup(int lanes, const DevTable& t, const void* keys, uint64_t
                         cudaStream_t s) {
     if (!n) return cudaSuccess;
     ProfScope ps(kKBucketLookup, s);
-    if (lanes == 2) return launch_wide<2, true>(t, keys, n, found, s);
-    if (lanes == 4) return launch_wide<4, true>(t, keys, n, found, s);
+    if (lanes == 2) return launch_wide<2, true, false>(t, keys, n, nullptr, found, nullptr, nullptr, 0, s);
+    if (lanes == 4) return launch_wide<4, true, false>(t, keys, n, nullptr, found, nullptr, nullptr, 0, s);
     return cudaErrorInvalidValue;
 }
 

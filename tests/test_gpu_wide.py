@@ -112,3 +112,52 @@ def test_unsupported_uses_are_rejected():
         ht.HashTable(64, "cuckoo", 128)
     with pytest.raises(ht.HtError):
         ht.HashTable(64, "bucket", 128, dict(bucket_slots=16))
+
+
+WIDE_MODELS = [
+    dict(seed=31, C=16, L=32, R=[2, 3, 2, 2, 3, 2, 2, 2, 2, 2, 2, 2, 3, 2, 2, 2], p_sync=0.0, P=0),
+    dict(seed=32, C=16, L=32, R=[3, 2, 3, 2, 2, 3, 2, 2, 3, 2, 2, 2, 2, 2, 3, 2], p_sync=0.4, P=4),
+    dict(seed=33, C=14, L=[32] * 8 + [16] * 6, R=[4, 3, 3, 2, 3, 2, 2, 3, 2, 2, 3, 2, 2, 3], p_sync=0.3, P=5),
+]
+
+
+def _hmodel(m):
+    return ht.make_model(m.C, m.bits, m.deg, m.tgt, m.lab, m.pairs)
+
+
+@pytest.mark.parametrize("spec", WIDE_MODELS)
+def test_wide_successors_match_oracle(oracle_lib, spec):
+    from workloads import statespace as ss
+    m = ss.random_model(spec["seed"], C=spec["C"], L=spec["L"], R=spec["R"], p_sync=spec["p_sync"], P=spec["P"])
+    assert m.key_width == 128
+    ref = oracle_lib.bfs(m, max_states=1 << 20, wide=True)
+    states = ref.states[: min(5000, ref.total)]
+    d = torch.from_numpy(np.ascontiguousarray(states).view(np.int64)).cuda()
+    succ = torch.empty((len(states) * 64, 2), dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ht.ht_successors(_hmodel(m), d, succ, cnt)
+    c = int(cnt.item())
+    exp = np.concatenate([oracle_lib.successors128(m, int(a) | (int(b) << 64)) for a, b in states.tolist()])
+    assert c == len(exp)
+    got = succ[:c].cpu().numpy().view(np.uint64)
+    assert sorted(map(tuple, got.tolist())) == sorted(map(tuple, exp.tolist()))
+
+
+@pytest.mark.parametrize("spec", WIDE_MODELS)
+def test_wide_bfs_matches_oracle_levels(oracle_lib, spec):
+    from workloads import statespace as ss
+    m = ss.random_model(spec["seed"], C=spec["C"], L=spec["L"], R=spec["R"], p_sync=spec["p_sync"], P=spec["P"])
+    ref = oracle_lib.bfs(m, max_states=1 << 22, wide=True)
+    assert ref.rc == 0
+    t = ht.HashTable(max(64, int(ref.total / 0.7)), "bucket", 128)
+    states = torch.empty((ref.total + 16, 2), dtype=torch.int64, device="cuda")
+    res, sizes = ht.ht_bfs(t.handle, _hmodel(m), 0, 4096, states)
+    assert res.complete == 1 and res.states == ref.total
+    assert res.successors == int(ref.level_succ.sum())
+    np.testing.assert_array_equal(np.array(sizes), ref.level_sizes)
+    got = states[:res.states].cpu().numpy().view(np.uint64)
+    off = 0
+    for d, n_d in enumerate(sizes):
+        assert set(map(tuple, got[off:off + n_d].tolist())) == set(map(tuple, ref.level(d).tolist())), d
+        off += n_d
+    assert t.size() == ref.total

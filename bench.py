@@ -412,6 +412,7 @@ def run_ours(a, rank, world, local):
         out["sweep_config2"] = run_sweep(ht, torch, dev)
         out["replay_multiplicity"] = run_replay(ht, torch, dev)
         out["wide_keys_128"] = run_wide(ht, torch, dev)
+        out["wide_bfs_80bit"] = run_wide_bfs(ht, torch, dev)
     if not a.no_bfs:
         out["bfs_config3"] = run_bfs(ht, torch, dev, schemes)
     if not a.no_batched:
@@ -769,6 +770,51 @@ def run_wide(ht, torch, dev, n_log2=26, batch_log2=24, dup=0.25, lf=0.8, reps=3)
                                   "exact": t.sync() == 0 and t.size() == n}
         t.close()
     return out
+
+
+def run_wide_bfs(ht, torch, dev, reps=2):
+    """BFS over 80-bit state vectors (16 components x 32 local states, windows
+    of 3, no synchronisation: 3^16 = 43 M states) in a 128-bit bucket table.
+    Without synchronisation the level sizes have a closed form -- the
+    convolution of the components' BFS-distance histograms -- which checks
+    the run exactly."""
+    from collections import deque
+    from workloads import statespace as ss
+    R = [3] * 16
+    m = ss.random_model(47, C=16, L=32, R=R, p_sync=0.0, P=0)
+    poly = np.array([1], dtype=np.int64)
+    for c in range(m.C):
+        dist = {0: 0}
+        q = deque([0])
+        while q:
+            u = q.popleft()
+            for j in range(int(m.deg[c, u])):
+                v = int(m.tgt[c, u, j])
+                if v not in dist:
+                    dist[v] = dist[u] + 1
+                    q.append(v)
+        poly = np.convolve(poly, np.bincount(list(dist.values())))
+    total = int(np.prod(R))
+    hm = _hmodel(ht, m)
+    states = torch.empty((total + 1024, 2), dtype=torch.int64, device=dev)
+    t = ht.HashTable(int(total / 0.8), "bucket", 128)
+    times = []
+    for r in range(reps + 1):
+        ht.ht_clear(t.handle)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res, sizes = ht.ht_bfs(t.handle, hm, 0, 4096, states)
+        torch.cuda.synchronize()
+        if r:
+            times.append(time.perf_counter() - t0)
+    sec = statistics.median(times)
+    ok = res.complete == 1 and res.states == total and sizes == poly.tolist() and t.size() == total
+    t.close()
+    del states
+    return {"workload": "16 components x 32 local states (80-bit vectors), windows of 3, no sync: %d states, "
+                        "%d levels, %d successors" % (total, len(sizes), res.successors),
+            "seconds": round(sec, 4), "states_per_s_M": round(total / sec / 1e6, 1),
+            "find_or_put_mops": round(res.successors / sec / 1e6, 1), "levels_match_closed_form": bool(ok)}
 
 
 def run_multi_table(ht, torch, dev, n_tables=1024, keys_per=4096, rounds=8):

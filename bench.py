@@ -738,7 +738,7 @@ def run_replay(ht, torch, dev, n=100_000_000, mults=(1, 2, 5, 10, 50, 100, 200, 
 
 
 def run_wide(ht, torch, dev, n_log2=26, batch_log2=24, dup=0.25, lf=0.8, reps=3):
-    """128-bit keys (state vectors wider than 64 bits), bucket scheme: a fill
+    """128-bit keys (state vectors wider than 64 bits), both schemes: a fill
     of 2^26 random keys to load 0.8 in batches of 2^24 with 25% repeats (two
     independent 63-bit streams as the words); exact when the table ends with
     exactly 2^26 keys."""
@@ -752,8 +752,9 @@ def run_wide(ht, torch, dev, n_log2=26, batch_log2=24, dup=0.25, lf=0.8, reps=3)
     pairs = [torch.stack([b, dk.mix63_perm_dev(b, 92)], dim=1).contiguous() for b in batches]
     issued = sum(p.shape[0] for p in pairs)
     flags = torch.empty(max(p.shape[0] for p in pairs), dtype=torch.uint8, device=dev)
-    for lanes in (2, 4):
-        t = ht.HashTable(int(np.ceil(n / lf)), "bucket", 128, dict(lanes_per_key=lanes))
+    for name, sch, params in (("bucket_lanes2", "bucket", dict(lanes_per_key=2)),
+                              ("bucket_lanes4", "bucket", dict(lanes_per_key=4)), ("cuckoo", "cuckoo", None)):
+        t = ht.HashTable(int(np.ceil(n / lf)), sch, 128, params)
         times = []
         for r in range(reps + 1):
             ht.ht_clear(t.handle)
@@ -766,8 +767,8 @@ def run_wide(ht, torch, dev, n_log2=26, batch_log2=24, dup=0.25, lf=0.8, reps=3)
             if r:
                 times.append(e0.elapsed_time(e1))
         ms = statistics.median(times)
-        out["lanes%d" % lanes] = {"ms_per_fill": round(ms, 2), "mops": round(issued / (ms / 1e3) / 1e6, 1),
-                                  "exact": t.sync() == 0 and t.size() == n}
+        out[name] = {"ms_per_fill": round(ms, 2), "mops": round(issued / (ms / 1e3) / 1e6, 1),
+                     "exact": t.sync() == 0 and t.size() == n}
         t.close()
     return out
 

@@ -109,15 +109,16 @@ ht_status ht_default_params(ht_scheme scheme, ht_params* p);
  * Cuckoo, the dedup scratch) in the order of `stream` (cudaMallocAsync) and
  * clears them on `stream`; use the table on other streams only after work
  * on `stream` is ordered before that use.
- * key_width 32 or 64; or 128 for the bucket scheme: keys of two 64-bit
- * words (low word first, 16-byte aligned, bit 63 of the high word reserved)
- * for state vectors wider than 64 bits, in 16-byte slots claimed with one
- * 16-byte compare-and-swap, buckets of 8 slots (bucket_slots must be 8,
- * lanes_per_key 2 or 4; with params NULL: 8 and 4), no stash, no values;
- * such tables support find-or-put (with append), insert without values,
- * lookup without values, export, size, clear, grow, stats, ht_successors
- * and ht_bfs over models up to 127 bits wide (not ht_bfs_fused, the batched
- * forms or Cuckoo).
+ * key_width 32, 64 or 128: 128-bit keys are two 64-bit words (low word
+ * first, 16-byte aligned, bit 63 of the high word reserved) for state
+ * vectors wider than 64 bits, in 16-byte slots written with 16-byte atomics
+ * (compare-and-swap claims, exchange evictions for Cuckoo); bucket scheme:
+ * buckets of 8 slots (bucket_slots must be 8, lanes_per_key 2 or 4; with
+ * params NULL: 8 and 4); no stash (the overflow set takes what does not
+ * fit), no values.  128-bit tables support find-or-put (with append),
+ * insert without values, lookup without values, export, size, clear, grow,
+ * stats, ht_successors and ht_bfs over models up to 127 bits wide (not
+ * ht_bfs_fused or the batched forms).
  * Errors: HT_ERR_INVALID (capacity 0 or > 2^40, key_width not 32/64/128,
  * bad params), HT_ERR_OOM, HT_ERR_CUDA.  *out is NULL on error. */
 ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width,

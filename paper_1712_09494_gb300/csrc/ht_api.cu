@@ -92,8 +92,18 @@ ht_status run_put(ht_table* t, const void* keys, const uint32_t* vals, uint64_t 
     if (n == 0) return HT_OK;
     if (t->kw == 128) {
         if (vals) return HT_ERR_INVALID;
-        return cuda_status(wide_find_or_put(int(t->p.lanes_per_key), t->dt, keys, n, d_n, is_new, new_out, new_count,
-                                            new_cap, s));
+        if (t->scheme == HT_BUCKET)
+            return cuda_status(wide_find_or_put(int(t->p.lanes_per_key), t->dt, keys, n, d_n, is_new, new_out,
+                                                new_count, new_cap, s));
+        for (uint64_t off = 0; off < n; off += t->chunk) {
+            const uint64_t m = std::min(t->chunk, n - off);
+            HT_TRY(wide_cuckoo_probe(t->dt, t->sc, t->parity, static_cast<const char*>(keys) + off * 16, m, d_n, off,
+                                     is_new ? is_new + off : nullptr, s));
+            HT_TRY(wide_cuckoo_insert(t->dt, t->sc, t->parity, new_out, new_count, new_cap,
+                                      std::min<uint64_t>(m, t->sc.win_cap), s));
+            t->parity ^= 1u;
+        }
+        return HT_OK;
     }
     if (t->scheme == HT_BUCKET) {
         return cuda_status(bucket_find_or_put(bucket_cfg(t), t->dt, keys, vals, n, d_n, is_new, new_out,
@@ -384,15 +394,17 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
     *out = nullptr;
     if (capacity == 0 || capacity > kMaxCapacity) return HT_ERR_INVALID;
     if (scheme != HT_BUCKET && scheme != HT_CUCKOO) return HT_ERR_INVALID;
-    if (key_width != 32 && key_width != 64 && !(key_width == 128 && scheme == HT_BUCKET)) return HT_ERR_INVALID;
+    if (key_width != 32 && key_width != 64 && key_width != 128) return HT_ERR_INVALID;
     ht_params p = complete_params(scheme, params);
     if (key_width == 128) {
-        // 16-byte slots: buckets of 8 (one 128-byte line), 2 or 4 lanes, no stash.
+        // 16-byte slots; no stash (the overflow set takes what does not fit).
+        // Bucket scheme: buckets of 8 (one 128-byte line), 2 or 4 lanes.
         if (!params) {
             p.bucket_slots = 8;
             p.lanes_per_key = 4;              // measured faster than 2 for 16-byte slots
         }
-        if (p.bucket_slots != 8 || (p.lanes_per_key != 2 && p.lanes_per_key != 4)) return HT_ERR_INVALID;
+        if (scheme == HT_BUCKET && (p.bucket_slots != 8 || (p.lanes_per_key != 2 && p.lanes_per_key != 4)))
+            return HT_ERR_INVALID;
         p.stash_slots = 0;
     }
     if (!valid_params(scheme, p)) return HT_ERR_INVALID;
@@ -443,9 +455,11 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
         const uint64_t sslots = next_pow2(2 * sc_cap);
         t->sc.mask = sslots - 1;
         t->sc.win_cap = sc_cap;
-        if ((e = cudaMallocAsync(&t->sc.set, sslots * 8, cs)) != cudaSuccess) return fail(e);
-        if ((e = cudaMallocAsync(&t->sc.win, sc_cap * sizeof(Winner), cs)) != cudaSuccess) return fail(e);
-        if ((e = fill_words(t->sc.set, sslots, kEmpty, cs)) != cudaSuccess) return fail(e);
+        const uint64_t set_words = key_width == 128 ? 2 : 1;
+        const uint64_t win_bytes = key_width == 128 ? kWideWinnerBytes : sizeof(Winner);
+        if ((e = cudaMallocAsync(&t->sc.set, sslots * 8 * set_words, cs)) != cudaSuccess) return fail(e);
+        if ((e = cudaMallocAsync(&t->sc.win, sc_cap * win_bytes, cs)) != cudaSuccess) return fail(e);
+        if ((e = fill_words(t->sc.set, sslots * set_words, kEmpty, cs)) != cudaSuccess) return fail(e);
     }
     ht_status st = clear_table(t, cs);
     if (st != HT_OK) {
@@ -507,6 +521,7 @@ ht_status ht_lookup(ht_table* t, const void* d_keys, uint64_t n, uint32_t* d_val
     const cudaStream_t s = as_stream(stream);
     if (t->kw == 128) {
         if (d_values) return HT_ERR_INVALID;
+        if (t->scheme == HT_CUCKOO) return cuda_status(wide_cuckoo_lookup(t->dt, d_keys, n, d_found, s));
         return cuda_status(wide_lookup(int(t->p.lanes_per_key), t->dt, d_keys, n, d_found, s));
     }
     if (t->scheme == HT_BUCKET)

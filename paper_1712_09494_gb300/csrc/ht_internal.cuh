@@ -431,6 +431,16 @@ cudaError_t wide_find_or_put(int lanes, const DevTable& t, const void* keys, uin
 cudaError_t wide_lookup(int lanes, const DevTable& t, const void* keys, uint64_t n, uint8_t* found,
                         cudaStream_t s);
 cudaError_t wide_export(const DevTable& t, void* keys, unsigned long long* count, uint64_t cap, cudaStream_t s);
+// Cuckoo tables of 128-bit keys: probe (dedup, winners of `parity`), insert
+// (eviction chains; winners appended to new_out when non-null), lookup.  The
+// claim set holds 16-byte entries and the winner list 32-byte records.
+cudaError_t wide_cuckoo_probe(const DevTable& t, const DevScratch& sc, uint32_t parity, const void* keys, uint64_t n,
+                              const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s);
+cudaError_t wide_cuckoo_insert(const DevTable& t, const DevScratch& sc, uint32_t parity, void* new_out,
+                               unsigned long long* new_count, uint64_t new_cap, uint64_t max_winners,
+                               cudaStream_t s);
+cudaError_t wide_cuckoo_lookup(const DevTable& t, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s);
+constexpr uint64_t kWideWinnerBytes = 32;
 
 // Read-only views of a table for the batched form (ht_api.cu).
 const DevTable& table_dev(const ht_table* t);

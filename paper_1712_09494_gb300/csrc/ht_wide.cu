@@ -48,6 +48,20 @@ __device__ __forceinline__ void cas128(uint64_t* addr, uint64_t new_lo, uint64_t
         : "memory");
 }
 
+__device__ __forceinline__ void exch128(uint64_t* addr, uint64_t lo, uint64_t hi, uint64_t& old_lo,
+                                        uint64_t& old_hi) {
+    asm volatile(
+        "{\n"
+        " .reg .b128 d, n;\n"
+        " mov.b128 n, {%2, %3};\n"
+        " atom.global.exch.b128 d, [%4], n;\n"
+        " mov.b128 {%0, %1}, d;\n"
+        "}\n"
+        : "=l"(old_lo), "=l"(old_hi)
+        : "l"(lo), "l"(hi), "l"(addr)
+        : "memory");
+}
+
 // Slot classes of a read: 2 = a complete key, 1 = a claim candidate.
 __device__ __forceinline__ int slot_class(uint64_t lo, uint64_t hi) {
     return (lo != kOnes && hi != kOnes) ? 2 : 1;
@@ -239,6 +253,184 @@ wide_export_kernel(const DevTable t, uint64_t* __restrict__ out, unsigned long l
     }
 }
 
+// ---------------------------------------------------------------------------
+// Cuckoo hashing of 128-bit keys (Section 4.1 with 16-byte slots; the
+// generalisation to longer keys is the paper's own future work, Section 7).
+// The same two kernels as for 64-bit keys: a probe that finds keys in h_1
+// (then h_2..h_k when h_1 is occupied) and elects one winner per absent key
+// through a claim set of 16-byte entries (one CAS per claim), and an insert
+// that runs each winner's eviction chain with 16-byte atomic exchanges.  No
+// writer runs during the probe launch, so its plain 16-byte reads are
+// complete; every write to a slot is one 16-byte atomic.
+
+struct WideWinner {
+    uint64_t lo, hi;
+    uint64_t spos;                        // its claim-set entry (cleared by the insert)
+    uint64_t pad_;
+};
+
+template <bool LOOKUP>
+__global__ void __launch_bounds__(kBlock)
+wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity, const ulonglong2* __restrict__ keys,
+                         uint64_t n, const unsigned long long* __restrict__ d_n, uint64_t off,
+                         uint8_t* __restrict__ out) {
+    if (d_n) {
+        const uint64_t total = __ldcg(d_n);
+        n = total > off ? min(n, total - off) : 0;
+    }
+    const uint32_t ovf_used = __ldcg(&t.ctr->ovf_used);
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t rounds = (n + stride - 1) / stride;          // warp-uniform trip count
+    const int lane = threadIdx.x & 31;
+    const uint64_t dseed = t.aux_seed * 3 + 1;
+    WideWinner* win = reinterpret_cast<WideWinner*>(sc.win);
+    for (uint64_t r = 0; r < rounds; ++r) {
+        const uint64_t i = r * stride + tid;
+        const bool act = i < n;
+        ulonglong2 k = make_ulonglong2(0, 0);
+        if (act) k = keys[i];
+        const bool ok = act && !wide_reserved(k.y);
+        if (act && !ok) set_flag(t.ctr, kFlagInvalidKey);
+        const uint64_t fold = wide_fold(k.x, k.y);
+        bool found = false;
+        if (ok) {
+            // h_1 first; an empty h_1 proves the key absent (every chain
+            // starts there and slots never return to EMPTY).
+            ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold, t.seed[0], t.nslots)));
+            found = w.x == k.x && w.y == k.y;
+            if (!found && !(w.x == kOnes && w.y == kOnes)) {
+                for (uint32_t a = 1; a < t.k && !found; ++a) {
+                    w = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold, t.seed[a], t.nslots)));
+                    found = w.x == k.x && w.y == k.y;
+                }
+            }
+            if (!found && ovf_used) found = wide_ovf_find(t, k.x, k.y);
+        }
+        if (LOOKUP) {
+            if (act && out) out[i] = uint8_t(found);
+            continue;
+        }
+        // In-batch dedup: one winner per distinct absent key.
+        bool winner = false;
+        uint64_t spos = mix64(fold ^ dseed) & sc.mask;
+        if (ok && !found) {
+            bool settled = false;
+            for (uint64_t probe = 0; probe <= sc.mask && !settled; ++probe) {
+                uint64_t ol, oh;
+                cas128(sc.set + 2 * spos, k.x, k.y, ol, oh);
+                if (ol == kOnes && oh == kOnes) {
+                    winner = settled = true;
+                } else if (ol == k.x && oh == k.y) {
+                    settled = true;                      // another copy of the key won
+                } else {
+                    spos = (spos + 1) & sc.mask;
+                }
+            }
+            if (!settled) {                              // more distinct misses than the table holds
+                set_flag(t.ctr, kFlagDropped);
+                atomicAdd(&t.ctr->dropped, 1ull);
+            }
+        }
+        // Append the winners, one atomic per warp.
+        const unsigned wm = __ballot_sync(kFull, winner);
+        unsigned int b = 0;
+        if (wm) {
+            if (lane == 0) b = atomicAdd(&t.ctr->winners[parity], unsigned(__popc(wm)));
+            b = __shfl_sync(kFull, b, 0);
+        }
+        if (winner) {
+            const uint64_t at = uint64_t(b) + __popc(wm & ((1u << lane) - 1));
+            if (at < sc.win_cap) {
+                WideWinner wn;
+                wn.lo = k.x;
+                wn.hi = k.y;
+                wn.spos = spos;
+                wn.pad_ = 0;
+                win[at] = wn;
+            } else {                                     // more winners than the table holds
+                winner = false;
+                sc.set[2 * spos] = kOnes;
+                sc.set[2 * spos + 1] = kOnes;
+                set_flag(t.ctr, kFlagDropped);
+                atomicAdd(&t.ctr->dropped, 1ull);
+            }
+        }
+        if (act && out) out[i] = uint8_t(winner);
+    }
+}
+
+template <bool APPEND>
+__global__ void __launch_bounds__(kBlock)
+wide_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uint64_t max_winners,
+                          ulonglong2* __restrict__ new_out, unsigned long long* __restrict__ new_count,
+                          uint64_t new_cap) {
+    const uint64_t count = min(uint64_t(__ldcg(&t.ctr->winners[parity])), max_winners);
+    if (blockIdx.x == 0 && threadIdx.x == 0) t.ctr->winners[parity ^ 1u] = 0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t rounds = (count + stride - 1) / stride;
+    const int lane = threadIdx.x & 31;
+    const WideWinner* win = reinterpret_cast<const WideWinner*>(sc.win);
+    __shared__ ulonglong2 s_new[APPEND ? kBlock / 32 : 1][APPEND ? kStageCap : 1];
+    WarpStage<ulonglong2, kStageCap> stage(s_new[APPEND ? (threadIdx.x >> 5) : 0]);
+    unsigned long long placed = 0, exchanges = 0;
+    for (uint64_t r = 0; r < rounds; ++r) {
+        const uint64_t i = r * stride + tid;
+        const bool live0 = i < count;
+        uint64_t lo = 0, hi = 0;
+        if (live0) {
+            const WideWinner wn = win[i];
+            sc.set[2 * wn.spos] = kOnes;                 // leave the claim set empty for the next batch
+            sc.set[2 * wn.spos + 1] = kOnes;
+            lo = wn.lo;
+            hi = wn.hi;
+        }
+        if (APPEND) stage.push(live0, make_ulonglong2(lo, hi), new_out, new_count, new_cap);
+        if (!live0) continue;
+        uint64_t pos = hidx(wide_fold(lo, hi), t.seed[0], t.nslots);
+        bool done = false;
+        // Bounded: at most max_evictions + 1 exchanges, then the overflow set.
+        for (uint32_t e = 0; e <= t.max_evict && !done; ++e) {
+            uint64_t ol, oh;
+            exch128(t.slots + 2 * pos, lo, hi, ol, oh);
+            ++exchanges;
+            if (ol == kOnes && oh == kOnes) {
+                done = true;
+                ++placed;
+                break;
+            }
+            // Section 4.1: the evicted key sat at h_a(key) = pos; it moves on
+            // to h_{a+1} (cyclically after h_k), a the smallest such index.
+            lo = ol;
+            hi = oh;
+            const uint64_t fold = wide_fold(lo, hi);
+            uint32_t a = 0;
+            for (; a + 1 < t.k; ++a)
+                if (hidx(fold, t.seed[a], t.nslots) == pos) break;
+            const uint32_t nxt = (a + 1 == t.k) ? 0u : a + 1;
+            pos = hidx(fold, t.seed[nxt], t.nslots);
+        }
+        if (!done) {
+            const int rr = wide_ovf_insert(t, lo, hi);
+            if (rr == 1) {
+                ++placed;
+                atomicAdd(&t.ctr->ovf_used, 1u);
+            } else if (rr < 0) {
+                set_flag(t.ctr, kFlagDropped);
+                atomicAdd(&t.ctr->dropped, 1ull);
+            }
+        }
+    }
+    if (APPEND) stage.flush(new_out, new_count, new_cap);
+    for (int o = 16; o; o >>= 1) {
+        placed += __shfl_down_sync(kFull, placed, o);
+        exchanges += __shfl_down_sync(kFull, exchanges, o);
+    }
+    if (lane == 0 && placed) atomicAdd(&t.ctr->size, placed);
+    if (lane == 0 && exchanges) atomicAdd(&t.ctr->exchanges, exchanges);
+}
+
 template <int G, bool LOOKUP, bool APPEND>
 cudaError_t launch_wide(const DevTable& t, const void* keys, uint64_t n, const unsigned long long* d_n,
                         uint8_t* out, void* new_out, unsigned long long* new_count, uint64_t new_cap,
@@ -272,6 +464,40 @@ cudaError_t wide_lookup(int lanes, const DevTable& t, const void* keys, uint64_t
     if (lanes == 2) return launch_wide<2, true, false>(t, keys, n, nullptr, found, nullptr, nullptr, 0, s);
     if (lanes == 4) return launch_wide<4, true, false>(t, keys, n, nullptr, found, nullptr, nullptr, 0, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t wide_cuckoo_probe(const DevTable& t, const DevScratch& sc, uint32_t parity, const void* keys, uint64_t n,
+                              const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s) {
+    ProfScope ps(kKCuckooProbe, s);
+    auto k = wide_cuckoo_probe_kernel<false>;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, sc, parity, static_cast<const ulonglong2*>(keys),
+                                                              n, d_n, off, is_new);
+    return cudaGetLastError();
+}
+
+cudaError_t wide_cuckoo_insert(const DevTable& t, const DevScratch& sc, uint32_t parity, void* new_out,
+                               unsigned long long* new_count, uint64_t new_cap, uint64_t max_winners,
+                               cudaStream_t s) {
+    ProfScope ps(kKCuckooInsert, s);
+    if (new_out) {
+        auto k = wide_cuckoo_insert_kernel<true>;
+        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, sc, parity, max_winners,
+                                                                  static_cast<ulonglong2*>(new_out), new_count, new_cap);
+    } else {
+        auto k = wide_cuckoo_insert_kernel<false>;
+        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, sc, parity, max_winners, nullptr, nullptr, 0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t wide_cuckoo_lookup(const DevTable& t, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    ProfScope ps(kKCuckooLookup, s);
+    DevScratch none{};
+    auto k = wide_cuckoo_probe_kernel<true>;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, none, 0u, static_cast<const ulonglong2*>(keys), n,
+                                                              nullptr, 0, found);
+    return cudaGetLastError();
 }
 
 cudaError_t wide_export(const DevTable& t, void* keys, unsigned long long* count, uint64_t cap, cudaStream_t s) {

@@ -41,13 +41,19 @@ def _ids(pairs):
     return pairs[:, 0].astype(object) * (1 << 64) + pairs[:, 1].astype(object)
 
 
-@pytest.mark.parametrize("lanes", [2, 4])
+# (scheme, params): the bucket scheme at 2 and 4 lanes per key, Cuckoo (k=4).
+TABLES = [("bucket", dict(bucket_slots=8, lanes_per_key=2)), ("bucket", dict(bucket_slots=8, lanes_per_key=4)),
+          ("cuckoo", None)]
+TABLE_IDS = ["bucket_g2", "bucket_g4", "cuckoo"]
+
+
+@pytest.mark.parametrize("table", TABLES, ids=TABLE_IDS)
 @pytest.mark.parametrize("share", [None, "lo", "hi"])
-def test_find_or_put_lookup_export_match_oracle(oracle_lib, lanes, share):
+def test_find_or_put_lookup_export_match_oracle(oracle_lib, table, share):
     rng = np.random.default_rng(5)
     n = 120_000
     pool = _pairs(n, seed=40, share=share)
-    t = ht.HashTable(int(n / 0.85), "bucket", 128, dict(bucket_slots=8, lanes_per_key=lanes))
+    t = ht.HashTable(int(n / 0.85), table[0], 128, table[1])
     orc = oracle_lib.OracleTable128()
     issued = 0
     while issued < n:
@@ -68,13 +74,14 @@ def test_find_or_put_lookup_export_match_oracle(oracle_lib, lanes, share):
     np.testing.assert_array_equal(f.cpu().numpy(), orc.lookup(q))
 
 
-def test_edge_keys_and_reserved(oracle_lib):
+@pytest.mark.parametrize("scheme", ["bucket", "cuckoo"])
+def test_edge_keys_and_reserved(oracle_lib, scheme):
     # Words that are all ones except the reserved bit, zeros, and a key with
     # an all-ones low word (a legal key that reads like a half-written slot).
     ones = np.uint64(2 ** 64 - 1)
     top = np.uint64(2 ** 63 - 1)
     keys = np.array([[0, 0], [ones, 0], [0, top], [ones, top], [1, 2], [ones, 0]], dtype=np.uint64)
-    t = ht.HashTable(64, "bucket", 128)
+    t = ht.HashTable(64, scheme, 128)
     got = t.find_or_put(_dev(keys)).cpu().numpy()
     np.testing.assert_array_equal(got, [1, 1, 1, 1, 1, 0])
     f, _ = t.lookup(_dev(keys))
@@ -85,11 +92,13 @@ def test_edge_keys_and_reserved(oracle_lib):
     assert t.sync() == 1
 
 
-def test_overflow_grow_and_full(oracle_lib):
+@pytest.mark.parametrize("scheme", ["bucket", "cuckoo"])
+def test_overflow_grow_and_full(oracle_lib, scheme):
     # A small table spills into its overflow set, reports full beyond it,
     # and growth moves every key to the new storage.
     keys = _pairs(3000, seed=77)
-    t = ht.HashTable(64, "bucket", 128, dict(num_hashes=2))
+    params = dict(num_hashes=2) if scheme == "bucket" else dict(num_hashes=2, max_evictions=4)
+    t = ht.HashTable(64, scheme, 128, params)
     t.find_or_put(_dev(keys[:600]))
     assert t.sync() == 0 and t.size() == 600
     assert t.stats()["overflow_used"] > 0
@@ -102,16 +111,19 @@ def test_overflow_grow_and_full(oracle_lib):
     more = keys[400:3000]
     assert_flags_per_key(_ids(more), t.find_or_put(_dev(more)).cpu().numpy(), orc.find_or_put(more))
     assert t.sync() == 0 and t.size() == 3000
-    small = ht.HashTable(8, "bucket", 128, dict(num_hashes=1))
+    small = ht.HashTable(8, scheme, 128, dict(num_hashes=1) if scheme == "bucket" else dict(num_hashes=2))
     small.find_or_put(_dev(_pairs(5000, seed=78)))
     assert small.sync() == 3
 
 
 def test_unsupported_uses_are_rejected():
     with pytest.raises(ht.HtError):
-        ht.HashTable(64, "cuckoo", 128)
-    with pytest.raises(ht.HtError):
         ht.HashTable(64, "bucket", 128, dict(bucket_slots=16))
+    t = ht.HashTable(1024, "bucket", 128)
+    from workloads import statespace as ss
+    m = ss.random_model(1, C=3, L=8, R=5)
+    with pytest.raises(ht.HtError):
+        ht.ht_bfs(t.handle, _hmodel(m), 0, 16, torch.empty((1024, 2), dtype=torch.int64, device="cuda"), fused=True)
 
 
 WIDE_MODELS = [
@@ -143,13 +155,14 @@ def test_wide_successors_match_oracle(oracle_lib, spec):
     assert sorted(map(tuple, got.tolist())) == sorted(map(tuple, exp.tolist()))
 
 
+@pytest.mark.parametrize("scheme", ["bucket", "cuckoo"])
 @pytest.mark.parametrize("spec", WIDE_MODELS)
-def test_wide_bfs_matches_oracle_levels(oracle_lib, spec):
+def test_wide_bfs_matches_oracle_levels(oracle_lib, spec, scheme):
     from workloads import statespace as ss
     m = ss.random_model(spec["seed"], C=spec["C"], L=spec["L"], R=spec["R"], p_sync=spec["p_sync"], P=spec["P"])
     ref = oracle_lib.bfs(m, max_states=1 << 22, wide=True)
     assert ref.rc == 0
-    t = ht.HashTable(max(64, int(ref.total / 0.7)), "bucket", 128)
+    t = ht.HashTable(max(64, int(ref.total / 0.7)), scheme, 128)
     states = torch.empty((ref.total + 16, 2), dtype=torch.int64, device="cuda")
     res, sizes = ht.ht_bfs(t.handle, _hmodel(m), 0, 4096, states)
     assert res.complete == 1 and res.states == ref.total

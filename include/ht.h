@@ -114,7 +114,7 @@ ht_status ht_default_params(ht_scheme scheme, ht_params* p);
  * vectors wider than 64 bits, in 16-byte slots written with 16-byte atomics
  * (compare-and-swap claims, exchange evictions for Cuckoo); bucket scheme:
  * buckets of 8 slots (bucket_slots must be 8, lanes_per_key 2 or 4; with
- * params NULL: 8 and 4); no stash (the overflow set takes what does not
+ * params NULL: 8 and 2); no stash (the overflow set takes what does not
  * fit), no values.  128-bit tables support find-or-put (with append),
  * insert without values, lookup without values, export, size, clear, grow,
  * stats, ht_successors and ht_bfs over models up to 127 bits wide (not

@@ -98,8 +98,8 @@ def ht_default_params(scheme):
 def ht_create(capacity, scheme, key_width, params=None, stream=None):
     scheme = scheme_of(scheme)
     if int(key_width) == 128 and isinstance(params, dict):
-        # 16-byte slots: 8 per 128-byte bucket, 4 lanes unless given.
-        params = dict(dict(bucket_slots=8, lanes_per_key=4), **params)
+        # 16-byte slots: 8 per 128-byte bucket unless given.
+        params = dict(dict(bucket_slots=8), **params)
     p = _params(params, scheme)
     out = ctypes.c_void_p()
     _check(load().ht_create(int(capacity), scheme, int(key_width),

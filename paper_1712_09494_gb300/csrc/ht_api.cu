@@ -399,10 +399,7 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
     if (key_width == 128) {
         // 16-byte slots; no stash (the overflow set takes what does not fit).
         // Bucket scheme: buckets of 8 (one 128-byte line), 2 or 4 lanes.
-        if (!params) {
-            p.bucket_slots = 8;
-            p.lanes_per_key = 4;              // measured faster than 2 for 16-byte slots
-        }
+        if (!params) p.bucket_slots = 8;      // lanes_per_key stays 2 (measured faster than 4)
         if (scheme == HT_BUCKET && (p.bucket_slots != 8 || (p.lanes_per_key != 2 && p.lanes_per_key != 4)))
             return HT_ERR_INVALID;
         p.stash_slots = 0;

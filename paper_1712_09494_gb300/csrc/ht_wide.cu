@@ -269,6 +269,8 @@ struct WideWinner {
     uint64_t pad_;
 };
 
+constexpr int kWU = 4;                    // keys (probe) or chains (insert) in flight per thread
+
 template <bool LOOKUP>
 __global__ void __launch_bounds__(kBlock)
 wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity, const ulonglong2* __restrict__ keys,
@@ -281,85 +283,140 @@ wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     const uint32_t ovf_used = __ldcg(&t.ctr->ovf_used);
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint64_t rounds = (n + stride - 1) / stride;          // warp-uniform trip count
+    const uint64_t rounds = (n + stride * kWU - 1) / (stride * kWU);   // warp-uniform trip count
     const int lane = threadIdx.x & 31;
     const uint64_t dseed = t.aux_seed * 3 + 1;
     WideWinner* win = reinterpret_cast<WideWinner*>(sc.win);
     for (uint64_t r = 0; r < rounds; ++r) {
-        const uint64_t i = r * stride + tid;
-        const bool act = i < n;
-        ulonglong2 k = make_ulonglong2(0, 0);
-        if (act) k = keys[i];
-        const bool ok = act && !wide_reserved(k.y);
-        if (act && !ok) set_flag(t.ctr, kFlagInvalidKey);
-        const uint64_t fold = wide_fold(k.x, k.y);
-        bool found = false;
-        if (ok) {
-            // h_1 first; an empty h_1 proves the key absent (every chain
-            // starts there and slots never return to EMPTY).
-            ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold, t.seed[0], t.nslots)));
-            found = w.x == k.x && w.y == k.y;
-            if (!found && !(w.x == kOnes && w.y == kOnes)) {
-                for (uint32_t a = 1; a < t.k && !found; ++a) {
-                    w = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold, t.seed[a], t.nslots)));
-                    found = w.x == k.x && w.y == k.y;
-                }
+        ulonglong2 k[kWU];
+        uint64_t fold[kWU];
+        bool act[kWU], ok[kWU], found[kWU], more[kWU];
+#pragma unroll
+        for (int u = 0; u < kWU; ++u) {
+            const uint64_t i = (r * kWU + u) * stride + tid;
+            act[u] = i < n;
+            k[u] = act[u] ? keys[i] : make_ulonglong2(0, 0);
+            ok[u] = act[u] && !wide_reserved(k[u].y);
+            if (act[u] && !ok[u]) set_flag(t.ctr, kFlagInvalidKey);
+            fold[u] = wide_fold(k[u].x, k[u].y);
+        }
+        // h_1 of every key first; an empty h_1 proves the key absent (every
+        // chain starts there and slots never return to EMPTY).
+        ulonglong2 w[kWU];
+#pragma unroll
+        for (int u = 0; u < kWU; ++u)
+            if (ok[u]) w[u] = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold[u], t.seed[0], t.nslots)));
+#pragma unroll
+        for (int u = 0; u < kWU; ++u) {
+            found[u] = ok[u] && w[u].x == k[u].x && w[u].y == k[u].y;
+            more[u] = ok[u] && !found[u] && !(w[u].x == kOnes && w[u].y == kOnes);
+        }
+        for (uint32_t a = 1; a < t.k; ++a) {
+#pragma unroll
+            for (int u = 0; u < kWU; ++u)
+                if (more[u] && !found[u])
+                    w[u] = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold[u], t.seed[a], t.nslots)));
+#pragma unroll
+            for (int u = 0; u < kWU; ++u)
+                if (more[u] && !found[u]) found[u] = w[u].x == k[u].x && w[u].y == k[u].y;
+        }
+        if (ovf_used) {
+#pragma unroll
+            for (int u = 0; u < kWU; ++u)
+                if (ok[u] && !found[u]) found[u] = wide_ovf_find(t, k[u].x, k[u].y);
+        }
+        if constexpr (LOOKUP) {
+#pragma unroll
+            for (int u = 0; u < kWU; ++u) {
+                const uint64_t i = (r * kWU + u) * stride + tid;
+                if (act[u] && out) out[i] = uint8_t(found[u]);
             }
-            if (!found && ovf_used) found = wide_ovf_find(t, k.x, k.y);
-        }
-        if (LOOKUP) {
-            if (act && out) out[i] = uint8_t(found);
-            continue;
-        }
-        // In-batch dedup: one winner per distinct absent key.
-        bool winner = false;
-        uint64_t spos = mix64(fold ^ dseed) & sc.mask;
-        if (ok && !found) {
-            bool settled = false;
-            for (uint64_t probe = 0; probe <= sc.mask && !settled; ++probe) {
+        } else {
+        // In-batch dedup: one winner per distinct absent key; every miss's
+        // first claim together, collisions probe on.
+        bool winner[kWU];
+        uint64_t spos[kWU];
+        ulonglong2 old[kWU];
+#pragma unroll
+        for (int u = 0; u < kWU; ++u) {
+            winner[u] = false;
+            spos[u] = mix64(fold[u] ^ dseed) & sc.mask;
+            old[u] = make_ulonglong2(0, 0);
+            if (ok[u] && !found[u]) {
                 uint64_t ol, oh;
-                cas128(sc.set + 2 * spos, k.x, k.y, ol, oh);
-                if (ol == kOnes && oh == kOnes) {
-                    winner = settled = true;
-                } else if (ol == k.x && oh == k.y) {
-                    settled = true;                      // another copy of the key won
-                } else {
-                    spos = (spos + 1) & sc.mask;
+                cas128(sc.set + 2 * spos[u], k[u].x, k[u].y, ol, oh);
+                old[u] = make_ulonglong2(ol, oh);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kWU; ++u) {
+            if (!ok[u] || found[u]) continue;
+            bool settled = false;
+            for (uint64_t probe = 0; probe <= sc.mask; ++probe) {
+                if (probe) {
+                    uint64_t ol, oh;
+                    cas128(sc.set + 2 * spos[u], k[u].x, k[u].y, ol, oh);
+                    old[u] = make_ulonglong2(ol, oh);
                 }
+                if (old[u].x == kOnes && old[u].y == kOnes) {
+                    winner[u] = settled = true;
+                    break;
+                }
+                if (old[u].x == k[u].x && old[u].y == k[u].y) {
+                    settled = true;                      // another copy of the key won
+                    break;
+                }
+                spos[u] = (spos[u] + 1) & sc.mask;
             }
             if (!settled) {                              // more distinct misses than the table holds
                 set_flag(t.ctr, kFlagDropped);
                 atomicAdd(&t.ctr->dropped, 1ull);
             }
         }
-        // Append the winners, one atomic per warp.
-        const unsigned wm = __ballot_sync(kFull, winner);
+        // Append the round's winners: one atomic per warp.
+        unsigned wm[kWU];
+        unsigned total = 0;
+#pragma unroll
+        for (int u = 0; u < kWU; ++u) {
+            wm[u] = __ballot_sync(kFull, winner[u]);
+            total += __popc(wm[u]);
+        }
         unsigned int b = 0;
-        if (wm) {
-            if (lane == 0) b = atomicAdd(&t.ctr->winners[parity], unsigned(__popc(wm)));
+        if (total) {
+            if (lane == 0) b = atomicAdd(&t.ctr->winners[parity], total);
             b = __shfl_sync(kFull, b, 0);
         }
-        if (winner) {
-            const uint64_t at = uint64_t(b) + __popc(wm & ((1u << lane) - 1));
-            if (at < sc.win_cap) {
-                WideWinner wn;
-                wn.lo = k.x;
-                wn.hi = k.y;
-                wn.spos = spos;
-                wn.pad_ = 0;
-                win[at] = wn;
-            } else {                                     // more winners than the table holds
-                winner = false;
-                sc.set[2 * spos] = kOnes;
-                sc.set[2 * spos + 1] = kOnes;
-                set_flag(t.ctr, kFlagDropped);
-                atomicAdd(&t.ctr->dropped, 1ull);
+#pragma unroll
+        for (int u = 0; u < kWU; ++u) {
+            const uint64_t i = (r * kWU + u) * stride + tid;
+            bool stored = winner[u];
+            if (stored) {
+                const uint64_t at = uint64_t(b) + __popc(wm[u] & ((1u << lane) - 1));
+                if (at < sc.win_cap) {
+                    WideWinner wn;
+                    wn.lo = k[u].x;
+                    wn.hi = k[u].y;
+                    wn.spos = spos[u];
+                    wn.pad_ = 0;
+                    win[at] = wn;
+                } else {                                 // more winners than the table holds
+                    stored = false;
+                    sc.set[2 * spos[u]] = kOnes;
+                    sc.set[2 * spos[u] + 1] = kOnes;
+                    set_flag(t.ctr, kFlagDropped);
+                    atomicAdd(&t.ctr->dropped, 1ull);
+                }
             }
+            if (act[u] && out) out[i] = uint8_t(stored);
+            b += __popc(wm[u]);
         }
-        if (act && out) out[i] = uint8_t(winner);
+        }
     }
 }
 
+// Eviction chains of the winners: each thread keeps kWU chains in flight and
+// replaces a chain that ends (an empty slot, or the overflow set) with its
+// next winner at once.
 template <bool APPEND>
 __global__ void __launch_bounds__(kBlock)
 wide_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uint64_t max_winners,
@@ -369,60 +426,93 @@ wide_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity
     if (blockIdx.x == 0 && threadIdx.x == 0) t.ctr->winners[parity ^ 1u] = 0;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint64_t rounds = (count + stride - 1) / stride;
     const int lane = threadIdx.x & 31;
     const WideWinner* win = reinterpret_cast<const WideWinner*>(sc.win);
-    __shared__ ulonglong2 s_new[APPEND ? kBlock / 32 : 1][APPEND ? kStageCap : 1];
-    WarpStage<ulonglong2, kStageCap> stage(s_new[APPEND ? (threadIdx.x >> 5) : 0]);
-    unsigned long long placed = 0, exchanges = 0;
-    for (uint64_t r = 0; r < rounds; ++r) {
-        const uint64_t i = r * stride + tid;
-        const bool live0 = i < count;
-        uint64_t lo = 0, hi = 0;
-        if (live0) {
-            const WideWinner wn = win[i];
-            sc.set[2 * wn.spos] = kOnes;                 // leave the claim set empty for the next batch
-            sc.set[2 * wn.spos + 1] = kOnes;
-            lo = wn.lo;
-            hi = wn.hi;
+    if (APPEND) {
+        __shared__ ulonglong2 s_new[kBlock / 32][kStageCap];
+        WarpStage<ulonglong2, kStageCap> stage(s_new[threadIdx.x >> 5]);
+        const uint64_t rounds = (count + stride - 1) / stride;
+        for (uint64_t r = 0; r < rounds; ++r) {
+            const uint64_t i = r * stride + tid;
+            ulonglong2 v = make_ulonglong2(0, 0);
+            if (i < count) v = make_ulonglong2(win[i].lo, win[i].hi);
+            stage.push(i < count, v, new_out, new_count, new_cap);
         }
-        if (APPEND) stage.push(live0, make_ulonglong2(lo, hi), new_out, new_count, new_cap);
-        if (!live0) continue;
-        uint64_t pos = hidx(wide_fold(lo, hi), t.seed[0], t.nslots);
-        bool done = false;
-        // Bounded: at most max_evictions + 1 exchanges, then the overflow set.
-        for (uint32_t e = 0; e <= t.max_evict && !done; ++e) {
-            uint64_t ol, oh;
-            exch128(t.slots + 2 * pos, lo, hi, ol, oh);
+        stage.flush(new_out, new_count, new_cap);
+    }
+    unsigned long long placed = 0, exchanges = 0;
+    uint64_t next = tid;                         // this thread's next winner: tid, tid + stride, ...
+    uint64_t lo[kWU], hi[kWU], pos[kWU];
+    uint32_t evictions[kWU];
+    bool live[kWU];
+#pragma unroll
+    for (int u = 0; u < kWU; ++u) {
+        live[u] = false;
+        lo[u] = hi[u] = pos[u] = 0;
+        evictions[u] = 0;
+    }
+    // Bounded: each winner is taken once and its chain ends after at most
+    // max_evictions + 1 exchanges.
+    for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < kWU; ++u) {
+            if (!live[u] && next < count) {
+                const WideWinner wn = win[next];
+                next += stride;
+                sc.set[2 * wn.spos] = kOnes;             // leave the claim set empty for the next batch
+                sc.set[2 * wn.spos + 1] = kOnes;
+                lo[u] = wn.lo;
+                hi[u] = wn.hi;
+                pos[u] = hidx(wide_fold(wn.lo, wn.hi), t.seed[0], t.nslots);
+                evictions[u] = 0;
+                live[u] = true;
+            }
+            any |= live[u];
+        }
+        if (!any) break;
+        ulonglong2 old[kWU];
+#pragma unroll
+        for (int u = 0; u < kWU; ++u)
+            if (live[u]) {
+                uint64_t ol, oh;
+                exch128(t.slots + 2 * pos[u], lo[u], hi[u], ol, oh);
+                old[u] = make_ulonglong2(ol, oh);
+            }
+#pragma unroll
+        for (int u = 0; u < kWU; ++u) {
+            if (!live[u]) continue;
             ++exchanges;
-            if (ol == kOnes && oh == kOnes) {
-                done = true;
+            if (old[u].x == kOnes && old[u].y == kOnes) {
+                live[u] = false;
                 ++placed;
-                break;
+                continue;
+            }
+            lo[u] = old[u].x;
+            hi[u] = old[u].y;
+            if (++evictions[u] > t.max_evict) {
+                // The chain hit the eviction bound: the held key goes to the overflow set.
+                const int rr = wide_ovf_insert(t, lo[u], hi[u]);
+                if (rr == 1) {
+                    ++placed;
+                    atomicAdd(&t.ctr->ovf_used, 1u);
+                } else if (rr < 0) {
+                    set_flag(t.ctr, kFlagDropped);
+                    atomicAdd(&t.ctr->dropped, 1ull);
+                }
+                live[u] = false;
+                continue;
             }
             // Section 4.1: the evicted key sat at h_a(key) = pos; it moves on
             // to h_{a+1} (cyclically after h_k), a the smallest such index.
-            lo = ol;
-            hi = oh;
-            const uint64_t fold = wide_fold(lo, hi);
+            const uint64_t fold = wide_fold(lo[u], hi[u]);
             uint32_t a = 0;
             for (; a + 1 < t.k; ++a)
-                if (hidx(fold, t.seed[a], t.nslots) == pos) break;
+                if (hidx(fold, t.seed[a], t.nslots) == pos[u]) break;
             const uint32_t nxt = (a + 1 == t.k) ? 0u : a + 1;
-            pos = hidx(fold, t.seed[nxt], t.nslots);
-        }
-        if (!done) {
-            const int rr = wide_ovf_insert(t, lo, hi);
-            if (rr == 1) {
-                ++placed;
-                atomicAdd(&t.ctr->ovf_used, 1u);
-            } else if (rr < 0) {
-                set_flag(t.ctr, kFlagDropped);
-                atomicAdd(&t.ctr->dropped, 1ull);
-            }
+            pos[u] = hidx(fold, t.seed[nxt], t.nslots);
         }
     }
-    if (APPEND) stage.flush(new_out, new_count, new_cap);
     for (int o = 16; o; o >>= 1) {
         placed += __shfl_down_sync(kFull, placed, o);
         exchanges += __shfl_down_sync(kFull, exchanges, o);

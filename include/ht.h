@@ -189,7 +189,10 @@ ht_status ht_grow(ht_table* t, uint64_t new_capacity, void* stream);
 ht_status ht_info(const ht_table* t, uint64_t* slots, uint32_t* num_hashes,
                   uint32_t* rebuilds);
 
-/* Counters of a table since its last clear (ht_clear) or rebuild. */
+/* Counters of a table since its last clear (ht_clear), rebuild or growth:
+ * what the paper's analysis turns on -- stored keys, the stash and rebuilds
+ * of Section 4.1, Cuckoo's eviction work (Section 4.1: chain length grows
+ * with the load) -- read from the device. */
 typedef struct ht_table_stats {
     uint64_t size;            /* keys stored (table + stash + overflow set) */
     uint64_t dropped;         /* keys that found no place (then HT_ERR_FULL) */
@@ -203,8 +206,9 @@ typedef struct ht_table_stats {
     uint64_t reserved_[4];
 } ht_table_stats;
 
-/* Reads the table's counters into *out; synchronises `stream`.
- * HT_ERR_INVALID for a NULL table or out. */
+/* Reads the table's counters into *out (caller-owned host memory);
+ * synchronises `stream`; changes nothing (no rebuild or growth runs).
+ * HT_ERR_INVALID for a NULL table or out; HT_ERR_CUDA if the copy fails. */
 ht_status ht_stats(ht_table* t, ht_table_stats* out, void* stream);
 
 const char* ht_status_str(ht_status s);

@@ -344,14 +344,20 @@ def run_ours(a, rank, world, local):
     # Roofline of the dominant kernel: algorithmic bytes per launch / event time.
     p_new = fs.n_distinct / fs.n_issued
     miss_probes = cuckoo_miss_probes(fs, tables.get("cuckoo"))
+    # Slots a Cuckoo probe reads per key: counted on the device over the last
+    # timed fill when available, else the model (one h_1 read per repeat,
+    # 1 + a(k-1) per new key).
+    probes_model = (1 - p_new) * 1 + p_new * miss_probes
+    probes_counted = (fill_stats["cuckoo"]["probes"] / fs.n_issued
+                      if "cuckoo" in fill_stats and fill_stats["cuckoo"].get("probes") else None)
+    probes_per_key = probes_counted if probes_counted is not None else probes_model
     cuckoo_exchanges_per_new = (fill_stats["cuckoo"]["exchanges"] / fs.n_distinct) if "cuckoo" in fill_stats else 1.0
     per_key = {
         # key read + flag write + one 128-byte bucket + the claimed sector for new keys
         "bucket_find_or_put": 8 + 1 + 128 + p_new * 32,
-        # key read + flag write + 32-byte sector of h_1 for hits; for misses the
-        # probed sectors (h_1, and h_2..h_k when h_1 is occupied) plus the
-        # 16-byte winner record
-        "cuckoo_probe": 8 + 1 + (1 - p_new) * 32 + p_new * (miss_probes * 32 + 16),
+        # key read + flag write + a 32-byte sector per slot probed (h_1, and
+        # h_2..h_k when h_1 is occupied) + the 16-byte winner record of new keys
+        "cuckoo_probe": 8 + 1 + probes_per_key * 32 + p_new * 16,
         # winner record + per exchange a 32-byte sector read and written
         # (exchanges per winner counted on the device over the last timed fill)
         "cuckoo_insert": 16 + 64 * max(1.0, cuckoo_exchanges_per_new),
@@ -378,7 +384,8 @@ def run_ours(a, rank, world, local):
                 "unit": "GB/s", "frac": round(kernels[dom]["achieved_gbs"] / peak, 3),
                 "frac_of_nominal_7900": round(kernels[dom]["achieved_gbs"] / 7900.0, 3),
                 "traffic": traffic, "alg_bytes_per_key": round(per_key[dom], 1),
-                "cuckoo_miss_probes": round(miss_probes, 3),
+                "cuckoo_probes_per_key": round(probes_per_key, 3), "cuckoo_probes_per_key_model": round(probes_model, 3),
+                "cuckoo_probes_counted": probes_counted is not None,
                 "cuckoo_exchanges_per_new_key": round(cuckoo_exchanges_per_new, 3)}
 
     out = {

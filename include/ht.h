@@ -203,7 +203,12 @@ typedef struct ht_table_stats {
     uint32_t rebuilds;        /* rebuilds since ht_create */
     uint32_t flags;           /* device status bits: 1 reserved key seen,
                                  2 rebuild pending, 4 key dropped */
-    uint64_t reserved_[4];
+    uint64_t probes;          /* Cuckoo: slots read by find-or-put and lookup
+                                 probes (h_1, then h_2..h_k when h_1 is occupied);
+                                 bucket scheme: buckets read beyond each key's
+                                 first (later hash functions, Section 4.2);
+                                 0 for 128-bit tables */
+    uint64_t reserved_[3];
 } ht_table_stats;
 
 /* Reads the table's counters into *out (caller-owned host memory);

@@ -62,7 +62,8 @@ class HtTableStats(ctypes.Structure):
     _fields_ = [
         ("size", ctypes.c_uint64), ("dropped", ctypes.c_uint64), ("exchanges", ctypes.c_uint64),
         ("stash_used", ctypes.c_uint32), ("overflow_used", ctypes.c_uint32),
-        ("rebuilds", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("reserved_", ctypes.c_uint64 * 4),
+        ("rebuilds", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("probes", ctypes.c_uint64),
+        ("reserved_", ctypes.c_uint64 * 3),
     ]
 
 

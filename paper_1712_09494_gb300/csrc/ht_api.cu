@@ -657,6 +657,7 @@ ht_status ht_stats(ht_table* t, ht_table_stats* out, void* stream) {
     out->size = c.size;
     out->dropped = c.dropped;
     out->exchanges = c.exchanges;
+    out->probes = c.probes;
     out->stash_used = c.stash_used;
     out->overflow_used = c.ovf_used;
     out->rebuilds = t->rebuilds;

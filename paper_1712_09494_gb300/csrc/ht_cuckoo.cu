@@ -62,6 +62,7 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     const uint64_t rounds = (n + stride * kU - 1) / (stride * kU);     // warp-uniform trip count
     const uint64_t dseed = t.aux_seed * 3 + 1;
     const int lane = threadIdx.x & 31;
+    unsigned long long probes = 0;            // slots read (h_1, then h_2..h_k if h_1 is occupied)
     // The next round's keys are loaded while this round waits on the table.
     uint64_t next_key[kU];
 #pragma unroll
@@ -97,6 +98,7 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         for (int u = 0; u < kU; ++u) {
             found[u] = act[u] && K::keyof(w[u]) == key[u];
             more[u] = act[u] && !found[u] && !K::empty(w[u]);
+            probes += act[u] ? (more[u] ? t.k : 1u) : 0u;
         }
         uint64_t ws[kU][KH];
 #pragma unroll
@@ -196,6 +198,8 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             }
         }
     }
+    for (int o = 16; o; o >>= 1) probes += __shfl_down_sync(0xFFFFFFFFu, probes, o);
+    if (lane == 0 && probes) atomicAdd(&t.ctr->probes, probes);
 }
 
 // Eviction-chain insert of the winners.  Each thread keeps U chains in

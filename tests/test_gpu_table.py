@@ -281,8 +281,12 @@ def test_stats_counters(oracle_lib, scheme):
     if scheme == "cuckoo":
         assert st["exchanges"] >= fs.n_distinct - st["stash_used"] - st["overflow_used"]
         assert st["exchanges"] < 50 * fs.n_distinct
+        # Every key reads h_1; a key reads all k slots only when h_1 is occupied.
+        assert fs.n_issued <= st["probes"] <= 4 * fs.n_issued
+        assert st["probes"] < 4 * fs.n_issued * 0.9           # early exits happen at load 0.85
     else:
         assert st["exchanges"] == 0
+        assert 0 <= st["probes"] < fs.n_issued                # later buckets are the exception
     t.clear()
     st = t.stats()
     assert st["size"] == st["exchanges"] == st["stash_used"] == st["overflow_used"] == 0

@@ -205,9 +205,9 @@ typedef struct ht_table_stats {
                                  2 rebuild pending, 4 key dropped */
     uint64_t probes;          /* Cuckoo: slots read by find-or-put and lookup
                                  probes (h_1, then h_2..h_k when h_1 is occupied);
-                                 bucket scheme: buckets read beyond each key's
-                                 first (later hash functions, Section 4.2);
-                                 0 for 128-bit tables */
+                                 0 for the bucket scheme (a per-key count there
+                                 would put one shared counter on the hot path)
+                                 and for 128-bit tables */
     uint64_t reserved_[3];
 } ht_table_stats;
 

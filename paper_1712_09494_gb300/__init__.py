@@ -496,3 +496,25 @@ class HashTable:
 
     def grow(self, new_capacity, stream=None):
         ht_grow(self._h, new_capacity, stream)
+
+    # Checkpoint / resume: the stored keys (and values) with the table's
+    # shape, written with numpy; load re-creates the table and inserts them.
+    def save(self, path, stream=None):
+        import numpy as np
+        keys, vals = self.export(stream)
+        info = self.info()
+        np.savez(path, keys=keys.cpu().numpy(), values=(vals.cpu().numpy() if vals is not None else np.empty(0)),
+                 scheme=int(self.scheme), key_width=self.key_width, slots=info["slots"])
+
+    @classmethod
+    def load(cls, path, params=None, stream=None):
+        import numpy as np
+        z = np.load(path)
+        t = cls(int(z["slots"]), int(z["scheme"]), int(z["key_width"]), params, stream)
+        keys = z["keys"]
+        if len(keys):
+            dev = torch.device("cuda", torch.cuda.current_device())
+            k = torch.from_numpy(keys).to(dev)
+            v = torch.from_numpy(z["values"]).to(dev) if t.key_width == 32 and len(z["values"]) else None
+            t.insert(k, v, stream)
+        return t

@@ -105,7 +105,6 @@ __device__ __noinline__ uint32_t claim_slow(const DevTable t, bool active, uint6
                 owner = gbase + __ffs(E) - 1;
             } else if (++f < t.k) {
                 b = hidx(key, t.seed[f], t.nbuckets);
-                if (sub == 0) atomicAdd(&t.ctr->probes, 1ull);   // rare: a later bucket
                 uint64_t nw[SPL];
                 load_lane<SPL>(t.slots + b * BS + sub * SPL, nw);
                 scan_lane<KW, SPL>(nw, key, lm, le);

@@ -32,8 +32,7 @@ struct DevCounters {
     unsigned int winners[2];      // Cuckoo dedup winners per chunk parity
     unsigned int pad0_;
     unsigned long long exchanges; // Cuckoo: atomic exchanges made by insert chains
-    unsigned long long probes;    // Cuckoo: slots the probes read; bucket: buckets read
-                                  // beyond each key's first (later hash functions)
+    unsigned long long probes;    // Cuckoo: slots the probes read (bucket scheme: not counted)
     unsigned int pad_[4];
 };
 static_assert(sizeof(DevCounters) == 72, "counter block layout");

@@ -286,7 +286,7 @@ def test_stats_counters(oracle_lib, scheme):
         assert st["probes"] < 4 * fs.n_issued * 0.9           # early exits happen at load 0.85
     else:
         assert st["exchanges"] == 0
-        assert 0 <= st["probes"] < fs.n_issued                # later buckets are the exception
+        assert st["probes"] == 0                              # not counted for the bucket scheme
     t.clear()
     st = t.stats()
     assert st["size"] == st["exchanges"] == st["stash_used"] == st["overflow_used"] == 0
@@ -354,3 +354,26 @@ def test_auto_grow_at_synchronising_calls(oracle_lib, scheme):
     assert t.size() == 200_000 and t.info()["slots"] >= 200_000 / 0.8
     k, _ = t.export()
     assert_same_set(keys_np(k, 64), orc.export()[0])
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("kw", [32, 64, 128])
+def test_checkpoint_save_and_load(oracle_lib, scheme, kw, tmp_path):
+    n = 30_000
+    if kw == 128:
+        lo = wk.distinct_keys(n, 64, seed=81)
+        keys = torch.from_numpy(np.stack([lo, lo ^ np.uint64(12345)], axis=1).view(np.int64)).cuda()
+        vals = None
+    else:
+        keys = to_dev(wk.distinct_keys(n, kw, seed=81))
+        vals = to_dev(np.arange(n, dtype=np.uint32)) if kw == 32 else None
+    t = ht.HashTable(40_000, scheme, kw)
+    t.insert(keys, vals)
+    path = str(tmp_path / "table.npz")
+    t.save(path)
+    r = ht.HashTable.load(path)
+    assert r.size() == n and r.info()["slots"] == t.info()["slots"] and r.key_width == kw
+    f, v = r.lookup(keys)
+    assert to_np(f).all()
+    if kw == 32:
+        np.testing.assert_array_equal(to_np(v, np.uint32), np.arange(n, dtype=np.uint32))

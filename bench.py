@@ -1079,15 +1079,18 @@ def run_cpu_oracle(a, sample_batches=4):
     import oracle
     from workloads import keys as wk
     n = 1 << a.n_log2
-    fs = wk.fill_stream(n, 1 << a.batch_log2, a.dup, 64, seed=a.seed)
-    nb = min(sample_batches, fs.n_batches)
+    B = 1 << a.batch_log2
+    per_batch_fresh = max(1, int(round(B * (1.0 - a.dup))))
+    total_batches = -(-n // per_batch_fresh)
+    fs = wk.fill_stream(n, B, a.dup, 64, seed=a.seed, max_batches=sample_batches)
+    nb = fs.n_batches
     keys = fs.keys[:fs.offsets[nb]]
     t = oracle.OracleTable(reserve=n)
     t0 = time.perf_counter()
     t.find_or_put(keys)
     dt = time.perf_counter() - t0
     return len(keys) / dt / 1e6, "first %d of %d batches of the stream (%d keys, one scheme-free set)" % (
-        nb, fs.n_batches, len(keys))
+        nb, total_batches, len(keys))
 
 
 def run_reference(a, rank, world):

@@ -46,6 +46,17 @@ def test_fill_stream_shape(d, width):
         assert abs(fs.n_issued - n / (1 - d)) < fs.n_batches + 2
 
 
+@pytest.mark.parametrize("nb", [1, 2, 5, 100])
+def test_fill_stream_prefix_matches_full(nb):
+    full = wk.fill_stream(5000, 1024, 0.25, 64, seed=7)
+    pre = wk.fill_stream(5000, 1024, 0.25, 64, seed=7, max_batches=nb)
+    m = min(nb, full.n_batches)
+    assert pre.n_batches == m
+    assert np.array_equal(pre.offsets, full.offsets[:m + 1])
+    assert np.array_equal(pre.keys, full.keys[:full.offsets[m]])
+    assert np.array_equal(pre.fresh_counts, full.fresh_counts[:m])
+
+
 def test_lookup_batch_split():
     keys, present = wk.lookup_batch(1000, 2001, 64, seed=1)
     stored = set(wk.distinct_keys(1000, 64, seed=1).tolist())

@@ -109,23 +109,29 @@ class FillStream:
         return int(self.offsets[-1])
 
 
-def fill_stream(n_distinct, batch, dup_rate, width, seed):
+def fill_stream(n_distinct, batch, dup_rate, width, seed, max_batches=None):
     """Batches that take an empty table to exactly ``n_distinct`` keys.
 
     Batch b holds f = round((1-d)*B) fresh keys (fewer in the last batch) and
     round(f*d/(1-d)) repeats drawn uniformly from every key issued up to and
     including this batch's fresh ones, so repeats occur both across and
     within batches.  Each batch is shuffled.
+
+    ``max_batches`` stops after that many batches; the batches made are the
+    same as the full stream's first ones (fresh key i depends only on i and
+    the random draws come in the same order), so a CPU sample of a large
+    stream need not generate all of it.
     """
     if not 0.0 <= dup_rate < 1.0:
         raise ValueError("dup_rate must be in [0, 1)")
     rng = np.random.Generator(np.random.PCG64(seed))
-    fresh = distinct_keys(n_distinct, width, seed)
     per_batch_fresh = max(1, int(round(batch * (1.0 - dup_rate))))
+    n_fresh = n_distinct if max_batches is None else min(n_distinct, max_batches * per_batch_fresh)
+    fresh = distinct_keys(n_fresh, width, seed)
     parts, offsets, fresh_counts = [], [0], []
     issued = 0
-    while issued < n_distinct:
-        nf = min(per_batch_fresh, n_distinct - issued)
+    while issued < n_fresh:
+        nf = min(per_batch_fresh, n_fresh - issued)
         nd = batch - nf if nf == per_batch_fresh else int(round(nf * dup_rate / (1.0 - dup_rate)))
         end = issued + nf
         b = np.empty(nf + nd, dtype=fresh.dtype)

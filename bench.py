@@ -419,6 +419,7 @@ def run_ours(a, rank, world, local):
         out["sweep_config2"] = run_sweep(ht, torch, dev)
         out["replay_multiplicity"] = run_replay(ht, torch, dev)
         out["wide_keys_128"] = run_wide(ht, torch, dev)
+        out["long_keys_256_512"] = run_long(ht, torch, dev)
         out["wide_bfs_80bit"] = run_wide_bfs(ht, torch, dev)
     if not a.no_bfs:
         out["bfs_config3"] = run_bfs(ht, torch, dev, schemes)
@@ -792,6 +793,58 @@ def run_wide(ht, torch, dev, n_log2=26, batch_log2=24, dup=0.25, lf=0.8, reps=3)
         out[name] = {"ms_per_fill": round(ms, 2), "mops": round(issued / (ms / 1e3) / 1e6, 1),
                      "exact": t.sync() == 0 and t.size() == n}
         t.close()
+    return out
+
+
+def run_long(ht, torch, dev, n_log2=25, batch_log2=23, dup=0.25, lf=0.8, reps=2):
+    """Keys of 4 and 8 64-bit words (256 and 512 bits), both schemes: a fill of
+    2^25 random keys to load 0.8 in batches of 2^23 with 25% repeats, then a
+    lookup of 2^23 stored and 2^23 absent keys.  Word 0 is a 63-bit stream
+    key and the others bijections of it, so distinct stream keys give
+    distinct keys; exact when the table ends with exactly 2^25 keys and the
+    lookups find exactly the stored half."""
+    from workloads import device_keys as dk
+    n = 1 << n_log2
+    batches, _ = dk.fill_batches_dev(n, 1 << batch_log2, dup, seed=93, device=dev)
+    issued = sum(b.numel() for b in batches)
+    out = {"workload": "2^%d random keys of 4 and 8 words to load %.1f, batches 2^%d, %d%% repeats; lookups of "
+                       "2^%d present + 2^%d absent" % (n_log2, lf, batch_log2, int(dup * 100), batch_log2, batch_log2)}
+    q_in = batches[0][: 1 << batch_log2]
+    for w in (4, 8):
+        def widen(b):
+            return torch.stack([b] + [dk.mix63_perm_dev(b, 95 + j) for j in range(w - 1)], dim=1).contiguous()
+        rows = [widen(b) for b in batches]
+        # Absent keys: stored keys with the last word's low bit flipped (a
+        # stored key's last word is fixed by its first).
+        absent = widen(q_in)
+        absent[:, w - 1] ^= 1
+        q = torch.cat([widen(q_in), absent])
+        flags = torch.empty(max(r.shape[0] for r in rows), dtype=torch.uint8, device=dev)
+        found = torch.empty(q.shape[0], dtype=torch.uint8, device=dev)
+        for sch in ("bucket", "cuckoo"):
+            t = ht.HashTable(int(np.ceil(n / lf)), sch, 64 * w)
+            times, ltimes = [], []
+            for r in range(reps + 1):
+                ht.ht_clear(t.handle)
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record()
+                for b in rows:
+                    ht.ht_find_or_put(t.handle, b, flags[:b.shape[0]])
+                e1.record()
+                ht.ht_lookup(t.handle, q, None, found)
+                e2.record()
+                torch.cuda.synchronize()
+                if r:
+                    times.append(e0.elapsed_time(e1))
+                    ltimes.append(e1.elapsed_time(e2))
+            ms, lms = statistics.median(times), statistics.median(ltimes)
+            half = q.shape[0] // 2
+            exact = (t.sync() == 0 and t.size() == n and bool(found[:half].all()) and not bool(found[half:].any()))
+            out["w%d_%s" % (w, sch)] = {"key_bits": 64 * w, "ms_per_fill": round(ms, 2),
+                                        "mops": round(issued / (ms / 1e3) / 1e6, 1),
+                                        "lookup_mops": round(q.shape[0] / (lms / 1e3) / 1e6, 1), "exact": exact}
+            t.close()
+        del rows, q
     return out
 
 

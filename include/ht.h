@@ -82,7 +82,13 @@ typedef enum {
  *                  using its overflow set, doubles its capacity (ht_grow)
  *                  until it is below (100..1000; 0 = off).  Between two
  *                  synchronising calls the keys still have to fit the table,
- *                  stash and overflow set as they are.  */
+ *                  stash and overflow set as they are.
+ *   digest_bits    keys wider than 128 bits only: 0 (default) or 64 keeps
+ *                  the whole 64-bit key digest; 1..63 keeps only its low
+ *                  bits, so that distinct keys share digests.  A test knob:
+ *                  it makes the full-key comparisons that tell such keys
+ *                  apart run often (results are unchanged; placement gets
+ *                  worse).  Other key widths: must be 0.  */
 typedef struct ht_params {
     uint32_t num_hashes;
     uint32_t max_evictions;
@@ -94,7 +100,8 @@ typedef struct ht_params {
     uint64_t seed;
     int32_t l2_persist;
     uint32_t grow_load_permille;
-    int32_t reserved_[2];
+    uint32_t digest_bits;
+    int32_t reserved_;
 } ht_params;
 
 typedef struct ht_table ht_table;

@@ -66,6 +66,15 @@ def _load():
         lib.orc128_lookup.argtypes = [VP, VP, U64, VP]
         lib.orc128_export.restype = U64
         lib.orc128_export.argtypes = [VP, VP, U64]
+        lib.orclong_new.restype = VP
+        lib.orclong_new.argtypes = [U32]
+        lib.orclong_free.argtypes = [VP]
+        lib.orclong_size.restype = U64
+        lib.orclong_size.argtypes = [VP]
+        lib.orclong_find_or_put.argtypes = [VP, VP, U64, VP]
+        lib.orclong_lookup.argtypes = [VP, VP, U64, VP]
+        lib.orclong_export.restype = U64
+        lib.orclong_export.argtypes = [VP, VP, U64]
         lib.orc_successors.restype = U64
         lib.orc_successors.argtypes = [P(Model), U64, VP, U64]
         lib.orc_successors128.restype = U64
@@ -130,6 +139,54 @@ class OracleTable128:
         n = self.size()
         out = np.empty((max(n, 1), 2), dtype=np.uint64)
         got = int(self._lib.orc128_export(self._h, _ptr(out), n))
+        return out[:got]
+
+
+class OracleTableLong:
+    """The plain set definition for keys of ``words`` 64-bit words (an
+    ordered std::set of word vectors, one thread).  Keys are (n, words)
+    uint64 arrays, one key per row."""
+
+    def __init__(self, words):
+        self._lib = _load()
+        self.words = int(words)
+        if self.words < 1:
+            raise ValueError("words must be >= 1")
+        self._h = self._lib.orclong_new(self.words)
+
+    def close(self):
+        if self._h:
+            self._lib.orclong_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def size(self):
+        return int(self._lib.orclong_size(self._h))
+
+    def _k(self, keys):
+        return np.ascontiguousarray(np.asarray(keys).astype(np.uint64, copy=False).reshape(-1, self.words))
+
+    def find_or_put(self, keys):
+        k = self._k(keys)
+        out = np.empty(len(k), dtype=np.uint8)
+        self._lib.orclong_find_or_put(self._h, _ptr(k), len(k), _ptr(out))
+        return out
+
+    def lookup(self, keys):
+        k = self._k(keys)
+        found = np.empty(len(k), dtype=np.uint8)
+        self._lib.orclong_lookup(self._h, _ptr(k), len(k), _ptr(found))
+        return found
+
+    def export(self):
+        n = self.size()
+        out = np.empty((max(n, 1), self.words), dtype=np.uint64)
+        got = int(self._lib.orclong_export(self._h, _ptr(out), n))
         return out[:got]
 
 

@@ -31,6 +31,7 @@
 #include <unordered_map>
 #include <unordered_set>
 #include <utility>
+#include <set>
 #include <vector>
 
 namespace {
@@ -155,6 +156,54 @@ uint64_t orc128_export(const void* h, uint64_t* keys, uint64_t cap) {
             keys[2 * i] = k.first;
             keys[2 * i + 1] = k.second;
         }
+        ++i;
+    }
+    return i;
+}
+
+// Sets of long keys (W 64-bit words each, W >= 1): keys[W*i .. W*i+W) is
+// key i.  The same definition as above -- find, else insert, in order
+// (Section 5) -- over an ordered set of word vectors, so two keys are equal
+// exactly when all their words are.
+struct TableLong {
+    uint32_t words;
+    std::set<std::vector<uint64_t>> s;
+};
+
+void* orclong_new(uint32_t words) {
+    if (words == 0) return nullptr;
+    TableLong* t = new TableLong();
+    t->words = words;
+    return t;
+}
+
+void orclong_free(void* h) { delete static_cast<TableLong*>(h); }
+
+uint64_t orclong_size(const void* h) { return static_cast<const TableLong*>(h)->s.size(); }
+
+void orclong_find_or_put(void* h, const uint64_t* keys, uint64_t n, uint8_t* is_new) {
+    TableLong* t = static_cast<TableLong*>(h);
+    const uint32_t w = t->words;
+    for (uint64_t i = 0; i < n; ++i) {
+        const bool inserted = t->s.insert(std::vector<uint64_t>(keys + w * i, keys + w * i + w)).second;
+        if (is_new) is_new[i] = inserted ? 1 : 0;
+    }
+}
+
+void orclong_lookup(const void* h, const uint64_t* keys, uint64_t n, uint8_t* found) {
+    const TableLong* t = static_cast<const TableLong*>(h);
+    const uint32_t w = t->words;
+    for (uint64_t i = 0; i < n; ++i)
+        found[i] = t->s.count(std::vector<uint64_t>(keys + w * i, keys + w * i + w)) ? 1 : 0;
+}
+
+// Copies out up to cap keys in the set's (lexicographic) order; returns |S|.
+uint64_t orclong_export(const void* h, uint64_t* keys, uint64_t cap) {
+    const TableLong* t = static_cast<const TableLong*>(h);
+    uint64_t i = 0;
+    for (const auto& k : t->s) {
+        if (i < cap)
+            for (uint32_t j = 0; j < t->words; ++j) keys[t->words * i + j] = k[j];
         ++i;
     }
     return i;

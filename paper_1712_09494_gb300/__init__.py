@@ -63,18 +63,19 @@ def _dptr(t, what):
 
 
 def _key_width(keys):
-    """32 or 64 for a 1-D int32/int64 tensor; 128 for an (n, 2) int64 tensor
-    of (low word, high word) pairs."""
+    """32 or 64 for a 1-D int32/int64 tensor; 64*W for an (n, W) int64
+    tensor of W words per key (W = 2: (low word, high word) pairs; W = 3..8:
+    long keys)."""
     es = keys.element_size()
-    if es == 8 and keys.dim() == 2 and keys.shape[1] == 2:
-        return 128
+    if es == 8 and keys.dim() == 2 and 2 <= keys.shape[1] <= 8:
+        return 64 * keys.shape[1]
     if es not in (4, 8):
         raise ValueError("keys must be 32- or 64-bit integers")
     return es * 8
 
 
 def _nkeys(keys):
-    return keys.shape[0] if _key_width(keys) == 128 else keys.numel()
+    return keys.shape[0] if _key_width(keys) >= 128 else keys.numel()
 
 
 def _params(params, scheme):
@@ -479,7 +480,7 @@ class HashTable:
         n = self.size(stream)
         dt = torch.int32 if self.key_width == 32 else torch.int64
         dev = torch.device("cuda", torch.cuda.current_device())
-        shape = (max(n, 1), 2) if self.key_width == 128 else (max(n, 1),)
+        shape = (max(n, 1), self.key_width // 64) if self.key_width >= 128 else (max(n, 1),)
         keys = torch.empty(shape, dtype=dt, device=dev)
         vals = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if self.key_width == 32 else None
         got = ht_export(self._h, keys, vals, stream)

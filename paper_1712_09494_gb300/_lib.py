@@ -15,7 +15,8 @@ class HtParams(ctypes.Structure):
         ("stash_slots", ctypes.c_uint32), ("bucket_slots", ctypes.c_uint32),
         ("lanes_per_key", ctypes.c_uint32), ("max_rebuilds", ctypes.c_uint32),
         ("max_batch", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-        ("l2_persist", ctypes.c_int32), ("grow_load_permille", ctypes.c_uint32), ("reserved_", ctypes.c_int32 * 2),
+        ("l2_persist", ctypes.c_int32), ("grow_load_permille", ctypes.c_uint32),
+        ("digest_bits", ctypes.c_uint32), ("reserved_", ctypes.c_int32),
     ]
 
 

@@ -39,6 +39,8 @@ void derive_seeds(ht_table* t) {
     t->dt.aux_seed = mix64(t->seed_base ^ 0xD1B54A32D192ED03ull);
 }
 
+bool is_long(uint32_t kw) { return kw > 128; }
+
 BucketCfg bucket_cfg(const ht_table* t) {
     return BucketCfg{int(t->kw), int(t->p.bucket_slots), int(t->p.lanes_per_key)};
 }
@@ -70,10 +72,12 @@ struct DeviceGuard {
 };
 
 ht_status clear_table(ht_table* t, cudaStream_t s) {
-    const uint64_t w = t->kw == 128 ? 2 : 1;     // words per slot
+    // Words per slot: 2 for 128-bit keys and long-key Cuckoo entries.
+    const uint64_t w = (t->kw == 128 || (is_long(t->kw) && t->scheme == HT_CUCKOO)) ? 2 : 1;
+    const uint64_t wo = t->kw >= 128 ? 2 : 1;    // words per overflow entry
     HT_TRY(fill_words(t->dt.slots, t->dt.nslots * w, kEmpty, s));
     HT_TRY(fill_words(t->dt.stash, t->dt.stash_slots, kEmpty, s));
-    HT_TRY(fill_words(t->dt.ovf, t->dt.ovf_slots * w, kEmpty, s));
+    HT_TRY(fill_words(t->dt.ovf, t->dt.ovf_slots * wo, kEmpty, s));
     HT_TRY(cudaMemsetAsync(t->dt.ctr, 0, sizeof(DevCounters), s));
     return HT_OK;
 }
@@ -82,6 +86,7 @@ ht_status clear_table(ht_table* t, cudaStream_t s) {
 cudaError_t export_any(ht_table* t, void* keys, uint32_t* vals, unsigned long long* cnt, uint64_t cap,
                        cudaStream_t s) {
     if (t->kw == 128) return wide_export(t->dt, keys, cnt, cap, s);
+    if (is_long(t->kw)) return long_export(t->dt, t->scheme == HT_CUCKOO, keys, cnt, cap, s);
     return table_export(int(t->kw), t->dt, keys, vals, cnt, cap, s);
 }
 
@@ -90,6 +95,19 @@ ht_status run_put(ht_table* t, const void* keys, const uint32_t* vals, uint64_t 
                   void* new_out, unsigned long long* new_count, cudaStream_t s,
                   const unsigned long long* d_n = nullptr, uint64_t new_cap = ~0ull) {
     if (n == 0) return HT_OK;
+    if (is_long(t->kw)) {
+        if (vals || new_out || d_n) return HT_ERR_INVALID;
+        if (t->scheme == HT_BUCKET) return cuda_status(long_find_or_put(t->dt, keys, n, is_new, s));
+        const size_t ksz = t->kw / 8;
+        for (uint64_t off = 0; off < n; off += t->chunk) {
+            const uint64_t m = std::min(t->chunk, n - off);
+            HT_TRY(long_cuckoo_probe(t->dt, t->sc, t->parity, static_cast<const char*>(keys) + off * ksz, m,
+                                     is_new ? is_new + off : nullptr, s));
+            HT_TRY(long_cuckoo_insert(t->dt, t->sc, t->parity, std::min<uint64_t>(m, t->sc.win_cap), s));
+            t->parity ^= 1u;
+        }
+        return HT_OK;
+    }
     if (t->kw == 128) {
         if (vals) return HT_ERR_INVALID;
         if (t->scheme == HT_BUCKET)
@@ -224,6 +242,7 @@ ht_status sync_and_status(ht_table* t, cudaStream_t s) {
         if (st != HT_OK) return st;
     }
     if (c.flags & kFlagDropped) t->sticky = HT_ERR_FULL;
+    if (c.flags & kFlagTimeout) t->sticky = HT_ERR_TIMEOUT;
     if (c.flags & kFlagInvalidKey) {
         // Reported once, then cleared.
         unsigned int f = c.flags & ~kFlagInvalidKey;
@@ -276,7 +295,7 @@ ht_params complete_params(ht_scheme scheme, const ht_params* in) {
 // table can be released without synchronising the whole device.
 void free_table(ht_table* t, cudaStream_t s) {
     if (!t) return;
-    void* ptrs[] = {t->dt.slots, t->dt.stash, t->dt.ovf, t->dt.ctr, t->sc.set, t->sc.win};
+    void* ptrs[] = {t->dt.slots, t->dt.stash, t->dt.ovf, t->dt.ctr, t->sc.set, t->sc.win, t->dt.kstore};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
     delete t;
@@ -394,8 +413,20 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
     *out = nullptr;
     if (capacity == 0 || capacity > kMaxCapacity) return HT_ERR_INVALID;
     if (scheme != HT_BUCKET && scheme != HT_CUCKOO) return HT_ERR_INVALID;
-    if (key_width != 32 && key_width != 64 && key_width != 128) return HT_ERR_INVALID;
+    const bool long_keys = is_long(key_width) && key_width % 64 == 0 && key_width / 64 >= kLongMinWords &&
+                           key_width / 64 <= kLongMaxWords;
+    if (key_width != 32 && key_width != 64 && key_width != 128 && !long_keys) return HT_ERR_INVALID;
     ht_params p = complete_params(scheme, params);
+    if (p.digest_bits > 64 || (p.digest_bits && !long_keys)) return HT_ERR_INVALID;
+    if (long_keys) {
+        // Bucket scheme: 16 header words per bucket, one thread per key
+        // (lanes_per_key unused).  Cuckoo: 16-byte entries, no stash.
+        if (scheme == HT_BUCKET) {
+            if (!params || !params->bucket_slots) p.bucket_slots = kLongBucketSlots;
+            if (p.bucket_slots != kLongBucketSlots) return HT_ERR_INVALID;
+        }
+        p.stash_slots = 0;
+    }
     if (key_width == 128) {
         // 16-byte slots; no stash (the overflow set takes what does not fit).
         // Bucket scheme: buckets of 8 (one 128-byte line), 2 or 4 lanes.
@@ -434,10 +465,20 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
         return cuda_status(e);
     };
     cudaError_t e;
-    const uint64_t slot_bytes = key_width == 128 ? 16 : 8;
+    const uint64_t slot_bytes = (key_width == 128 || (long_keys && scheme == HT_CUCKOO)) ? 16 : 8;
+    const uint64_t ovf_bytes = key_width >= 128 ? 16 : 8;
     if ((e = cudaMallocAsync(&t->dt.slots, t->dt.nslots * slot_bytes, cs)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocAsync(&t->dt.stash, std::max<uint32_t>(t->dt.stash_slots, 1) * 8, cs)) != cudaSuccess) return fail(e);
-    if ((e = cudaMallocAsync(&t->dt.ovf, uint64_t(t->dt.ovf_slots) * slot_bytes, cs)) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocAsync(&t->dt.ovf, uint64_t(t->dt.ovf_slots) * ovf_bytes, cs)) != cudaSuccess) return fail(e);
+    t->dt.digest_mask = p.digest_bits == 0 || p.digest_bits == 64 ? ~0ull : (1ull << p.digest_bits) - 1;
+    if (long_keys) {
+        // Key store: one row per slot (bucket scheme), or one per key the
+        // table, its overflow set included, can hold (Cuckoo).
+        t->dt.words = key_width / 64;
+        t->dt.kstore_rows = t->dt.nslots + (scheme == HT_CUCKOO ? t->dt.ovf_slots : 0);
+        if ((e = cudaMallocAsync(&t->dt.kstore, t->dt.kstore_rows * t->dt.words * 8, cs)) != cudaSuccess)
+            return fail(e);
+    }
     if ((e = cudaMallocAsync(&t->dt.ctr, sizeof(DevCounters), cs)) != cudaSuccess) return fail(e);
     if (scheme == HT_CUCKOO) {
         // Keys per probe/insert launch pair: max_batch.  Unless the table
@@ -452,8 +493,8 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
         const uint64_t sslots = next_pow2(2 * sc_cap);
         t->sc.mask = sslots - 1;
         t->sc.win_cap = sc_cap;
-        const uint64_t set_words = key_width == 128 ? 2 : 1;
-        const uint64_t win_bytes = key_width == 128 ? kWideWinnerBytes : sizeof(Winner);
+        const uint64_t set_words = key_width >= 128 ? 2 : 1;
+        const uint64_t win_bytes = key_width >= 128 ? kWideWinnerBytes : sizeof(Winner);
         if ((e = cudaMallocAsync(&t->sc.set, sslots * 8 * set_words, cs)) != cudaSuccess) return fail(e);
         if ((e = cudaMallocAsync(&t->sc.win, sc_cap * win_bytes, cs)) != cudaSuccess) return fail(e);
         if ((e = fill_words(t->sc.set, sslots * set_words, kEmpty, cs)) != cudaSuccess) return fail(e);
@@ -471,7 +512,7 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
         cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
         const size_t table_bytes = t->dt.nslots * slot_bytes;
         if (table_bytes <= size_t(max_persist)) t->win = l2_window(t->dt.slots, table_bytes);
-        else if (scheme == HT_CUCKOO) t->win = l2_window(t->sc.set, (t->sc.mask + 1) * 8);
+        else if (scheme == HT_CUCKOO) t->win = l2_window(t->sc.set, (t->sc.mask + 1) * (key_width >= 128 ? 16 : 8));
     }
     *out = t;
     return HT_OK;
@@ -492,6 +533,7 @@ static ht_status put_common(ht_table* t, const void* keys, const uint32_t* vals,
     if (n && !keys) return HT_ERR_INVALID;
     if (vals && t->kw != 32) return HT_ERR_INVALID;
     if ((new_out == nullptr) != (new_count == nullptr)) return HT_ERR_INVALID;
+    if (is_long(t->kw) && (new_out || (reinterpret_cast<uintptr_t>(keys) & 7))) return HT_ERR_INVALID;
     DeviceGuard g(t->device);
     return run_put(t, keys, vals, n, is_new, new_out, new_count, as_stream(stream));
 }
@@ -516,6 +558,11 @@ ht_status ht_lookup(ht_table* t, const void* d_keys, uint64_t n, uint32_t* d_val
     if (n == 0) return HT_OK;
     DeviceGuard g(t->device);
     const cudaStream_t s = as_stream(stream);
+    if (is_long(t->kw)) {
+        if (d_values || (reinterpret_cast<uintptr_t>(d_keys) & 7)) return HT_ERR_INVALID;
+        if (t->scheme == HT_CUCKOO) return cuda_status(long_cuckoo_lookup(t->dt, d_keys, n, d_found, s));
+        return cuda_status(long_lookup(t->dt, d_keys, n, d_found, s));
+    }
     if (t->kw == 128) {
         if (d_values) return HT_ERR_INVALID;
         if (t->scheme == HT_CUCKOO) return cuda_status(wide_cuckoo_lookup(t->dt, d_keys, n, d_found, s));
@@ -530,7 +577,7 @@ ht_status ht_multi_find_or_put(ht_table* const* tables, uint32_t ntables, const 
                                void* stream) {
     if (m && (!tables || !list)) return HT_ERR_INVALID;
     for (uint32_t i = 0; i < m; ++i) {
-        if (list[i].table >= ntables || !tables[list[i].table] || tables[list[i].table]->kw == 128)
+        if (list[i].table >= ntables || !tables[list[i].table] || tables[list[i].table]->kw >= 128)
             return HT_ERR_INVALID;
         if (list[i].n && !list[i].d_keys) return HT_ERR_INVALID;
     }
@@ -686,6 +733,7 @@ namespace {
 // returns the largest number of successors one state can have (0 = invalid).
 uint64_t ht::model_max_successors(const ht_model* m, uint32_t key_width) {
     if (!m || m->num_components < 1 || m->num_components > 16 || m->num_pairs < 0 || m->num_pairs > 8) return 0;
+    if (key_width != 32 && key_width != 64 && key_width != 128) return 0;
     uint32_t bits = 0;
     for (int c = 0; c < m->num_components; ++c) {
         if (m->bits[c] < 1 || m->bits[c] > 5) return 0;

@@ -21,6 +21,7 @@ enum : uint32_t {
     kFlagInvalidKey = 1u,   // a reserved key was seen
     kFlagRebuild = 2u,      // the stash overflowed: rebuild with new constants
     kFlagDropped = 4u,      // a key found no place at all (table full)
+    kFlagTimeout = 8u,      // a bounded wait for a claimed slot's publish gave up
 };
 
 struct DevCounters {
@@ -33,7 +34,8 @@ struct DevCounters {
     unsigned int pad0_;
     unsigned long long exchanges; // Cuckoo: atomic exchanges made by insert chains
     unsigned long long probes;    // Cuckoo: slots the probes read (bucket scheme: not counted)
-    unsigned int pad_[4];
+    unsigned long long ids;       // long-key Cuckoo: key-store rows handed out
+    unsigned int pad_[2];
 };
 static_assert(sizeof(DevCounters) == 72, "counter block layout");
 
@@ -51,6 +53,14 @@ struct DevTable {
     uint32_t max_evict;       // Cuckoo eviction bound
     uint64_t aux_seed;        // stash / overflow / dedup start positions
     uint64_t seed[kMaxHashes];
+    // Keys of more than two words (ht_long.cu): the key store (words per key
+    // x rows), its rows, and the mask applied to every key digest (all ones
+    // except in tests that force digest collisions).
+    uint64_t* kstore;
+    uint64_t kstore_rows;
+    uint64_t digest_mask;
+    uint32_t words;
+    uint32_t pad_w_;
 };
 
 // A Cuckoo insertion job: the packed word and where its dedup claim sits.
@@ -442,6 +452,24 @@ cudaError_t wide_cuckoo_insert(const DevTable& t, const DevScratch& sc, uint32_t
                                cudaStream_t s);
 cudaError_t wide_cuckoo_lookup(const DevTable& t, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s);
 constexpr uint64_t kWideWinnerBytes = 32;
+
+// Tables of keys of W = 3..8 64-bit words (ht_long.cu).  Keys are rows of W
+// words, 8-byte aligned.  Bucket scheme: `slots` holds one header word per
+// slot and the key store one row per slot; Cuckoo: `slots` holds 16-byte
+// (digest, row) entries and the key store one row per key placed.
+constexpr uint32_t kLongMinWords = 3;
+constexpr uint32_t kLongMaxWords = 8;
+constexpr uint32_t kLongBucketSlots = 16;
+cudaError_t long_find_or_put(const DevTable& t, const void* keys, uint64_t n, uint8_t* is_new, cudaStream_t s);
+cudaError_t long_lookup(const DevTable& t, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s);
+cudaError_t long_cuckoo_probe(const DevTable& t, const DevScratch& sc, uint32_t parity, const void* keys, uint64_t n,
+                              uint8_t* is_new, cudaStream_t s);
+cudaError_t long_cuckoo_insert(const DevTable& t, const DevScratch& sc, uint32_t parity, uint64_t max_winners,
+                               cudaStream_t s);
+cudaError_t long_cuckoo_lookup(const DevTable& t, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s);
+// Every stored key of a long-key table of either scheme to keys (rows).
+cudaError_t long_export(const DevTable& t, bool cuckoo, void* keys, unsigned long long* count, uint64_t cap,
+                        cudaStream_t s);
 
 // Read-only views of a table for the batched form (ht_api.cu).
 const DevTable& table_dev(const ht_table* t);

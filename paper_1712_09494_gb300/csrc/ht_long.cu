@@ -1,0 +1,522 @@
+// Tables of long keys: W = 3..8 64-bit words (192 to 512 bits).  These are
+// GPUexplore's multi-word state vectors (Sections 3.2, 4.2) past what one
+// 16-byte atomic covers, and the generalisation of Cuckoo hashing to keys of
+// any length that Section 7 leaves as future work.
+//
+// No atomic covers a whole key, so a key cannot go from EMPTY to stored in
+// one step; a reader could otherwise see part of a key (the long-element
+// race of Section 4.2).  Both schemes therefore claim a short word
+// atomically and keep the key's words apart from it.
+//
+// Bucket scheme: claim, then publish.  A bucket is 16 header words, one
+// 128-byte line; the key of slot s is row s of the key store.  A header is
+//     EMPTY (all ones) -> BUSY | tag (compare-and-swap claim) -> tag (release store)
+// with tag = the key digest's low 62 bits and BUSY = bit 62.  The claimer
+// writes the key's words between its two steps and waits on nothing there.
+// A reader whose tag matches a header waits (bounded) until the header is
+// published, reads it with acquire semantics and then compares the whole
+// key.  Claims go in slot order over the slots read as EMPTY, and a claim's
+// compare-and-swap returns the header's true state, so the slot-order
+// argument of the one-word kernels carries over unchanged: a key is claimed
+// in at most one slot, and it sits in bucket h_f only if h_1 .. h_{f-1} were
+// full.
+//
+// Cuckoo: indirection.  A slot is a 16-byte entry (digest, row); the key's
+// words sit in row `row` of the key store, written once by the probe kernel
+// that elects the key's winner.  Eviction chains move entries with 16-byte
+// atomic exchanges and take the next position from the digest alone, so a
+// chain reads no key words.  The insert kernel starts after the probe
+// kernel has ended, so every row is complete before an entry points to it.
+#include "ht_internal.cuh"
+
+namespace ht {
+namespace {
+
+constexpr uint64_t kBusy = 1ull << 62;
+constexpr uint64_t kTagMask = kBusy - 1;
+constexpr unsigned kFullMask = 0xFFFFFFFFu;
+constexpr uint32_t kSpinLimit = 1u << 20;     // bounded wait for a publish (~0.1 s)
+constexpr int kLBS = int(kLongBucketSlots);
+
+struct LongWinner {
+    uint64_t digest;
+    uint64_t row;
+    uint64_t spos;     // its entry in the claim set, cleared by the insert
+    uint64_t pad_;
+};
+static_assert(sizeof(LongWinner) == kWideWinnerBytes, "winner record size");
+
+// The digest of a key: mix64 chained over its words, seeded with W.  Hash
+// positions and tags are taken from the digest; equal digests of different
+// keys are told apart by comparing the words.
+__device__ __forceinline__ uint64_t digest_of(const uint64_t (&k)[kLongMaxWords], uint32_t W, uint64_t mask) {
+    uint64_t h = mix64(0x9E3779B97F4A7C15ull * (W + 1));
+#pragma unroll
+    for (uint32_t j = 0; j < kLongMaxWords; ++j)
+        if (j < W) h = mix64(h ^ k[j]);
+    return h & mask;
+}
+
+__device__ __forceinline__ void load_key(const uint64_t* __restrict__ keys, uint64_t i, uint32_t W,
+                                         uint64_t (&k)[kLongMaxWords]) {
+    const uint64_t* p = keys + i * W;
+#pragma unroll
+    for (uint32_t j = 0; j < kLongMaxWords; ++j) k[j] = j < W ? __ldg(p + j) : 0;
+}
+
+__device__ __forceinline__ bool row_equals(const uint64_t* row, const uint64_t (&k)[kLongMaxWords], uint32_t W) {
+    bool eq = true;
+#pragma unroll
+    for (uint32_t j = 0; j < kLongMaxWords; ++j)
+        if (j < W) eq &= __ldcg(reinterpret_cast<const unsigned long long*>(row + j)) == k[j];
+    return eq;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void cas128(uint64_t* addr, uint64_t new_lo, uint64_t new_hi, uint64_t& old_lo,
+                                       uint64_t& old_hi) {
+    asm volatile(
+        "{\n"
+        " .reg .b128 d, c, n;\n"
+        " mov.b128 c, {%2, %3};\n"
+        " mov.b128 n, {%4, %5};\n"
+        " atom.global.cas.b128 d, [%6], c, n;\n"
+        " mov.b128 {%0, %1}, d;\n"
+        "}\n"
+        : "=l"(old_lo), "=l"(old_hi)
+        : "l"(kEmpty), "l"(kEmpty), "l"(new_lo), "l"(new_hi), "l"(addr)
+        : "memory");
+}
+
+__device__ __forceinline__ void exch128(uint64_t* addr, uint64_t lo, uint64_t hi, uint64_t& old_lo,
+                                        uint64_t& old_hi) {
+    asm volatile(
+        "{\n"
+        " .reg .b128 d, n;\n"
+        " mov.b128 n, {%2, %3};\n"
+        " atom.global.exch.b128 d, [%4], n;\n"
+        " mov.b128 {%0, %1}, d;\n"
+        "}\n"
+        : "=l"(old_lo), "=l"(old_hi)
+        : "l"(lo), "l"(hi), "l"(addr)
+        : "memory");
+}
+
+// Bucket scheme: does slot `slot`, whose header carries the key's tag, hold
+// the key?  Waits until the header is published (bounded: past the limit
+// the timeout flag is set and the slot is taken as another key's).
+__device__ bool slot_holds(const DevTable& t, uint64_t slot, const uint64_t (&k)[kLongMaxWords], uint32_t W) {
+    uint64_t h = ld_acquire(t.slots + slot);
+    uint32_t spins = 0;
+    while (h & kBusy) {
+        if (++spins > kSpinLimit) {
+            set_flag(t.ctr, kFlagTimeout);
+            return false;
+        }
+        __nanosleep(100);
+        h = ld_acquire(t.slots + slot);
+    }
+    return row_equals(t.kstore + slot * W, k, W);
+}
+
+// Bucket-scheme find-or-put (LOOKUP: lookup), one thread per key: the thread
+// reads the 16 headers of bucket h_f (one line, 8 16-byte loads), checks the
+// slots whose tag matches, and, if the key is not there and the bucket has
+// EMPTY slots, claims them in slot order until one claim succeeds or
+// another copy of the key turns up.  A lookup stops at the first bucket
+// with an EMPTY slot.
+template <bool LOOKUP>
+__global__ void __launch_bounds__(kBlock)
+long_bucket_kernel(const DevTable t, const uint64_t* __restrict__ keys, uint64_t n, uint8_t* __restrict__ out) {
+    const uint32_t W = t.words;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    unsigned long long added = 0;
+    for (uint64_t i = tid; i < n; i += stride) {
+        uint64_t k[kLongMaxWords];
+        load_key(keys, i, W, k);
+        const uint64_t d = digest_of(k, W, t.digest_mask);
+        const uint64_t tag = d & kTagMask;
+        int res = 0;                      // 0: not found (absent, or no room), 1: claimed, 2: found
+        for (uint32_t f = 0; f < t.k && res == 0; ++f) {
+            const uint64_t base = hidx(d, t.seed[f], t.nbuckets) * kLBS;
+            const ulonglong2* hp = reinterpret_cast<const ulonglong2*>(t.slots + base);
+            uint32_t match = 0, empty = 0;
+#pragma unroll
+            for (int q = 0; q < kLBS / 2; ++q) {
+                const ulonglong2 v = __ldcg(hp + q);
+                match |= uint32_t((v.x & ~kBusy) == tag) << (2 * q);
+                match |= uint32_t((v.y & ~kBusy) == tag) << (2 * q + 1);
+                empty |= uint32_t(v.x == kEmpty) << (2 * q);
+                empty |= uint32_t(v.y == kEmpty) << (2 * q + 1);
+            }
+            while (match && res == 0) {
+                const int s = __ffs(match) - 1;
+                match &= match - 1;
+                if (slot_holds(t, base + s, k, W)) res = 2;
+            }
+            if (res || !empty) continue;  // found, or the bucket is full: next function
+            if (LOOKUP) break;            // an EMPTY slot: the key would sit in this bucket
+            while (empty && res == 0) {
+                const int s = __ffs(empty) - 1;
+                empty &= empty - 1;
+                uint64_t* hdr = t.slots + base + s;
+                const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(hdr), kEmpty, tag | kBusy);
+                if (old == kEmpty) {
+                    uint64_t* row = t.kstore + (base + s) * W;
+#pragma unroll
+                    for (uint32_t j = 0; j < kLongMaxWords; ++j)
+                        if (j < W) row[j] = k[j];
+                    st_release(hdr, tag);
+                    res = 1;
+                } else if ((old & ~kBusy) == tag && slot_holds(t, base + s, k, W)) {
+                    res = 2;
+                }
+            }
+        }
+        if (LOOKUP) {
+            if (out) out[i] = uint8_t(res == 2);
+        } else {
+            if (res == 0) {               // all k buckets full
+                set_flag(t.ctr, kFlagDropped);
+                atomicAdd(&t.ctr->dropped, 1ull);
+            }
+            added += res == 1;
+            if (out) out[i] = uint8_t(res == 1);
+        }
+    }
+    if (!LOOKUP) {
+        for (int o = 16; o; o >>= 1) added += __shfl_down_sync(kFullMask, added, o);
+        if ((threadIdx.x & 31) == 0 && added) atomicAdd(&t.ctr->size, added);
+    }
+}
+
+// Cuckoo overflow set: linear probing over 16-byte (digest, row) entries.
+__device__ int ovf_insert(const DevTable& t, uint64_t d, uint64_t row) {
+    const uint32_t n = t.ovf_slots;
+    uint32_t p = uint32_t(mix64(d ^ t.aux_seed) & (n - 1));
+    for (uint32_t i = 0; i < n; ++i) {
+        uint64_t ol, oh;
+        cas128(t.ovf + 2 * uint64_t(p), d, row, ol, oh);
+        if (ol == kEmpty && oh == kEmpty) return 1;
+        p = (p + 1) & (n - 1);
+    }
+    return -1;
+}
+
+__device__ bool ovf_find(const DevTable& t, uint64_t d, const uint64_t (&k)[kLongMaxWords], uint32_t W) {
+    const uint32_t n = t.ovf_slots;
+    uint32_t p = uint32_t(mix64(d ^ t.aux_seed) & (n - 1));
+    for (uint32_t i = 0; i < n; ++i) {
+        const ulonglong2 e = __ldcg(reinterpret_cast<const ulonglong2*>(t.ovf + 2 * uint64_t(p)));
+        if (e.x == kEmpty && e.y == kEmpty) return false;
+        if (e.x == d && e.y < t.kstore_rows && row_equals(t.kstore + e.y * W, k, W)) return true;
+        p = (p + 1) & (n - 1);
+    }
+    return false;
+}
+
+// Cuckoo probe (LOOKUP: lookup), one thread per key.  Section 4.1: the key
+// is at one of h_1 .. h_k (or in the overflow set); every chain starts at
+// h_1, an evicted entry moves from h_a to h_{a+1}, and slots never return to
+// EMPTY, so an EMPTY h_a proves the key absent.  A miss claims the key's
+// entry (digest, batch index) in the claim set; an entry of equal digest is
+// told apart by comparing the two batch keys.  Each winner takes a row of
+// the key store (one counter atomic per warp), writes its words there and is
+// listed for the insert kernel.
+template <bool LOOKUP>
+__global__ void __launch_bounds__(kBlock)
+long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity, const uint64_t* __restrict__ keys,
+                         uint64_t n, uint8_t* __restrict__ out) {
+    const uint32_t W = t.words;
+    const uint32_t ovf_used = __ldcg(&t.ctr->ovf_used);
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t rounds = (n + stride - 1) / stride;      // warp-uniform trip count
+    const uint64_t dseed = t.aux_seed * 3 + 1;
+    const int lane = threadIdx.x & 31;
+    LongWinner* win = reinterpret_cast<LongWinner*>(sc.win);
+    unsigned long long probes = 0;
+    for (uint64_t r = 0; r < rounds; ++r) {
+        const uint64_t i = r * stride + tid;
+        const bool act = i < n;
+        uint64_t k[kLongMaxWords];
+        uint64_t d = 0;
+        bool found = false;
+        if (act) {
+            load_key(keys, i, W, k);
+            d = digest_of(k, W, t.digest_mask);
+            for (uint32_t a = 0; a < t.k; ++a) {
+                const ulonglong2 e =
+                    __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(d, t.seed[a], t.nslots)));
+                ++probes;
+                if (e.x == kEmpty && e.y == kEmpty) break;
+                if (e.x == d && e.y < t.kstore_rows && row_equals(t.kstore + e.y * W, k, W)) {
+                    found = true;
+                    break;
+                }
+            }
+            if (!found && ovf_used) found = ovf_find(t, d, k, W);
+        }
+        if (LOOKUP) {
+            if (act && out) out[i] = uint8_t(found);
+            continue;
+        }
+        bool winner = false;
+        uint64_t spos = 0;
+        if (act && !found) {
+            spos = mix64(d ^ dseed) & sc.mask;
+            bool settled = false;
+            for (uint64_t p = 0; p <= sc.mask; ++p) {
+                uint64_t ol, oh;
+                cas128(sc.set + 2 * spos, d, i, ol, oh);
+                if (ol == kEmpty && oh == kEmpty) {
+                    winner = settled = true;
+                    break;
+                }
+                if (ol == d && oh < n && row_equals(keys + oh * W, k, W)) {
+                    settled = true;                        // another copy of the key won
+                    break;
+                }
+                spos = (spos + 1) & sc.mask;
+            }
+            if (!settled) {                                // more distinct misses than the set holds
+                set_flag(t.ctr, kFlagDropped);
+                atomicAdd(&t.ctr->dropped, 1ull);
+            }
+        }
+        const unsigned wm = __ballot_sync(kFullMask, winner);
+        if (wm) {
+            unsigned long long row0 = 0, at0 = 0;
+            if (lane == 0) {
+                row0 = atomicAdd(&t.ctr->ids, (unsigned long long)__popc(wm));
+                at0 = atomicAdd(&t.ctr->winners[parity], unsigned(__popc(wm)));
+            }
+            row0 = __shfl_sync(kFullMask, row0, 0);
+            at0 = __shfl_sync(kFullMask, at0, 0);
+            if (winner) {
+                const unsigned rank = __popc(wm & ((1u << lane) - 1));
+                const uint64_t row = row0 + rank, at = at0 + rank;
+                if (row < t.kstore_rows && at < sc.win_cap) {
+                    uint64_t* dst = t.kstore + row * W;
+#pragma unroll
+                    for (uint32_t j = 0; j < kLongMaxWords; ++j)
+                        if (j < W) dst[j] = k[j];
+                    LongWinner wn;
+                    wn.digest = d;
+                    wn.row = row;
+                    wn.spos = spos;
+                    wn.pad_ = 0;
+                    win[at] = wn;
+                } else {                                   // more keys than the table holds
+                    // Release the claim with one 16-byte atomic: other
+                    // threads may be comparing against it right now.
+                    winner = false;
+                    uint64_t ol, oh;
+                    exch128(sc.set + 2 * spos, kEmpty, kEmpty, ol, oh);
+                    set_flag(t.ctr, kFlagDropped);
+                    atomicAdd(&t.ctr->dropped, 1ull);
+                }
+            }
+        }
+        if (act && out) out[i] = uint8_t(winner);
+    }
+    if (!LOOKUP) {
+        for (int o = 16; o; o >>= 1) probes += __shfl_down_sync(kFullMask, probes, o);
+        if (lane == 0 && probes) atomicAdd(&t.ctr->probes, probes);
+    }
+}
+
+// Eviction chains of the winners' (digest, row) entries; each thread keeps
+// four chains in flight and refills a chain that ends with its next winner.
+__global__ void __launch_bounds__(kBlock)
+long_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uint64_t max_winners) {
+    constexpr int U = 4;
+    const uint64_t count = min(uint64_t(__ldcg(&t.ctr->winners[parity])), max_winners);
+    if (blockIdx.x == 0 && threadIdx.x == 0) t.ctr->winners[parity ^ 1u] = 0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const LongWinner* win = reinterpret_cast<const LongWinner*>(sc.win);
+    unsigned long long placed = 0, exchanges = 0;
+    uint64_t next = tid;
+    uint64_t dg[U], row[U], pos[U];
+    uint32_t evictions[U];
+    bool live[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        live[u] = false;
+        dg[u] = row[u] = pos[u] = 0;
+        evictions[u] = 0;
+    }
+    // Bounded: each winner is taken once and its chain ends after at most
+    // max_evictions + 1 exchanges.
+    for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!live[u] && next < count) {
+                const LongWinner wn = win[next];
+                next += stride;
+                sc.set[2 * wn.spos] = kEmpty;              // leave the claim set empty for the next batch
+                sc.set[2 * wn.spos + 1] = kEmpty;
+                dg[u] = wn.digest;
+                row[u] = wn.row;
+                pos[u] = hidx(wn.digest, t.seed[0], t.nslots);
+                evictions[u] = 0;
+                live[u] = true;
+            }
+            any |= live[u];
+        }
+        if (!any) break;
+        ulonglong2 old[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (live[u]) {
+                uint64_t ol, oh;
+                exch128(t.slots + 2 * pos[u], dg[u], row[u], ol, oh);
+                old[u] = make_ulonglong2(ol, oh);
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!live[u]) continue;
+            ++exchanges;
+            if (old[u].x == kEmpty && old[u].y == kEmpty) {
+                live[u] = false;
+                ++placed;
+                continue;
+            }
+            dg[u] = old[u].x;
+            row[u] = old[u].y;
+            if (++evictions[u] > t.max_evict) {
+                // The chain hit the eviction bound: the held entry goes to the overflow set.
+                if (ovf_insert(t, dg[u], row[u]) == 1) {
+                    ++placed;
+                    atomicAdd(&t.ctr->ovf_used, 1u);
+                    set_flag(t.ctr, kFlagRebuild);
+                } else {
+                    set_flag(t.ctr, kFlagDropped);
+                    atomicAdd(&t.ctr->dropped, 1ull);
+                }
+                live[u] = false;
+                continue;
+            }
+            // Section 4.1: the evicted entry sat at h_a(digest) = pos, a the
+            // smallest such index; it moves on to h_{a+1} (after h_k: h_1).
+            uint32_t a = 0;
+            for (; a + 1 < t.k; ++a)
+                if (hidx(dg[u], t.seed[a], t.nslots) == pos[u]) break;
+            const uint32_t nxt = (a + 1 == t.k) ? 0u : a + 1;
+            pos[u] = hidx(dg[u], t.seed[nxt], t.nslots);
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        placed += __shfl_down_sync(kFullMask, placed, o);
+        exchanges += __shfl_down_sync(kFullMask, exchanges, o);
+    }
+    if ((threadIdx.x & 31) == 0 && placed) atomicAdd(&t.ctr->size, placed);
+    if ((threadIdx.x & 31) == 0 && exchanges) atomicAdd(&t.ctr->exchanges, exchanges);
+}
+
+// Export: the rows of every published header (bucket scheme) or every
+// entry of the table and the overflow set (Cuckoo), appended per warp.
+__global__ void __launch_bounds__(kBlock)
+long_export_kernel(const DevTable t, bool cuckoo, uint64_t* __restrict__ out, unsigned long long* __restrict__ count,
+                   uint64_t cap) {
+    const uint32_t W = t.words;
+    const uint64_t total = t.nslots + (cuckoo ? t.ovf_slots : 0);
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t rounds = (total + stride - 1) / stride;
+    const int lane = threadIdx.x & 31;
+    for (uint64_t r = 0; r < rounds; ++r) {
+        const uint64_t s = r * stride + tid;
+        bool have = false;
+        uint64_t src = 0;
+        if (s < total) {
+            if (!cuckoo) {
+                const uint64_t h = __ldcg(reinterpret_cast<const unsigned long long*>(t.slots + s));
+                have = (h >> 62) == 0;
+                src = s;
+            } else {
+                const uint64_t* e = s < t.nslots ? t.slots + 2 * s : t.ovf + 2 * (s - t.nslots);
+                const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(e));
+                have = !(v.x == kEmpty && v.y == kEmpty);
+                src = v.y;
+            }
+        }
+        const unsigned m = __ballot_sync(kFullMask, have);
+        if (!m) continue;
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(count, (unsigned long long)__popc(m));
+        b = __shfl_sync(kFullMask, b, 0);
+        const uint64_t at = b + __popc(m & ((1u << lane) - 1));
+        if (have && at < cap && src < t.kstore_rows) {
+            const uint64_t* row = t.kstore + src * W;
+            for (uint32_t j = 0; j < W; ++j) out[at * W + j] = __ldcg(reinterpret_cast<const unsigned long long*>(row + j));
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t long_find_or_put(const DevTable& t, const void* keys, uint64_t n, uint8_t* is_new, cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    ProfScope ps(kKBucketFop, s);
+    auto k = long_bucket_kernel<false>;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, static_cast<const uint64_t*>(keys), n, is_new);
+    return cudaGetLastError();
+}
+
+cudaError_t long_lookup(const DevTable& t, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    ProfScope ps(kKBucketLookup, s);
+    auto k = long_bucket_kernel<true>;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, static_cast<const uint64_t*>(keys), n, found);
+    return cudaGetLastError();
+}
+
+cudaError_t long_cuckoo_probe(const DevTable& t, const DevScratch& sc, uint32_t parity, const void* keys, uint64_t n,
+                              uint8_t* is_new, cudaStream_t s) {
+    ProfScope ps(kKCuckooProbe, s);
+    auto k = long_cuckoo_probe_kernel<false>;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, sc, parity, static_cast<const uint64_t*>(keys), n,
+                                                              is_new);
+    return cudaGetLastError();
+}
+
+cudaError_t long_cuckoo_insert(const DevTable& t, const DevScratch& sc, uint32_t parity, uint64_t max_winners,
+                               cudaStream_t s) {
+    ProfScope ps(kKCuckooInsert, s);
+    auto k = long_cuckoo_insert_kernel;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, sc, parity, max_winners);
+    return cudaGetLastError();
+}
+
+cudaError_t long_cuckoo_lookup(const DevTable& t, const void* keys, uint64_t n, uint8_t* found, cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    ProfScope ps(kKCuckooLookup, s);
+    DevScratch none{};
+    auto k = long_cuckoo_probe_kernel<true>;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, none, 0u, static_cast<const uint64_t*>(keys), n,
+                                                              found);
+    return cudaGetLastError();
+}
+
+cudaError_t long_export(const DevTable& t, bool cuckoo, void* keys, unsigned long long* count, uint64_t cap,
+                        cudaStream_t s) {
+    ProfScope ps(kKExport, s);
+    auto k = long_export_kernel;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, cuckoo, static_cast<uint64_t*>(keys), count, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace ht

@@ -258,6 +258,43 @@ def test_oracle128_find_or_put_lookup_export_against_brute_force(oracle_lib):
     assert set(map(tuple, t.export().tolist())) == seen
 
 
+@pytest.mark.parametrize("words", [1, 3, 8])
+def test_oracle_long_find_or_put_lookup_export_against_brute_force(oracle_lib, words):
+    # Keys of `words` words drawn from 3 values per word, so that many keys
+    # agree on all but one word; a Python set of tuples is the brute force.
+    rng = np.random.default_rng(words)
+    vals = np.array([0, 7, 2 ** 64 - 1], dtype=np.uint64)
+    keys = vals[rng.integers(0, 3, size=(4000, words))]
+    t = oracle_lib.OracleTableLong(words)
+    seen, exp = set(), []
+    for row in map(tuple, keys.tolist()):
+        exp.append(int(row not in seen))
+        seen.add(row)
+    got = np.concatenate([t.find_or_put(keys[i:i + 900]) for i in range(0, len(keys), 900)])
+    np.testing.assert_array_equal(got, np.array(exp, dtype=np.uint8))
+    assert t.size() == len(seen) == min(3 ** words, len(seen))
+    if words <= 3:
+        assert len(seen) == 3 ** words             # every combination drawn
+    absent = np.full((1, words), 5, dtype=np.uint64)
+    q = np.concatenate([keys[:50], absent])
+    np.testing.assert_array_equal(t.lookup(q), [1] * 50 + [0])
+    assert set(map(tuple, t.export().tolist())) == seen
+
+
+def test_oracle_long_reduces_to_the_one_and_two_word_sets(oracle_lib):
+    # With one word the long-key set is the 64-bit set; with two, the
+    # 128-bit set: the same flags, sizes and contents on the same stream.
+    rng = np.random.default_rng(9)
+    k1 = rng.integers(0, 500, size=5000).astype(np.uint64)
+    a, b = oracle_lib.OracleTableLong(1), oracle_lib.OracleTable()
+    np.testing.assert_array_equal(a.find_or_put(k1.reshape(-1, 1)), b.find_or_put(k1))
+    assert a.size() == b.size()
+    k2 = rng.integers(0, 40, size=(5000, 2)).astype(np.uint64)
+    c, d = oracle_lib.OracleTableLong(2), oracle_lib.OracleTable128()
+    np.testing.assert_array_equal(c.find_or_put(k2), d.find_or_put(k2))
+    assert set(map(tuple, c.export().tolist())) == set(map(tuple, d.export().tolist()))
+
+
 def _component_hist(m, c):
     a = sp.lil_matrix((int(m.L[c]), int(m.L[c])))
     for u in range(int(m.L[c])):

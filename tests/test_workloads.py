@@ -57,6 +57,32 @@ def test_fill_stream_prefix_matches_full(nb):
     assert np.array_equal(pre.fresh_counts, full.fresh_counts[:m])
 
 
+@pytest.mark.parametrize("width", [192, 256, 512])
+@pytest.mark.parametrize("shared", [False, True])
+def test_long_keys_distinct_and_span_every_bit(width, shared):
+    w = width // 64
+    k = wk.distinct_keys(20000, width, seed=4, shared_prefix=shared)
+    assert k.shape == (20000, w) and k.dtype == np.uint64
+    assert len(np.unique(k, axis=0)) == 20000
+    other = wk.distinct_keys(5000, width, seed=4, start=20000, shared_prefix=shared)
+    both = np.concatenate([k, other])
+    assert len(np.unique(both, axis=0)) == 25000           # disjoint index ranges, disjoint keys
+    assert (k[:, -1] >> np.uint64(63)).any()                 # the top bit of the last word is used
+    if shared:
+        assert len(np.unique(k[:, :-1], axis=0)) <= 4 ** (w - 1)   # many keys share every word but the last
+        assert set(np.unique(k[:, 0]).tolist()) <= {0, 1, 2, 3}
+    else:
+        assert (k[:, 0] >> np.uint64(63)).any()
+
+
+def test_long_fill_stream_rows():
+    fs = wk.fill_stream(3000, 512, 0.4, 256, seed=6)
+    assert fs.keys.shape[1] == 4
+    assert len(np.unique(fs.keys, axis=0)) == 3000 and fs.fresh_counts.sum() == 3000
+    with pytest.raises(ValueError):
+        wk.distinct_keys(10, 160, seed=1)
+
+
 def test_lookup_batch_split():
     keys, present = wk.lookup_batch(1000, 2001, 64, seed=1)
     stored = set(wk.distinct_keys(1000, 64, seed=1).tolist())

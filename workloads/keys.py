@@ -71,11 +71,32 @@ def mix32_perm(x, seed=0):
     return z
 
 
-def distinct_keys(n, width, seed, start=0):
+def _word_mix(x, salt):
+    """SplitMix64-style finaliser over the full 64-bit range (not a bijection
+    requirement here: these words only fill out long keys)."""
+    with np.errstate(over="ignore"):
+        z = np.asarray(x, dtype=np.uint64) + np.uint64(salt)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def long_words(width):
+    """Words per key of a long-key width (64 * W, W = 3..8), else None."""
+    if width % 64 == 0 and 3 <= width // 64 <= 8:
+        return width // 64
+    return None
+
+
+def distinct_keys(n, width, seed, start=0, shared_prefix=False):
     """Keys ``start .. start+n-1`` of the seeded stream; all distinct.
 
     width 64 -> uint64 in [0, 2^63); width 32 -> uint32 != 0xFFFFFFFF
-    (indices must stay below 2^32 - 1).
+    (indices must stay below 2^32 - 1).  width 64*W (W = 3..8) -> (n, W)
+    uint64 rows over the full 64-bit range of every word: the last word is
+    a bijection of the index (so rows are distinct) and the others are
+    mixed from the index -- or, with ``shared_prefix``, drawn from 4 values
+    each, so that many keys agree on every word but the last.
     """
     idx = np.arange(start, start + n, dtype=np.uint64)
     if width == 64:
@@ -84,7 +105,18 @@ def distinct_keys(n, width, seed, start=0):
         if start + n > EMPTY32:
             raise ValueError("32-bit key stream holds at most 2^32-1 keys")
         return mix32_perm(idx, seed).astype(np.uint32)
-    raise ValueError("width must be 32 or 64")
+    w = long_words(width)
+    if w is None:
+        raise ValueError("width must be 32, 64 or 64*W with W in 3..8")
+    out = np.empty((n, w), dtype=np.uint64)
+    for j in range(w - 1):
+        v = _word_mix(idx, (seed * 0x632BE59BD9B4E019 + 0x9E3779B97F4A7C15 * (j + 1)) & ((1 << 64) - 1))
+        out[:, j] = v & np.uint64(3) if shared_prefix else v
+    # Bit 63 of the last word comes from the index too, so every word spans 64 bits.
+    last = mix63_perm(idx, seed + 17)
+    top = (_word_mix(idx, seed ^ 0x5851F42D4C957F2D) >> np.uint64(63)) << np.uint64(63)
+    out[:, w - 1] = last | top
+    return out
 
 
 class FillStream:
@@ -134,7 +166,7 @@ def fill_stream(n_distinct, batch, dup_rate, width, seed, max_batches=None):
         nf = min(per_batch_fresh, n_fresh - issued)
         nd = batch - nf if nf == per_batch_fresh else int(round(nf * dup_rate / (1.0 - dup_rate)))
         end = issued + nf
-        b = np.empty(nf + nd, dtype=fresh.dtype)
+        b = np.empty((nf + nd,) + fresh.shape[1:], dtype=fresh.dtype)
         b[:nf] = fresh[issued:end]
         if nd:
             b[nf:] = fresh[rng.integers(0, end, size=nd)]
@@ -143,7 +175,7 @@ def fill_stream(n_distinct, batch, dup_rate, width, seed, max_batches=None):
         offsets.append(offsets[-1] + len(b))
         fresh_counts.append(nf)
         issued = end
-    keys = np.concatenate(parts) if parts else np.empty(0, dtype=fresh.dtype)
+    keys = np.concatenate(parts) if parts else np.empty((0,) + fresh.shape[1:], dtype=fresh.dtype)
     return FillStream(keys, np.asarray(offsets, dtype=np.int64),
                       np.asarray(fresh_counts, dtype=np.int64), n_distinct, width)
 

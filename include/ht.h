@@ -126,8 +126,23 @@ ht_status ht_default_params(ht_scheme scheme, ht_params* p);
  * insert without values, lookup without values, export, size, clear, grow,
  * stats, ht_successors and ht_bfs over models up to 127 bits wide (not
  * ht_bfs_fused or the batched forms).
- * Errors: HT_ERR_INVALID (capacity 0 or > 2^40, key_width not 32/64/128,
- * bad params), HT_ERR_OOM, HT_ERR_CUDA.  *out is NULL on error. */
+ * key_width 192, 256, ..., 512 (W = key_width / 64 words, 3..8): long keys
+ * (multi-word state vectors; Sections 3.2 and 4.2 for GPUexplore's vectors,
+ * Section 7 for Cuckoo hashing of keys of any length).  A key is W uint64
+ * words, one key per row of the caller's array (row-major n x W, 8-byte
+ * aligned); no value is reserved.  No atomic covers a whole key, so the
+ * words sit in a key store beside the slots: bucket scheme -- one 8-byte
+ * header per slot, 16 to a 128-byte bucket (bucket_slots must be 16;
+ * lanes_per_key unused), claimed with a compare-and-swap and published with
+ * a release store after the key's words are written (a reader that meets a
+ * claimed, unpublished header of its tag waits, bounded; HT_ERR_TIMEOUT if
+ * the bound is hit); Cuckoo -- 16-byte (digest, row) entries moved by
+ * eviction chains, the words written once to their row, no stash.  Long-key
+ * tables support find-or-put, insert and lookup without values or append,
+ * export (rows of W words), size, clear, grow and stats; not ht_bfs,
+ * ht_successors, the batched forms or ht_multi_find_or_put.
+ * Errors: HT_ERR_INVALID (capacity 0 or > 2^40, key_width not one of the
+ * above, bad params), HT_ERR_OOM, HT_ERR_CUDA.  *out is NULL on error. */
 ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width,
                     const ht_params* params, void* stream, ht_table** out);
 

@@ -475,8 +475,9 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
         // Key store: one row per slot (bucket scheme), or one per key the
         // table, its overflow set included, can hold (Cuckoo).
         t->dt.words = key_width / 64;
+        t->dt.row_words = (t->dt.words + 1) & ~1u;
         t->dt.kstore_rows = t->dt.nslots + (scheme == HT_CUCKOO ? t->dt.ovf_slots : 0);
-        if ((e = cudaMallocAsync(&t->dt.kstore, t->dt.kstore_rows * t->dt.words * 8, cs)) != cudaSuccess)
+        if ((e = cudaMallocAsync(&t->dt.kstore, t->dt.kstore_rows * t->dt.row_words * 8, cs)) != cudaSuccess)
             return fail(e);
     }
     if ((e = cudaMallocAsync(&t->dt.ctr, sizeof(DevCounters), cs)) != cudaSuccess) return fail(e);

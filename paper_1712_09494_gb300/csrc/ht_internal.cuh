@@ -53,14 +53,16 @@ struct DevTable {
     uint32_t max_evict;       // Cuckoo eviction bound
     uint64_t aux_seed;        // stash / overflow / dedup start positions
     uint64_t seed[kMaxHashes];
-    // Keys of more than two words (ht_long.cu): the key store (words per key
-    // x rows), its rows, and the mask applied to every key digest (all ones
-    // except in tests that force digest collisions).
+    // Keys of more than two words (ht_long.cu): the key store (rows of
+    // row_words words: the key's words, then a zero word when the count is
+    // odd, so that rows are 16-byte aligned), its rows, and the mask applied
+    // to every key digest (all ones except in tests that force digest
+    // collisions).
     uint64_t* kstore;
     uint64_t kstore_rows;
     uint64_t digest_mask;
     uint32_t words;
-    uint32_t pad_w_;
+    uint32_t row_words;
 };
 
 // A Cuckoo insertion job: the packed word and where its dedup claim sits.

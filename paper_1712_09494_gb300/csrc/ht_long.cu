@@ -64,12 +64,40 @@ __device__ __forceinline__ void load_key(const uint64_t* __restrict__ keys, uint
     for (uint32_t j = 0; j < kLongMaxWords; ++j) k[j] = j < W ? __ldg(p + j) : 0;
 }
 
-__device__ __forceinline__ bool row_equals(const uint64_t* row, const uint64_t (&k)[kLongMaxWords], uint32_t W) {
+// A key of the input batch (W words, 8-byte aligned) against k.
+__device__ __forceinline__ bool input_equals(const uint64_t* row, const uint64_t (&k)[kLongMaxWords], uint32_t W) {
     bool eq = true;
 #pragma unroll
     for (uint32_t j = 0; j < kLongMaxWords; ++j)
-        if (j < W) eq &= __ldcg(reinterpret_cast<const unsigned long long*>(row + j)) == k[j];
+        if (j < W) eq &= __ldg(row + j) == k[j];
     return eq;
+}
+
+// A key-store row (RW words, 16-byte aligned; a padding word is 0, as in k)
+// against k, with 16-byte loads.
+__device__ __forceinline__ bool row_equals(const uint64_t* row, const uint64_t (&k)[kLongMaxWords], uint32_t RW) {
+    bool eq = true;
+#pragma unroll
+    for (uint32_t j = 0; j < kLongMaxWords; j += 2)
+        if (j < RW) {
+            const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(row + j));
+            eq &= v.x == k[j] && v.y == k[j + 1];
+        }
+    return eq;
+}
+
+__device__ __forceinline__ void write_row(uint64_t* row, const uint64_t (&k)[kLongMaxWords], uint32_t RW) {
+#pragma unroll
+    for (uint32_t j = 0; j < kLongMaxWords; j += 2)
+        if (j < RW) *reinterpret_cast<ulonglong2*>(row + j) = make_ulonglong2(k[j], k[j + 1]);
+}
+
+// Bit p of x (p < 8) to bit 2p.
+__device__ __forceinline__ uint32_t spread8(uint32_t x) {
+    x = (x | (x << 4)) & 0x0F0Fu;
+    x = (x | (x << 2)) & 0x3333u;
+    x = (x | (x << 1)) & 0x5555u;
+    return x;
 }
 
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
@@ -114,7 +142,7 @@ __device__ __forceinline__ void exch128(uint64_t* addr, uint64_t lo, uint64_t hi
 // Bucket scheme: does slot `slot`, whose header carries the key's tag, hold
 // the key?  Waits until the header is published (bounded: past the limit
 // the timeout flag is set and the slot is taken as another key's).
-__device__ bool slot_holds(const DevTable& t, uint64_t slot, const uint64_t (&k)[kLongMaxWords], uint32_t W) {
+__device__ bool slot_holds(const DevTable& t, uint64_t slot, const uint64_t (&k)[kLongMaxWords], uint32_t RW) {
     uint64_t h = ld_acquire(t.slots + slot);
     uint32_t spins = 0;
     while (h & kBusy) {
@@ -125,78 +153,116 @@ __device__ bool slot_holds(const DevTable& t, uint64_t slot, const uint64_t (&k)
         __nanosleep(100);
         h = ld_acquire(t.slots + slot);
     }
-    return row_equals(t.kstore + slot * W, k, W);
+    return row_equals(t.kstore + slot * RW, k, RW);
 }
 
-// Bucket-scheme find-or-put (LOOKUP: lookup), one thread per key: the thread
-// reads the 16 headers of bucket h_f (one line, 8 16-byte loads), checks the
-// slots whose tag matches, and, if the key is not there and the bucket has
-// EMPTY slots, claims them in slot order until one claim succeeds or
-// another copy of the key turns up.  A lookup stops at the first bucket
-// with an EMPTY slot.
+// Bucket-scheme find-or-put (LOOKUP: lookup).  A warp takes 32 keys, one
+// per lane.  Each round every lane still searching names its bucket h_f, and
+// the warp reads those buckets together: in load j, lanes 8g .. 8g+7 read the
+// eight 16-byte pieces of the bucket of lane 4j+g, so a bucket is one
+// coalesced 128-byte access; ballots hand each owner its 16-bit masks of
+// slots whose tag matches and of EMPTY slots.  The owner then checks the
+// matching slots and, if the key is not there and the bucket has EMPTY
+// slots, claims them in slot order until one claim succeeds or another copy
+// of the key turns up.  A lookup stops at the first bucket with an EMPTY
+// slot.
+enum : int { kSearching = 0, kClaimed = 1, kFound = 2, kAbsent = 3, kIdle = 4 };
+
 template <bool LOOKUP>
 __global__ void __launch_bounds__(kBlock)
 long_bucket_kernel(const DevTable t, const uint64_t* __restrict__ keys, uint64_t n, uint8_t* __restrict__ out) {
-    const uint32_t W = t.words;
-    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint32_t W = t.words, RW = t.row_words;
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    const uint64_t ntiles = (n + 31) >> 5;
     unsigned long long added = 0;
-    for (uint64_t i = tid; i < n; i += stride) {
+    for (uint64_t tile = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; tile < ntiles; tile += nwarps) {
+        const uint64_t i = tile * 32 + lane;
+        const bool act = i < n;
         uint64_t k[kLongMaxWords];
-        load_key(keys, i, W, k);
+        if (act) {
+            load_key(keys, i, W, k);
+        } else {
+#pragma unroll
+            for (uint32_t j = 0; j < kLongMaxWords; ++j) k[j] = 0;
+        }
         const uint64_t d = digest_of(k, W, t.digest_mask);
         const uint64_t tag = d & kTagMask;
-        int res = 0;                      // 0: not found (absent, or no room), 1: claimed, 2: found
-        for (uint32_t f = 0; f < t.k && res == 0; ++f) {
-            const uint64_t base = hidx(d, t.seed[f], t.nbuckets) * kLBS;
-            const ulonglong2* hp = reinterpret_cast<const ulonglong2*>(t.slots + base);
+        int res = act ? kSearching : kIdle;
+        uint32_t f = 0;
+        // Bounded: a searching lane moves to its next function or settles
+        // every round, and there are k functions.
+        while (__any_sync(kFullMask, res == kSearching)) {
+            const int need = res == kSearching;
+            const uint64_t base = need ? hidx(d, t.seed[f], t.nbuckets) * kLBS : 0;
+            ulonglong2 v[8];
+            int on[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int owner = 4 * j + (lane >> 3);
+                const uint64_t ob = __shfl_sync(kFullMask, base, owner);
+                on[j] = __shfl_sync(kFullMask, need, owner);
+                v[j] = make_ulonglong2(0, 0);
+                if (on[j]) v[j] = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + ob) + (lane & 7));
+            }
             uint32_t match = 0, empty = 0;
 #pragma unroll
-            for (int q = 0; q < kLBS / 2; ++q) {
-                const ulonglong2 v = __ldcg(hp + q);
-                match |= uint32_t((v.x & ~kBusy) == tag) << (2 * q);
-                match |= uint32_t((v.y & ~kBusy) == tag) << (2 * q + 1);
-                empty |= uint32_t(v.x == kEmpty) << (2 * q);
-                empty |= uint32_t(v.y == kEmpty) << (2 * q + 1);
-            }
-            while (match && res == 0) {
-                const int s = __ffs(match) - 1;
-                match &= match - 1;
-                if (slot_holds(t, base + s, k, W)) res = 2;
-            }
-            if (res || !empty) continue;  // found, or the bucket is full: next function
-            if (LOOKUP) break;            // an EMPTY slot: the key would sit in this bucket
-            while (empty && res == 0) {
-                const int s = __ffs(empty) - 1;
-                empty &= empty - 1;
-                uint64_t* hdr = t.slots + base + s;
-                const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(hdr), kEmpty, tag | kBusy);
-                if (old == kEmpty) {
-                    uint64_t* row = t.kstore + (base + s) * W;
-#pragma unroll
-                    for (uint32_t j = 0; j < kLongMaxWords; ++j)
-                        if (j < W) row[j] = k[j];
-                    st_release(hdr, tag);
-                    res = 1;
-                } else if ((old & ~kBusy) == tag && slot_holds(t, base + s, k, W)) {
-                    res = 2;
+            for (int j = 0; j < 8; ++j) {
+                const uint64_t ot = __shfl_sync(kFullMask, tag, 4 * j + (lane >> 3));
+                const bool m0 = on[j] && (v[j].x & ~kBusy) == ot, m1 = on[j] && (v[j].y & ~kBusy) == ot;
+                const bool e0 = on[j] && v[j].x == kEmpty, e1 = on[j] && v[j].y == kEmpty;
+                const uint32_t bm0 = __ballot_sync(kFullMask, m0), bm1 = __ballot_sync(kFullMask, m1);
+                const uint32_t be0 = __ballot_sync(kFullMask, e0), be1 = __ballot_sync(kFullMask, e1);
+                if ((lane >> 2) == j) {
+                    const int sh = 8 * (lane & 3);
+                    match = spread8((bm0 >> sh) & 0xFFu) | (spread8((bm1 >> sh) & 0xFFu) << 1);
+                    empty = spread8((be0 >> sh) & 0xFFu) | (spread8((be1 >> sh) & 0xFFu) << 1);
                 }
             }
+            if (!need) continue;
+            while (match && res == kSearching) {
+                const int sl = __ffs(match) - 1;
+                match &= match - 1;
+                if (slot_holds(t, base + sl, k, RW)) res = kFound;
+            }
+            if (res == kSearching && empty) {
+                if (LOOKUP) {
+                    res = kAbsent;        // an EMPTY slot: the key would sit in this bucket
+                } else {
+                    while (empty && res == kSearching) {
+                        const int sl = __ffs(empty) - 1;
+                        empty &= empty - 1;
+                        uint64_t* hdr = t.slots + base + sl;
+                        const uint64_t old =
+                            atomicCAS(reinterpret_cast<unsigned long long*>(hdr), kEmpty, tag | kBusy);
+                        if (old == kEmpty) {
+                            write_row(t.kstore + (base + sl) * RW, k, RW);
+                            st_release(hdr, tag);
+                            res = kClaimed;
+                        } else if ((old & ~kBusy) == tag && slot_holds(t, base + sl, k, RW)) {
+                            res = kFound;
+                        }
+                    }
+                }
+            }
+            // Still searching: the bucket is full; the next function, if any.
+            if (res == kSearching && ++f >= t.k) res = kAbsent;
         }
+        if (!act) continue;
         if (LOOKUP) {
-            if (out) out[i] = uint8_t(res == 2);
+            if (out) out[i] = uint8_t(res == kFound);
         } else {
-            if (res == 0) {               // all k buckets full
+            if (res == kAbsent) {         // all k buckets full
                 set_flag(t.ctr, kFlagDropped);
                 atomicAdd(&t.ctr->dropped, 1ull);
             }
-            added += res == 1;
-            if (out) out[i] = uint8_t(res == 1);
+            added += res == kClaimed;
+            if (out) out[i] = uint8_t(res == kClaimed);
         }
     }
     if (!LOOKUP) {
         for (int o = 16; o; o >>= 1) added += __shfl_down_sync(kFullMask, added, o);
-        if ((threadIdx.x & 31) == 0 && added) atomicAdd(&t.ctr->size, added);
+        if (lane == 0 && added) atomicAdd(&t.ctr->size, added);
     }
 }
 
@@ -213,13 +279,13 @@ __device__ int ovf_insert(const DevTable& t, uint64_t d, uint64_t row) {
     return -1;
 }
 
-__device__ bool ovf_find(const DevTable& t, uint64_t d, const uint64_t (&k)[kLongMaxWords], uint32_t W) {
+__device__ bool ovf_find(const DevTable& t, uint64_t d, const uint64_t (&k)[kLongMaxWords], uint32_t RW) {
     const uint32_t n = t.ovf_slots;
     uint32_t p = uint32_t(mix64(d ^ t.aux_seed) & (n - 1));
     for (uint32_t i = 0; i < n; ++i) {
         const ulonglong2 e = __ldcg(reinterpret_cast<const ulonglong2*>(t.ovf + 2 * uint64_t(p)));
         if (e.x == kEmpty && e.y == kEmpty) return false;
-        if (e.x == d && e.y < t.kstore_rows && row_equals(t.kstore + e.y * W, k, W)) return true;
+        if (e.x == d && e.y < t.kstore_rows && row_equals(t.kstore + e.y * RW, k, RW)) return true;
         p = (p + 1) & (n - 1);
     }
     return false;
@@ -237,7 +303,7 @@ template <bool LOOKUP>
 __global__ void __launch_bounds__(kBlock)
 long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity, const uint64_t* __restrict__ keys,
                          uint64_t n, uint8_t* __restrict__ out) {
-    const uint32_t W = t.words;
+    const uint32_t W = t.words, RW = t.row_words;
     const uint32_t ovf_used = __ldcg(&t.ctr->ovf_used);
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -260,12 +326,12 @@ long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(d, t.seed[a], t.nslots)));
                 ++probes;
                 if (e.x == kEmpty && e.y == kEmpty) break;
-                if (e.x == d && e.y < t.kstore_rows && row_equals(t.kstore + e.y * W, k, W)) {
+                if (e.x == d && e.y < t.kstore_rows && row_equals(t.kstore + e.y * RW, k, RW)) {
                     found = true;
                     break;
                 }
             }
-            if (!found && ovf_used) found = ovf_find(t, d, k, W);
+            if (!found && ovf_used) found = ovf_find(t, d, k, RW);
         }
         if (LOOKUP) {
             if (act && out) out[i] = uint8_t(found);
@@ -283,7 +349,7 @@ long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     winner = settled = true;
                     break;
                 }
-                if (ol == d && oh < n && row_equals(keys + oh * W, k, W)) {
+                if (ol == d && oh < n && input_equals(keys + oh * W, k, W)) {
                     settled = true;                        // another copy of the key won
                     break;
                 }
@@ -307,10 +373,7 @@ long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                 const unsigned rank = __popc(wm & ((1u << lane) - 1));
                 const uint64_t row = row0 + rank, at = at0 + rank;
                 if (row < t.kstore_rows && at < sc.win_cap) {
-                    uint64_t* dst = t.kstore + row * W;
-#pragma unroll
-                    for (uint32_t j = 0; j < kLongMaxWords; ++j)
-                        if (j < W) dst[j] = k[j];
+                    write_row(t.kstore + row * RW, k, RW);
                     LongWinner wn;
                     wn.digest = d;
                     wn.row = row;
@@ -431,7 +494,7 @@ long_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity
 __global__ void __launch_bounds__(kBlock)
 long_export_kernel(const DevTable t, bool cuckoo, uint64_t* __restrict__ out, unsigned long long* __restrict__ count,
                    uint64_t cap) {
-    const uint32_t W = t.words;
+    const uint32_t W = t.words, RW = t.row_words;
     const uint64_t total = t.nslots + (cuckoo ? t.ovf_slots : 0);
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -460,7 +523,7 @@ long_export_kernel(const DevTable t, bool cuckoo, uint64_t* __restrict__ out, un
         b = __shfl_sync(kFullMask, b, 0);
         const uint64_t at = b + __popc(m & ((1u << lane) - 1));
         if (have && at < cap && src < t.kstore_rows) {
-            const uint64_t* row = t.kstore + src * W;
+            const uint64_t* row = t.kstore + src * RW;
             for (uint32_t j = 0; j < W; ++j) out[at * W + j] = __ldcg(reinterpret_cast<const unsigned long long*>(row + j));
         }
     }

@@ -237,6 +237,44 @@ def random_access_roofline(scheme, fs, table, stats, ms_per_fill, probe):
             "read_gaccess_per_s": round(r_read / 1e9, 2), "rmw_gaccess_per_s": round(r_rmw / 1e9, 2)}
 
 
+def lower_bound_roofline(scheme, fs, ms_per_fill, probe, copy_gbs):
+    """The stable lower-bound variant of a fill's algorithmic bytes per key:
+    one probe unit (a 128-byte bucket, or one 32-byte Cuckoo slot sector) at
+    the random-gather rate of its granularity, a 32-byte claimed sector per
+    new key at the 32-byte gather rate, and the streamed key read and flag
+    write (9 bytes) at the copy rate.  Independent of counted probes and
+    chain lengths, so it moves only with the measured rates."""
+    if not probe or "32B" not in probe or "128B" not in probe:
+        return None
+    p_new = fs.n_distinct / fs.n_issued
+    unit, r_unit = (128, probe["128B"]["requested_gbs"]) if scheme == "bucket" else (32, probe["32B"]["requested_gbs"])
+    r32 = probe["32B"]["requested_gbs"]
+    s_per_key = unit / (r_unit * 1e9) + p_new * 32 / (r32 * 1e9) + 9 / (copy_gbs * 1e9)
+    t_min_ms = s_per_key * fs.n_issued * 1e3
+    return {"bytes_per_key": round(unit + p_new * 32 + 9, 1), "min_ms_per_fill": round(t_min_ms, 3),
+            "mops_bound": round(1 / s_per_key / 1e6, 1), "frac": round(t_min_ms / ms_per_fill, 3)}
+
+
+def cpu_host():
+    """The host's core count and CPU model (from /proc/cpuinfo: the model
+    name, or on Arm the implementer and part numbers)."""
+    info = {"nproc": os.cpu_count(), "machine": os.uname().machine}
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except OSError:
+        return info
+    m = re.search(r"^model name\s*:\s*(.+)$", txt, re.M)
+    if m:
+        info["cpu"] = m.group(1).strip()
+    else:
+        imp = re.search(r"^CPU implementer\s*:\s*(\S+)", txt, re.M)
+        part = re.search(r"^CPU part\s*:\s*(\S+)", txt, re.M)
+        if imp and part:
+            known = {("0x41", "0xd4f"): "Arm Neoverse-V2"}
+            info["cpu"] = known.get((imp.group(1), part.group(1)), "implementer %s part %s" % (imp.group(1), part.group(1)))
+    return info
+
+
 def kernel_random_access(name, k, fs, tables, stats, probe, steps):
     """The dominant kernel against the measured random-access rates: its
     minimum time per launch (lines it must read at the random-read rate +
@@ -286,10 +324,14 @@ def run_ours(a, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     n_ops = fs.n_issued * len(schemes)
 
-    def fill(t):
+    def fill(t, last=None):
         ht.ht_clear(t.handle)
         for b in range(fs.n_batches):
+            if last is not None and b == fs.n_batches - 1:
+                last[0].record(stream)
             ht.ht_find_or_put(t.handle, keys_d[offs[b]:offs[b + 1]], is_new_d[:offs[b + 1] - offs[b]])
+        if last is not None:
+            last[1].record(stream)
 
     ev = {s: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for s in schemes}
     per_ms = {s: 0.0 for s in schemes}
@@ -313,13 +355,16 @@ def run_ours(a, rank, world, local):
     ht.ht_prof_enable(True)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms_each = {s: [] for s in schemes}
+    last_each = {s: [] for s in schemes}        # the last batch of each fill ("at load")
     barrier()
     clocks.start()
     t0.record(stream)
     for _ in range(a.steps):
         for s in schemes:
             ev[s][0].record(stream)
-            fill(tables[s])
+            last = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            fill(tables[s], last)
+            last_each[s].append(last)
             ev[s][1].record(stream)
             step_ms_each[s].append((ev[s][0], ev[s][1]))
             ev[s] = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -394,7 +439,10 @@ def run_ours(a, rank, world, local):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": workload_config(a, schemes),
         "per_scheme": {s: {"ms_per_fill": round(per_ms[s], 3), "median_ms_per_fill": round(med_ms[s], 3),
-                           "mops": round(fs.n_issued / (per_ms[s] / 1e3) / 1e6, 1)} for s in schemes},
+                           "mops": round(fs.n_issued / (per_ms[s] / 1e3) / 1e6, 1),
+                           "at_load_mops": round((offs[-1] - offs[-2]) / (statistics.median(
+                               [e0.elapsed_time(e1) for e0, e1 in last_each[s]]) / 1e3) / 1e6, 1)}
+                       for s in schemes},
         "roofline": roofline, "kernels": kernels, "clocks": clk,
         "gpu_launches": int(sum(v[0] for v in kern.values())),
     }
@@ -407,6 +455,8 @@ def run_ours(a, rank, world, local):
         for s in schemes:
             out["per_scheme"][s]["random_access_roofline"] = random_access_roofline(
                 s, fs, tables[s], fill_stats[s], per_ms[s], out["random_read_roofline"])
+            out["per_scheme"][s]["lower_bound_roofline"] = lower_bound_roofline(
+                s, fs, per_ms[s], out["random_read_roofline"], peak)
         out["roofline"]["random_access"] = kernel_random_access(
             dom, kernels[dom], fs, tables, fill_stats, out["random_read_roofline"], a.steps)
     for t in tables.values():
@@ -1165,7 +1215,8 @@ def run_reference(a, rank, world):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(wall / a.steps * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": workload_config(a, schemes),
-        "cpu_baseline": {"value": round(v, 2), "unit": "Mops/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": round(v, 2), "unit": "Mops/s", "cores": 1, "kind": "oracle", "sample": desc,
+                         "host": cpu_host()},
         "e2e": {"value": round(v, 2), "unit": "Mops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -1183,7 +1234,7 @@ def main():
         if not a.no_cpu and world == 1:
             v, desc = run_cpu_oracle(a)
             out["cpu_baseline"] = {"value": round(v, 2), "unit": "Mops/s", "cores": 1, "kind": "oracle",
-                                   "sample": desc}
+                                   "sample": desc, "host": cpu_host()}
         print(json.dumps(out), flush=True)
 
 

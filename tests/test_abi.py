@@ -46,6 +46,11 @@ def test_default_params(lib):
     (1 << 41, 0, 64, None, None),
     (1024, 0, 48, None, None),
     (1024, 5, 64, None, None),
+    (1024, 0, 160, None, None),            # not a multiple of 64
+    (1024, 1, 576, None, None),            # more than 8 words
+    (1024, 0, 64, "digest_bits", 8),       # a long-key knob only
+    (1024, 1, 256, "digest_bits", 65),
+    (1024, 0, 256, "bucket_slots", 8),     # long-key buckets are 16 headers
     (1024, 0, 64, "bucket_slots", 12),
     (1024, 0, 64, "num_hashes", 17),
     (1024, 0, 64, "lanes_per_key", 3),
@@ -62,6 +67,20 @@ def test_create_rejects_bad_arguments_before_any_cuda_call(lib, cap, scheme, kw,
     out = ctypes.c_void_p(123)
     assert lib.ht_create(cap, scheme, kw, ctypes.byref(p), None, ctypes.byref(out)) == 1
     assert not out.value
+
+
+def test_key_width_of_tensors():
+    # The binding reads the key width from the tensor's shape: 1-D 32/64-bit,
+    # or (n, W) int64 words for W = 2..8.
+    import torch
+    from paper_1712_09494_gb300 import _key_width, _nkeys
+    assert _key_width(torch.empty(5, dtype=torch.int32)) == 32
+    assert _key_width(torch.empty(5, dtype=torch.int64)) == 64
+    for w in range(2, 9):
+        t = torch.empty((5, w), dtype=torch.int64)
+        assert _key_width(t) == 64 * w and _nkeys(t) == 5
+    with pytest.raises(ValueError):
+        _key_width(torch.empty(5, dtype=torch.int16))
 
 
 def test_null_arguments_are_invalid(lib):

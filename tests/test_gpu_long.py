@@ -116,6 +116,20 @@ def test_edge_keys(oracle_lib, scheme, width):
 
 
 @pytest.mark.parametrize("scheme", ["bucket", "cuckoo"])
+def test_single_key_repeated(scheme):
+    # 2^16 copies of one key in one batch: exactly one copy is new.  In the
+    # bucket scheme every other copy meets the one claimed header and waits
+    # for its publish before comparing.
+    key = np.array([[2 ** 64 - 1, 0, 12345, 2 ** 63]], dtype=np.uint64)
+    keys = np.repeat(key, 1 << 16, axis=0)
+    t = ht.HashTable(1024, scheme, 256)
+    assert int(t.find_or_put(_dev(keys)).sum()) == 1
+    assert int(t.find_or_put(_dev(keys)).sum()) == 0
+    assert t.sync() == 0 and t.size() == 1
+    assert t.lookup(_dev(keys))[0].cpu().numpy().all()
+
+
+@pytest.mark.parametrize("scheme", ["bucket", "cuckoo"])
 def test_full_grow_and_checkpoint(oracle_lib, scheme, tmp_path):
     keys = wk.distinct_keys(6000, 320, seed=70)
     # Too small: keys are dropped and the table reports full.

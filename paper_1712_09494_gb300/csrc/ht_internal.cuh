@@ -124,6 +124,37 @@ template <> struct Keys<64> {
     }
 };
 
+// 16-byte atomics on a 16-byte-aligned pair of words (sm_90 and later):
+// compare-and-swap from EMPTY (all ones in both words), and exchange.
+__device__ __forceinline__ void cas128(uint64_t* addr, uint64_t new_lo, uint64_t new_hi, uint64_t& old_lo,
+                                       uint64_t& old_hi) {
+    asm volatile(
+        "{\n"
+        " .reg .b128 d, c, n;\n"
+        " mov.b128 c, {%2, %3};\n"
+        " mov.b128 n, {%4, %5};\n"
+        " atom.global.cas.b128 d, [%6], c, n;\n"
+        " mov.b128 {%0, %1}, d;\n"
+        "}\n"
+        : "=l"(old_lo), "=l"(old_hi)
+        : "l"(kEmpty), "l"(kEmpty), "l"(new_lo), "l"(new_hi), "l"(addr)
+        : "memory");
+}
+
+__device__ __forceinline__ void exch128(uint64_t* addr, uint64_t lo, uint64_t hi, uint64_t& old_lo,
+                                        uint64_t& old_hi) {
+    asm volatile(
+        "{\n"
+        " .reg .b128 d, n;\n"
+        " mov.b128 n, {%2, %3};\n"
+        " atom.global.exch.b128 d, [%4], n;\n"
+        " mov.b128 {%0, %1}, d;\n"
+        "}\n"
+        : "=l"(old_lo), "=l"(old_hi)
+        : "l"(lo), "l"(hi), "l"(addr)
+        : "memory");
+}
+
 __device__ __forceinline__ void set_flag(DevCounters* c, uint32_t f) {
     if ((*(volatile unsigned int*)&c->flags & f) != f) atomicOr(&c->flags, f);
 }

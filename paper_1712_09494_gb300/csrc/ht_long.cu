@@ -110,35 +110,6 @@ __device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ void cas128(uint64_t* addr, uint64_t new_lo, uint64_t new_hi, uint64_t& old_lo,
-                                       uint64_t& old_hi) {
-    asm volatile(
-        "{\n"
-        " .reg .b128 d, c, n;\n"
-        " mov.b128 c, {%2, %3};\n"
-        " mov.b128 n, {%4, %5};\n"
-        " atom.global.cas.b128 d, [%6], c, n;\n"
-        " mov.b128 {%0, %1}, d;\n"
-        "}\n"
-        : "=l"(old_lo), "=l"(old_hi)
-        : "l"(kEmpty), "l"(kEmpty), "l"(new_lo), "l"(new_hi), "l"(addr)
-        : "memory");
-}
-
-__device__ __forceinline__ void exch128(uint64_t* addr, uint64_t lo, uint64_t hi, uint64_t& old_lo,
-                                        uint64_t& old_hi) {
-    asm volatile(
-        "{\n"
-        " .reg .b128 d, n;\n"
-        " mov.b128 n, {%2, %3};\n"
-        " atom.global.exch.b128 d, [%4], n;\n"
-        " mov.b128 {%0, %1}, d;\n"
-        "}\n"
-        : "=l"(old_lo), "=l"(old_hi)
-        : "l"(lo), "l"(hi), "l"(addr)
-        : "memory");
-}
-
 // Bucket scheme: does slot `slot`, whose header carries the key's tag, hold
 // the key?  Waits until the header is published (bounded: past the limit
 // the timeout flag is set and the slot is taken as another key's).

@@ -33,35 +33,6 @@ __device__ __forceinline__ uint64_t wide_fold(uint64_t lo, uint64_t hi) {
     return lo ^ mix64(hi ^ 0xD1B54A32D192ED03ull);
 }
 
-__device__ __forceinline__ void cas128(uint64_t* addr, uint64_t new_lo, uint64_t new_hi, uint64_t& old_lo,
-                                       uint64_t& old_hi) {
-    asm volatile(
-        "{\n"
-        " .reg .b128 d, c, n;\n"
-        " mov.b128 c, {%2, %3};\n"
-        " mov.b128 n, {%4, %5};\n"
-        " atom.global.cas.b128 d, [%6], c, n;\n"
-        " mov.b128 {%0, %1}, d;\n"
-        "}\n"
-        : "=l"(old_lo), "=l"(old_hi)
-        : "l"(kOnes), "l"(kOnes), "l"(new_lo), "l"(new_hi), "l"(addr)
-        : "memory");
-}
-
-__device__ __forceinline__ void exch128(uint64_t* addr, uint64_t lo, uint64_t hi, uint64_t& old_lo,
-                                        uint64_t& old_hi) {
-    asm volatile(
-        "{\n"
-        " .reg .b128 d, n;\n"
-        " mov.b128 n, {%2, %3};\n"
-        " atom.global.exch.b128 d, [%4], n;\n"
-        " mov.b128 {%0, %1}, d;\n"
-        "}\n"
-        : "=l"(old_lo), "=l"(old_hi)
-        : "l"(lo), "l"(hi), "l"(addr)
-        : "memory");
-}
-
 // Slot classes of a read: 2 = a complete key, 1 = a claim candidate.
 __device__ __forceinline__ int slot_class(uint64_t lo, uint64_t hi) {
     return (lo != kOnes && hi != kOnes) ? 2 : 1;

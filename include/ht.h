@@ -188,7 +188,9 @@ ht_status ht_size(ht_table* t, uint64_t* out, void* stream);
 
 /* Copies every stored key (and value, if d_values_out is non-NULL) into the
  * caller's buffers of `cap` entries, in unspecified order; *count = number of
- * stored keys (synchronises).  HT_ERR_INVALID if cap < count (nothing is
+ * stored keys (synchronises).  An entry is a key in the table's input layout:
+ * one uint32/uint64, a 16-byte (low, high) pair for 128-bit keys, or a row of
+ * W words for long keys.  HT_ERR_INVALID if cap < count (nothing is
  * guaranteed about the buffers then). */
 ht_status ht_export(ht_table* t, void* d_keys_out, uint32_t* d_values_out,
                     uint64_t cap, uint64_t* count, void* stream);

@@ -27,6 +27,10 @@
 // atomic exchanges and take the next position from the digest alone, so a
 // chain reads no key words.  The insert kernel starts after the probe
 // kernel has ended, so every row is complete before an entry points to it.
+//
+// Key-store rows hold the key's words and, for an odd word count, a zero
+// word, so every row is 16-byte aligned and is read and written with 16-byte
+// accesses.
 #include "ht_internal.cuh"
 
 namespace ht {

@@ -11,9 +11,11 @@ This model runs that protocol with each memory access as one atomic step and
 explores every interleaving of a few threads (depth-first, over distinct
 states).  In every final state each key new to the table is claimed by
 exactly one of its threads and found by the others, no key is stored twice,
-and no state is stuck.  Planted mistakes in the model -- skipping the tag
-check of the snapshot, or publishing before the row is written -- must be
-caught, so that the checker is known to see such bugs.
+and no state is stuck.  The same model with the key as the slot word (one CAS
+stores it whole, no publish) is the 64-bit kernels' protocol.  Planted
+mistakes in the model -- skipping the tag check of the snapshot, or
+publishing before the row is written -- must be caught, so that the checker
+is known to see such bugs.
 """
 import pytest
 
@@ -35,8 +37,9 @@ class Model:
     initial row contents (stale words left from earlier use)."""
 
     def __init__(self, keys, tag, seq, S, nbuckets, pre=None, rows=None,
-                 skip_match=False, publish_first=False):
+                 skip_match=False, publish_first=False, one_word=False):
         self.keys, self.tag, self.seq, self.S = list(keys), tag, seq, S
+        self.one_word = one_word
         self.nslots = S * nbuckets
         self.skip_match, self.publish_first = skip_match, publish_first
         hdr = [EMPTY] * self.nslots
@@ -96,6 +99,10 @@ class Model:
             s = base + empty[pos]
             old = hdr[s]
             if old == EMPTY:
+                if self.one_word:             # the word is the key: stored whole by the CAS
+                    hdr[s] = _ready(tag)
+                    row[s] = key
+                    return put(("done", f, 0, (), (), "claimed"))
                 if self.publish_first:
                     hdr[s] = _ready(tag)
                     return put(("write", f, empty[pos], snap, todo, None))
@@ -215,6 +222,21 @@ def test_stored_keys_and_stale_rows():
               pre={0: "c"}, rows=["c", "a", "a"])
     finals, n, bad = _check(m)
     assert not bad, bad[0]
+
+
+@pytest.mark.parametrize("keys,pre", [
+    (("a", "a", "b", "b"), None),
+    (("a", "b", "c", "a"), {1: "c"}),
+])
+def test_one_word_claims(keys, pre):
+    # The 64-bit kernels' protocol: the slot word is the key, so a claim
+    # stores it whole and there is no publish step (each key its own tag).
+    tag = {"a": 1, "b": 2, "c": 3}
+    seq = {"a": [0, 1], "b": [1, 0], "c": [0, 1]}
+    m = Model(keys, tag, seq, S=2, nbuckets=2, pre=pre, one_word=True)
+    finals, n, bad = _check(m)
+    assert not bad, bad[0]
+    assert n > 100
 
 
 def test_checker_catches_a_skipped_tag_check():

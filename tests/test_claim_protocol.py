@@ -239,6 +239,17 @@ def test_one_word_claims(keys, pre):
     assert n > 100
 
 
+def test_claim_set_with_colliding_digests():
+    # The long-key Cuckoo claim set: linear probing (one-slot buckets in
+    # probe order, wrapping) over entries that one 16-byte CAS writes whole;
+    # 'a' and 'b' share a digest and are told apart by comparing batch keys.
+    seq = {"a": [0, 1, 2], "b": [1, 2, 0]}
+    m = Model(("a", "b", "a", "b"), TAG, seq, S=1, nbuckets=3, one_word=True)
+    finals, n, bad = _check(m)
+    assert not bad, bad[0]
+    assert n > 100
+
+
 def test_checker_catches_a_skipped_tag_check():
     # Planted: the snapshot's tag matches are ignored, so a copy that sees
     # its key already published claims another slot -- a key stored twice.

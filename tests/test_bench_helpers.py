@@ -1,5 +1,8 @@
-"""Host-side arithmetic of the benchmark line (no GPU): the lower-bound
-roofline variant, the random-access bound and the host description."""
+"""Host-side parts of the benchmark (no GPU): the lower-bound roofline
+variant, the random-access bound, the host description, and the reference
+arm's JSON line (the oracle timed on the host)."""
+import os
+
 import pytest
 
 import bench
@@ -39,3 +42,23 @@ def test_random_access_bound_bucket_counts_lines():
 def test_cpu_host_names_the_cores():
     h = bench.cpu_host()
     assert h["nproc"] >= 1 and h["machine"]
+
+
+def test_reference_arm_prints_the_contract_line():
+    # The reference arm times the oracle on the host (no GPU): one JSON line
+    # with the metric, the oracle's throughput and an e2e of no copies.
+    import json
+    import subprocess
+    import sys
+    out = subprocess.check_output(
+        [sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "2", "--warmup", "1",
+         "--n-log2", "18", "--batch-log2", "14"], text=True, timeout=300)
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "Mops/s"
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["host"]["nproc"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "Mops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["n_distinct"] == 1 << 18

@@ -24,9 +24,12 @@
  *  * Operations on one table must be issued in order on one stream at a time.
  *    Different tables are independent.
  *  * Keys: key_width 32 -> uint32 keys, 0xFFFFFFFF reserved (empty marker);
- *    key_width 64 -> uint64 keys whose top bit must be 0.  A reserved key in a
- *    batch is skipped (is_new/found = 0) and makes the next synchronising call
- *    on the table return HT_ERR_INVALID; the rest of the batch is processed.
+ *    key_width 64 -> uint64 keys whose top bit must be 0; key_width 128 ->
+ *    (low, high) uint64 pairs, bit 63 of the high word reserved; key_width
+ *    192..512 -> rows of key_width/64 uint64 words, no value reserved (see
+ *    ht_create).  A reserved key in a batch is skipped (is_new/found = 0) and
+ *    makes the next synchronising call on the table return HT_ERR_INVALID;
+ *    the rest of the batch is processed.
  *  * Values (maps): only tables with key_width 32 carry a uint32 value, packed
  *    with the key in one 64-bit slot so that a slot moves atomically.
  *  * Table memory is allocated by ht_create and freed by ht_destroy.

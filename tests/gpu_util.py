@@ -44,3 +44,36 @@ def assert_same_set(gpu_keys, oracle_keys):
     assert len(a) == len(b), "sizes differ: gpu %d oracle %d" % (len(a), len(b))
     assert len(np.unique(a)) == len(a), "a key is stored twice"
     assert np.array_equal(a, b)
+
+
+def check_batch_flags(batch, flags, fresh, sample_pos):
+    """Exactly-once check of one find-or-put batch at any size, without the
+    oracle's whole history: `fresh` holds the keys issued for the first time
+    in this batch (from the generator), `sample_pos` positions of the batch
+    to check.  For each sampled key the flags over all its occurrences in the
+    batch must sum to 1 if it is fresh, else 0; and the batch's flags must
+    sum to the number of fresh keys.  Returns a list of problems."""
+    batch = np.asarray(batch)
+    flags = np.asarray(flags).astype(np.int64)
+    bad = []
+    if set(np.unique(flags).tolist()) - {0, 1}:
+        bad.append("flags other than 0/1")
+    if int(flags.sum()) != len(fresh):
+        bad.append("batch flags %d, fresh keys %d" % (int(flags.sum()), len(fresh)))
+    # Membership by binary search in sorted arrays (np.isin of a small array
+    # in a large one is far slower): each batch element's sampled key, if
+    # any, then the flag count per sampled key; fresh keys likewise.
+    kk = np.unique(batch[np.asarray(sample_pos)])
+    at = np.minimum(np.searchsorted(kk, batch), len(kk) - 1)
+    hit = kk[at] == batch
+    per_key = np.bincount(at[hit], weights=flags[hit], minlength=len(kk)).astype(np.int64)
+    sf = np.sort(np.asarray(fresh))
+    if len(sf):
+        want = (sf[np.minimum(np.searchsorted(sf, kk), len(sf) - 1)] == kk).astype(np.int64)
+    else:
+        want = np.zeros(len(kk), dtype=np.int64)
+    wrong = np.nonzero(per_key != want)[0]
+    if len(wrong):
+        bad.append("%d sampled keys with wrong flag counts, e.g. %s: %s (want %s)" % (
+            len(wrong), kk[wrong[:3]], per_key[wrong[:3]], want[wrong[:3]]))
+    return bad

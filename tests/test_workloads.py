@@ -154,3 +154,32 @@ def test_multiplicity_sequence_shape():
         # Uniform draws: the expected number of distinct values is rng (1 - e^-mult).
         exp = rng * (1 - np.exp(-mult))
         assert abs(len(u) - exp) < 5 * np.sqrt(exp) + 10
+
+
+def test_batch_flag_check_accepts_exactly_once_and_catches_mistakes():
+    # The full-size fill test's checker, on a small stream with flags made
+    # from the generator's fresh keys (first occurrence flagged).
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from gpu_util import check_batch_flags
+    fs = wk.fill_stream(20_000, 4096, 0.25, 64, seed=5)
+    rng = np.random.default_rng(0)
+    issued = 0
+    for b in range(fs.n_batches):
+        kb = fs.batch(b)
+        nf = int(fs.fresh_counts[b])
+        fresh = wk.distinct_keys(nf, 64, seed=5, start=issued)
+        issued += nf
+        flags = np.zeros(len(kb), dtype=np.uint8)
+        _, first = np.unique(kb, return_index=True)
+        flags[first[np.isin(kb[first], fresh)]] = 1
+        pos = rng.integers(0, len(kb), size=500)
+        assert check_batch_flags(kb, flags, fresh, pos) == []
+        if b == 1:
+            f2 = flags.copy()
+            f2[np.nonzero(f2)[0][0]] = 0                       # a new key left unflagged
+            assert check_batch_flags(kb, f2, fresh, np.arange(len(kb)))
+            f3 = flags.copy()
+            dup = np.nonzero(~np.isin(kb, fresh))[0][0]          # an old key flagged new
+            f3[dup] = 1
+            assert check_batch_flags(kb, f3, fresh, np.array([dup]))

@@ -21,7 +21,7 @@ __all__ = [
     "HT_BUCKET", "HT_CUCKOO", "HtError", "HtParams", "HashTable", "load",
     "ht_default_params", "ht_create", "ht_destroy", "ht_find_or_put", "ht_find_or_put_append",
     "ht_insert", "ht_lookup", "ht_sync", "ht_size", "ht_export", "ht_clear", "ht_info",
-    "ht_compact", "ht_prof_enable", "ht_prof_reset", "ht_prof_read", "ht_prof_kernels",
+    "ht_compact", "ht_table_words", "ht_prof_enable", "ht_prof_reset", "ht_prof_read", "ht_prof_kernels",
     "ht_probe_random_read", "ht_probe_random_rmw", "ht_stats", "ht_grow", "ht_multi_find_or_put", "ht_cuckoo_find_or_put_noalloc", "NOALLOC_STATE_BYTES",
     "NOALLOC_MAX_BATCH", "scheme_of", "HtModel", "HtBfsResult", "make_model", "ht_successors", "ht_bfs",
     "MultiExploration", "Server", "HtServerConfig", "HtServerStats",
@@ -161,6 +161,13 @@ def ht_info(table):
     return dict(slots=s.value, num_hashes=k.value, rebuilds=r.value)
 
 
+def ht_table_words(table):
+    """(device address, bytes) of the table's slot array."""
+    ptr, nbytes = ctypes.c_void_p(), ctypes.c_uint64()
+    _check(load().ht_table_words(table, ctypes.byref(ptr), ctypes.byref(nbytes)), "ht_table_words")
+    return ptr.value, nbytes.value
+
+
 def ht_multi_find_or_put(tables, items, stream=None):
     """find-or-put over many tables in one call: `tables` a list of handles,
     `items` a list of (table index, keys tensor, is_new uint8 tensor or None)."""
@@ -243,12 +250,38 @@ def ht_probe_random_rmw(buf, n_access, seed, stream=None):
                                       int(seed), _stream(stream)), "ht_probe_random_rmw")
 
 
+def _noalloc_args(slots, state, keys, is_new):
+    """Checks the tensors of ht_cuckoo_find_or_put_noalloc before any pointer
+    reaches the device: a wrong dtype or a short buffer would make the kernels
+    read or write past the end of a caller's allocation."""
+    if slots.dtype not in (torch.int64, torch.uint64) or slots.dim() != 1 or slots.numel() == 0:
+        raise ValueError("slots must be a non-empty 1-D int64/uint64 tensor")
+    if state.numel() * state.element_size() < NOALLOC_STATE_BYTES:
+        raise ValueError("state must hold at least %d bytes" % NOALLOC_STATE_BYTES)
+    if keys.dtype not in (torch.int64, torch.uint64) or keys.dim() != 1:
+        raise ValueError("keys must be a 1-D int64/uint64 tensor")
+    n = keys.numel()
+    if n > NOALLOC_MAX_BATCH:
+        raise ValueError("at most %d keys per call" % NOALLOC_MAX_BATCH)
+    if is_new is not None and (is_new.dtype != torch.uint8 or is_new.numel() < n):
+        raise ValueError("is_new must be a uint8 tensor of at least %d entries" % n)
+    devs = {t.device for t in (slots, state, keys, is_new) if t is not None}
+    if len(devs) != 1:
+        raise ValueError("slots, state, keys and is_new must be on one CUDA device")
+    return n
+
+
 def ht_cuckoo_find_or_put_noalloc(slots, state, seed, keys, is_new=None, reset=False, stream=None):
     """Find-or-put into a Cuckoo set held in caller tensors (``slots``: int64
-    table words, ``state``: NOALLOC_STATE_BYTES bytes); allocates nothing."""
-    return load().ht_cuckoo_find_or_put_noalloc(
-        _dptr(slots, "slots"), slots.numel() * slots.element_size() // 8, _dptr(state, "state"), int(seed),
-        _dptr(keys, "keys"), keys.numel(), _dptr(is_new, "is_new"), 1 if reset else 0, _stream(stream))
+    table words, ``state``: NOALLOC_STATE_BYTES bytes); allocates nothing.
+    Raises ValueError on a malformed tensor and HtError on a non-OK status.
+    Reserved keys, overflow use and dropped keys are reported only in the
+    state block's status word (bytes 24..27), which the call does not read."""
+    n = _noalloc_args(slots, state, keys, is_new)
+    _check(load().ht_cuckoo_find_or_put_noalloc(
+        _dptr(slots, "slots"), slots.numel(), _dptr(state, "state"), int(seed) & (2**64 - 1),
+        _dptr(keys, "keys"), n, _dptr(is_new, "is_new"), 1 if reset else 0, _stream(stream)),
+        "ht_cuckoo_find_or_put_noalloc")
 
 
 def make_model(num_components, bits, deg, tgt, lab, pairs):

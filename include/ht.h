@@ -91,7 +91,19 @@ typedef enum {
  *                  bits, so that distinct keys share digests.  A test knob:
  *                  it makes the full-key comparisons that tell such keys
  *                  apart run often (results are unchanged; placement gets
- *                  worse).  Other key widths: must be 0.  */
+ *                  worse).  Other key widths: must be 0.
+ *   cuckoo_chain_h1  Cuckoo, 64-bit and narrower keys: 0 (default) starts a
+ *                  new key's eviction chain at the first of its slots
+ *                  h_1..h_k that the probe of the same batch saw empty (h_1
+ *                  when it saw none); 1 always starts it at h_1, as Section
+ *                  4.1 describes.  Both keep "a key stored at h_j has h_1 ..
+ *                  h_(j-1) occupied" (slots never become empty again), so
+ *                  results are the same; the default makes fewer exchanges.
+ *   publish_wait_polls  keys wider than 128 bits, bucket scheme: how many
+ *                  times a reader polls a claimed, unpublished slot header
+ *                  of its key's tag (with back-off) before it gives up and
+ *                  the table reports HT_ERR_TIMEOUT; 0 = default 2^20 (about
+ *                  0.1 s).  Tests set it small.  */
 typedef struct ht_params {
     uint32_t num_hashes;
     uint32_t max_evictions;
@@ -104,7 +116,9 @@ typedef struct ht_params {
     int32_t l2_persist;
     uint32_t grow_load_permille;
     uint32_t digest_bits;
-    int32_t reserved_;
+    uint32_t cuckoo_chain_h1;
+    uint32_t publish_wait_polls;
+    uint32_t reserved_;
 } ht_params;
 
 typedef struct ht_table ht_table;
@@ -170,8 +184,13 @@ ht_status ht_find_or_put_append(ht_table* t, const void* d_keys, uint64_t n,
                                 unsigned long long* d_new_count, void* stream);
 
 /* Insert-if-absent with values (key_width 32 maps; d_values must be NULL for
- * key_width 64).  A key already present keeps its value; among equal keys in
- * one batch one of the supplied values wins. */
+ * key_width 64): Section 5's find-or-insert applied to (key, value) pairs,
+ * where a key that is found is left as it is, and Section 5.1.1's rule that
+ * a duplicate must not be stored twice.  A key already present keeps its
+ * value; among equal keys in one batch one of the supplied values wins.
+ * d_keys, d_values: n device words owned by the caller.  Asynchronous on
+ * `stream`; reserved keys and a full table are reported by the next
+ * synchronising call (ht_sync, ht_size). */
 ht_status ht_insert(ht_table* t, const void* d_keys, const uint32_t* d_values,
                     uint64_t n, void* stream);
 
@@ -497,6 +516,13 @@ ht_status ht_prof_read(uint32_t id, uint64_t* launches, double* total_ms);
 ht_status ht_probe_random_read(const void* d_buf, uint64_t bytes, uint32_t gran,
                                uint64_t n_access, uint64_t seed,
                                unsigned long long* d_sink, void* stream);
+/* The device address of the table's slot array and its size in bytes
+ * (the words the scheme's kernels read and claim; 8 or 16 bytes per slot,
+ * laid out as ht_create describes).  For tests and tools that inspect the
+ * words or prepare a slot state on purpose; a caller that writes them must
+ * keep the table's invariants.  Host only; HT_ERR_INVALID for NULL. */
+ht_status ht_table_words(const ht_table* t, void** d_slots, uint64_t* bytes);
+
 /* Random read-modify-write probe (not part of the hash table): n_access
  * 8-byte atomic adds of 1 at uniformly random 128-byte-aligned offsets of
  * d_buf[0..bytes) (the buffer's words change), eight in flight per thread;
@@ -520,10 +546,20 @@ ht_status ht_probe_random_rmw(void* d_buf, uint64_t bytes, uint64_t n_access, ui
  * d_slots   caller-owned device array of nslots uint64 words: the table.
  * d_state   caller-owned device block of HT_NOALLOC_STATE_BYTES bytes,
  *           16-byte aligned: counters, a 101-word stash and a 64-word
- *           overflow area.  After the work completes, bytes 0..7 hold the
- *           number of stored keys (uint64) and bytes 8..15 the number of
- *           keys dropped because no slot, stash or overflow word was left
- *           (non-zero means the set is incomplete; there is no rebuild).
+ *           overflow area.  After the work completes:
+ *             bytes 0..7    stored keys (uint64);
+ *             bytes 8..15   keys dropped because no slot, stash or overflow
+ *                           word was left (uint64; non-zero means the set is
+ *                           incomplete: there is no rebuild);
+ *             bytes 16..19  stash words in use (uint32);
+ *             bytes 20..23  overflow words in use (uint32);
+ *             bytes 24..27  sticky status bits (uint32): 1 = a reserved key
+ *                           (top bit set) was seen and skipped, 2 = the
+ *                           overflow area took a key (a regular table would
+ *                           rebuild now), 4 = a key was dropped.
+ *           The call itself returns HT_OK in all three cases: it does not
+ *           synchronise, so these facts are only in the block.  Only a
+ *           reset clears them.
  * seed      hash-constant seed; use the same seed for every call on a table.
  * d_keys    n uint64 keys, top bit 0; n <= HT_NOALLOC_MAX_BATCH, else
  *           HT_ERR_INVALID (split larger batches).
@@ -533,10 +569,14 @@ ht_status ht_probe_random_rmw(void* d_buf, uint64_t bytes, uint64_t n_access, ui
  * Semantics per call are those of ht_find_or_put on a Cuckoo table with 4
  * hash functions and an eviction bound of 256.
  * The first call on each device looks up the static array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array and each call clears the part it needs, so calls
- * whose work overlaps on the GPU (other streams, other host threads) race:
- * order them on one stream.
+ * (cudaGetSymbolAddress) and keeps it; make that first call before any
+ * stream capture.  A cudaDeviceReset ends the context that address belongs
+ * to: do not call this entry point on that device afterwards.
+ * All calls share the array.  Each call with n > 0 first empties the whole
+ * dedup set (a 4 MiB fill, a fixed cost of a few microseconds per call) and
+ * zeroes its winner count, so no call depends on what an earlier, possibly
+ * aborted, call left there.  Calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on the array: order them on one stream.
  * ------------------------------------------------------------------------- */
 #define HT_NOALLOC_STATE_BYTES 2048
 #define HT_NOALLOC_MAX_BATCH (1u << 18)

@@ -16,7 +16,8 @@ class HtParams(ctypes.Structure):
         ("lanes_per_key", ctypes.c_uint32), ("max_rebuilds", ctypes.c_uint32),
         ("max_batch", ctypes.c_uint64), ("seed", ctypes.c_uint64),
         ("l2_persist", ctypes.c_int32), ("grow_load_permille", ctypes.c_uint32),
-        ("digest_bits", ctypes.c_uint32), ("reserved_", ctypes.c_int32),
+        ("digest_bits", ctypes.c_uint32), ("cuckoo_chain_h1", ctypes.c_uint32),
+        ("publish_wait_polls", ctypes.c_uint32), ("reserved_", ctypes.c_uint32),
     ]
 
 
@@ -98,6 +99,7 @@ SIGNATURES = {
     "ht_export": (_I32, [_VP, _VP, _VP, _U64, _P(_U64), _VP]),
     "ht_clear": (_I32, [_VP, _VP]),
     "ht_info": (_I32, [_VP, _P(_U64), _P(_U32), _P(_U32)]),
+    "ht_table_words": (_I32, [_VP, _P(_VP), _P(_U64)]),
     "ht_stats": (_I32, [_VP, _P(HtTableStats), _VP]),
     "ht_grow": (_I32, [_VP, _U64, _VP]),
     "ht_multi_find_or_put": (_I32, [_VP, _U32, _VP, _U32, _VP]),

@@ -4,7 +4,8 @@ hash functions (bucket scheme); hash functions and eviction bound (Cuckoo).
 For a workload class -- scheme, key width, capacity (rounded to a power of
 two), target load and repeat rate -- it fills a table of that class with
 synthetic keys under every candidate parameter set, keeps only candidates
-whose fill is exact (every distinct key stored once), and caches the fastest
+whose fill is exact (every key new to the table flagged exactly once in its
+batch, no other key flagged, every distinct key stored), and caches the fastest
 in a JSON file keyed by device name and class.  The timing runs the library's
 own kernels; only the bookkeeping is Python.
 """
@@ -81,33 +82,46 @@ def measure_fill(params, scheme, key_width, capacity, load, dup, trials=3, seed=
     n = fresh.numel()
     B = 1 << 20
     per = max(1, int(B * (1 - dup)))
-    batches, issued = [], 0
+    batches, fresh_of, issued = [], [], 0
     while issued < n:
         nf = min(per, n - issued)
         nd = int(nf * dup / max(1e-9, 1 - dup))
         dups = fresh[torch.randint(0, issued + nf, (nd,), device=dev, generator=g)] if nd else fresh[:0]
         b = torch.cat([fresh[issued:issued + nf], dups]).to(dt)
         batches.append(b[torch.randperm(b.numel(), device=dev, generator=g)])
+        fresh_of.append(fresh[issued:issued + nf].to(dt))
         issued += nf
     try:
         t = HashTable(cap, scheme, key_width, params)
     except Exception:
         return None
-    flags = torch.empty(B + B, dtype=torch.uint8, device=dev)
+    flags = [torch.empty(b.numel(), dtype=torch.uint8, device=dev) for b in batches]
     times = []
     for r in range(trials + 1):
         ht_clear(t.handle)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for b in batches:
-            ht_find_or_put(t.handle, b, flags[:b.numel()])
+        for b, f in zip(batches, flags):
+            ht_find_or_put(t.handle, b, f)
         e1.record()
         torch.cuda.synchronize()
         if r:
             times.append(e0.elapsed_time(e1) / 1e3)
-    exact = t.sync() == 0 and t.size() == n
+    exact = t.sync() == 0 and t.size() == n and flags_exact(batches, flags, fresh_of)
     t.close()
     return min(times) if exact else None
+
+
+def flags_exact(batches, flags, fresh_of):
+    """Per key, for the last fill: in every batch the keys flagged new are
+    exactly that batch's fresh keys, each once (sorted flagged keys == sorted
+    fresh keys), so a candidate that loses or doubles a key is rejected."""
+    import torch
+    for b, f, fr in zip(batches, flags, fresh_of):
+        got = torch.sort(b[f.bool()]).values
+        if got.numel() != fr.numel() or not torch.equal(got, torch.sort(fr).values):
+            return False
+    return True
 
 
 def tune(scheme, key_width, capacity, load=0.8, dup=0.25, cache_path=None, candidates=None, measure=None,

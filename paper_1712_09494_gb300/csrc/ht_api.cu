@@ -270,6 +270,7 @@ bool valid_params(ht_scheme scheme, const ht_params& p) {
         if (p.max_evictions < 1 || p.max_evictions > 4096) return false;
         if (p.bucket_slots != 8 && p.bucket_slots != 16 && p.bucket_slots != 32) return false;
     }
+    if (p.cuckoo_chain_h1 > 1) return false;
     if (p.stash_slots > 4096) return false;
     if (p.max_batch < 1 || p.max_batch > (1ull << 26)) return false;
     if (p.max_rebuilds > 64) return false;
@@ -457,6 +458,8 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
     t->dt.ovf_slots = uint32_t(std::min<uint64_t>(kOvfSlots, std::max<uint64_t>(1024, next_pow2(t->dt.nslots / 64))));
     t->dt.k = p.num_hashes;
     t->dt.max_evict = p.max_evictions;
+    t->dt.chain_h1 = p.cuckoo_chain_h1;
+    t->dt.spin_limit = p.publish_wait_polls ? p.publish_wait_polls : kDefaultSpinLimit;
     derive_seeds(t);
 
     const cudaStream_t cs = as_stream(stream);
@@ -710,6 +713,14 @@ ht_status ht_stats(ht_table* t, ht_table_stats* out, void* stream) {
     out->overflow_used = c.ovf_used;
     out->rebuilds = t->rebuilds;
     out->flags = c.flags;
+    return HT_OK;
+}
+
+ht_status ht_table_words(const ht_table* t, void** d_slots, uint64_t* bytes) {
+    if (!t || !d_slots || !bytes) return HT_ERR_INVALID;
+    const uint64_t slot_bytes = (t->kw == 128 || (is_long(t->kw) && t->scheme == HT_CUCKOO)) ? 16 : 8;
+    *d_slots = t->dt.slots;
+    *bytes = t->dt.nslots * slot_bytes;
     return HT_OK;
 }
 

@@ -9,11 +9,21 @@
 //     claimant per distinct key becomes a "winner" (is_new = 1) appended to
 //     a compact list.
 //  2. insert: each winner runs the eviction chain: exchange the word into
-//     slot h_1(k); if the slot held a word k', find a with h_a(k') = slot and
-//     move k' to h_{a+1}(k') (Fig. 2: key 18 evicts 26 from its h_2 slot and
-//     26 moves to h_3), until an empty slot takes the word or max_evictions
-//     is reached; then the stash takes it (Section 4.1: a small stash, and a
-//     rebuild with new hash constants when it overflows).
+//     its first slot; if the slot held a word k', find a with h_a(k') = slot
+//     and move k' to h_{a+1}(k') (Fig. 2: key 18 evicts 26 from its h_2 slot
+//     and 26 moves to h_3), until an empty slot takes the word or
+//     max_evictions is reached; then the stash takes it (Section 4.1: a small
+//     stash, and a rebuild with new hash constants when it overflows).
+//     Section 4.1 starts every chain at h_1.  Here a chain starts by default
+//     at the first of h_1..h_k that the probe saw EMPTY (h_1 if none): the
+//     probe has read those slots anyway, and most new keys then need one
+//     exchange instead of an eviction at h_1 (t.chain_h1 = 1 keeps h_1).
+//
+// The probe stops at an empty h_1 (a key is never stored past an empty
+// slot of its own).  Why that holds with either start: slots never return
+// to EMPTY (an exchange always leaves a word), a chain's key is placed at
+// h_j only when h_1..h_(j-1) were seen occupied, and an evicted key moves
+// from h_a to h_(a+1) with h_a now occupied by its evictor.
 //
 // Why the dedup set: the paper's duplicate handling (Section 5.1.1: a thread
 // that evicts its own key stops) does not stop a duplicate whose first copy
@@ -89,10 +99,9 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
 #pragma unroll
         for (int u = 0; u < kU; ++u)
             if (act[u]) w[u] = __ldcg(reinterpret_cast<const unsigned long long*>(t.slots + hidx(key[u], t.seed[0], t.nslots)));
-        // An empty h_1 slot ends the table probe: every chain starts at h_1,
-        // an evicted key moves from h_a to h_{a+1}, and slots never return to
-        // EMPTY, so a key stored at h_j has h_1 .. h_{j-1} all occupied.  A
-        // miss at table load a then costs 1 + a (k - 1) probes, not k.
+        // An empty h_1 slot ends the table probe: a key stored at h_j has
+        // h_1 .. h_{j-1} all occupied (see the top of this file).  A miss at
+        // table load a then costs 1 + a (k - 1) probes, not k.
         bool more[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
@@ -107,14 +116,22 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             for (int a = 1; a < KH; ++a)
                 if (a < int(t.k) && more[u])
                     ws[u][a] = __ldcg(reinterpret_cast<const unsigned long long*>(t.slots + hidx(key[u], t.seed[a], t.nslots)));
+        // The chain start of a miss: the first of h_2..h_k seen EMPTY (0 =
+        // h_1: empty, or every slot occupied).
+        uint32_t start[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
+        for (int u = 0; u < kU; ++u) {
+            start[u] = 0;
 #pragma unroll
-            for (int a = 1; a < KH; ++a)
-                if (a < int(t.k) && more[u] && !found[u] && K::keyof(ws[u][a]) == key[u]) {
-                    found[u] = true;
-                    w[u] = ws[u][a];
+            for (int a = KH - 1; a >= 1; --a)
+                if (a < int(t.k) && more[u]) {
+                    if (K::keyof(ws[u][a]) == key[u]) {
+                        found[u] = true;
+                        w[u] = ws[u][a];
+                    }
+                    if (K::empty(ws[u][a])) start[u] = uint32_t(a);
                 }
+        }
         if (stash_used | ovf_used) {
 #pragma unroll
             for (int u = 0; u < kU; ++u)
@@ -184,7 +201,7 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                         Winner wn;
                         wn.word = K::word(key[u], VALUES ? vals[i] : 0u);
                         wn.spos = spos[u];
-                        wn.pad_ = 0;
+                        wn.start = t.chain_h1 ? 0u : start[u];
                         sc.win[at] = wn;
                     } else {                                   // more winners than the table holds
                         stored = false;
@@ -251,7 +268,7 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
                 next += stride;
                 sc.set[wn.spos] = kEmpty;      // leave the dedup set empty for the next batch
                 word[u] = wn.word;
-                pos[u] = hidx(K::keyof(wn.word), t.seed[0], t.nslots);
+                pos[u] = hidx(K::keyof(wn.word), t.seed[wn.start < t.k ? wn.start : 0u], t.nslots);
                 evictions[u] = 0;
                 live[u] = true;
             }

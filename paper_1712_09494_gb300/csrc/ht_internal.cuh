@@ -15,6 +15,7 @@ constexpr int kMaxHashes = 16;              // bucket scheme upper bound
 constexpr int kMaxCuckooHashes = 8;
 constexpr uint32_t kOvfSlots = 1u << 16;    // overflow set behind the stash
 constexpr int kBlock = 256;
+constexpr uint32_t kDefaultSpinLimit = 1u << 20;   // long-key publish wait, polls (~0.1 s)
 
 // Sticky device flags.
 enum : uint32_t {
@@ -63,13 +64,20 @@ struct DevTable {
     uint64_t digest_mask;
     uint32_t words;
     uint32_t row_words;
+    // Cuckoo: 1 starts every insertion chain at h_1 (Section 4.1); 0 at the
+    // first slot the probe saw empty.
+    uint32_t chain_h1;
+    // Long-key bucket scheme: polls of a claimed, unpublished header before
+    // a reader gives up (kFlagTimeout).
+    uint32_t spin_limit;
 };
 
-// A Cuckoo insertion job: the packed word and where its dedup claim sits.
+// A Cuckoo insertion job: the packed word, where its dedup claim sits, and
+// the hash index its eviction chain starts at (0 = h_1).
 struct Winner {
     uint64_t word;
     uint32_t spos;
-    uint32_t pad_;
+    uint32_t start;
 };
 
 // Dedup scratch of one Cuckoo table: a linear-probing set of keys.

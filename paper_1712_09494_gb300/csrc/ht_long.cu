@@ -39,7 +39,6 @@ namespace {
 constexpr uint64_t kBusy = 1ull << 62;
 constexpr uint64_t kTagMask = kBusy - 1;
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
-constexpr uint32_t kSpinLimit = 1u << 20;     // bounded wait for a publish (~0.1 s)
 constexpr int kLBS = int(kLongBucketSlots);
 
 struct LongWinner {
@@ -115,13 +114,14 @@ __device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
 }
 
 // Bucket scheme: does slot `slot`, whose header carries the key's tag, hold
-// the key?  Waits until the header is published (bounded: past the limit
-// the timeout flag is set and the slot is taken as another key's).
+// the key?  Waits until the header is published (bounded: after
+// t.spin_limit polls the timeout flag is set and the slot is taken as
+// another key's).
 __device__ bool slot_holds(const DevTable& t, uint64_t slot, const uint64_t (&k)[kLongMaxWords], uint32_t RW) {
     uint64_t h = ld_acquire(t.slots + slot);
     uint32_t spins = 0;
     while (h & kBusy) {
-        if (++spins > kSpinLimit) {
+        if (++spins > t.spin_limit) {
             set_flag(t.ctr, kFlagTimeout);
             return false;
         }

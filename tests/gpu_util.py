@@ -77,3 +77,27 @@ def check_batch_flags(batch, flags, fresh, sample_pos):
         bad.append("%d sampled keys with wrong flag counts, e.g. %s: %s (want %s)" % (
             len(wrong), kk[wrong[:3]], per_key[wrong[:3]], want[wrong[:3]]))
     return bad
+
+
+def check_batch_flags_exact(batch, flags, fresh):
+    """The complete exactly-once check of one find-or-put batch, for every key
+    of it: the flagged keys, sorted, must equal the batch's fresh keys
+    (those issued for the first time in it), sorted.  Since the fresh keys
+    are distinct, that says each fresh key is flagged exactly once and no
+    other key is flagged -- the same facts as the oracle's per-key flag
+    counts, for a stream whose earlier batches were exact.  Returns a list
+    of problems."""
+    batch = np.asarray(batch)
+    flags = np.asarray(flags)
+    bad = []
+    if set(np.unique(flags).tolist()) - {0, 1}:
+        bad.append("flags other than 0/1")
+    flagged = np.sort(batch[flags.astype(bool)])
+    want = np.sort(np.asarray(fresh))
+    if len(flagged) != len(want):
+        bad.append("batch flags %d, fresh keys %d" % (len(flagged), len(want)))
+    elif not np.array_equal(flagged, want):
+        at = np.nonzero(flagged != want)[0]
+        bad.append("%d flagged keys differ from the fresh keys, e.g. %s vs %s" % (
+            len(at), flagged[at[:3]], want[at[:3]]))
+    return bad

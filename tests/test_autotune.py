@@ -54,3 +54,17 @@ def test_tuned_parameters_fill_exactly(tmp_path, scheme, oracle_lib):
     keys = wk.distinct_keys(50_000, 64, seed=3)
     got = t.find_or_put(torch.from_numpy(keys.view(np.int64)).cuda()).cpu().numpy()
     assert got.sum() == 50_000 and t.size() == 50_000
+
+
+def test_flags_exact_rejects_a_lost_or_doubled_key():
+    import torch
+    fresh = [torch.tensor([5, 9, 2]), torch.tensor([7])]
+    batches = [torch.tensor([9, 5, 5, 2, 9]), torch.tensor([2, 7, 7, 5])]
+    good = [torch.tensor([1, 0, 1, 1, 0], dtype=torch.uint8), torch.tensor([0, 0, 1, 0], dtype=torch.uint8)]
+    assert at.flags_exact(batches, good, fresh)
+    lost = [good[0].clone(), torch.tensor([0, 0, 0, 0], dtype=torch.uint8)]
+    assert not at.flags_exact(batches, lost, fresh)
+    doubled = [torch.tensor([1, 1, 1, 1, 0], dtype=torch.uint8), good[1]]
+    assert not at.flags_exact(batches, doubled, fresh)
+    old_flagged = [good[0], torch.tensor([1, 1, 0, 0], dtype=torch.uint8)]   # 2 was stored before
+    assert not at.flags_exact(batches, old_flagged, fresh)

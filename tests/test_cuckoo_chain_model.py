@@ -1,11 +1,15 @@
 """Every interleaving of concurrent Cuckoo eviction chains, on a small model (no GPU).
 
 The insert kernel runs one chain per winner (a key new to the table,
-distinct from every other winner): the key is exchanged into its slot h_1;
-an evicted key k' that sat at slot s moves to h_{a+1}(k'), a the smallest
-index with h_a(k') = s (after h_k: h_1); after max_evictions exchanges the
-held key goes to the stash.  Section 4.1 gives the chain; the smallest-index
-rule and the wrap are this project's reading of it.
+distinct from every other winner): the key is exchanged into its first
+slot; an evicted key k' that sat at slot s moves to h_{a+1}(k'), a the
+smallest index with h_a(k') = s (after h_k: h_1); after max_evictions
+exchanges the held key goes to the stash.  Section 4.1 gives the chain and
+starts it at h_1; the smallest-index rule and the wrap are this project's
+reading of it.  The kernel's default starts a chain instead at the first
+slot h_j that the probe, run on the same table before any insert, saw EMPTY
+(h_1 when it saw none): modelled here by choosing each winner's start from
+the table as it is before the chains run.
 
 Two facts of the design are checked in every reachable state, with each
 exchange one atomic step:
@@ -14,22 +18,40 @@ exchange one atomic step:
 * the probe's early exit: a key stored at h_j (j the smallest index naming
   its slot) has h_1 .. h_{j-1} all occupied, so a probe that finds h_1 EMPTY
   may stop.  Slots never return to EMPTY, which is what makes it hold.
-A planted off-by-one (an evicted key moves on to h_{a+2} instead of
-h_{a+1}) must break the second fact, so the checker is known to see it.
+Both start rules are checked.  Two planted mistakes must break the second
+fact, so the checker is known to see them: an off-by-one (an evicted key
+moves on to h_{a+2} instead of h_{a+1}), and a start at the LAST empty slot
+the probe saw instead of the first.
 """
 import pytest
 
 E = None   # an empty slot
 
 
+def start_index(table, hs, rule):
+    """The hash index a winner's chain starts at, from the probe's view of the
+    table: "h1" (Section 4.1), "first_empty" (the kernel's default: the probe
+    stops at an empty h_1, else reads h_2..h_k, and the chain starts at the
+    first of them it saw EMPTY, else at h_1) or "last_empty" (a planted
+    mistake)."""
+    if rule == "h1":
+        return 0
+    empties = [j for j in range(len(hs)) if table[hs[j]] is E]
+    if not empties:
+        return 0
+    return empties[0] if rule == "first_empty" else empties[-1]
+
+
 class Chains:
-    def __init__(self, h, table, winners, max_evict, skip_one=False):
+    def __init__(self, h, table, winners, max_evict, skip_one=False, start="h1"):
         self.h = h                          # key -> its slots h_1 .. h_k
         self.k = len(next(iter(h.values())))
         self.max_evict = max_evict
         self.skip_one = skip_one
         self.keys = sorted([x for x in table if x is not E] + list(winners))
-        threads = tuple((w, h[w][0], 0) for w in winners)    # (held key, target slot, evictions)
+        # (held key, target slot, evictions); every start is taken from the
+        # table before any chain runs, as the probe kernel sees it.
+        threads = tuple((w, h[w][start_index(table, h[w], start)], 0) for w in winners)
         self.start = (tuple(table), (), threads)
 
     def step(self, state, i):
@@ -94,11 +116,11 @@ class Chains:
         return None, len(seen), finals
 
 
-def _sequential_table(h, keys, m, max_evict):
+def _sequential_table(h, keys, m, max_evict, start="h1"):
     """A table built by inserting keys one at a time with the same chains."""
     table, stash = [E] * m, []
     for key in keys:
-        c = Chains(h, table, [key], max_evict)
+        c = Chains(h, table, [key], max_evict, start=start)
         st = c.start
         while st[2][0] is not None:
             st = c.step(st, 0)
@@ -113,17 +135,18 @@ H = {  # 6 slots, k = 3; 'q' names slot 1 twice (h_1 = h_3)
 }
 
 
+@pytest.mark.parametrize("start", ["h1", "first_empty"])
 @pytest.mark.parametrize("pre,winners", [
     (["p", "q"], ["r", "s", "t"]),
     (["p", "q", "r"], ["s", "t", "u"]),
     (["p", "s", "u"], ["q", "v", "w"]),
 ])
-def test_concurrent_chains_conserve_keys_and_keep_the_early_exit(pre, winners):
-    table = _sequential_table(H, pre, 6, max_evict=8)
-    c = Chains(H, table, winners, max_evict=8)
+def test_concurrent_chains_conserve_keys_and_keep_the_early_exit(pre, winners, start):
+    table = _sequential_table(H, pre, 6, max_evict=8, start=start)
+    c = Chains(H, table, winners, max_evict=8, start=start)
     bad, n, finals = c.explore()
     assert bad is None, bad
-    assert finals and n > 20
+    assert finals and n > 5
     for table_f, stash, _ in finals:
         # every key once; a probe with the early exit finds each stored key
         for x in c.keys:
@@ -140,8 +163,13 @@ def test_concurrent_chains_conserve_keys_and_keep_the_early_exit(pre, winners):
             assert found, (x, table_f)
 
 
-@pytest.mark.parametrize("slots,npre,seed", [(9, 5, 1), (9, 5, 3), (10, 6, 1)])
-def test_four_concurrent_chains_on_random_hashes(slots, npre, seed):
+@pytest.mark.parametrize("slots,npre,seed,start", [
+    (9, 5, 1, "h1"), (9, 5, 3, "h1"), (10, 6, 1, "h1"),
+    # Seeds where several winners saw the same first empty slot: their chains
+    # collide there, one takes it and the others evict it.
+    (9, 5, 11, "first_empty"), (9, 5, 16, "first_empty"), (8, 4, 18, "first_empty"), (9, 5, 3, "first_empty"),
+])
+def test_four_concurrent_chains_on_random_hashes(slots, npre, seed, start):
     # k = 3 slots per key drawn at random (repeats allowed), npre keys stored
     # one at a time, then 4 chains at once into a table of load near 1: long
     # chains, some ending in the stash; thousands of states.
@@ -149,8 +177,8 @@ def test_four_concurrent_chains_on_random_hashes(slots, npre, seed):
     rng = random.Random(seed)
     names = ["k%d" % i for i in range(npre + 4)]
     h = {x: [rng.randrange(slots) for _ in range(3)] for x in names}
-    table = _sequential_table(h, names[:npre], slots, max_evict=10)
-    c = Chains(h, table, names[npre:], max_evict=10)
+    table = _sequential_table(h, names[:npre], slots, max_evict=10, start=start)
+    c = Chains(h, table, names[npre:], max_evict=10, start=start)
     bad, n, finals = c.explore()
     assert bad is None, bad
     assert n > 1000 and any(f[1] for f in finals)
@@ -174,3 +202,29 @@ def test_checker_catches_a_skipped_slot():
     c = Chains(H, table, ["r", "s", "t"], max_evict=8, skip_one=True)
     bad, n, finals = c.explore()
     assert bad is not None
+
+
+def test_first_empty_start_saves_exchanges():
+    # The reason for the default: at the same table and winners, starting at
+    # the first empty slot the probe saw never takes more exchanges in a
+    # sequential run than starting at h_1, and here takes fewer.
+    def exchanges(start):
+        table, total = _sequential_table(H, ["p", "q", "s"], 6, max_evict=8, start=start), 0
+        for w in ["r", "t", "v"]:
+            c = Chains(H, table, [w], max_evict=8, start=start)
+            st = c.start
+            while st[2][0] is not None:
+                st = c.step(st, 0)
+                total += 1
+            table = list(st[0])
+        return total
+    assert exchanges("first_empty") < exchanges("h1")
+
+
+def test_checker_catches_a_start_past_an_empty_slot():
+    # Planted: the chain starts at the LAST empty slot the probe saw.  The key
+    # then sits past an EMPTY slot of its own, which the early exit misses.
+    table = _sequential_table(H, ["p", "q"], 6, max_evict=8)
+    c = Chains(H, table, ["r", "s", "t"], max_evict=8, start="last_empty")
+    bad, n, finals = c.explore()
+    assert bad is not None and "empty" in bad

@@ -203,3 +203,47 @@ def test_unsupported_uses_are_rejected():
                                  torch.empty(10, dtype=torch.uint8, device="cuda"))
     with pytest.raises(ht.HtError):
         ht.ht_multi_find_or_put([t.handle], [(0, keys, torch.empty(10, dtype=torch.uint8, device="cuda"))])
+
+
+class _DeviceWords:
+    """A view of device memory the library owns, for torch to write into."""
+
+    def __init__(self, ptr, nwords):
+        self.__cuda_array_interface__ = {"shape": (nwords,), "typestr": "<i8", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def test_publish_wait_runs_out_and_reports_timeout():
+    """Section 4.2: a reader that meets a claimed, unpublished slot of its
+    key's tag must wait for the writer.  Here no writer exists: every header
+    of the table is claimed (busy) and never published, with tags 0..3, and
+    the digest is cut to 2 bits so every key's tag matches some of them.  The
+    wait is bounded by the table's publish_wait_polls: the kernel gives up,
+    the lookup finishes, and the next synchronising call returns
+    HT_ERR_TIMEOUT.  Nothing on the device waits without a bound."""
+    import time
+    busy = 1 << 62
+    t = ht.HashTable(1024, "bucket", 256, dict(digest_bits=2, publish_wait_polls=64))
+    ptr, nbytes = ht.ht_table_words(t.handle)
+    nwords = nbytes // 8
+    words = torch.as_tensor(_DeviceWords(ptr, nwords), device="cuda")
+    words.copy_(busy | (torch.arange(nwords, device="cuda", dtype=torch.int64) & 3))
+    torch.cuda.synchronize()
+    keys = _dev(wk.distinct_keys(256, 256, seed=5))
+    t0 = time.time()
+    found, _ = t.lookup(keys)
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 30
+    assert int(found.sum()) == 0
+    assert t.sync() == 5                                      # HT_ERR_TIMEOUT
+    assert ht.ht_stats(t.handle)["flags"] & 8
+    # find-or-put meets the same claimed headers: bounded again, no key stored.
+    flags = t.find_or_put(keys)
+    torch.cuda.synchronize()
+    assert int(flags.sum()) == 0 and t.sync() == 5
+    # Cleared, the table works normally again.
+    t.clear()
+    assert int(t.find_or_put(keys).sum()) == 256
+    assert t.sync() == 0 and t.size() == 256
+    found, _ = t.lookup(keys)
+    assert int(found.sum()) == 256

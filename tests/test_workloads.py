@@ -183,3 +183,46 @@ def test_batch_flag_check_accepts_exactly_once_and_catches_mistakes():
             dup = np.nonzero(~np.isin(kb, fresh))[0][0]          # an old key flagged new
             f3[dup] = 1
             assert check_batch_flags(kb, f3, fresh, np.array([dup]))
+
+
+def test_exact_batch_flag_check_accepts_exactly_once_and_catches_mistakes():
+    # The full-size fill test's checker of every key of every batch, on a
+    # small stream with flags made from the generator's fresh keys.
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from gpu_util import check_batch_flags_exact
+    fs = wk.fill_stream(20_000, 4096, 0.25, 64, seed=6)
+    issued = 0
+    for b in range(fs.n_batches):
+        kb = fs.batch(b)
+        nf = int(fs.fresh_counts[b])
+        fresh = wk.distinct_keys(nf, 64, seed=6, start=issued)
+        issued += nf
+        flags = np.zeros(len(kb), dtype=np.uint8)
+        _, first = np.unique(kb, return_index=True)
+        flags[first[np.isin(kb[first], fresh)]] = 1
+        # any occurrence may carry the flag: move some to the last occurrence
+        _, last = np.unique(kb[::-1], return_index=True)
+        last = len(kb) - 1 - last
+        fl2 = flags.copy()
+        moved = first[np.isin(kb[first], fresh)][:50]
+        fl2[moved] = 0
+        fl2[last[np.searchsorted(np.unique(kb), kb[moved])]] = 1
+        assert check_batch_flags_exact(kb, flags, fresh) == []
+        assert check_batch_flags_exact(kb, fl2, fresh) == []
+        if b == 1:
+            f2 = flags.copy()
+            f2[np.nonzero(f2)[0][0]] = 0                        # a new key left unflagged
+            assert check_batch_flags_exact(kb, f2, fresh)
+            f3 = flags.copy()
+            f3[np.nonzero(~np.isin(kb, fresh))[0][0]] = 1       # an old key flagged new
+            assert check_batch_flags_exact(kb, f3, fresh)
+            f4 = f3.copy()
+            f4[np.nonzero(flags)[0][0]] = 0                     # both at once: the count still matches
+            assert int(f4.sum()) == nf and check_batch_flags_exact(kb, f4, fresh)
+            rep = np.nonzero(np.isin(kb, fresh) & (flags == 0))[0][0]
+            f5 = flags.copy()
+            f5[rep] = 1                                         # a fresh key flagged twice ...
+            other = np.nonzero(flags & (kb != kb[rep]))[0][0]
+            f5[other] = 0                                       # ... and another left out
+            assert int(f5.sum()) == nf and check_batch_flags_exact(kb, f5, fresh)

@@ -486,37 +486,44 @@ def run_ours(a, rank, world, local):
     return out
 
 
-def run_e2e(a, ht, torch, dev, fs, tables, schemes, world):
+def run_e2e(a, ht, torch, dev, fs, tables, schemes, world, nbuf=3):
     """Same step through the public API with the keys in pinned host memory
     and the is_new flags returned to pinned host memory, every copy inside
     the timed region.  Copies overlap the kernels as a user would arrange
-    it: batch b+1 is copied in on one stream and batch b-1's flags copied
-    out on another while batch b runs (two device buffers, events guard
-    their reuse)."""
+    it: keys are copied in on one stream up to nbuf - 1 batches ahead of the
+    find-or-put calls and flags copied out on another, through nbuf device
+    buffers used round robin across batches, fills and steps (events guard
+    their reuse), so the copy of a fill's first batch overlaps the previous
+    fill's last kernels.  Reported beside the rate: the host link's measured
+    rate, the time the find-or-put calls kept the device busy, and the rest
+    of the step (copies or gaps the kernels waited on)."""
     B = 1 << a.batch_log2
     keys_h = torch.from_numpy(fs.keys.view(np.int64)).pin_memory()
     out_h = torch.empty(fs.n_issued, dtype=torch.uint8).pin_memory()
-    kbuf = [torch.empty(B, dtype=torch.int64, device=dev) for _ in range(2)]
-    fbuf = [torch.empty(B, dtype=torch.uint8, device=dev) for _ in range(2)]
+    kbuf = [torch.empty(B, dtype=torch.int64, device=dev) for _ in range(nbuf)]
+    fbuf = [torch.empty(B, dtype=torch.uint8, device=dev) for _ in range(nbuf)]
     offs = fs.offsets.tolist()
     comp = torch.cuda.current_stream(dev)
     h2d = torch.cuda.Stream(dev)
     d2h = torch.cuda.Stream(dev)
     ev = lambda: torch.cuda.Event()
-    k_free = [ev() for _ in range(2)]     # kernel done reading kbuf[i]
-    f_free = [ev() for _ in range(2)]     # copy-out done reading fbuf[i]
-    k_full = [ev() for _ in range(2)]
-    f_full = [ev() for _ in range(2)]
-    for i in range(2):
+    k_free = [ev() for _ in range(nbuf)]     # kernel done reading kbuf[i]
+    f_free = [ev() for _ in range(nbuf)]     # copy-out done reading fbuf[i]
+    k_full = [ev() for _ in range(nbuf)]
+    f_full = [ev() for _ in range(nbuf)]
+    for i in range(nbuf):
         k_free[i].record(comp)
         f_free[i].record(comp)
+    seq = [0]                                # batches issued so far (round-robin buffer index)
+    busy = []                                # (start, end) events around each find-or-put call
 
-    def step():
+    def step(record=False):
         for s in schemes:
             t = tables[s]
             ht.ht_clear(t.handle)
             for b in range(fs.n_batches):
-                i = b & 1
+                i = seq[0] % nbuf
+                seq[0] += 1
                 m = offs[b + 1] - offs[b]
                 h2d.wait_event(k_free[i])
                 with torch.cuda.stream(h2d):
@@ -524,7 +531,13 @@ def run_e2e(a, ht, torch, dev, fs, tables, schemes, world):
                 k_full[i].record(h2d)
                 comp.wait_event(k_full[i])
                 comp.wait_event(f_free[i])
+                if record:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(comp)
                 ht.ht_find_or_put(t.handle, kbuf[i][:m], fbuf[i][:m], stream=comp)
+                if record:
+                    e1.record(comp)
+                    busy.append((e0, e1))
                 k_free[i].record(comp)
                 f_full[i].record(comp)
                 d2h.wait_event(f_full[i])
@@ -540,10 +553,11 @@ def run_e2e(a, ht, torch, dev, fs, tables, schemes, world):
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(comp)
     for _ in range(a.steps):
-        step()
+        step(record=True)
     t1.record(comp)
     torch.cuda.synchronize()
     ms = reduce_max(t0.elapsed_time(t1) / a.steps, dev)
+    busy_ms = sum(e0.elapsed_time(e1) for e0, e1 in busy) / a.steps
     # the last step's flags must count exactly the distinct keys
     if int(out_h.sum()) != fs.n_distinct:
         raise RuntimeError("e2e flags do not count the distinct keys")
@@ -566,9 +580,11 @@ def run_e2e(a, ht, torch, dev, fs, tables, schemes, world):
     return {"value": round(fs.n_issued * len(schemes) * world / (ms / 1e3) / 1e6, 1), "unit": "Mops/s",
             "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d_bytes),
             "d2h_bytes_per_step": int(fs.n_issued * len(schemes)),
-            "overlap": "3 streams (copy-in, kernels, copy-out), 2 device buffers",
+            "overlap": "3 streams (copy-in, kernels, copy-out), %d device buffers round robin" % nbuf,
             "h2d_gbs_measured": round(h2d_gbs, 1),
-            "link_bound_ms_per_step": round(h2d_bytes / (h2d_gbs * 1e9) * 1e3, 2)}
+            "link_bound_ms_per_step": round(h2d_bytes / (h2d_gbs * 1e9) * 1e3, 2),
+            "find_or_put_busy_ms_per_step": round(busy_ms, 3),
+            "kernel_stream_waiting_ms_per_step": round(ms - busy_ms, 3)}
 
 
 def run_probe(ht, torch, dev):
@@ -660,61 +676,66 @@ def run_bfs(ht, torch, dev, schemes, warmup=1, reps=3):
 
 def run_batched(ht, torch):
     """Config 4: 256 explorations (6-10 components, 8-32 local states,
-    2^10..2^20 states each): graph-captured batched steps vs one exploration
-    at a time, same tables; results checked against the stored levels."""
+    2^10..2^20 states each), bucket and Cuckoo tables: the persistent launch
+    (one cooperative kernel per table kind runs every level of every
+    exploration), the per-step graph and per-step launches (bucket), and one
+    exploration at a time (the baseline), same tables; every run's levels
+    checked against the stored oracle levels.  Then the same with each
+    exploration's table parameters picked by the autotuner."""
     from workloads import statespace as ss
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "statespace_batched.json")))
     models = ss.batched_models(gold["model"]["count"], seed=gold["model"]["seed"])
     caps = [max(256, int(g["states"] / 0.7)) for g in gold["explorations"]]
-    mx = ht.MultiExploration([_hmodel(ht, m) for m in models], [0] * len(models), caps)
+    tot = sum(g["successors"] for g in gold["explorations"])
     res = {"workload": "%d explorations, %d states, %d successors in total" % (
-        len(models), sum(g["states"] for g in gold["explorations"]), sum(g["successors"] for g in gold["explorations"]))}
-    for mode, name in ((0, "batched_graph"), (1, "batched_launches"), (2, "one_table_at_a_time")):
-        times = []
-        for r in range(3):
+        len(models), sum(g["states"] for g in gold["explorations"]), tot)}
+
+    def exact(mx):
+        return all(mx.result(i)["states"] == g["states"] and
+                   mx.result(i)["level_sizes"] == [lv[0] for lv in g["levels"]]
+                   for i, g in enumerate(gold["explorations"]))
+
+    def timed(mx, mode, reps=3):
+        times, steps = [], 0
+        for r in range(reps):
             mx.reset()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             steps = mx.run(mode=mode)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
-        ok = all(mx.result(i)["states"] == g["states"] and mx.result(i)["level_sizes"] == [lv[0] for lv in g["levels"]]
-                 for i, g in enumerate(gold["explorations"]))
         sec = min(times[1:])
-        tot = sum(g["successors"] for g in gold["explorations"])
-        res[name] = {"seconds": round(sec, 4), "steps": steps, "find_or_put_mops": round(tot / sec / 1e6, 1),
-                     "levels_match_oracle": bool(ok)}
-    res["speedup_batched_vs_per_table"] = round(res["one_table_at_a_time"]["seconds"] / res["batched_graph"]["seconds"], 2)
-    mx.close()
-    # Autotuned: each exploration's capacity class tuned once (bucket width,
-    # lanes per key, hash functions) for a BFS-like repeat rate.
-    import tempfile
-    from paper_1712_09494_gb300 import autotune
-    t0 = time.perf_counter()
-    with tempfile.TemporaryDirectory() as d:
-        cache = os.path.join(d, "autotune.json")
-        params = [autotune.tune("bucket", m.key_width, c, load=0.7, dup=0.9, cache_path=cache)
-                  for m, c in zip(models, caps)]
-        n_classes = len(json.load(open(cache)))
-    tune_s = time.perf_counter() - t0
-    mx = ht.MultiExploration([_hmodel(ht, m) for m in models], [0] * len(models), caps, params=params)
-    times = []
-    for r in range(3):
-        mx.reset()
-        torch.cuda.synchronize()
+        return {"seconds": round(sec, 4), "steps": steps, "find_or_put_mops": round(tot / sec / 1e6, 1),
+                "levels_match_oracle": bool(exact(mx))}
+
+    runs = {"bucket": ((0, "batched_persistent"), (3, "batched_graph"), (1, "batched_launches"),
+                       (2, "one_table_at_a_time")),
+            "cuckoo": ((0, "batched_persistent"), (2, "one_table_at_a_time"))}
+    for scheme, modes in runs.items():
+        mx = ht.MultiExploration([_hmodel(ht, m) for m in models], [0] * len(models), caps, schemes=scheme)
+        r = {name: timed(mx, mode) for mode, name in modes}
+        r["speedup_persistent_vs_per_table"] = round(r["one_table_at_a_time"]["seconds"] /
+                                                     r["batched_persistent"]["seconds"], 2)
+        mx.close()
+        # Autotuned: each exploration's capacity class tuned once (bucket:
+        # width, lanes, hash functions; Cuckoo: hash functions, eviction
+        # bound) for a BFS-like repeat rate, then the persistent run.
+        import tempfile
+        from paper_1712_09494_gb300 import autotune
         t0 = time.perf_counter()
-        steps = mx.run(mode=0)
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
-    ok = all(mx.result(i)["states"] == g["states"] and mx.result(i)["level_sizes"] == [lv[0] for lv in g["levels"]]
-             for i, g in enumerate(gold["explorations"]))
-    shapes = sorted({"%dx%d/k%d" % (p["bucket_slots"], p["lanes_per_key"], p["num_hashes"]) for p in params})
-    tot = sum(g["successors"] for g in gold["explorations"])
-    res["batched_graph_autotuned"] = {"seconds": round(min(times[1:]), 4), "steps": steps,
-                                      "find_or_put_mops": round(tot / min(times[1:]) / 1e6, 1),
-                                      "levels_match_oracle": bool(ok), "tuning_seconds": round(tune_s, 2),
-                                      "classes_tuned": n_classes, "chosen": shapes}
-    mx.close()
+        with tempfile.TemporaryDirectory() as d:
+            cache = os.path.join(d, "autotune.json")
+            params = [autotune.tune(scheme, m.key_width, c, load=0.7, dup=0.9, cache_path=cache)
+                      for m, c in zip(models, caps)]
+            n_classes = len(json.load(open(cache)))
+        tune_s = time.perf_counter() - t0
+        mx = ht.MultiExploration([_hmodel(ht, m) for m in models], [0] * len(models), caps, params=params,
+                                 schemes=scheme)
+        r["batched_persistent_autotuned"] = dict(timed(mx, 0), tuning_seconds=round(tune_s, 2),
+                                                 classes_tuned=n_classes,
+                                                 chosen=sorted({json.dumps(p, sort_keys=True) for p in params}))
+        mx.close()
+        res[scheme] = r
     return res
 
 
@@ -1093,7 +1114,7 @@ def serving_keys(trace, load=0.8, seed=6):
     return keys
 
 
-def run_serving_once(ht, a, pack, inflight, trace, keys):
+def run_serving_once(ht, a, pack, inflight, trace, keys, schemes=None):
     import threading
     caps, table, sizes, arrivals = trace
     n_req = len(sizes)
@@ -1130,7 +1151,7 @@ def run_serving_once(ht, a, pack, inflight, trace, keys):
     for i in range(n_req):
         t = int(table[i])
         if t not in tid:
-            tid[t] = srv.open_table(int(caps[t]), "bucket")
+            tid[t] = srv.open_table(int(caps[t]), schemes[t] if schemes is not None else "bucket")
         now = time.perf_counter() - t0
         if arrivals[i] > now:
             time.sleep(arrivals[i] - now)
@@ -1144,13 +1165,21 @@ def run_serving_once(ht, a, pack, inflight, trace, keys):
             len(errors), a.serve_deadline, errors[0])}
     srv.close()
     lat = np.array(done_lat)
+    # Where the worker's wall time goes: admission (allocating and clearing
+    # tables), packing keys into staging, finishing (results out), and the
+    # device time of the batches; the largest share names the limiter.
+    dev_s = st["batches"] * st["batch_gpu_us_mean"] / 1e6
+    shares = {"admission": st["admit_seconds"] / wall, "packing": st["pack_seconds"] / wall,
+              "finishing": st["finish_seconds"] / wall, "device_batches": dev_s / wall}
     return {"p50_us": round(float(np.percentile(lat, 50)), 1), "p99_us": round(float(np.percentile(lat, 99)), 1),
             "mean_us": round(float(lat.mean()), 1), "sustained_mops": round(float(sizes.sum()) / wall / 1e6, 1),
             "wall_s": round(wall, 3), "batches": int(st["batches"]), "errors": len(errors),
             "worker": {"admit_s": round(st["admit_seconds"], 3), "pack_s": round(st["pack_seconds"], 3),
                        "finish_s": round(st["finish_seconds"], 3), "batch_us_mean": round(st["batch_us_mean"], 1),
                        "batch_gpu_us_mean": round(st["batch_gpu_us_mean"], 1),
-                       "tables_created": int(st["tables_created"])}}
+                       "tables_created": int(st["tables_created"]),
+                       "share_of_wall": {k: round(v, 3) for k, v in shares.items()},
+                       "limiter": max(shares, key=shares.get)}}
 
 
 def run_serving(ht, a):
@@ -1165,7 +1194,20 @@ def run_serving(ht, a):
     pinned = [torch.from_numpy(k.view(np.int64)).pin_memory() for k in serving_keys(trace)]
     keys = [p.numpy().view(np.uint64) for p in pinned]
     out["continuous_batching"] = run_serving_once(ht, a, pack=1, inflight=4, trace=trace, keys=keys)
+    # Packing alone: the same four batch slots in flight, one launch per request.
+    out["per_request_launches_inflight4"] = run_serving_once(ht, a, pack=0, inflight=4, trace=trace, keys=keys)
     out["per_request_launches"] = run_serving_once(ht, a, pack=0, inflight=1, trace=trace, keys=keys)
+    out["packing_speedup_at_inflight4"] = round(
+        out["continuous_batching"].get("sustained_mops", 0) /
+        max(1e-9, out["per_request_launches_inflight4"].get("sustained_mops", 0)), 2)
+    # Cuckoo tables in the same trace: every other table is a Cuckoo table
+    # (its requests run the probe / insert kernels; bucket tables share the
+    # packed kernel).
+    mixed = ["cuckoo" if t % 2 else "bucket" for t in range(len(caps))]
+    out["continuous_batching_mixed_schemes"] = run_serving_once(ht, a, pack=1, inflight=4, trace=trace, keys=keys,
+                                                                schemes=mixed)
+    out["per_request_launches_mixed_schemes"] = run_serving_once(ht, a, pack=0, inflight=4, trace=trace, keys=keys,
+                                                                 schemes=mixed)
     # Offered rate swept towards saturation (continuous batching; the same
     # requests, only the arrival times change).
     sweep = []

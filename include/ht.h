@@ -380,32 +380,49 @@ ht_status ht_multi_find_or_put(ht_table* const* tables, uint32_t ntables, const 
 
 /* ---------------------------------------------------------------------------
  * Batched exploration: `count` independent explorations (models of uneven
- * sizes) advanced together.  Each exploration gets its own bucket-scheme
- * table of h_capacity[i] slots (h_params: NULL or `count` parameter sets;
- * key width 32 when the model's vector fits 31 bits, else 64) and a states
- * array holding its reachable states in level order.  One step expands a
- * share of every active exploration's current level with three kernels over
- * all explorations (advance cursors, generate successors, find-or-put and
- * append); the step is captured once as a CUDA graph and replayed.
- * Allocates everything at creation (cudaMalloc), frees at destroy.
+ * sizes) advanced together.  The paper times one kernel launch per batch
+ * and table (Sections 4.1, 5); this form advances many tables' BFS levels
+ * (Section 3.2) together.  Each exploration gets its own table of
+ * h_capacity[i] slots (scheme h_schemes[i], bucket when h_schemes is NULL;
+ * h_params: NULL or `count` parameter sets; key width 32 when the model's
+ * vector fits 31 bits, else 64) and a states array holding its reachable
+ * states in level order.  A step expands a share of every active
+ * exploration's current level: advance the cursors and share the successor
+ * buffer, generate successors, find-or-put them each against its own table
+ * and append the new states.  Explorations are grouped by table kind (key
+ * width, scheme, bucket shape).  Allocates everything at creation
+ * (cudaMalloc), frees at destroy.  Errors: HT_ERR_INVALID (count 0 or
+ * > 65536, a malformed model, a reserved initial state, max_levels 0 or
+ * > 65536, a scheme other than HT_BUCKET / HT_CUCKOO), HT_ERR_OOM.
  * ------------------------------------------------------------------------- */
 typedef struct ht_multi ht_multi;
 
 ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64_t* h_s0,
                           const uint64_t* h_capacity, const ht_params* h_params, uint32_t max_levels,
                           void* stream, ht_multi** out);
+ht_status ht_multi_create_ex(uint32_t count, const ht_model* h_models, const uint64_t* h_s0,
+                             const uint64_t* h_capacity, const ht_scheme* h_schemes, const ht_params* h_params,
+                             uint32_t max_levels, void* stream, ht_multi** out);
 
 /* Empties every table and states array (required before every run but the
  * first after creation). */
 ht_status ht_multi_reset(ht_multi* m, void* stream);
 
 /* Runs every exploration to completion (or to max_levels / a full states
- * array).  mode 0: batched, graph-captured steps; mode 1: the same steps as
- * plain launches; mode 2: one exploration after another with ht_bfs (one
- * table per launch sequence, the baseline).  max_steps 0 = no limit beyond a
- * safety bound.  Synchronises once per step.  HT_ERR_FULL when a table had
- * to drop a key (its capacity was too small for its exploration); the
- * results are then inexact. */
+ * array).  mode 0: persistent -- one cooperative launch per group runs
+ * every step of every exploration on the device, with grid-wide barriers
+ * between the phases of a step; each barrier wait is bounded (2 s), and a
+ * wait that runs out ends the launch and the call returns HT_ERR_TIMEOUT.
+ * The host synchronises once, to read the results.  Bucket and Cuckoo
+ * tables.  mode 1: the same steps as one launch per phase, the host reading
+ * an activity flag after every step (bucket tables only); mode 2: one
+ * exploration after another with ht_bfs (per-level launches for one table
+ * at a time: the baseline; both schemes); mode 3: mode 1's step captured
+ * once as a CUDA graph and replayed per step (bucket tables only).  Modes
+ * 1 and 3 with a Cuckoo exploration: HT_ERR_INVALID.  max_steps 0 = no
+ * limit beyond a safety bound.  HT_ERR_FULL when a table had to drop a key
+ * (its capacity was too small for its exploration); the results are then
+ * inexact.  Tables must be empty when a run starts (ht_multi_reset). */
 ht_status ht_multi_run(ht_multi* m, int mode, uint64_t max_steps, void* stream);
 
 /* Result of exploration i after a run: non-empty levels, states, successors
@@ -417,7 +434,8 @@ ht_status ht_multi_result(const ht_multi* m, uint32_t i, uint64_t* levels, uint6
                           uint64_t* successors, int32_t* complete, uint64_t* h_level_sizes,
                           const void** d_states, void* h_states, uint64_t h_states_cap);
 
-/* Steps (graph launches, or levels in mode 2) the last run took. */
+/* Steps the last run took (steps of the largest group in modes 0, 1 and 3;
+ * the sum of the explorations' levels in mode 2). */
 uint64_t ht_multi_steps(const ht_multi* m);
 
 ht_status ht_multi_destroy(ht_multi* m);

@@ -329,24 +329,34 @@ def ht_bfs(table, model, s0=0, max_levels=4096, states=None, states_cap=0, strea
 
 
 class MultiExploration:
-    """Many explorations advanced together (ht_multi_*)."""
+    """Many explorations advanced together (ht_multi_*).  `schemes`: None
+    (all bucket), one scheme for all, or one per exploration.  run(mode):
+    0 persistent launch, 1 per-step launches, 2 one exploration at a time,
+    3 per-step graph replay."""
 
-    def __init__(self, models, s0, capacities, params=None, max_levels=4096, stream=None):
+    def __init__(self, models, s0, capacities, params=None, max_levels=4096, stream=None, schemes=None):
         n = len(models)
         arr_m = (HtModel * n)(*models)
         arr_s0 = (ctypes.c_uint64 * n)(*[int(x) for x in s0])
         arr_c = (ctypes.c_uint64 * n)(*[int(x) for x in capacities])
+        if schemes is None:
+            sch = [HT_BUCKET] * n
+        elif isinstance(schemes, (str, int)):
+            sch = [scheme_of(schemes)] * n
+        else:
+            sch = [scheme_of(x) for x in schemes]
+        arr_s = (ctypes.c_int32 * n)(*sch)
         arr_p = None
         if params is not None:
-            arr_p = (HtParams * n)(*[_params(p, HT_BUCKET) if p is not None else ht_default_params(HT_BUCKET)
-                                    for p in params])
+            arr_p = (HtParams * n)(*[_params(p, sc) if p is not None else ht_default_params(sc)
+                                    for p, sc in zip(params, sch)])
         out = ctypes.c_void_p()
-        _check(load().ht_multi_create(n, arr_m, arr_s0, arr_c, arr_p, int(max_levels), _stream(stream),
-                                      ctypes.byref(out)), "ht_multi_create")
+        _check(load().ht_multi_create_ex(n, arr_m, arr_s0, arr_c, arr_s, arr_p, int(max_levels), _stream(stream),
+                                         ctypes.byref(out)), "ht_multi_create_ex")
         self._h = out
         self.count = n
         self.max_levels = int(max_levels)
-        self._keepalive = (arr_m, arr_s0, arr_c, arr_p)
+        self._keepalive = (arr_m, arr_s0, arr_c, arr_p, arr_s)
 
     def reset(self, stream=None):
         _check(load().ht_multi_reset(self._h, _stream(stream)), "ht_multi_reset")

@@ -117,6 +117,7 @@ SIGNATURES = {
     "ht_bfs": (_I32, [_VP, _P(HtModel), _U64, _U32, _VP, _VP, _U64, _P(HtBfsResult), _VP]),
     "ht_bfs_fused": (_I32, [_VP, _P(HtModel), _U64, _U32, _VP, _VP, _U64, _P(HtBfsResult), _VP]),
     "ht_multi_create": (_I32, [_U32, _VP, _VP, _VP, _VP, _U32, _VP, _P(_VP)]),
+    "ht_multi_create_ex": (_I32, [_U32, _VP, _VP, _VP, _VP, _VP, _U32, _VP, _P(_VP)]),
     "ht_multi_reset": (_I32, [_VP, _VP]),
     "ht_multi_run": (_I32, [_VP, ctypes.c_int, _U64, _VP]),
     "ht_multi_result": (_I32, [_VP, _U32, _P(_U64), _P(_U64), _P(_U64), _P(ctypes.c_int32), _VP, _P(_VP), _VP,

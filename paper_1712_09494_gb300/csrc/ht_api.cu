@@ -785,6 +785,7 @@ uint64_t ht::model_max_successors(const ht_model* m, uint32_t key_width) {
 }
 
 const DevTable& ht::table_dev(const ht_table* t) { return t->dt; }
+const DevScratch& ht::table_scratch(const ht_table* t) { return t->sc; }
 void ht::table_release(ht_table* t, cudaStream_t s) {
     if (!t) return;
     DeviceGuard g(t->device);

@@ -5,7 +5,7 @@
 #include <cstring>
 #include <type_traits>
 
-#include "ht_internal.cuh"
+#include "ht_multi_dev.cuh"
 
 namespace ht {
 namespace {
@@ -87,59 +87,11 @@ successors_kernel(const PreparedModel* __restrict__ model, const T* __restrict__
 }
 
 // Multi-table successors: the expanded states of every exploration form one
-// index space [0, work_total); a thread finds its exploration by binary
-// search over the prefix work_off and appends to that exploration's segment
-// of the successor buffer.
-template <typename T>
+// index space; each thread finds its exploration by binary search and
+// appends to that exploration's segment of the successor buffer.
 __global__ void __launch_bounds__(kBlock) multi_successors_kernel(const MultiDev m, uint64_t max_work) {
-    const uint64_t work = min(uint64_t(__ldcg(m.work_total)), max_work);
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    const uint64_t rounds = (work + stride - 1) / stride;          // warp-uniform trip count
-    const int lane = threadIdx.x & 31;
-    for (uint64_t r = 0; r < rounds; ++r) {
-        const uint64_t v = r * stride + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-        const bool act = v < work;
-        uint32_t e = 0;
-        uint32_t cnt = 0;
-        uint64_t s = 0;
-        if (act) {
-            uint32_t a = 0, b = m.count;               // largest e with work_off[e] <= v
-            while (b - a > 1) {
-                const uint32_t mid = (a + b) / 2;
-                if (__ldcg(m.work_off + mid) <= v) a = mid; else b = mid;
-            }
-            e = a;
-            const uint64_t idx = __ldcg(m.cur + e) + (v - __ldcg(m.work_off + e));
-            s = uint64_t(static_cast<const T*>(m.states[e])[idx]);
-            cnt = count_successors(m.models[e], s);
-        }
-        // Consecutive lanes hold consecutive v, so lanes of one exploration
-        // form a contiguous run; the run's first lane reserves for the run.
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, act ? e : 0xFFFFFFFFu);
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += x;
-        }
-        const int first = __ffs(peers) - 1;
-        const int last = 31 - __clz(peers);
-        const uint32_t before = __shfl_sync(0xFFFFFFFFu, incl - cnt, first);
-        const uint32_t run = __shfl_sync(0xFFFFFFFFu, incl, last) - before;
-        unsigned long long base = 0;
-        if (act && lane == first && run) {
-            base = atomicAdd(m.seg_cnt + e, (unsigned long long)run);
-            atomicAdd(m.gen + e, (unsigned long long)run);
-        }
-        base = __shfl_sync(0xFFFFFFFFu, base, first);
-        if (!act || !cnt) continue;
-        uint64_t pos = __ldcg(m.seg_off + e) + base + (incl - cnt - before);
-        const uint64_t end = __ldcg(m.seg_off + e) + __ldcg(m.take + e) * __ldcg(m.msucc + e);
-        for_each_successor(m.models[e], s, [&](uint64_t x) {
-            if (pos < end && pos < m.succ_cap) m.succ[pos] = x;
-            ++pos;
-        });
-    }
+    multi::successors(m, max_work, uint64_t(blockIdx.x) * blockDim.x + threadIdx.x, stride);
 }
 
 }  // namespace
@@ -177,15 +129,10 @@ PreparedModel prepare_model(const ht_model& h) {
     return p;
 }
 
-cudaError_t multi_successors(int kw, const MultiDev& m, uint64_t max_work, cudaStream_t s) {
+cudaError_t multi_successors(int, const MultiDev& m, uint64_t max_work, cudaStream_t s) {
     ProfScope ps(kKSuccessors, s);
-    if (kw == 32) {
-        auto k = multi_successors_kernel<uint32_t>;
-        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(m, max_work);
-    } else {
-        auto k = multi_successors_kernel<uint64_t>;
-        k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(m, max_work);
-    }
+    auto k = multi_successors_kernel;
+    k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(m, max_work);
     return cudaGetLastError();
 }
 

@@ -177,6 +177,7 @@ Prof& prof() {
 const char* kNames[kKNumKernels] = {
     "bucket_find_or_put", "bucket_lookup", "cuckoo_probe", "cuckoo_insert", "cuckoo_lookup",
     "export", "clear", "compact", "probe_random_read", "successors", "probe_random_rmw",
+    "multi_persistent",
 };
 
 }  // namespace

@@ -309,6 +309,7 @@ enum KernelId : uint32_t {
     kKProbeRead,
     kKSuccessors,
     kKProbeRmw,
+    kKMultiPersistent,
     kKNumKernels
 };
 
@@ -514,6 +515,7 @@ cudaError_t long_export(const DevTable& t, bool cuckoo, void* keys, unsigned lon
 
 // Read-only views of a table for the batched form (ht_api.cu).
 const DevTable& table_dev(const ht_table* t);
+const DevScratch& table_scratch(const ht_table* t);
 BucketCfg table_bucket_cfg(const ht_table* t);
 ht_scheme table_scheme(const ht_table* t);
 uint32_t table_key_width(const ht_table* t);
@@ -532,6 +534,7 @@ cudaError_t successors(int kw, const PreparedModel* model, const void* states, u
 // Batched exploration of many models at once (ht_multi.cu).  One step
 // processes a slice of every exploration's current BFS level.
 // ---------------------------------------------------------------------------
+struct MultiWinner;
 struct MultiDev {
     uint32_t count;                  // explorations in this group
     uint32_t max_levels;
@@ -558,10 +561,48 @@ struct MultiDev {
     uint64_t* succ;                  // successor buffer (64-bit words)
     uint64_t succ_cap;
     const unsigned long long* s0;    // [count] initial states
+    // Per exploration, the width of its states: 1 = 32-bit words (a model of
+    // at most 31 bits), 0 = 64-bit words.  The tables of a group are always
+    // addressed as 64-bit key tables: a 32-bit set table holds a key k as
+    // the word k (value 0 above it), exactly the word a 64-bit table holds.
+    const uint8_t* narrow;           // [count]
+    // Cuckoo groups: each table's dedup scratch, a cap on the states one
+    // step may expand (0 = none; keeps a step's keys within the table's
+    // dedup capacity), and one winner list for all tables of the group.
+    const DevScratch* scratch;       // [count] (nullptr for bucket groups)
+    const unsigned long long* take_cap;  // [count] (nullptr: no cap)
+    MultiWinner* win;                // [win_cap]
+    unsigned long long* win_count;   // [1] winners of this step
+    uint64_t win_cap;
+    // Persistent form: grid barrier words (arrivals, generation), sticky
+    // status bits of the run and the number of steps it made.
+    unsigned int* bar;               // [2]
+    unsigned int* status;            // [1]
+    unsigned long long* steps;       // [1]
+};
+
+// A Cuckoo insertion job of the batched form: the packed word, its claim in
+// its table's dedup set, and tag = (exploration << 8) | chain start index.
+struct MultiWinner {
+    uint64_t word;
+    uint32_t spos;
+    uint32_t tag;
+};
+
+// Status bits of a persistent batched run (MultiDev::status).
+enum : uint32_t {
+    kMultiTimeout = 1u,     // a grid barrier wait ran past its bound
+    kMultiBadInit = 2u,     // an initial state could not be placed (table not empty)
 };
 
 // budget: successors the step may generate (the buffer holds budget + slack).
 cudaError_t multi_advance(const MultiDev& m, uint64_t budget, cudaStream_t s);
+// The whole batched run of one group in one cooperative (co-resident)
+// launch: every level of every exploration, with bounded grid barriers
+// between the phases of a step (ht_persist.cu).  scheme: HT_BUCKET (c gives
+// the bucket shape) or HT_CUCKOO.
+cudaError_t multi_persistent(ht_scheme scheme, const BucketCfg& c, const MultiDev& m, uint64_t budget,
+                             uint64_t max_steps, uint64_t max_work, uint64_t max_tiles, cudaStream_t s);
 cudaError_t multi_successors(int kw, const MultiDev& m, uint64_t max_work, cudaStream_t s);
 // Tiles of 32 successors, each against its own exploration's table; new
 // states are appended to that exploration's states.

@@ -1,25 +1,34 @@
 // Batched exploration: many independent state-space BFS runs of uneven
-// sizes advanced together, one step of every run per graph launch.
+// sizes advanced together (ht_multi_*).
 //
 // Each exploration e owns a table, a states array (all its states in level
 // order: level d is [lo, hi) when it is being expanded) and a cursor `cur`
-// into the current level.  One step is three kernels over all explorations
-// of a group (tables of the same key width and bucket shape):
-//   advance     one block: moves every cursor past the states expanded in the
-//               previous step, opens the next level when a level is done,
-//               and shares the successor buffer among the explorations that
-//               still have work (`take` states each), with prefix sums;
-//   successors  one thread per expanded state, found by binary search;
-//   find-or-put one warp per 32 successors of one exploration (bucket_tile),
-//               new states appended to that exploration's states array.
-// The step is captured once as a CUDA graph and replayed until no
-// exploration is active; the host reads one flag per step.
+// into the current level.  Explorations are grouped by table kind (key
+// width, scheme, bucket shape); a step of a group is advance / successors /
+// find-or-put over all its explorations (ht_multi_dev.cuh).  Four ways to
+// run them (ht_multi_run's mode):
+//   0  persistent: one cooperative launch per group runs every step, with
+//      bounded grid barriers between phases (ht_persist.cu); the host waits
+//      once, for the results.  Bucket and Cuckoo groups.
+//   1  one launch per phase and step, the host reading an `active` flag
+//      after every step (bucket groups).
+//   2  one exploration after another with ht_bfs (the baseline: per-level
+//      launches for one table at a time).  Bucket and Cuckoo.
+//   3  mode 1's step captured once as a CUDA graph and replayed per step
+//      (bucket groups).
 #include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
 
-#include "ht_internal.cuh"
+#include "ht_multi_dev.cuh"
+
+// Successors a step may generate (the upper bound take * msucc summed over
+// the explorations); the successor buffer holds that plus per-exploration
+// rounding slack.
+#ifndef HT_MULTI_BUDGET_LOG2
+#define HT_MULTI_BUDGET_LOG2 26
+#endif
 
 using namespace ht;
 
@@ -35,111 +44,9 @@ __global__ void multi_flags_kernel(const DevTable* __restrict__ tables, uint32_t
 
 constexpr int kAdvThreads = 1024;
 
-// Block-wide sum of one value per thread (blockDim.x == kAdvThreads).
-__device__ unsigned long long block_sum(unsigned long long v, unsigned long long* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    unsigned long long t = 0;
-    if (warp == 0) {
-        t = lane < (kAdvThreads / 32) ? sh[lane] : 0;
-        for (int o = 16; o; o >>= 1) t += __shfl_down_sync(0xFFFFFFFFu, t, o);
-        if (lane == 0) sh[32] = t;
-    }
-    __syncthreads();
-    return sh[32];
-}
-
-// Block-wide exclusive scan of one value per thread.
-__device__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long incl = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += x;
-    }
-    __syncthreads();
-    if (lane == 31) sh[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        unsigned long long w = lane < (kAdvThreads / 32) ? sh[lane] : 0;
-        unsigned long long wi = w;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long x = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-            if (lane >= o) wi += x;
-        }
-        sh[lane] = wi - w;
-    }
-    __syncthreads();
-    return sh[warp] + incl - v;
-}
-
 __global__ void __launch_bounds__(kAdvThreads) multi_advance_kernel(const MultiDev m, uint64_t budget) {
-    __shared__ unsigned long long sh[40];
-    const uint32_t per = (m.count + kAdvThreads - 1) / kAdvThreads;
-    const uint32_t e0 = min(m.count, threadIdx.x * per), e1 = min(m.count, e0 + per);
-    unsigned long long want = 0, act = 0;
-    for (uint32_t e = e0; e < e1; ++e) {
-        if (m.done[e]) {
-            m.take[e] = 0;
-            continue;
-        }
-        const unsigned long long cur = m.cur[e] + m.take[e];
-        unsigned long long hi = m.hi[e];
-        m.cur[e] = cur;
-        m.take[e] = 0;
-        if (cur >= hi) {                               // the level is fully expanded
-            const unsigned long long nh = __ldcg(m.total + e);
-            if (nh > m.states_cap[e]) {
-                m.done[e] = 2;                         // states array full
-            } else if (nh == hi) {
-                m.done[e] = 1;                         // no new states: finished
-            } else if (m.level[e] + 1 >= m.max_levels) {
-                m.done[e] = 2;
-            } else {
-                const unsigned int lvl = m.level[e] + 1;
-                m.level[e] = lvl;
-                m.level_sizes[uint64_t(e) * m.max_levels + lvl] = nh - hi;
-                m.lo[e] = hi;
-                m.hi[e] = nh;
-                hi = nh;
-            }
-        }
-        if (!m.done[e]) {
-            want += (hi - cur) * m.msucc[e];
-            ++act;
-        }
-    }
-    const unsigned long long total_want = block_sum(want, sh);
-    const unsigned long long total_act = block_sum(act, sh);
-    // Fair share of the successor buffer, in proportion to remaining work.
-    const double scale = total_want <= budget ? 1.0 : double(budget) / double(total_want);
-    unsigned long long my_take = 0, my_seg = 0;
-    for (uint32_t e = e0; e < e1; ++e) {
-        if (m.done[e]) continue;
-        const unsigned long long rem = m.hi[e] - m.cur[e];
-        unsigned long long tk = scale >= 1.0 ? rem : (unsigned long long)(double(rem) * scale);
-        tk = max(1ull, min(tk, rem));
-        m.take[e] = tk;
-        my_take += tk;
-        my_seg += (tk * m.msucc[e] + 31) / 32 * 32;
-    }
-    unsigned long long w_off = block_excl_scan(my_take, sh);
-    unsigned long long s_off = block_excl_scan(my_seg, sh);
-    for (uint32_t e = e0; e < e1; ++e) {
-        m.work_off[e] = w_off;
-        m.seg_off[e] = s_off;
-        m.seg_cnt[e] = 0;
-        w_off += m.take[e];
-        s_off += (m.take[e] * m.msucc[e] + 31) / 32 * 32;
-    }
-    if (threadIdx.x == kAdvThreads - 1) {
-        *m.work_total = w_off;
-        *m.tiles_total = s_off / 32;
-        *m.active = unsigned(total_act);
-    }
+    __shared__ unsigned long long sh[multi::kAdvShared];
+    multi::advance<kAdvThreads>(m, budget, sh);
 }
 
 }  // namespace
@@ -155,6 +62,7 @@ namespace {
 
 struct Group {
     BucketCfg cfg;
+    ht_scheme scheme = HT_BUCKET;
     std::vector<uint32_t> members;   // exploration ids
     MultiDev dev;
     void* arena = nullptr;           // counters and tables
@@ -197,6 +105,7 @@ void destroy_multi(ht_multi* m) {
     for (auto& g : m->groups) {
         cudaFree(g.arena);
         cudaFree(g.dev.succ);
+        cudaFree(g.dev.win);
         cudaFree(g.d_flags);
         cudaFreeHost(g.h_active);
         if (g.s) cudaStreamDestroy(g.s);
@@ -216,7 +125,7 @@ T* carve(char*& p, uint64_t n) {
     return r;
 }
 
-// One step: each group (explorations of one key width and bucket shape)
+// One step: each group (explorations of one scheme and bucket shape)
 // advances, generates successors and finds-or-puts them.  Groups are
 // independent, so groups after the first run on their own streams, forked
 // from and joined back into the main stream (parallel branches when the step
@@ -247,7 +156,7 @@ ht_status reset_multi(ht_multi* m) {
         const uint64_t n = g.members.size();
         // Zero every counter array (they sit contiguously at the arena's start).
         const char* first = reinterpret_cast<const char*>(g.dev.total);
-        const char* last = reinterpret_cast<const char*>(g.dev.active) + 256;
+        const char* last = reinterpret_cast<const char*>(g.dev.steps) + 256;
         if (cudaMemsetAsync(const_cast<char*>(first), 0, size_t(last - first), m->stream) != cudaSuccess)
             return HT_ERR_CUDA;
         if (cudaMemsetAsync(g.dev.level_sizes, 0, n * m->max_levels * sizeof(unsigned long long), m->stream) !=
@@ -257,15 +166,81 @@ ht_status reset_multi(ht_multi* m) {
     return HT_OK;
 }
 
+// Reads every exploration's counters, level sizes and table status after a
+// batched run (modes 0, 1, 3): all groups' copies, then one synchronisation.
+// The persistent mode also reports its steps and its status word.
+ht_status collect_results(ht_multi* m, bool persistent) {
+    const size_t G = m->groups.size();
+    std::vector<std::vector<unsigned long long>> tot(G), gen(G), sz(G);
+    std::vector<std::vector<unsigned int>> lvl(G), done(G), flags(G);
+    std::vector<unsigned long long> steps(G, 0);
+    std::vector<unsigned int> status(G, 0);
+    for (size_t gi = 0; gi < G; ++gi) {
+        Group& g = m->groups[gi];
+        const uint64_t n = g.members.size();
+        tot[gi].resize(n);
+        gen[gi].resize(n);
+        sz[gi].resize(n * m->max_levels);
+        lvl[gi].resize(n);
+        done[gi].resize(n);
+        flags[gi].resize(n);
+        multi_flags_kernel<<<uint32_t((n + 255) / 256), 256, 0, m->stream>>>(g.dev.tables, uint32_t(n), g.d_flags);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(flags[gi].data(), g.d_flags, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+            cudaMemcpyAsync(tot[gi].data(), g.dev.total, n * 8, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+            cudaMemcpyAsync(gen[gi].data(), g.dev.gen, n * 8, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+            cudaMemcpyAsync(lvl[gi].data(), g.dev.level, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+            cudaMemcpyAsync(done[gi].data(), g.dev.done, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+            cudaMemcpyAsync(sz[gi].data(), g.dev.level_sizes, n * m->max_levels * 8, cudaMemcpyDeviceToHost,
+                            m->stream) != cudaSuccess)
+            return HT_ERR_CUDA;
+        if (persistent &&
+            (cudaMemcpyAsync(&steps[gi], g.dev.steps, 8, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+             cudaMemcpyAsync(&status[gi], g.dev.status, 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess))
+            return HT_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return HT_ERR_CUDA;
+    ht_status st = HT_OK;
+    for (size_t gi = 0; gi < G; ++gi) {
+        Group& g = m->groups[gi];
+        if (persistent) {
+            m->steps = std::max<uint64_t>(m->steps, steps[gi]);
+            if (status[gi] & kMultiTimeout) return HT_ERR_TIMEOUT;
+            if (status[gi] & kMultiBadInit) return HT_ERR_INVALID;
+        }
+        for (uint64_t i = 0; i < g.members.size(); ++i) {
+            const uint32_t e = g.members[i];
+            // A table that dropped a key makes the exploration inexact.
+            if (flags[gi][i] & kFlagDropped) st = HT_ERR_FULL;
+            m->res_complete[e] = done[gi][i] == 1;
+            m->res_states[e] = std::min<uint64_t>(tot[gi][i], m->states_cap[e]);
+            m->res_levels[e] = tot[gi][i] ? uint64_t(lvl[gi][i]) + 1 : 0;
+            m->res_gen[e] = gen[gi][i];
+            std::copy(sz[gi].begin() + i * m->max_levels, sz[gi].begin() + (i + 1) * m->max_levels,
+                      m->res_sizes.begin() + uint64_t(e) * m->max_levels);
+        }
+    }
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
 
 ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64_t* h_s0, const uint64_t* h_capacity,
                           const ht_params* h_params, uint32_t max_levels, void* stream, ht_multi** out) {
+    return ht_multi_create_ex(count, h_models, h_s0, h_capacity, nullptr, h_params, max_levels, stream, out);
+}
+
+ht_status ht_multi_create_ex(uint32_t count, const ht_model* h_models, const uint64_t* h_s0,
+                             const uint64_t* h_capacity, const ht_scheme* h_schemes, const ht_params* h_params,
+                             uint32_t max_levels, void* stream, ht_multi** out) {
     if (!out || count == 0 || count > (1u << 16) || !h_models || !h_s0 || !h_capacity || max_levels == 0 ||
         max_levels > 65536)
         return HT_ERR_INVALID;
+    if (h_schemes)
+        for (uint32_t e = 0; e < count; ++e)
+            if (h_schemes[e] != HT_BUCKET && h_schemes[e] != HT_CUCKOO) return HT_ERR_INVALID;
     *out = nullptr;
     ht_multi* m = new (std::nothrow) ht_multi();
     if (!m) return HT_ERR_OOM;
@@ -278,7 +253,8 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
         delete m;
         return HT_ERR_CUDA;
     }
-    // One table per exploration (bucket scheme), key width from the model.
+    // One table per exploration (h_schemes[e], bucket if NULL), key width
+    // from the model.
     std::vector<uint64_t> msucc(count);
     std::vector<uint32_t> kws(count);
     for (uint32_t e = 0; e < count; ++e) {
@@ -289,7 +265,7 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
         const ht_params* p = h_params ? &h_params[e] : nullptr;
         ht_table* t = nullptr;
         ht_status st = msucc[e] && (kws[e] == 64 || h_s0[e] < 0xFFFFFFFFull) && (kws[e] == 32 || !(h_s0[e] >> 63))
-                           ? ht_create(h_capacity[e], HT_BUCKET, kws[e], p, m->stream, &t)
+                           ? ht_create(h_capacity[e], h_schemes ? h_schemes[e] : HT_BUCKET, kws[e], p, m->stream, &t)
                            : HT_ERR_INVALID;
         if (st != HT_OK) {
             destroy_multi(m);
@@ -307,16 +283,24 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
         }
         m->states.push_back(sp);
     }
-    // Group explorations by (key width, bucket shape).
+    // Group explorations by (scheme, bucket shape).  Key widths share a
+    // group: the group's kernels address every table as a 64-bit key table
+    // (a 32-bit set table holds key k as the word k, the same word) and read
+    // and write each exploration's states in its own width.
     for (uint32_t e = 0; e < count; ++e) {
-        const BucketCfg c = table_bucket_cfg(m->tables[e]);
+        const ht_scheme sch = table_scheme(m->tables[e]);
+        BucketCfg c = table_bucket_cfg(m->tables[e]);
+        c.kw = 64;
+        if (sch == HT_CUCKOO) c.bucket_slots = c.lanes = 0;    // no bucket shape
         Group* g = nullptr;
         for (auto& x : m->groups)
-            if (x.cfg.kw == c.kw && x.cfg.bucket_slots == c.bucket_slots && x.cfg.lanes == c.lanes) g = &x;
+            if (x.scheme == sch && x.cfg.kw == c.kw && x.cfg.bucket_slots == c.bucket_slots && x.cfg.lanes == c.lanes)
+                g = &x;
         if (!g) {
             m->groups.emplace_back();
             g = &m->groups.back();
             g->cfg = c;
+            g->scheme = sch;
         }
         g->members.push_back(e);
     }
@@ -336,11 +320,17 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
         const uint64_t n = g.members.size();
         uint64_t most = 1;
         for (uint32_t e : g.members) most = std::max(most, msucc[e]);
-        g.budget = uint64_t(1) << 24;
+        g.budget = uint64_t(1) << HT_MULTI_BUDGET_LOG2;
         const uint64_t succ_cap = g.budget + n * (32 + most) + 32;
-        const uint64_t bytes = 16 * ((n * 8 + 255) / 256 * 256) + ((n * max_levels * 8 + 255) / 256 * 256) +
-                               3 * 256 + n * sizeof(DevTable) + 256 + n * sizeof(PreparedModel) + 256 +
-                               n * sizeof(void*) + 256;
+        const uint64_t bytes = 18 * ((n * 8 + 255) / 256 * 256) + ((n * max_levels * 8 + 255) / 256 * 256) +
+                               8 * 256 + n * sizeof(DevTable) + 256 + n * sizeof(PreparedModel) + 256 +
+                               n * sizeof(void*) + 256 + n * sizeof(DevScratch) + 256 + n + 256;
+        // Cuckoo: one winner record per successor of a step at most.
+        if (g.scheme == HT_CUCKOO && cudaMalloc(&g.dev.win, succ_cap * sizeof(MultiWinner)) != cudaSuccess) {
+            destroy_multi(m);
+            return HT_ERR_OOM;
+        }
+        g.dev.win_cap = g.scheme == HT_CUCKOO ? succ_cap : 0;
         if (cudaMalloc(&g.arena, bytes) != cudaSuccess || cudaMalloc(&g.dev.succ, succ_cap * 8) != cudaSuccess ||
             cudaMalloc(&g.d_flags, n * sizeof(unsigned int)) != cudaSuccess ||
             cudaMallocHost(&g.h_active, sizeof(unsigned int)) != cudaSuccess) {
@@ -367,6 +357,10 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
         d.work_total = carve<unsigned long long>(p, 1);
         d.tiles_total = carve<unsigned long long>(p, 1);
         d.active = carve<unsigned int>(p, 1);
+        d.win_count = carve<unsigned long long>(p, 1);
+        d.bar = carve<unsigned int>(p, 2);
+        d.status = carve<unsigned int>(p, 1);
+        d.steps = carve<unsigned long long>(p, 1);      // last of the zeroed counters
         // Constant per-exploration data.
         unsigned long long* caps = carve<unsigned long long>(p, n);
         unsigned long long* ms = carve<unsigned long long>(p, n);
@@ -375,6 +369,12 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
         DevTable* tabs = carve<DevTable>(p, n);
         PreparedModel* mods = carve<PreparedModel>(p, n);
         void** sts = carve<void*>(p, n);
+        DevScratch* scr = carve<DevScratch>(p, n);
+        unsigned long long* tcap = carve<unsigned long long>(p, n);
+        uint8_t* nar = carve<uint8_t>(p, n);
+        d.narrow = nar;
+        d.scratch = g.scheme == HT_CUCKOO ? scr : nullptr;
+        d.take_cap = g.scheme == HT_CUCKOO ? tcap : nullptr;
         d.states_cap = caps;
         d.msucc = ms;
         d.s0 = s0;
@@ -385,6 +385,9 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
         std::vector<DevTable> ht(n);
         std::vector<PreparedModel> hp(n);
         std::vector<void*> hst(n);
+        std::vector<DevScratch> hsc(n);
+        std::vector<unsigned long long> htc(n, 0);
+        std::vector<uint8_t> hnar(n);
         for (uint64_t i = 0; i < n; ++i) {
             const uint32_t e = g.members[i];
             hc[i] = m->states_cap[e];
@@ -393,6 +396,19 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
             ht[i] = table_dev(m->tables[e]);
             hp[i] = prepare_model(h_models[e]);
             hst[i] = m->states[e];
+            hnar[i] = kws[e] == 32;
+            if (g.scheme == HT_CUCKOO) {
+                // A step's distinct absent keys are at most the states the
+                // exploration can still hold, and the claim set has twice
+                // win_cap slots: when win_cap covers the states array, the
+                // set stays at most half full whatever the step's size.
+                // Otherwise (a table larger than its claim set, max_batch
+                // below its size) a step expands at most as many states as
+                // keep its successors within win_cap, as the single-table
+                // path chunks a batch.
+                hsc[i] = table_scratch(m->tables[e]);
+                if (hsc[i].win_cap < m->states_cap[e]) htc[i] = std::max<uint64_t>(1, hsc[i].win_cap / msucc[e]);
+            }
         }
         cudaStream_t s = m->stream;
         if (cudaMemcpyAsync(caps, hc.data(), n * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -401,6 +417,9 @@ ht_status ht_multi_create(uint32_t count, const ht_model* h_models, const uint64
             cudaMemcpyAsync(tabs, ht.data(), n * sizeof(DevTable), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(mods, hp.data(), n * sizeof(PreparedModel), cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(sts, hst.data(), n * sizeof(void*), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(scr, hsc.data(), n * sizeof(DevScratch), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(tcap, htc.data(), n * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(nar, hnar.data(), n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             destroy_multi(m);
             return HT_ERR_CUDA;
@@ -448,7 +467,10 @@ ht_status ht_multi_destroy(ht_multi* m) {
 }
 
 ht_status ht_multi_run(ht_multi* m, int mode, uint64_t max_steps, void* stream) {
-    if (!m || mode < 0 || mode > 2) return HT_ERR_INVALID;
+    if (!m || mode < 0 || mode > 3) return HT_ERR_INVALID;
+    if (mode == 1 || mode == 3)
+        for (auto& g : m->groups)
+            if (g.scheme != HT_BUCKET) return HT_ERR_INVALID;     // per-step kernels: bucket tables only
     cudaSetDevice(m->device);
     cudaStream_t caller = static_cast<cudaStream_t>(stream);
     cudaEvent_t ev;
@@ -474,10 +496,22 @@ ht_status ht_multi_run(ht_multi* m, int mode, uint64_t max_steps, void* stream) 
                       m->res_sizes.begin() + uint64_t(e) * m->max_levels);
             m->steps += r.levels;
         }
+    } else if (st == HT_OK && mode == 0) {
+        // One persistent launch per group, one after another on the stream
+        // (each fills the device, so they would not overlap anyway).
+        const uint64_t limit = max_steps ? max_steps : (uint64_t(1) << 22);
+        for (auto& g : m->groups) {
+            if (cudaMemsetAsync(g.dev.win_count, 0, 256 * 4, m->stream) != cudaSuccess ||   // win_count .. steps
+                multi_persistent(g.scheme, g.cfg, g.dev, g.budget, limit, g.max_work, g.max_tiles, m->stream) !=
+                    cudaSuccess) {
+                st = HT_ERR_CUDA;
+                break;
+            }
+        }
     } else if (st == HT_OK) {
         for (auto& g : m->groups)
             if (multi_bucket_init(g.cfg, g.dev, m->stream) != cudaSuccess) st = HT_ERR_CUDA;
-        if (st == HT_OK && mode == 0 && !m->graph) {
+        if (st == HT_OK && mode == 3 && !m->graph) {
             // Capture one step (all groups) as a graph, once.
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = HT_ERR_CUDA;
@@ -488,7 +522,7 @@ ht_status ht_multi_run(ht_multi* m, int mode, uint64_t max_steps, void* stream) 
         }
         const uint64_t limit = max_steps ? max_steps : (uint64_t(1) << 22);
         while (st == HT_OK && m->steps < limit) {
-            if (mode == 0) {
+            if (mode == 3) {
                 if (cudaGraphLaunch(m->graph, m->stream) != cudaSuccess) st = HT_ERR_CUDA;
             } else {
                 st = step_launches(m);
@@ -502,38 +536,8 @@ ht_status ht_multi_run(ht_multi* m, int mode, uint64_t max_steps, void* stream) 
             for (auto& g : m->groups) active += *g.h_active;
             if (!active) break;
         }
-        // Collect per-exploration results.
-        for (auto& g : m->groups) {
-            if (st != HT_OK) break;
-            const uint64_t n = g.members.size();
-            std::vector<unsigned long long> tot(n), gen(n), sz(n * m->max_levels);
-            std::vector<unsigned int> lvl(n), done(n), flags(n);
-            multi_flags_kernel<<<uint32_t((n + 255) / 256), 256, 0, m->stream>>>(g.dev.tables, uint32_t(n), g.d_flags);
-            if (cudaGetLastError() != cudaSuccess ||
-                cudaMemcpyAsync(flags.data(), g.d_flags, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
-                cudaMemcpyAsync(tot.data(), g.dev.total, n * 8, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
-                cudaMemcpyAsync(gen.data(), g.dev.gen, n * 8, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
-                cudaMemcpyAsync(lvl.data(), g.dev.level, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
-                cudaMemcpyAsync(done.data(), g.dev.done, n * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
-                cudaMemcpyAsync(sz.data(), g.dev.level_sizes, n * m->max_levels * 8, cudaMemcpyDeviceToHost,
-                                m->stream) != cudaSuccess ||
-                cudaStreamSynchronize(m->stream) != cudaSuccess) {
-                st = HT_ERR_CUDA;
-                break;
-            }
-            for (uint64_t i = 0; i < n; ++i) {
-                const uint32_t e = g.members[i];
-                // A table that dropped a key makes the exploration inexact.
-                if (flags[i] & kFlagDropped) st = HT_ERR_FULL;
-                m->res_complete[e] = done[i] == 1;
-                m->res_states[e] = std::min<uint64_t>(tot[i], m->states_cap[e]);
-                m->res_levels[e] = tot[i] ? uint64_t(lvl[i]) + 1 : 0;
-                m->res_gen[e] = gen[i];
-                std::copy(sz.begin() + i * m->max_levels, sz.begin() + (i + 1) * m->max_levels,
-                          m->res_sizes.begin() + uint64_t(e) * m->max_levels);
-            }
-        }
     }
+    if (st == HT_OK && mode != 2) st = collect_results(m, mode == 0);
     cudaEventRecord(ev, m->stream);
     cudaStreamWaitEvent(caller, ev, 0);
     cudaEventDestroy(ev);

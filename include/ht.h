@@ -440,6 +440,17 @@ uint64_t ht_multi_steps(const ht_multi* m);
 
 ht_status ht_multi_destroy(ht_multi* m);
 
+/* Failure-detection test hooks of the persistent mode (mode 0), for tests
+ * only.  barrier_timeout_ns: the bound on one grid-barrier wait (0 = the
+ * default, 2 s).  absent_block: the index of one block of each persistent
+ * launch that leaves before its first barrier, as a block that died would,
+ * so that every other block's wait runs out (-1 = none, the default).  The
+ * next ht_multi_run then returns HT_ERR_TIMEOUT within about the bound, the
+ * device stays usable, and after ht_multi_reset (and the hooks set back to
+ * 0, -1) runs are exact again.  HT_ERR_INVALID for NULL or absent_block <
+ * -1.  Host only. */
+ht_status ht_multi_test_hooks(ht_multi* m, uint64_t barrier_timeout_ns, int32_t absent_block);
+
 /* ---------------------------------------------------------------------------
  * Serving: a request loop over many device-resident tables (64-bit keys).
  * A worker thread inside the library forms batches continuously: whenever

@@ -361,6 +361,11 @@ class MultiExploration:
     def reset(self, stream=None):
         _check(load().ht_multi_reset(self._h, _stream(stream)), "ht_multi_reset")
 
+    def test_hooks(self, barrier_timeout_ns=0, absent_block=-1):
+        """Failure-detection test hooks of the persistent mode (ht_multi_test_hooks)."""
+        _check(load().ht_multi_test_hooks(self._h, int(barrier_timeout_ns), int(absent_block)),
+               "ht_multi_test_hooks")
+
     def run(self, mode=0, max_steps=0, stream=None):
         _check(load().ht_multi_run(self._h, int(mode), int(max_steps), _stream(stream)), "ht_multi_run")
         return int(load().ht_multi_steps(self._h))

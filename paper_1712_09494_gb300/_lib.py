@@ -124,6 +124,7 @@ SIGNATURES = {
                                _U64]),
     "ht_multi_steps": (_U64, [_VP]),
     "ht_multi_destroy": (_I32, [_VP]),
+    "ht_multi_test_hooks": (_I32, [_VP, _U64, ctypes.c_int32]),
     "ht_server_default_config": (_I32, [_P(HtServerConfig)]),
     "ht_server_create": (_I32, [_P(HtServerConfig), _P(_VP)]),
     "ht_server_destroy": (_I32, [_VP]),

@@ -579,6 +579,8 @@ struct MultiDev {
     unsigned int* bar;               // [2]
     unsigned int* status;            // [1]
     unsigned long long* steps;       // [1]
+    uint64_t barrier_ns;             // bound on one barrier wait
+    int32_t absent_block;            // failure test: this block leaves before its first barrier (-1: none)
 };
 
 // A Cuckoo insertion job of the batched form: the packed word, its claim in

@@ -30,6 +30,10 @@
 #define HT_MULTI_BUDGET_LOG2 26
 #endif
 
+namespace {
+constexpr uint64_t kDefaultBarrierNs = 2000000000ull;   // a persistent run's bound on one barrier wait
+}
+
 using namespace ht;
 
 namespace ht {
@@ -361,6 +365,8 @@ ht_status ht_multi_create_ex(uint32_t count, const ht_model* h_models, const uin
         d.bar = carve<unsigned int>(p, 2);
         d.status = carve<unsigned int>(p, 1);
         d.steps = carve<unsigned long long>(p, 1);      // last of the zeroed counters
+        d.barrier_ns = kDefaultBarrierNs;
+        d.absent_block = -1;
         // Constant per-exploration data.
         unsigned long long* caps = carve<unsigned long long>(p, n);
         unsigned long long* ms = carve<unsigned long long>(p, n);
@@ -569,5 +575,14 @@ ht_status ht_multi_result(const ht_multi* m, uint32_t i, uint64_t* levels, uint6
 }
 
 uint64_t ht_multi_steps(const ht_multi* m) { return m ? m->steps : 0; }
+
+ht_status ht_multi_test_hooks(ht_multi* m, uint64_t barrier_timeout_ns, int32_t absent_block) {
+    if (!m || absent_block < -1) return HT_ERR_INVALID;
+    for (auto& g : m->groups) {
+        g.dev.barrier_ns = barrier_timeout_ns ? barrier_timeout_ns : kDefaultBarrierNs;
+        g.dev.absent_block = absent_block;
+    }
+    return HT_OK;
+}
 
 }  // extern "C"

@@ -17,17 +17,18 @@
 //
 // Co-residency: the kernel is launched cooperatively with at most as many
 // blocks as fit on the device at once, so every block runs while the others
-// wait at a barrier.  Every barrier wait is bounded in time: a block that
-// waits too long sets kMultiTimeout in the run's status word and returns,
-// and every other block then leaves at its next barrier; the host reports
-// HT_ERR_TIMEOUT.
+// wait at a barrier.  Every barrier wait is bounded in time (barrier_ns,
+// 2 s by default, far above any phase of a step): a block that waits too
+// long sets kMultiTimeout in the run's status word and returns, and every
+// other block then leaves at its next barrier; the host reports
+// HT_ERR_TIMEOUT.  A test makes one block leave before its first barrier,
+// as a block that died would, and checks that status.
 #include "ht_bucket_tile.cuh"
 
 namespace ht {
 namespace {
 
-constexpr uint64_t kBarrierNs = 2000000000ull;   // 2 s: far above any phase of a step
-constexpr uint32_t kBarrierPolls = 1u << 24;      // a second bound, in polls
+constexpr uint32_t kBarrierPolls = 1u << 24;      // a second bound, in polls (~16 s at most)
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
@@ -67,7 +68,7 @@ __device__ bool grid_sync(const MultiDev& m, int* s_ok) {
             unsigned ns = 32;
             for (uint32_t polls = 0; ld_acquire_u32(gen) == g; ++polls) {
                 if ((ld_acquire_u32(m.status) & kMultiTimeout) || polls > kBarrierPolls ||
-                    globaltimer_ns() - t0 > kBarrierNs) {
+                    globaltimer_ns() - t0 > m.barrier_ns) {
                     atomicOr(m.status, kMultiTimeout);
                     ok = 0;
                     break;
@@ -344,6 +345,7 @@ multi_persistent_kernel(const __grid_constant__ MultiDev m, uint64_t budget, uin
     const uint64_t gw = gtid >> 5, nwarps = nthreads >> 5;
     uint64_t* stage = s_new[threadIdx.x >> 5];
     place_initial_states<CUCKOO, BS>(m, gtid, nthreads);
+    if (int(blockIdx.x) == m.absent_block) return;     // failure test: a block that never arrives
     if (!grid_sync(m, &s_ok)) return;
     uint64_t step = 0;
     for (; step < max_steps; ++step) {

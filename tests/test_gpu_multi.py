@@ -160,3 +160,31 @@ def test_multi_reports_a_table_too_small_for_its_exploration(oracle_lib, mode, s
         mx.run(mode=mode)
     assert e.value.status == 3
     mx.close()
+
+
+@pytest.mark.parametrize("scheme", ["bucket", "cuckoo"])
+def test_persistent_barrier_wait_runs_out_and_reports_timeout(oracle_lib, scheme):
+    """A block of the persistent launch leaves before its first grid barrier,
+    as a block that died would: every other block's bounded wait (50 ms here)
+    runs out, the launch ends, and the run returns HT_ERR_TIMEOUT.  The device
+    stays usable: with the hooks cleared and the tables reset, the next run
+    is exact."""
+    import time
+    models = ss.batched_models(6, seed=11)
+    refs = [oracle_lib.bfs(m, max_states=1 << 22) for m in models]
+    caps = [max(256, int(r.total / 0.7)) for r in refs]
+    mx = ht.MultiExploration([hmodel(m) for m in models], [0] * 6, caps, schemes=scheme)
+    mx.test_hooks(barrier_timeout_ns=50_000_000, absent_block=1)
+    t0 = time.time()
+    with pytest.raises(ht.HtError) as e:
+        mx.run(mode=0)
+    assert e.value.status == 5
+    assert time.time() - t0 < 30
+    mx.test_hooks()
+    mx.reset()
+    mx.run(mode=0)
+    for i, r in enumerate(refs):
+        res = mx.result(i)
+        assert res["complete"] == 1 and res["states"] == r.total
+        np.testing.assert_array_equal(res["level_sizes"], r.level_sizes)
+    mx.close()

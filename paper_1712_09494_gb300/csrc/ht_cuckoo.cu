@@ -54,6 +54,19 @@ constexpr int kU = HT_CUCKOO_KEYS_PER_THREAD;   // keys in flight per thread
 // the table's k at compile time (4 for the usual k <= 4, else 8): the probe
 // words in flight are held in registers, and sizing them for k <= 4 keeps
 // enough warps resident per SM.
+#ifndef HT_CUCKOO_STAGE
+#define HT_CUCKOO_STAGE 128                    // staged winners per warp
+#endif
+
+// A winner waiting in a warp's shared-memory stage: its record and its
+// position in the batch (to clear its flag if the list turns out full).
+struct StagedWinner {
+    uint64_t word;
+    uint64_t i;
+    uint32_t spos;
+    uint32_t start;
+};
+
 template <int KW, bool VALUES, bool LOOKUP, int KH>
 __global__ void __launch_bounds__(kBlock, KH <= 4 ? HT_CUCKOO_PROBE_MIN_BLOCKS : 1)
 cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
@@ -73,6 +86,39 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     const uint64_t dseed = t.aux_seed * 3 + 1;
     const int lane = threadIdx.x & 31;
     unsigned long long probes = 0;            // slots read (h_1, then h_2..h_k if h_1 is occupied)
+    constexpr int kStage = LOOKUP ? 1 : HT_CUCKOO_STAGE;
+    __shared__ StagedWinner s_win[kBlock / 32][kStage];
+    StagedWinner* stage = s_win[threadIdx.x >> 5];
+    uint32_t pend = 0;
+    // Lists the staged winners: one atomic on the winner count per flush.
+    // Entries past the list's capacity (more winners than the table holds)
+    // give their claim back, are reported dropped and lose their flag.
+    auto flush = [&]() {
+        __syncwarp();
+        if (pend) {
+            unsigned int b = 0;
+            if (lane == 0) b = atomicAdd(&t.ctr->winners[parity], pend);
+            b = __shfl_sync(0xFFFFFFFFu, b, 0);
+            for (uint32_t j = lane; j < pend; j += 32) {
+                const StagedWinner e = stage[j];
+                const uint64_t at = uint64_t(b) + j;
+                if (at < sc.win_cap) {
+                    Winner wn;
+                    wn.word = e.word;
+                    wn.spos = e.spos;
+                    wn.start = e.start;
+                    sc.win[at] = wn;
+                } else {
+                    sc.set[e.spos] = kEmpty;       // no insert will clear its claim
+                    set_flag(t.ctr, kFlagDropped);
+                    atomicAdd(&t.ctr->dropped, 1ull);
+                    if (out_flag) out_flag[e.i] = 0;
+                }
+            }
+        }
+        __syncwarp();
+        pend = 0;
+    };
     // The next round's keys are loaded while this round waits on the table.
     uint64_t next_key[kU];
 #pragma unroll
@@ -178,43 +224,29 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     }
                 }
             }
-            // Append the round's winners to the insert list: one atomic per warp.
-            unsigned wm[kU];
-            unsigned total = 0;
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                wm[u] = __ballot_sync(0xFFFFFFFFu, winner[u]);
-                total += __popc(wm[u]);
-            }
-            unsigned int b = 0;
-            if (total) {
-                if (lane == 0) b = atomicAdd(&t.ctr->winners[parity], total);
-                b = __shfl_sync(0xFFFFFFFFu, b, 0);
-            }
+            // The round's winners go to the warp's stage in shared memory,
+            // listed with one atomic per flush rather than one per round, so
+            // the next round does not wait on a shared counter.
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const uint64_t i = (r * kU + u) * stride + tid;
-                bool stored = winner[u];
-                if (stored) {
-                    const uint64_t at = uint64_t(b) + __popc(wm[u] & ((1u << lane) - 1));
-                    if (at < sc.win_cap) {
-                        Winner wn;
-                        wn.word = K::word(key[u], VALUES ? vals[i] : 0u);
-                        wn.spos = spos[u];
-                        wn.start = t.chain_h1 ? 0u : start[u];
-                        sc.win[at] = wn;
-                    } else {                                   // more winners than the table holds
-                        stored = false;
-                        sc.set[spos[u]] = kEmpty;              // no insert will clear its claim
-                        set_flag(t.ctr, kFlagDropped);
-                        atomicAdd(&t.ctr->dropped, 1ull);
+                const unsigned wm = __ballot_sync(0xFFFFFFFFu, winner[u]);
+                if (wm) {
+                    if (pend + __popc(wm) > uint32_t(kStage)) flush();
+                    if (winner[u]) {
+                        StagedWinner& e = stage[pend + __popc(wm & ((1u << lane) - 1))];
+                        e.word = K::word(key[u], VALUES ? vals[i] : 0u);
+                        e.i = i;
+                        e.spos = spos[u];
+                        e.start = t.chain_h1 ? 0u : start[u];
                     }
+                    pend += __popc(wm);
                 }
-                if (i < n && out_flag) out_flag[i] = uint8_t(stored);
-                b += __popc(wm[u]);
+                if (i < n && out_flag) out_flag[i] = uint8_t(winner[u]);
             }
         }
     }
+    if constexpr (!LOOKUP) flush();
     for (int o = 16; o; o >>= 1) probes += __shfl_down_sync(0xFFFFFFFFu, probes, o);
     if (lane == 0 && probes) atomicAdd(&t.ctr->probes, probes);
 }

@@ -1165,12 +1165,17 @@ def run_serving_once(ht, a, pack, inflight, trace, keys, schemes=None):
             len(errors), a.serve_deadline, errors[0])}
     srv.close()
     lat = np.array(done_lat)
-    # Where the worker's wall time goes: admission (allocating and clearing
-    # tables), packing keys into staging, finishing (results out), and the
-    # device time of the batches; the largest share names the limiter.
-    dev_s = st["batches"] * st["batch_gpu_us_mean"] / 1e6
-    shares = {"admission": st["admit_seconds"] / wall, "packing": st["pack_seconds"] / wall,
-              "finishing": st["finish_seconds"] / wall, "device_batches": dev_s / wall}
+    # Where the wall time goes: the worker thread's own work (admission --
+    # allocating tables and launching their clears --, packing keys into
+    # staging, finishing -- results out), and the time with at least one
+    # batch in flight on the device.  The worker's host work and the
+    # in-flight time are each a share of the wall; the device-side work
+    # behind them is estimated from the bytes moved at measured rates
+    # (table clears at the copy peak, keys over the host link).
+    shares = {"worker_admission": st["admit_seconds"] / wall, "worker_packing": st["pack_seconds"] / wall,
+              "worker_finishing": st["finish_seconds"] / wall,
+              "batch_in_flight": st["inflight_seconds"] / wall}
+    worker = (st["admit_seconds"] + st["pack_seconds"] + st["finish_seconds"]) / wall
     return {"p50_us": round(float(np.percentile(lat, 50)), 1), "p99_us": round(float(np.percentile(lat, 99)), 1),
             "mean_us": round(float(lat.mean()), 1), "sustained_mops": round(float(sizes.sum()) / wall / 1e6, 1),
             "wall_s": round(wall, 3), "batches": int(st["batches"]), "errors": len(errors),
@@ -1178,8 +1183,11 @@ def run_serving_once(ht, a, pack, inflight, trace, keys, schemes=None):
                        "finish_s": round(st["finish_seconds"], 3), "batch_us_mean": round(st["batch_us_mean"], 1),
                        "batch_gpu_us_mean": round(st["batch_gpu_us_mean"], 1),
                        "tables_created": int(st["tables_created"]),
+                       "table_gb_cleared": round(st["table_bytes_created"] / 1e9, 1),
+                       "clear_ms_at_copy_peak": round(st["table_bytes_created"] / (measured_peaks()[0] * 1e9) * 1e3, 1),
                        "share_of_wall": {k: round(v, 3) for k, v in shares.items()},
-                       "limiter": max(shares, key=shares.get)}}
+                       "worker_busy_share": round(worker, 3),
+                       "limiter": "worker thread (host)" if worker > shares["batch_in_flight"] else "device batches"}}
 
 
 def run_serving(ht, a):

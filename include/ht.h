@@ -495,6 +495,8 @@ typedef struct ht_server_stats {
     double batch_us_mean;             /* mean issue-to-completion time of a batch (host view) */
     double batch_gpu_us_mean;         /* mean device time of a batch (events on its stream) */
     uint64_t tables_created;
+    double inflight_seconds;          /* wall time with at least one batch in flight (host view) */
+    uint64_t table_bytes_created;     /* device bytes of the tables created (each one cleared) */
 } ht_server_stats;
 
 ht_status ht_server_default_config(ht_server_config* cfg);

@@ -56,7 +56,8 @@ class HtServerStats(ctypes.Structure):
         ("admit_seconds", ctypes.c_double), ("pack_seconds", ctypes.c_double),
         ("finish_seconds", ctypes.c_double), ("batch_us_mean", ctypes.c_double),
         ("batch_gpu_us_mean", ctypes.c_double),
-        ("tables_created", ctypes.c_uint64),
+        ("tables_created", ctypes.c_uint64), ("inflight_seconds", ctypes.c_double),
+        ("table_bytes_created", ctypes.c_uint64),
     ]
 
 

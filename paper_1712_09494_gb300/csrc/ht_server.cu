@@ -113,9 +113,14 @@ struct ht_server {
     uint64_t pool_threshold = 0;   // the default pool's release threshold before this server
     bool pool_kept = false;
     size_t rr = 0;                 // round-robin start over tables
+    uint32_t first_waiting = 0;    // tables below this id are admitted or closed
     std::vector<double> lat_us;
     uint64_t keys_done = 0, batches = 0, requests_done = 0, tables_created = 0;
     double admit_s = 0, pack_s = 0, finish_s = 0, batch_us = 0, batch_gpu_us = 0;
+    double inflight_s = 0;         // wall time with a batch in flight
+    uint64_t table_bytes = 0;      // bytes of the tables created
+    uint32_t inflight = 0;         // batches in flight
+    Clock::time_point inflight_t0;
     Clock::time_point stats_t0;
     ht_status fault = HT_OK;
 };
@@ -152,14 +157,26 @@ void trim_pool(ht_server* sv) {
     if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
 }
 
-// Admits waiting tables, in id order, while free memory covers them.
+// Admits waiting tables, in id order, while free memory covers them.  The
+// free memory is queried once per pass (a device query costs tens of
+// microseconds) and reduced by each table admitted in the pass; a table
+// that then fails to allocate waits for the next pass.
 bool admit(ht_server* sv) {
     bool any = false;
     const auto t0 = Clock::now();
-    for (uint32_t id = 0; id < sv->tabs.size(); ++id) {
+    bool queried = false;
+    uint64_t avail = 0;
+    for (uint32_t id = sv->first_waiting; id < sv->tabs.size(); ++id) {
         Tab& tb = sv->tabs[id];
-        if (tb.admitted || tb.closed) continue;
-        if (free_bytes(sv) < tb.bytes + sv->cfg.hbm_reserve_bytes) break;   // keep admission in order
+        if (tb.admitted || tb.closed) {
+            if (id == sv->first_waiting) ++sv->first_waiting;    // every table before it is settled
+            continue;
+        }
+        if (!queried) {
+            avail = free_bytes(sv);
+            queried = true;
+        }
+        if (avail < tb.bytes + sv->cfg.hbm_reserve_bytes) break;   // keep admission in order
         ht_params p = sv->cfg.table_params;
         if (tb.scheme == HT_CUCKOO) {
             const uint64_t seed = p.seed;
@@ -194,6 +211,8 @@ bool admit(ht_server* sv) {
         tb.ready_seen = false;
         tb.admitted = true;
         sv->admitted_bytes += tb.bytes;
+        sv->table_bytes += tb.bytes;
+        avail -= std::min(avail, tb.bytes);
         sv->tables_created += 1;
         any = true;
     }
@@ -228,6 +247,7 @@ void finish(ht_server* sv, Slot& sl) {
     }
     sl.reqs.clear();
     sl.busy = false;
+    if (--sv->inflight == 0) sv->inflight_s += std::chrono::duration<double>(now - sv->inflight_t0).count();
     sv->finish_s += std::chrono::duration<double>(Clock::now() - now).count();
 }
 
@@ -314,6 +334,7 @@ bool launch(ht_server* sv, Slot& sl) {
     if (e != cudaSuccess) sv->fault = HT_ERR_CUDA;
     sl.busy = true;
     sl.issued = Clock::now();
+    if (sv->inflight++ == 0) sv->inflight_t0 = sl.issued;
     sv->batches += 1;
     sv->pack_s += std::chrono::duration<double>(sl.issued - t0).count();
     return true;
@@ -607,10 +628,13 @@ ht_status ht_server_get_stats(ht_server* sv, ht_server_stats* out, int reset) {
     out->batch_us_mean = sv->batches ? sv->batch_us / double(sv->batches) : 0.0;
     out->batch_gpu_us_mean = sv->batches ? sv->batch_gpu_us / double(sv->batches) : 0.0;
     out->tables_created = sv->tables_created;
+    out->inflight_seconds = sv->inflight_s;
+    out->table_bytes_created = sv->table_bytes;
     if (reset) {
         sv->lat_us.clear();
-        sv->admit_s = sv->pack_s = sv->finish_s = sv->batch_us = sv->batch_gpu_us = 0;
+        sv->admit_s = sv->pack_s = sv->finish_s = sv->batch_us = sv->batch_gpu_us = sv->inflight_s = 0;
         sv->tables_created = 0;
+        sv->table_bytes = 0;
         sv->requests_done = sv->keys_done = sv->batches = 0;
         sv->stats_t0 = Clock::now();
     }

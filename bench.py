@@ -177,11 +177,15 @@ def recorded_traffic(kernel):
         name, src, nbytes, sha = m.groups()
         if name != kernel:
             continue
+        # The sources the kernel is compiled from (comma-separated), hashed
+        # together in the order given.
+        h = hashlib.sha256()
         try:
-            cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+            for f in src.split(","):
+                h.update(open(os.path.join(ROOT, f), "rb").read())
         except OSError:
             return None, None
-        if cur == sha:
+        if h.hexdigest()[:16] == sha:
             return int(nbytes), src
     return None, None
 

@@ -45,7 +45,7 @@ struct LongWinner {
     uint64_t digest;
     uint64_t row;
     uint64_t spos;     // its entry in the claim set, cleared by the insert
-    uint64_t pad_;
+    uint64_t start;    // the hash index its eviction chain starts at
 };
 static_assert(sizeof(LongWinner) == kWideWinnerBytes, "winner record size");
 
@@ -267,9 +267,10 @@ __device__ bool ovf_find(const DevTable& t, uint64_t d, const uint64_t (&k)[kLon
 }
 
 // Cuckoo probe (LOOKUP: lookup), one thread per key.  Section 4.1: the key
-// is at one of h_1 .. h_k (or in the overflow set); every chain starts at
-// h_1, an evicted entry moves from h_a to h_{a+1}, and slots never return to
-// EMPTY, so an EMPTY h_a proves the key absent.  A miss claims the key's
+// is at one of h_1 .. h_k (or in the overflow set); a chain starts at the
+// first slot its probe saw EMPTY (h_1 if none), an evicted entry moves from
+// h_a to h_{a+1}, and slots never return to EMPTY, so an EMPTY h_a proves
+// the key absent -- and is where a new key's chain starts.  A miss claims the key's
 // entry (digest, batch index) in the claim set; an entry of equal digest is
 // told apart by comparing the two batch keys.  Each winner takes a row of
 // the key store (one counter atomic per warp), writes its words there and is
@@ -293,6 +294,7 @@ long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         uint64_t k[kLongMaxWords];
         uint64_t d = 0;
         bool found = false;
+        uint32_t start = 0;            // the first function whose slot was seen EMPTY (0: none)
         if (act) {
             load_key(keys, i, W, k);
             d = digest_of(k, W, t.digest_mask);
@@ -300,7 +302,10 @@ long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                 const ulonglong2 e =
                     __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(d, t.seed[a], t.nslots)));
                 ++probes;
-                if (e.x == kEmpty && e.y == kEmpty) break;
+                if (e.x == kEmpty && e.y == kEmpty) {
+                    start = a;         // the key is not past it; its chain starts there
+                    break;
+                }
                 if (e.x == d && e.y < t.kstore_rows && row_equals(t.kstore + e.y * RW, k, RW)) {
                     found = true;
                     break;
@@ -353,7 +358,7 @@ long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     wn.digest = d;
                     wn.row = row;
                     wn.spos = spos;
-                    wn.pad_ = 0;
+                    wn.start = t.chain_h1 ? 0u : start;
                     win[at] = wn;
                 } else {                                   // more keys than the table holds
                     // Release the claim with one 16-byte atomic: other
@@ -408,7 +413,7 @@ long_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity
                 sc.set[2 * wn.spos + 1] = kEmpty;
                 dg[u] = wn.digest;
                 row[u] = wn.row;
-                pos[u] = hidx(wn.digest, t.seed[0], t.nslots);
+                pos[u] = hidx(wn.digest, t.seed[wn.start < t.k ? wn.start : 0], t.nslots);
                 evictions[u] = 0;
                 live[u] = true;
             }

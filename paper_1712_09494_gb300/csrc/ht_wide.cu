@@ -230,20 +230,24 @@ wide_export_kernel(const DevTable t, uint64_t* __restrict__ out, unsigned long l
 // The same two kernels as for 64-bit keys: a probe that finds keys in h_1
 // (then h_2..h_k when h_1 is occupied) and elects one winner per absent key
 // through a claim set of 16-byte entries (one CAS per claim), and an insert
-// that runs each winner's eviction chain with 16-byte atomic exchanges.  No
+// that runs each winner's eviction chain with 16-byte atomic exchanges,
+// starting at the first slot the probe saw empty (h_1 if none).  No
 // writer runs during the probe launch, so its plain 16-byte reads are
 // complete; every write to a slot is one 16-byte atomic.
 
 struct WideWinner {
     uint64_t lo, hi;
     uint64_t spos;                        // its claim-set entry (cleared by the insert)
-    uint64_t pad_;
+    uint64_t start;                       // the hash index its eviction chain starts at
 };
 
 constexpr int kWU = 4;                    // keys (probe) or chains (insert) in flight per thread
 
+#ifndef HT_WIDE_PROBE_MIN_BLOCKS
+#define HT_WIDE_PROBE_MIN_BLOCKS 2
+#endif
 template <bool LOOKUP>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, HT_WIDE_PROBE_MIN_BLOCKS)
 wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity, const ulonglong2* __restrict__ keys,
                          uint64_t n, const unsigned long long* __restrict__ d_n, uint64_t off,
                          uint8_t* __restrict__ out) {
@@ -271,25 +275,36 @@ wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             if (act[u] && !ok[u]) set_flag(t.ctr, kFlagInvalidKey);
             fold[u] = wide_fold(k[u].x, k[u].y);
         }
-        // h_1 of every key first; an empty h_1 proves the key absent (every
-        // chain starts there and slots never return to EMPTY).
+        // h_1 of every key first; an empty h_1 proves the key absent (a key
+        // stored at h_j has h_1..h_(j-1) occupied: slots never return to
+        // EMPTY and a chain starts only past slots seen occupied).
         ulonglong2 w[kWU];
 #pragma unroll
         for (int u = 0; u < kWU; ++u)
             if (ok[u]) w[u] = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold[u], t.seed[0], t.nslots)));
+        uint32_t start[kWU];                  // first of h_2..h_k seen EMPTY (0: none)
 #pragma unroll
         for (int u = 0; u < kWU; ++u) {
             found[u] = ok[u] && w[u].x == k[u].x && w[u].y == k[u].y;
             more[u] = ok[u] && !found[u] && !(w[u].x == kOnes && w[u].y == kOnes);
+            start[u] = 0;
         }
-        for (uint32_t a = 1; a < t.k; ++a) {
+        // h_2..h_k one function at a time (16-byte words of four keys in
+        // flight per thread); an EMPTY h_a ends the search: a key never sits
+        // past an empty slot of its own.  The first EMPTY is the chain start.
+        {
+            for (uint32_t a = 1; a < t.k; ++a) {
 #pragma unroll
-            for (int u = 0; u < kWU; ++u)
-                if (more[u] && !found[u])
-                    w[u] = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold[u], t.seed[a], t.nslots)));
+                for (int u = 0; u < kWU; ++u)
+                    if (more[u] && !found[u] && !start[u])
+                        w[u] = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold[u], t.seed[a], t.nslots)));
 #pragma unroll
-            for (int u = 0; u < kWU; ++u)
-                if (more[u] && !found[u]) found[u] = w[u].x == k[u].x && w[u].y == k[u].y;
+                for (int u = 0; u < kWU; ++u)
+                    if (more[u] && !found[u] && !start[u]) {
+                        found[u] = w[u].x == k[u].x && w[u].y == k[u].y;
+                        if (w[u].x == kOnes && w[u].y == kOnes) start[u] = a;
+                    }
+            }
         }
         if (ovf_used) {
 #pragma unroll
@@ -368,7 +383,7 @@ wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     wn.lo = k[u].x;
                     wn.hi = k[u].y;
                     wn.spos = spos[u];
-                    wn.pad_ = 0;
+                    wn.start = t.chain_h1 ? 0u : start[u];
                     win[at] = wn;
                 } else {                                 // more winners than the table holds
                     stored = false;
@@ -435,7 +450,7 @@ wide_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity
                 sc.set[2 * wn.spos + 1] = kOnes;
                 lo[u] = wn.lo;
                 hi[u] = wn.hi;
-                pos[u] = hidx(wide_fold(wn.lo, wn.hi), t.seed[0], t.nslots);
+                pos[u] = hidx(wide_fold(wn.lo, wn.hi), t.seed[wn.start < t.k ? wn.start : 0], t.nslots);
                 evictions[u] = 0;
                 live[u] = true;
             }

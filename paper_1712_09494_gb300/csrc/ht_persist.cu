@@ -121,10 +121,38 @@ __device__ void place_initial_states(const MultiDev& m, uint64_t gtid, uint64_t 
 // per distinct key is the winner: it is appended to e's states and to the
 // group's winner list with its exploration and the first empty slot the
 // probe saw (its chain start).
+constexpr int kWinStage = 64;            // staged winner records per warp
+
 __device__ void cuckoo_probe_tiles(const MultiDev& m, const multi::TileMap& tm, uint64_t gw, uint64_t nwarps,
-                                   uint64_t* stage_buf) {
+                                   uint64_t* stage_buf, MultiWinner* wstage) {
     constexpr int KW = 64;
     using K = Keys<KW>;
+    uint32_t wpend = 0;
+    // Lists the staged winners with one atomic on the group's count.  The
+    // list holds a whole step's successors, so it cannot run out; if it did,
+    // the record's claim is given back and its table reports a dropped key.
+    auto flush_winners = [&]() {
+        __syncwarp();
+        if (wpend) {
+            const int ln = threadIdx.x & 31;
+            unsigned long long b = 0;
+            if (ln == 0) b = atomicAdd(m.win_count, (unsigned long long)wpend);
+            b = __shfl_sync(0xFFFFFFFFu, b, 0);
+            for (uint32_t j = ln; j < wpend; j += 32) {
+                const MultiWinner wn = wstage[j];
+                if (b + j < m.win_cap) {
+                    m.win[b + j] = wn;
+                } else {
+                    const uint32_t we = wn.tag >> 8;
+                    m.scratch[we].set[wn.spos] = kEmpty;
+                    set_flag(m.tables[we].ctr, kFlagDropped);
+                    atomicAdd(&m.tables[we].ctr->dropped, 1ull);
+                }
+            }
+        }
+        __syncwarp();
+        wpend = 0;
+    };
     const uint64_t tiles = tm.total(m);
     const int lane = threadIdx.x & 31;
     const uint64_t per = (tiles + nwarps - 1) / nwarps;
@@ -168,19 +196,17 @@ __device__ void cuckoo_probe_tiles(const MultiDev& m, const multi::TileMap& tm, 
         bool found = ok && K::keyof(w) == key;
         const bool more = ok && !found && !K::empty(w);
         uint32_t start = 0;
-        if (__any_sync(0xFFFFFFFFu, more)) {
-            const uint32_t k = t.k;
-            uint64_t ws[kMaxCuckooHashes];
-#pragma unroll
-            for (int a = 1; a < kMaxCuckooHashes; ++a)
-                if (more && a < int(k))
-                    ws[a] = __ldcg(reinterpret_cast<const unsigned long long*>(t.slots + hidx(key, t.seed[a], t.nslots)));
-#pragma unroll
-            for (int a = kMaxCuckooHashes - 1; a >= 1; --a)
-                if (more && a < int(k)) {
-                    if (K::keyof(ws[a]) == key) found = true;
-                    if (K::empty(ws[a])) start = uint32_t(a);
-                }
+        // h_2..h_k one slot at a time, stopping at the key or at the first
+        // EMPTY slot (the key is not past it; a new key's chain starts
+        // there): the probe is bound by the random lines it reads.
+        bool go = more;
+        for (uint32_t a = 1; a < t.k && __any_sync(0xFFFFFFFFu, go); ++a) {
+            if (go) {
+                const uint64_t v = __ldcg(reinterpret_cast<const unsigned long long*>(t.slots + hidx(key, t.seed[a], t.nslots)));
+                if (K::keyof(v) == key) found = true;
+                else if (K::empty(v)) start = a;
+                go = !found && start == 0;
+            }
         }
         if ((stash_used | ovf_used) && ok && !found) {
             uint64_t sw;
@@ -208,32 +234,23 @@ __device__ void cuckoo_probe_tiles(const MultiDev& m, const multi::TileMap& tm, 
                 }
             }
         }
-        // Winners to the group's list (one atomic per warp and tile) and to e's states.
+        // Winners to the warp's stage of winner records (listed with one
+        // atomic per flush) and to e's states.
         const unsigned wm = __ballot_sync(0xFFFFFFFFu, winner);
-        bool listed = false;
         if (wm) {
-            unsigned long long b = 0;
-            if (lane == 0) b = atomicAdd(m.win_count, (unsigned long long)__popc(wm));
-            b = __shfl_sync(0xFFFFFFFFu, b, 0);
+            if (wpend + __popc(wm) > uint32_t(kWinStage)) flush_winners();
             if (winner) {
-                const uint64_t at = b + __popc(wm & ((1u << lane) - 1));
-                if (at < m.win_cap) {
-                    MultiWinner wn;
-                    wn.word = K::word(key, 0u);
-                    wn.spos = spos;
-                    wn.tag = (e << 8) | (t.chain_h1 ? 0u : start);
-                    m.win[at] = wn;
-                    listed = true;
-                } else {                               // cannot happen: the list holds a whole step
-                    m.scratch[e].set[spos] = kEmpty;
-                    set_flag(t.ctr, kFlagDropped);
-                    atomicAdd(&t.ctr->dropped, 1ull);
-                }
+                MultiWinner& wn = wstage[wpend + __popc(wm & ((1u << lane) - 1))];
+                wn.word = K::word(key, 0u);
+                wn.spos = spos;
+                wn.tag = (e << 8) | (t.chain_h1 ? 0u : start);
             }
+            wpend += __popc(wm);
         }
-        stage.push(listed, key, m, e);
+        stage.push(winner, key, m, e);
     }
     stage.flush(m, e);
+    flush_winners();
 }
 
 // Cuckoo insert of the step's winners over threads [gtid] of [nthreads]:
@@ -339,6 +356,7 @@ multi_persistent_kernel(const __grid_constant__ MultiDev m, uint64_t budget, uin
     __shared__ uint64_t s_new[kBlock / 32][kStageCap];
     __shared__ unsigned long long sh[multi::kAdvShared];
     __shared__ unsigned int s_first[multi::kExactTileExpl + 1];
+    __shared__ MultiWinner s_win[kBlock / 32][CUCKOO ? kWinStage : 1];
     __shared__ int s_ok;
     const uint64_t gtid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const uint64_t nthreads = uint64_t(gridDim.x) * blockDim.x;
@@ -357,7 +375,7 @@ multi_persistent_kernel(const __grid_constant__ MultiDev m, uint64_t budget, uin
         // Every block numbers the step's tiles over the successors made.
         const multi::TileMap tm = multi::tile_map<kBlock>(m, s_first, sh);
         if constexpr (CUCKOO) {
-            cuckoo_probe_tiles(m, tm, gw, nwarps, stage);
+            cuckoo_probe_tiles(m, tm, gw, nwarps, stage, s_win[threadIdx.x >> 5]);
             if (!grid_sync(m, &s_ok)) return;
             cuckoo_insert_winners(m, gtid, nthreads);
         } else {

@@ -44,7 +44,7 @@ constexpr int kU = HT_CUCKOO_KEYS_PER_THREAD;   // keys in flight per thread
 #define HT_CUCKOO_PROBE_MIN_BLOCKS 3
 #endif
 #ifndef HT_CUCKOO_INSERT_MIN_BLOCKS
-#define HT_CUCKOO_INSERT_MIN_BLOCKS 4
+#define HT_CUCKOO_INSERT_MIN_BLOCKS 3
 #endif
 
 // Probe (and, for find-or-put, dedup).  Each thread holds U keys of a round,
@@ -54,6 +54,9 @@ constexpr int kU = HT_CUCKOO_KEYS_PER_THREAD;   // keys in flight per thread
 // the table's k at compile time (4 for the usual k <= 4, else 8): the probe
 // words in flight are held in registers, and sizing them for k <= 4 keeps
 // enough warps resident per SM.
+#ifndef HT_CUCKOO_INSERT_PREFETCH
+#define HT_CUCKOO_INSERT_PREFETCH 1
+#endif
 #ifndef HT_CUCKOO_PROBE_SPLIT
 #define HT_CUCKOO_PROBE_SPLIT 2
 #endif
@@ -317,12 +320,19 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
     uint64_t word[kU], pos[kU];
     uint32_t evictions[kU];
     bool live[kU];
+    // Each chain slot's next winner record is loaded one winner ahead, so a
+    // slot that frees up starts its next chain without waiting for the read.
+    Winner pre[kU];
+    bool pre_ok[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
         live[u] = false;
         word[u] = 0;
         pos[u] = 0;
         evictions[u] = 0;
+        pre_ok[u] = HT_CUCKOO_INSERT_PREFETCH && next < count;
+        if (pre_ok[u]) pre[u] = sc.win[next];
+        if (HT_CUCKOO_INSERT_PREFETCH) next += stride;
     }
     // Bounded: each winner is taken once and its chain ends after at most
     // max_evictions + 1 exchanges.
@@ -330,8 +340,15 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
         bool any = false;
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            if (!live[u] && next < count) {
-                const Winner wn = sc.win[next];
+            if (!live[u] && (HT_CUCKOO_INSERT_PREFETCH ? pre_ok[u] : next < count)) {
+                Winner wn;
+                if (HT_CUCKOO_INSERT_PREFETCH) {
+                    wn = pre[u];
+                    pre_ok[u] = next < count;
+                    if (pre_ok[u]) pre[u] = sc.win[next];
+                } else {
+                    wn = sc.win[next];
+                }
                 next += stride;
                 sc.set[wn.spos] = kEmpty;      // leave the dedup set empty for the next batch
                 word[u] = wn.word;

@@ -215,12 +215,12 @@ def random_access_roofline(scheme, fs, table, stats, ms_per_fill, probe):
     """Lower bound on a fill's time from the measured random-access rates:
     the lines a scheme must only read at the random-read rate plus the lines
     it must claim in at the random read-modify-write rate.  Bucket: one line
-    per key, read-only for repeats, claimed for new keys.  Cuckoo: one line
-    (h_1) per repeat; per new key the extra probes h_2..h_k when h_1 is
-    occupied; and every exchange its insertion chains made (counted on the
-    device, `stats`), each a claimed line.  In-batch repeats that miss and
-    the dedup set (kept in L2) are not counted, so the bound is optimistic
-    and the fraction conservative."""
+    per key, read-only for repeats, claimed for new keys.  Cuckoo: every slot
+    its probes read (counted on the device, `stats`), except one per new key
+    -- the slot its chain starts at, which the insert claims -- and every
+    exchange its insertion chains made (counted), each a claimed line.  In-
+    batch repeats that miss and the dedup set (kept in L2) are not counted,
+    so the bound is optimistic and the fraction conservative."""
     if not probe or "rmw_line" not in probe:
         return None
     r_rmw = probe["rmw_line"]["gaccess_per_s"] * 1e9
@@ -231,8 +231,11 @@ def random_access_roofline(scheme, fs, table, stats, ms_per_fill, probe):
         reads, claims = n_rep, n_new
     else:
         r_read = probe["8B"]["gaccess_per_s"] * 1e9
-        info = table.info()
-        reads = n_rep + n_new * new_key_load(fs, info["slots"]) * (info["num_hashes"] - 1)
+        if stats.get("probes"):
+            reads = max(0, stats["probes"] - n_new)
+        else:                       # the model: h_1, then h_2..h_k when h_1 is occupied
+            info = table.info()
+            reads = n_rep + n_new * new_key_load(fs, info["slots"]) * (info["num_hashes"] - 1)
         claims = max(n_new, stats["exchanges"])
     t_min = reads / r_read + claims / r_rmw
     return {"min_ms_per_fill": round(t_min * 1e3, 3), "frac": round(t_min * 1e3 / ms_per_fill, 3),
@@ -290,8 +293,11 @@ def kernel_random_access(name, k, fs, tables, stats, probe, steps):
     if name == "bucket_find_or_put":
         reads, claims = n_rep, n_new
     elif name == "cuckoo_probe":
-        info = tables["cuckoo"].info()
-        reads = n_rep + n_new * (1 + new_key_load(fs, info["slots"]) * (info["num_hashes"] - 1))
+        if stats["cuckoo"].get("probes"):
+            reads = stats["cuckoo"]["probes"]          # every slot the probes read, counted
+        else:
+            info = tables["cuckoo"].info()
+            reads = n_rep + n_new * (1 + new_key_load(fs, info["slots"]) * (info["num_hashes"] - 1))
         claims = 0
     elif name == "cuckoo_insert":
         reads, claims = 0, stats["cuckoo"]["exchanges"]

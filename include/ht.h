@@ -254,7 +254,11 @@ typedef struct ht_table_stats {
                                  0 for the bucket scheme (a per-key count there
                                  would put one shared counter on the hot path)
                                  and for 128-bit tables */
-    uint64_t reserved_[3];
+    uint64_t probe_misses;    /* Cuckoo (32/64-bit keys): probed keys found
+                                 nowhere (absent from the table) ... */
+    uint64_t probe_miss_reads;/* ... and the slots their probes read (h_1,
+                                 then h_2.. up to the first empty slot) */
+    uint64_t reserved_;
 } ht_table_stats;
 
 /* Reads the table's counters into *out (caller-owned host memory);

@@ -92,6 +92,7 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     const uint64_t dseed = t.aux_seed * 3 + 1;
     const int lane = threadIdx.x & 31;
     unsigned long long probes = 0;            // slots read (h_1, then h_2..h_k if h_1 is occupied)
+    unsigned long long misses = 0, miss_reads = 0;   // keys found nowhere, and the slots they read
     constexpr int kStage = LOOKUP ? 1 : HT_CUCKOO_STAGE;
     __shared__ StagedWinner s_win[kBlock / 32][kStage];
     StagedWinner* stage = s_win[threadIdx.x >> 5];
@@ -154,11 +155,12 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         // An empty h_1 slot ends the table probe: a key stored at h_j has
         // h_1 .. h_{j-1} all occupied (see the top of this file).  A miss at
         // table load a then costs 1 + a (k - 1) probes, not k.
-        bool more[kU];
+        bool more[kU], occ1[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             found[u] = act[u] && K::keyof(w[u]) == key[u];
             more[u] = act[u] && !found[u] && !K::empty(w[u]);
+            occ1[u] = more[u];
             probes += act[u] ? 1u : 0u;
         }
         // The chain start of a miss: the first of h_2..h_k seen EMPTY (0 =
@@ -221,6 +223,18 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             for (int u = 0; u < kU; ++u)
                 if (act[u] && !found[u]) found[u] = find_spill<KW>(t, key[u], stash_used, ovf_used, &w[u]);
         }
+        // The slots read by the keys found nowhere (the table counters keep
+        // them apart from the hits' reads).
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (act[u] && !found[u]) {
+                ++misses;
+                const uint32_t k = t.k;
+                miss_reads += !occ1[u] ? 1u
+                              : HT_CUCKOO_PROBE_SPLIT == 0 ? k
+                              : HT_CUCKOO_PROBE_SPLIT == 1 ? (start[u] == 1 ? 2u : k)
+                                                           : (start[u] ? 1u + start[u] : k);
+            }
         if constexpr (LOOKUP) {
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
@@ -285,8 +299,16 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         }
     }
     if constexpr (!LOOKUP) flush();
-    for (int o = 16; o; o >>= 1) probes += __shfl_down_sync(0xFFFFFFFFu, probes, o);
+    for (int o = 16; o; o >>= 1) {
+        probes += __shfl_down_sync(0xFFFFFFFFu, probes, o);
+        misses += __shfl_down_sync(0xFFFFFFFFu, misses, o);
+        miss_reads += __shfl_down_sync(0xFFFFFFFFu, miss_reads, o);
+    }
     if (lane == 0 && probes) atomicAdd(&t.ctr->probes, probes);
+    if (lane == 0 && misses) {
+        atomicAdd(&t.ctr->probe_misses, misses);
+        atomicAdd(&t.ctr->probe_miss_reads, miss_reads);
+    }
 }
 
 // Eviction-chain insert of the winners.  Each thread keeps U chains in

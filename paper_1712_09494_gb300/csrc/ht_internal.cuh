@@ -36,9 +36,10 @@ struct DevCounters {
     unsigned long long exchanges; // Cuckoo: atomic exchanges made by insert chains
     unsigned long long probes;    // Cuckoo: slots the probes read (bucket scheme: not counted)
     unsigned long long ids;       // long-key Cuckoo: key-store rows handed out
-    unsigned int pad_[2];
+    unsigned long long probe_misses;      // Cuckoo: probed keys found nowhere (64-bit path)
+    unsigned long long probe_miss_reads;  // ... and the slots those keys' probes read
 };
-static_assert(sizeof(DevCounters) == 72, "counter block layout");
+static_assert(sizeof(DevCounters) == 80, "counter block layout");
 
 // Everything a kernel needs to address a table; passed by value.
 struct DevTable {

@@ -295,6 +295,26 @@ def test_stats_counters(oracle_lib, scheme):
     assert st["size"] == st["exchanges"] == st["stash_used"] == st["overflow_used"] == 0
 
 
+def test_cuckoo_probe_miss_counters():
+    """The probe's miss counters: n distinct keys into an empty table all
+    miss (each read at least h_1, at most k slots); the same keys again all
+    hit, adding reads but no misses."""
+    n = 100_000
+    keys = wk.distinct_keys(n, 64, seed=44)
+    t = ht.HashTable(int(n / 0.8), "cuckoo", 64)
+    t.find_or_put(to_dev(keys))
+    st = t.stats()
+    assert st["probe_misses"] == n
+    assert n <= st["probe_miss_reads"] <= 4 * n and st["probe_miss_reads"] == st["probes"]
+    t.find_or_put(to_dev(keys))
+    st2 = t.stats()
+    assert st2["probe_misses"] == n and st2["probe_miss_reads"] == st["probe_miss_reads"]
+    assert st2["probes"] - st["probes"] >= n                   # every hit read h_1 at least
+    found, _ = t.lookup(to_dev(wk.distinct_keys(1000, 64, seed=44, start=n + 5)))
+    assert int(found.sum()) == 0
+    assert t.stats()["probe_misses"] == n + 1000
+
+
 @pytest.mark.parametrize("scheme", SCHEMES)
 def test_clear_empties(oracle_lib, scheme):
     t = ht.HashTable(4096, scheme, 64)

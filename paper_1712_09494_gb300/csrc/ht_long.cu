@@ -272,9 +272,33 @@ __device__ bool ovf_find(const DevTable& t, uint64_t d, const uint64_t (&k)[kLon
 // h_a to h_{a+1}, and slots never return to EMPTY, so an EMPTY h_a proves
 // the key absent -- and is where a new key's chain starts.  A miss claims the key's
 // entry (digest, batch index) in the claim set; an entry of equal digest is
-// told apart by comparing the two batch keys.  Each winner takes a row of
-// the key store (one counter atomic per warp), writes its words there and is
-// listed for the insert kernel.
+// told apart by comparing the two batch keys.  Winners wait in a per-warp
+// stage in shared memory; a flush lists a stage's winners with one atomic on
+// the winner count, and a winner listed at position `at` owns key-store row
+// ids + at (ids: the rows handed out before this batch, advanced by the
+// insert kernel), copies its words there from the batch and writes its
+// record.  One atomic per flush instead of two per warp and round: those
+// same-address atomics set the probe's pace when every warp issued them.
+constexpr int kLongStage = 128;
+struct LongStaged {
+    uint64_t digest;
+    uint64_t i;        // batch index
+    uint64_t spos;
+    uint64_t start;
+};
+
+// The words of batch key i to key-store row `row` (a zero padding word for
+// an odd W), with 16-byte stores.
+__device__ __forceinline__ void copy_row(uint64_t* row, const uint64_t* __restrict__ key, uint32_t W, uint32_t RW) {
+#pragma unroll
+    for (uint32_t j = 0; j < kLongMaxWords; j += 2)
+        if (j < RW) {
+            const uint64_t a = __ldg(key + j);
+            const uint64_t b = j + 1 < W ? __ldg(key + j + 1) : 0;
+            *reinterpret_cast<ulonglong2*>(row + j) = make_ulonglong2(a, b);
+        }
+}
+
 template <bool LOOKUP>
 __global__ void __launch_bounds__(kBlock)
 long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity, const uint64_t* __restrict__ keys,
@@ -288,6 +312,48 @@ long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     const int lane = threadIdx.x & 31;
     LongWinner* win = reinterpret_cast<LongWinner*>(sc.win);
     unsigned long long probes = 0;
+    constexpr int kStage = LOOKUP ? 1 : kLongStage;
+    __shared__ LongStaged s_win[kBlock / 32][kStage];
+    LongStaged* stage = s_win[threadIdx.x >> 5];
+    uint32_t pend = 0;
+    const uint64_t row_base = LOOKUP ? 0 : __ldcg(&t.ctr->ids);
+    // Lists the staged winners.  A winner past the list's capacity or past
+    // the key store (more keys than the table holds) gives its claim back
+    // with one 16-byte atomic (other threads may be comparing against it),
+    // is reported dropped and loses its flag; inside the list it leaves a
+    // record with row = EMPTY that the insert kernel skips.
+    auto flush = [&]() {
+        __syncwarp();
+        if (pend) {
+            unsigned int b = 0;
+            if (lane == 0) b = atomicAdd(&t.ctr->winners[parity], pend);
+            b = __shfl_sync(kFullMask, b, 0);
+            for (uint32_t j = lane; j < pend; j += 32) {
+                const LongStaged e = stage[j];
+                const uint64_t at = uint64_t(b) + j;
+                const uint64_t row = row_base + at;
+                const bool listed = at < sc.win_cap, stored = listed && row < t.kstore_rows;
+                if (stored) copy_row(t.kstore + row * RW, keys + e.i * W, W, RW);
+                if (listed) {
+                    LongWinner wn;
+                    wn.digest = e.digest;
+                    wn.row = stored ? row : kEmpty;
+                    wn.spos = e.spos;
+                    wn.start = e.start;
+                    win[at] = wn;
+                }
+                if (!stored) {
+                    uint64_t ol, oh;
+                    exch128(sc.set + 2 * e.spos, kEmpty, kEmpty, ol, oh);
+                    set_flag(t.ctr, kFlagDropped);
+                    atomicAdd(&t.ctr->dropped, 1ull);
+                    if (out) out[e.i] = 0;
+                }
+            }
+        }
+        __syncwarp();
+        pend = 0;
+    };
     for (uint64_t r = 0; r < rounds; ++r) {
         const uint64_t i = r * stride + tid;
         const bool act = i < n;
@@ -340,40 +406,22 @@ long_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                 atomicAdd(&t.ctr->dropped, 1ull);
             }
         }
+        if (act && out) out[i] = uint8_t(winner);
         const unsigned wm = __ballot_sync(kFullMask, winner);
         if (wm) {
-            unsigned long long row0 = 0, at0 = 0;
-            if (lane == 0) {
-                row0 = atomicAdd(&t.ctr->ids, (unsigned long long)__popc(wm));
-                at0 = atomicAdd(&t.ctr->winners[parity], unsigned(__popc(wm)));
-            }
-            row0 = __shfl_sync(kFullMask, row0, 0);
-            at0 = __shfl_sync(kFullMask, at0, 0);
+            if (pend + __popc(wm) > uint32_t(kStage)) flush();
             if (winner) {
-                const unsigned rank = __popc(wm & ((1u << lane) - 1));
-                const uint64_t row = row0 + rank, at = at0 + rank;
-                if (row < t.kstore_rows && at < sc.win_cap) {
-                    write_row(t.kstore + row * RW, k, RW);
-                    LongWinner wn;
-                    wn.digest = d;
-                    wn.row = row;
-                    wn.spos = spos;
-                    wn.start = t.chain_h1 ? 0u : start;
-                    win[at] = wn;
-                } else {                                   // more keys than the table holds
-                    // Release the claim with one 16-byte atomic: other
-                    // threads may be comparing against it right now.
-                    winner = false;
-                    uint64_t ol, oh;
-                    exch128(sc.set + 2 * spos, kEmpty, kEmpty, ol, oh);
-                    set_flag(t.ctr, kFlagDropped);
-                    atomicAdd(&t.ctr->dropped, 1ull);
-                }
+                LongStaged& e = stage[pend + __popc(wm & ((1u << lane) - 1))];
+                e.digest = d;
+                e.i = i;
+                e.spos = spos;
+                e.start = t.chain_h1 ? 0u : start;
             }
+            pend += __popc(wm);
         }
-        if (act && out) out[i] = uint8_t(winner);
     }
     if (!LOOKUP) {
+        flush();
         for (int o = 16; o; o >>= 1) probes += __shfl_down_sync(kFullMask, probes, o);
         if (lane == 0 && probes) atomicAdd(&t.ctr->probes, probes);
     }
@@ -385,7 +433,14 @@ __global__ void __launch_bounds__(kBlock)
 long_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uint64_t max_winners) {
     constexpr int U = 4;
     const uint64_t count = min(uint64_t(__ldcg(&t.ctr->winners[parity])), max_winners);
-    if (blockIdx.x == 0 && threadIdx.x == 0) t.ctr->winners[parity ^ 1u] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        t.ctr->winners[parity ^ 1u] = 0;
+        // Rows ids .. ids + count - 1 went to this batch's listed winners
+        // (those past the key store were dropped); no other thread of this
+        // kernel reads ids, and the next probe starts after it ends.
+        const unsigned long long ids = t.ctr->ids;
+        t.ctr->ids = min(uint64_t(ids) + count, t.kstore_rows);
+    }
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const LongWinner* win = reinterpret_cast<const LongWinner*>(sc.win);
@@ -406,9 +461,10 @@ long_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity
         bool any = false;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (!live[u] && next < count) {
+            while (!live[u] && next < count) {
                 const LongWinner wn = win[next];
                 next += stride;
+                if (wn.row >= t.kstore_rows) continue;     // dropped in the probe; its claim is back
                 sc.set[2 * wn.spos] = kEmpty;              // leave the claim set empty for the next batch
                 sc.set[2 * wn.spos + 1] = kEmpty;
                 dg[u] = wn.digest;

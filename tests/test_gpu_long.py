@@ -5,6 +5,8 @@ The bucket scheme claims a header word and publishes the key's words after
 writing them; Cuckoo keeps (digest, row) entries pointing into a key store.
 Tests with a shortened digest make distinct keys share digests, so the
 full-key comparisons that tell them apart run on most probes."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -152,6 +154,33 @@ def test_full_grow_and_checkpoint(oracle_lib, scheme, tmp_path):
     u = ht.HashTable.load(path)
     assert u.key_width == 320 and u.size() == 6000
     assert _rows(u.export()[0]) == set(map(tuple, keys.tolist()))
+
+
+def test_cuckoo_past_the_key_store_keeps_a_consistent_set():
+    # More distinct keys than the key store has rows: winners past its last
+    # row give their claims back and leave list records that the insert
+    # kernel skips, so every stored key is stored once, came from the input
+    # and is found, and the size counts exactly the stored keys.
+    keys = wk.distinct_keys(3000, 256, seed=73)
+    t = ht.HashTable(64, "cuckoo", 256)
+    for lo in range(0, 3000, 1000):
+        t.find_or_put(_dev(keys[lo:lo + 1000]))
+    assert t.sync() == 3
+    # Export into room for four times the size: a key stored twice, or an
+    # entry left by a stale list record, would show up as extra entries.
+    lib, stream = ht.load(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    size = ctypes.c_uint64()
+    assert lib.ht_size(t.handle, ctypes.byref(size), stream) == 3       # the size still reads out
+    n = size.value
+    buf = torch.empty((4 * n + 64, 4), dtype=torch.int64, device="cuda")
+    cnt = ctypes.c_uint64()
+    st = lib.ht_export(t.handle, ctypes.c_void_p(buf.data_ptr()), None, buf.shape[0], ctypes.byref(cnt), stream)
+    assert st == 3 and 0 < cnt.value == n
+    ex = buf[:n]
+    rows = _rows(ex)
+    assert len(rows) == n
+    assert rows <= set(map(tuple, keys.tolist()))
+    assert t.lookup(ex)[0].cpu().numpy().all()
 
 
 def test_cuckoo_overflow_and_rebuild_stay_exact(oracle_lib):

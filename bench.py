@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--only", default="",
+                    help="comma list: of the sections after the headline fill run only these (small, sweep, replay, "
+                         "wide, long, wide_bfs, bfs, batched, serving)")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-rate", type=float, default=40000.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-deadline", type=float, default=120.0, help="seconds before a serving run gives up")
@@ -495,20 +498,29 @@ def run_ours(a, rank, world, local):
     for t in tables.values():
         t.close()
     tables = {}
-    if not a.no_small:
+    only = {x for x in a.only.split(",") if x}
+
+    def want(section, off):
+        return section in only if only else not off
+
+    if want("small", a.no_small):
         out["small_map_config1"] = run_small_map(ht, torch, dev, schemes)
         out["many_tables_one_call"] = run_multi_table(ht, torch, dev)
-    if not a.no_sweep:
+    if want("sweep", a.no_sweep):
         out["sweep_config2"] = run_sweep(ht, torch, dev)
+    if want("replay", a.no_sweep):
         out["replay_multiplicity"] = run_replay(ht, torch, dev)
+    if want("wide", a.no_sweep):
         out["wide_keys_128"] = run_wide(ht, torch, dev)
+    if want("long", a.no_sweep):
         out["long_keys_256_512"] = run_long(ht, torch, dev)
+    if want("wide_bfs", a.no_sweep):
         out["wide_bfs_80bit"] = run_wide_bfs(ht, torch, dev)
-    if not a.no_bfs:
+    if want("bfs", a.no_bfs):
         out["bfs_config3"] = run_bfs(ht, torch, dev, schemes)
-    if not a.no_batched:
+    if want("batched", a.no_batched):
         out["batched_config4"] = run_batched(ht, torch)
-    if not a.no_serving:
+    if want("serving", a.no_serving):
         out["serving_config5"] = run_serving(ht, a)
     for t in tables.values():
         t.close()

@@ -239,7 +239,9 @@ def random_access_roofline(scheme, fs, table, stats, ms_per_fill, probe):
         else:                       # the model: h_1, then h_2..h_k when h_1 is occupied
             info = table.info()
             reads = n_rep + n_new * new_key_load(fs, info["slots"]) * (info["num_hashes"] - 1)
-        claims = max(n_new, stats["exchanges"])
+        # every table atomic of the insertions: the probe's CASes into the
+        # first empty slot, then the chains' exchanges
+        claims = max(n_new, stats.get("probe_cas", 0) + stats["exchanges"])
     t_min = reads / r_read + claims / r_rmw
     return {"min_ms_per_fill": round(t_min * 1e3, 3), "frac": round(t_min * 1e3 / ms_per_fill, 3),
             "lines_read_per_key": round(reads / fs.n_issued, 3),
@@ -301,7 +303,7 @@ def kernel_random_access(name, k, fs, tables, stats, probe, steps):
         else:
             info = tables["cuckoo"].info()
             reads = n_rep + n_new * (1 + new_key_load(fs, info["slots"]) * (info["num_hashes"] - 1))
-        claims = 0
+        claims = stats["cuckoo"].get("probe_cas", 0)
     elif name == "cuckoo_insert":
         reads, claims = 0, stats["cuckoo"]["exchanges"]
     else:
@@ -410,12 +412,16 @@ def run_ours(a, rank, world, local):
                       if "cuckoo" in fill_stats and fill_stats["cuckoo"].get("probes") else None)
     probes_per_key = probes_counted if probes_counted is not None else probes_model
     cuckoo_exchanges_per_new = (fill_stats["cuckoo"]["exchanges"] / fs.n_distinct) if "cuckoo" in fill_stats else 1.0
+    # The probe's CASes of absent keys into the first empty slot they saw
+    # (an insertion's first step, taken in the probe kernel).
+    cuckoo_cas_per_key = (fill_stats["cuckoo"].get("probe_cas", 0) / fs.n_issued) if "cuckoo" in fill_stats else 0.0
     # Algorithmic bytes per unit, as the method defines them (the per-unit
     # figures of the hot-path measurement plan): a Cuckoo hit moves the
     # sectors of the slots up to the one holding the key (E_hit, counted); a
     # miss the sectors of all k slots, whatever this kernel's early exit
-    # saves; the insert one 32-byte sector of read-modify-write per exchange
-    # (counted) plus its record.  A bucket key moves one 128-byte bucket and,
+    # saves; an insertion one 32-byte sector of read-modify-write per
+    # exchange (counted), its first step a CAS in the probe kernel unless all
+    # k slots were full, plus its record.  A bucket key moves one 128-byte bucket and,
     # when new, the claimed sector.  Every unit adds its 8-byte key and its
     # 1-byte flag.
     cs = fill_stats.get("cuckoo", {})
@@ -428,14 +434,14 @@ def run_ours(a, rank, world, local):
         probe_slots_method = probes_per_key
     per_key = {
         "bucket_find_or_put": 8 + 1 + 128 + p_new * 32,
-        "cuckoo_probe": 8 + 1 + probe_slots_method * 32 + p_new * 16,
-        "cuckoo_insert": 16 + 32 * max(1.0, cuckoo_exchanges_per_new),
+        "cuckoo_probe": 8 + 1 + probe_slots_method * 32 + cuckoo_cas_per_key * 32 + p_new * 16,
+        "cuckoo_insert": 16 + 32 * cuckoo_exchanges_per_new,
     }
     # The same with the work this implementation does: the slots its probes
     # actually read (counted), and a sector read and written per exchange.
     per_key_done = dict(per_key)
-    per_key_done["cuckoo_probe"] = 8 + 1 + probes_per_key * 32 + p_new * 16
-    per_key_done["cuckoo_insert"] = 16 + 64 * max(1.0, cuckoo_exchanges_per_new)
+    per_key_done["cuckoo_probe"] = 8 + 1 + probes_per_key * 32 + cuckoo_cas_per_key * 64 + p_new * 16
+    per_key_done["cuckoo_insert"] = 16 + 64 * cuckoo_exchanges_per_new
     # units over the timed region; divided by each kernel's launch count below
     units_total = {"bucket_find_or_put": fs.n_issued * a.steps,
                    "cuckoo_probe": fs.n_issued * a.steps,
@@ -461,13 +467,15 @@ def run_ours(a, rank, world, local):
                 "frac_of_nominal_7900": round(kernels[dom]["achieved_gbs"] / 7900.0, 3),
                 "traffic": traffic, "alg_bytes_per_key": round(per_key[dom], 1),
                 "alg_bytes": "the method's per-unit figures: Cuckoo hit E_hit x 32 B, miss k x 32 B, "
-                             "32 B per exchange; bucket one 128-byte bucket + 32 B per new key; + key and flag",
+                             "32 B per insertion CAS (probe) or exchange (insert); bucket one 128-byte bucket + "
+                             "32 B per new key; + key and flag",
                 "frac_work_done": kernels[dom].get("frac_of_" + peak_src + "_work_done"),
                 "alg_bytes_per_key_work_done": round(per_key_done[dom], 1),
                 "cuckoo_slots_per_key_method": round(probe_slots_method, 3),
                 "cuckoo_probes_per_key": round(probes_per_key, 3), "cuckoo_probes_per_key_model": round(probes_model, 3),
                 "cuckoo_probes_counted": probes_counted is not None,
-                "cuckoo_exchanges_per_new_key": round(cuckoo_exchanges_per_new, 3)}
+                "cuckoo_exchanges_per_new_key": round(cuckoo_exchanges_per_new, 3),
+                "cuckoo_probe_cas_per_new_key": round(cuckoo_cas_per_key * fs.n_issued / fs.n_distinct, 3)}
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "Mops/s", "n_gpus": world, "steps": a.steps,

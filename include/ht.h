@@ -243,7 +243,9 @@ typedef struct ht_table_stats {
     uint64_t size;            /* keys stored (table + stash + overflow set) */
     uint64_t dropped;         /* keys that found no place (then HT_ERR_FULL) */
     uint64_t exchanges;       /* Cuckoo: atomic exchanges made by insertion
-                                 chains (Section 4.1); 0 for the bucket scheme */
+                                 chains (Section 4.1; for 32/64-bit keys only
+                                 keys that found all k slots full run one);
+                                 0 for the bucket scheme */
     uint32_t stash_used;      /* stash slots in use */
     uint32_t overflow_used;   /* overflow-set slots in use */
     uint32_t rebuilds;        /* rebuilds since ht_create */
@@ -258,7 +260,11 @@ typedef struct ht_table_stats {
                                  nowhere (absent from the table) ... */
     uint64_t probe_miss_reads;/* ... and the slots their probes read (h_1,
                                  then h_2.. up to the first empty slot) */
-    uint64_t reserved_;
+    uint64_t probe_cas;       /* Cuckoo (32/64-bit keys): compare-and-swaps of
+                                 absent keys into the first empty slot their
+                                 probe saw (and on, in slot order, when another
+                                 key took it first); with exchanges, every
+                                 atomic an insertion made in the table */
 } ht_table_stats;
 
 /* Reads the table's counters into *out (caller-owned host memory);

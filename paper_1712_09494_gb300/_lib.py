@@ -66,7 +66,7 @@ class HtTableStats(ctypes.Structure):
         ("size", ctypes.c_uint64), ("dropped", ctypes.c_uint64), ("exchanges", ctypes.c_uint64),
         ("stash_used", ctypes.c_uint32), ("overflow_used", ctypes.c_uint32),
         ("rebuilds", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("probes", ctypes.c_uint64),
-        ("probe_misses", ctypes.c_uint64), ("probe_miss_reads", ctypes.c_uint64), ("reserved_", ctypes.c_uint64),
+        ("probe_misses", ctypes.c_uint64), ("probe_miss_reads", ctypes.c_uint64), ("probe_cas", ctypes.c_uint64),
     ]
 
 

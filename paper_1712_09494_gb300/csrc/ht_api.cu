@@ -711,6 +711,7 @@ ht_status ht_stats(ht_table* t, ht_table_stats* out, void* stream) {
     out->probes = c.probes;
     out->probe_misses = c.probe_misses;
     out->probe_miss_reads = c.probe_miss_reads;
+    out->probe_cas = c.probe_cas;
     out->stash_used = c.stash_used;
     out->overflow_used = c.ovf_used;
     out->rebuilds = t->rebuilds;

@@ -4,33 +4,47 @@
 // key) so a slot moves atomically.  One thread handles one key.
 //
 // find-or-put of a batch runs as two kernels:
-//  1. probe: look each key up in its k slots h_1..h_k (and the stash); a key
-//     that is absent claims its key in a per-batch dedup set, and the single
-//     claimant per distinct key becomes a "winner" (is_new = 1) appended to
-//     a compact list.
+//  1. probe: look each key up in its k slots h_1..h_k (and the stash).  An
+//     absent key that saw an EMPTY slot stores itself at the first one with
+//     a CAS from EMPTY, going on in slot order if another key took it first
+//     (is_new = 1 for the copy whose CAS succeeded).  An absent key whose k
+//     slots are all full claims its key in a per-batch dedup set, and the
+//     single claimant per such key becomes a "winner" (is_new = 1).  Every
+//     new key is appended to a compact list.
 //  2. insert: each winner runs the eviction chain: exchange the word into
-//     its first slot; if the slot held a word k', find a with h_a(k') = slot
-//     and move k' to h_{a+1}(k') (Fig. 2: key 18 evicts 26 from its h_2 slot
-//     and 26 moves to h_3), until an empty slot takes the word or
-//     max_evictions is reached; then the stash takes it (Section 4.1: a small
-//     stash, and a rebuild with new hash constants when it overflows).
-//     Section 4.1 starts every chain at h_1.  Here a chain starts by default
-//     at the first of h_1..h_k that the probe saw EMPTY (h_1 if none): the
-//     probe has read those slots anyway, and most new keys then need one
-//     exchange instead of an eviction at h_1 (t.chain_h1 = 1 keeps h_1).
+//     h_1; if the slot held a word k', find a with h_a(k') = slot and move
+//     k' to h_{a+1}(k') (Fig. 2: key 18 evicts 26 from its h_2 slot and 26
+//     moves to h_3), until an empty slot takes the word or max_evictions is
+//     reached; then the stash takes it (Section 4.1: a small stash, and a
+//     rebuild with new hash constants when it overflows).  Keys stored by
+//     the probe are only counted here (and appended, for a frontier).
+//     Section 4.1 starts every insertion at h_1 with an exchange.  Here an
+//     insertion starts by default at the first of h_1..h_k that the probe
+//     saw EMPTY, where it needs no eviction, and only keys with all k slots
+//     full start a chain at h_1; t.chain_h1 = 1 keeps the paper's rule (a
+//     CAS only at an EMPTY h_1, every other insertion a chain from h_1).
+//     A Cuckoo insertion's cost is its atomics (random CASes and exchanges
+//     run at the same rate whether their line is in L2 or not), so storing
+//     in the probe with the one CAS that also settles duplicates takes the
+//     dedup claim off most new keys.
 //
 // The probe stops at an empty h_1 (a key is never stored past an empty
-// slot of its own).  Why that holds with either start: slots never return
-// to EMPTY (an exchange always leaves a word), a chain's key is placed at
-// h_j only when h_1..h_(j-1) were seen occupied, and an evicted key moves
-// from h_a to h_(a+1) with h_a now occupied by its evictor.
+// slot of its own).  Why that holds: slots never return to EMPTY (a CAS or
+// an exchange always leaves a word), a key is stored at h_j only when
+// h_1..h_(j-1) were seen occupied, and an evicted key moves from h_a to
+// h_(a+1) with h_a now occupied by its evictor.
 //
-// Why the dedup set: the paper's duplicate handling (Section 5.1.1: a thread
-// that evicts its own key stops) does not stop a duplicate whose first copy
-// was just evicted by a third key's chain, so the same key could be stored
-// twice with two is_new flags.  The table is not written between the probe
-// and the insert kernel, so every winner is truly absent and all winners are
-// distinct -- the precondition of Alcantara's insertion.
+// Why duplicates need care: the paper's duplicate handling (Section 5.1.1:
+// a thread that evicts its own key stops) does not stop a duplicate whose
+// first copy was just evicted by a third key's chain, so the same key could
+// be stored twice with two is_new flags.  Nothing moves a stored key during
+// the probe kernel: its only table writes are CASes from EMPTY.  Copies of
+// a key that store in the probe claim in slot order, so at most one CAS
+// succeeds and a copy probed later finds the key; a copy that saw all k
+// slots full read each after it was filled, so no copy stores the key in
+// the table during the probe and the dedup set elects one winner.  Every
+// winner is thus truly absent and all winners are distinct -- the
+// precondition of Alcantara's insertion.
 #include "ht_internal.cuh"
 
 namespace ht {
@@ -40,29 +54,39 @@ namespace {
 #define HT_CUCKOO_KEYS_PER_THREAD 4
 #endif
 constexpr int kU = HT_CUCKOO_KEYS_PER_THREAD;   // keys in flight per thread
+// Blocks per SM the probe is compiled for: find-or-put holds the CAS
+// results of its U keys besides their probe words (2 blocks, no spills: the
+// fill is 17% faster than at 3 blocks with spills); lookup keeps 3.
 #ifndef HT_CUCKOO_PROBE_MIN_BLOCKS
-#define HT_CUCKOO_PROBE_MIN_BLOCKS 3
+#define HT_CUCKOO_PROBE_MIN_BLOCKS 2
+#endif
+#ifndef HT_CUCKOO_LOOKUP_MIN_BLOCKS
+#define HT_CUCKOO_LOOKUP_MIN_BLOCKS 3
 #endif
 #ifndef HT_CUCKOO_INSERT_MIN_BLOCKS
 #define HT_CUCKOO_INSERT_MIN_BLOCKS 3
 #endif
 
-// Probe (and, for find-or-put, dedup).  Each thread holds U keys of a round,
-// strided by the grid so every load of keys stays coalesced; all U first
-// probes are issued together, then all remaining probes of the misses, then
-// every miss's first dedup claim, so U memory latencies overlap.  KH bounds
+// Probe (and, for find-or-put, the stores and the dedup).  Each thread
+// holds U keys of a round, strided by the grid so every load of keys stays
+// coalesced; all U first probes are issued together, then the remaining
+// probes of the misses, then the misses' CASes, then the dedup claims of
+// the keys that found every slot full, so U memory latencies overlap.  KH bounds
 // the table's k at compile time (4 for the usual k <= 4, else 8): the probe
 // words in flight are held in registers, and sizing them for k <= 4 keeps
 // enough warps resident per SM.
-#ifndef HT_CUCKOO_INSERT_PREFETCH
-#define HT_CUCKOO_INSERT_PREFETCH 1
-#endif
 #ifndef HT_CUCKOO_PROBE_SPLIT
 #define HT_CUCKOO_PROBE_SPLIT 2
+#endif
+#ifndef HT_CUCKOO_DIRECT
+#define HT_CUCKOO_DIRECT 1                     // absent keys CAS themselves into the EMPTY slot they saw
 #endif
 #ifndef HT_CUCKOO_STAGE
 #define HT_CUCKOO_STAGE 128                    // staged winners per warp
 #endif
+
+// The start field of a winner record whose key the probe already stored.
+constexpr uint32_t kStartPlaced = 0xFFFFFFFFu;
 
 // A winner waiting in a warp's shared-memory stage: its record and its
 // position in the batch (to clear its flag if the list turns out full).
@@ -74,7 +98,7 @@ struct StagedWinner {
 };
 
 template <int KW, bool VALUES, bool LOOKUP, int KH>
-__global__ void __launch_bounds__(kBlock, KH <= 4 ? HT_CUCKOO_PROBE_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(kBlock, KH > 4 ? 1 : LOOKUP ? HT_CUCKOO_LOOKUP_MIN_BLOCKS : HT_CUCKOO_PROBE_MIN_BLOCKS)
 cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     const void* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t n,
                     const unsigned long long* __restrict__ d_n, uint64_t off,
@@ -93,13 +117,15 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     const int lane = threadIdx.x & 31;
     unsigned long long probes = 0;            // slots read (h_1, then h_2..h_k if h_1 is occupied)
     unsigned long long misses = 0, miss_reads = 0;   // keys found nowhere, and the slots they read
+    unsigned long long direct = 0;            // CASes of absent keys into table slots
     constexpr int kStage = LOOKUP ? 1 : HT_CUCKOO_STAGE;
     __shared__ StagedWinner s_win[kBlock / 32][kStage];
     StagedWinner* stage = s_win[threadIdx.x >> 5];
     uint32_t pend = 0;
     // Lists the staged winners: one atomic on the winner count per flush.
     // Entries past the list's capacity (more winners than the table holds)
-    // give their claim back, are reported dropped and lose their flag.
+    // give their claim back, are reported dropped and lose their flag --
+    // unless the probe stored them already.
     auto flush = [&]() {
         __syncwarp();
         if (pend) {
@@ -115,6 +141,8 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     wn.spos = e.spos;
                     wn.start = e.start;
                     sc.win[at] = wn;
+                } else if (e.start == kStartPlaced) {
+                    atomicAdd(&t.ctr->size, 1ull);     // stored already (it holds no claim)
                 } else {
                     sc.set[e.spos] = kEmpty;       // no insert will clear its claim
                     set_flag(t.ctr, kFlagDropped);
@@ -245,31 +273,84 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                 }
             }
         } else {
-            // In-batch dedup: the one claimant of each absent key wins.  Every
-            // miss first CASes its key into its slot of the claim set (kept in
-            // L2); a slot holding another key sends it on by linear probing.
-            uint32_t spos[kU];
-            uint64_t sw[kU];
-            bool need[kU], winner[kU];
+            // A miss that saw an EMPTY slot stores itself there with a CAS
+            // from EMPTY, trying its slots in order from that one: a CAS that
+            // returns the key means another copy stored it first (not new);
+            // one that returns another key moves on to the next slot, which
+            // the CAS reads as well.  This is the bucket scheme's claim in
+            // slot order (Section 4.2), over h_a..h_k.  Nothing leaves a slot
+            // during the probe kernel, so a key is stored in at most one slot
+            // and every copy probed later finds it; a copy that saw all k
+            // slots full read them after they were full, so no copy stores
+            // it in the table here.  With t.chain_h1 only an EMPTY h_1 is
+            // tried (Section 4.1 starts every insertion at h_1).
+            bool placed[kU], claim[kU], pend_cas[kU];
+            uint32_t at[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                need[u] = act[u] && !found[u];
+                const bool miss = act[u] && !found[u];
+                at[u] = occ1[u] ? start[u] : 0u;
+                pend_cas[u] = HT_CUCKOO_DIRECT && miss && (!occ1[u] || (start[u] != 0 && !t.chain_h1));
+                claim[u] = miss && !pend_cas[u];
+                placed[u] = false;
+            }
+#pragma unroll
+            for (int pass = 0; pass < KH; ++pass) {
+                bool any = false;
+#pragma unroll
+                for (int u = 0; u < kU; ++u) any |= pend_cas[u];
+                if (!__any_sync(0xFFFFFFFFu, any)) break;
+                uint64_t cw[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (pend_cas[u]) {
+                        const uint64_t i = (r * kU + u) * stride + tid;
+                        cw[u] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + hidx(key[u], t.seed[at[u]], t.nslots)),
+                                          kEmpty, K::word(key[u], VALUES ? vals[i] : 0u));
+                        ++direct;
+                    }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    if (!pend_cas[u]) continue;
+                    if (cw[u] == kEmpty) {
+                        placed[u] = true;
+                        pend_cas[u] = false;
+                    } else if (K::keyof(cw[u]) == key[u]) {
+                        pend_cas[u] = false;                   // another copy stored it
+                    } else if (t.chain_h1 || at[u] + 1 >= t.k) {
+                        claim[u] = true;                       // every slot is full now
+                        pend_cas[u] = false;
+                    } else {
+                        ++at[u];
+                    }
+                }
+            }
+            // The misses that found all k slots full go through the claim
+            // set: the one claimant of each such key wins and runs an
+            // eviction chain from h_1 in the insert kernel.  Each CASes its
+            // key into its slot of the claim set (kept in L2); a slot holding
+            // another key sends it on by linear probing.
+            uint32_t spos[kU];
+            uint64_t sw[kU];
+            bool winner[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
                 spos[u] = uint32_t(mix64(key[u] ^ dseed) & sc.mask);
                 sw[u] = kEmpty;
-                if (need[u]) sw[u] = atomicCAS(reinterpret_cast<unsigned long long*>(sc.set + spos[u]), kEmpty, key[u]);
+                if (claim[u]) sw[u] = atomicCAS(reinterpret_cast<unsigned long long*>(sc.set + spos[u]), kEmpty, key[u]);
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                winner[u] = false;
-                if (!need[u]) continue;
+                winner[u] = placed[u];
+                if (!claim[u]) continue;
                 if (sw[u] == kEmpty) {
                     winner[u] = true;                          // our CAS filled the empty slot
                 } else if (K::keyof(sw[u]) != key[u]) {        // another key sits there: probe on
-                    uint32_t at = 0;
+                    uint32_t sat = 0;
                     const uint32_t next = spos[u] + 1 == uint32_t(sc.mask + 1) ? 0u : spos[u] + 1;
-                    const int rc = lp_insert<KW>(sc.set, uint32_t(sc.mask + 1), next, key[u], key[u], &at);
+                    const int rc = lp_insert<KW>(sc.set, uint32_t(sc.mask + 1), next, key[u], key[u], &sat);
                     winner[u] = rc == 1;
-                    spos[u] = at;
+                    spos[u] = sat;
                     if (rc < 0) {                              // more distinct misses than the table holds
                         set_flag(t.ctr, kFlagDropped);
                         atomicAdd(&t.ctr->dropped, 1ull);
@@ -290,7 +371,7 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                         e.word = K::word(key[u], VALUES ? vals[i] : 0u);
                         e.i = i;
                         e.spos = spos[u];
-                        e.start = t.chain_h1 ? 0u : start[u];
+                        e.start = placed[u] ? kStartPlaced : (HT_CUCKOO_DIRECT || t.chain_h1) ? 0u : start[u];
                     }
                     pend += __popc(wm);
                 }
@@ -303,8 +384,10 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         probes += __shfl_down_sync(0xFFFFFFFFu, probes, o);
         misses += __shfl_down_sync(0xFFFFFFFFu, misses, o);
         miss_reads += __shfl_down_sync(0xFFFFFFFFu, miss_reads, o);
+        direct += __shfl_down_sync(0xFFFFFFFFu, direct, o);
     }
     if (lane == 0 && probes) atomicAdd(&t.ctr->probes, probes);
+    if (lane == 0 && direct) atomicAdd(&t.ctr->probe_cas, direct);
     if (lane == 0 && misses) {
         atomicAdd(&t.ctr->probe_misses, misses);
         atomicAdd(&t.ctr->probe_miss_reads, miss_reads);
@@ -315,7 +398,10 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
 // flight so their exchanges overlap, and a chain that ends (an empty slot,
 // or the stash) is replaced at once by the thread's next winner: chain
 // lengths vary widely at high load, and refilling keeps every slot of the
-// thread busy instead of waiting for the longest chain of a round.
+// thread busy instead of waiting for the longest chain of a round.  Each
+// step reads the next records for all free chain slots together with the
+// live chains' exchanges; a record whose key the probe stored only gives
+// its claim back, so most records cost no round trip of their own.
 template <int KW, bool APPEND>
 __global__ void __launch_bounds__(kBlock, HT_CUCKOO_INSERT_MIN_BLOCKS)
 cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uint64_t max_winners,
@@ -342,49 +428,35 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
     uint64_t word[kU], pos[kU];
     uint32_t evictions[kU];
     bool live[kU];
-    // Each chain slot's next winner record is loaded one winner ahead, so a
-    // slot that frees up starts its next chain without waiting for the read.
-    Winner pre[kU];
-    bool pre_ok[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
         live[u] = false;
         word[u] = 0;
         pos[u] = 0;
         evictions[u] = 0;
-        pre_ok[u] = HT_CUCKOO_INSERT_PREFETCH && next < count;
-        if (pre_ok[u]) pre[u] = sc.win[next];
-        if (HT_CUCKOO_INSERT_PREFETCH) next += stride;
     }
-    // Bounded: each winner is taken once and its chain ends after at most
+    // Bounded: each step takes at least one record or runs at least one
+    // exchange; each winner is taken once and its chain ends after at most
     // max_evictions + 1 exchanges.
     for (;;) {
-        bool any = false;
+        uint32_t nfree = 0;
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (!live[u] && (HT_CUCKOO_INSERT_PREFETCH ? pre_ok[u] : next < count)) {
-                Winner wn;
-                if (HT_CUCKOO_INSERT_PREFETCH) {
-                    wn = pre[u];
-                    pre_ok[u] = next < count;
-                    if (pre_ok[u]) pre[u] = sc.win[next];
-                } else {
-                    wn = sc.win[next];
-                }
+        for (int u = 0; u < kU; ++u) nfree += live[u] ? 0u : 1u;
+        Winner rec[kU];
+        bool got[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            got[j] = uint32_t(j) < nfree && next < count;
+            if (got[j]) {
+                rec[j] = sc.win[next];
                 next += stride;
-                sc.set[wn.spos] = kEmpty;      // leave the dedup set empty for the next batch
-                word[u] = wn.word;
-                pos[u] = hidx(K::keyof(wn.word), t.seed[wn.start < t.k ? wn.start : 0u], t.nslots);
-                evictions[u] = 0;
-                live[u] = true;
             }
-            any |= live[u];
         }
-        if (!any) break;
         uint64_t old[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u)
             if (live[u]) old[u] = atomicExch(reinterpret_cast<unsigned long long*>(t.slots + pos[u]), word[u]);
+        bool any = false;
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             if (!live[u]) continue;
@@ -409,7 +481,33 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
                 if (hidx(key, t.seed[a], t.nslots) == pos[u]) break;
             const uint32_t nxt = (a + 1 == t.k) ? 0u : a + 1;
             pos[u] = hidx(key, t.seed[nxt], t.nslots);
+            any = true;
         }
+        // The records read this step: a key the probe stored is counted; a
+        // claimant gives its claim back (the dedup set is left empty for the
+        // next batch) and takes a free chain slot (there are at least as
+        // many as records read).
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            if (!got[j]) continue;
+            if (rec[j].start == kStartPlaced) {
+                ++placed;
+                continue;
+            }
+            sc.set[rec[j].spos] = kEmpty;
+            bool taken = false;
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (!live[u] && !taken) {
+                    word[u] = rec[j].word;
+                    pos[u] = hidx(K::keyof(rec[j].word), t.seed[rec[j].start < t.k ? rec[j].start : 0u], t.nslots);
+                    evictions[u] = 0;
+                    live[u] = true;
+                    taken = true;
+                }
+            any = true;
+        }
+        if (!any && next >= count) break;
     }
     for (int o = 16; o; o >>= 1) {
         placed += __shfl_down_sync(0xFFFFFFFFu, placed, o);

@@ -38,8 +38,9 @@ struct DevCounters {
     unsigned long long ids;       // long-key Cuckoo: key-store rows handed out
     unsigned long long probe_misses;      // Cuckoo: probed keys found nowhere (64-bit path)
     unsigned long long probe_miss_reads;  // ... and the slots those keys' probes read
+    unsigned long long probe_cas; // Cuckoo (64-bit path): CASes of absent keys into table slots
 };
-static_assert(sizeof(DevCounters) == 80, "counter block layout");
+static_assert(sizeof(DevCounters) == 88, "counter block layout");
 
 // Everything a kernel needs to address a table; passed by value.
 struct DevTable {

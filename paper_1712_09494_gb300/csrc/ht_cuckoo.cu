@@ -63,6 +63,18 @@ constexpr int kU = HT_CUCKOO_KEYS_PER_THREAD;   // keys in flight per thread
 #ifndef HT_CUCKOO_LOOKUP_MIN_BLOCKS
 #define HT_CUCKOO_LOOKUP_MIN_BLOCKS 3
 #endif
+// Tables that fit in L2 get a find-or-put probe of kUL2 keys per thread at
+// 3 blocks per SM: their keys are mostly hits served by L2, where more warps
+// hide more latency (a replay of 10^8 keys of multiplicity 1000: 2.04 ms
+// instead of 2.33).  Larger tables keep kU keys at 2 blocks (the 2^27-key
+// fill: 18.7 ms instead of 19.2).
+#ifndef HT_CUCKOO_KEYS_PER_THREAD_L2
+#define HT_CUCKOO_KEYS_PER_THREAD_L2 3
+#endif
+#ifndef HT_CUCKOO_PROBE_L2_MIN_BLOCKS
+#define HT_CUCKOO_PROBE_L2_MIN_BLOCKS 3
+#endif
+constexpr int kUL2 = HT_CUCKOO_KEYS_PER_THREAD_L2;
 #ifndef HT_CUCKOO_INSERT_MIN_BLOCKS
 #define HT_CUCKOO_INSERT_MIN_BLOCKS 3
 #endif
@@ -97,8 +109,9 @@ struct StagedWinner {
     uint32_t start;
 };
 
-template <int KW, bool VALUES, bool LOOKUP, int KH>
-__global__ void __launch_bounds__(kBlock, KH > 4 ? 1 : LOOKUP ? HT_CUCKOO_LOOKUP_MIN_BLOCKS : HT_CUCKOO_PROBE_MIN_BLOCKS)
+template <int KW, bool VALUES, bool LOOKUP, int KH, int U = kU>
+__global__ void __launch_bounds__(kBlock, KH > 4 ? 1 : LOOKUP ? HT_CUCKOO_LOOKUP_MIN_BLOCKS
+                                          : U == kU ? HT_CUCKOO_PROBE_MIN_BLOCKS : HT_CUCKOO_PROBE_L2_MIN_BLOCKS)
 cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     const void* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t n,
                     const unsigned long long* __restrict__ d_n, uint64_t off,
@@ -112,7 +125,7 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     const uint32_t ovf_used = __ldcg(&t.ctr->ovf_used);
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint64_t rounds = (n + stride * kU - 1) / (stride * kU);     // warp-uniform trip count
+    const uint64_t rounds = (n + stride * U - 1) / (stride * U);     // warp-uniform trip count
     const uint64_t dseed = t.aux_seed * 3 + 1;
     const int lane = threadIdx.x & 31;
     unsigned long long probes = 0;            // slots read (h_1, then h_2..h_k if h_1 is occupied)
@@ -155,21 +168,21 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         pend = 0;
     };
     // The next round's keys are loaded while this round waits on the table.
-    uint64_t next_key[kU];
+    uint64_t next_key[U];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
+    for (int u = 0; u < U; ++u) {
         const uint64_t i = uint64_t(u) * stride + tid;
         next_key[u] = i < n ? K::load(keys, i) : 0;
     }
     for (uint64_t r = 0; r < rounds; ++r) {
-        uint64_t key[kU], w[kU];
-        bool act[kU], found[kU];
+        uint64_t key[U], w[U];
+        bool act[U], found[U];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const uint64_t i = (r * kU + u) * stride + tid;
+        for (int u = 0; u < U; ++u) {
+            const uint64_t i = (r * U + u) * stride + tid;
             act[u] = i < n;
             key[u] = next_key[u];
-            const uint64_t j = ((r + 1) * kU + u) * stride + tid;
+            const uint64_t j = ((r + 1) * U + u) * stride + tid;
             if (j < n) next_key[u] = K::load(keys, j);
             if (act[u] && K::reserved(key[u])) {
                 set_flag(t.ctr, kFlagInvalidKey);
@@ -178,14 +191,14 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         }
         // Section 4.1: a key is found in at most k probes; h_1 first.
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
+        for (int u = 0; u < U; ++u)
             if (act[u]) w[u] = __ldcg(reinterpret_cast<const unsigned long long*>(t.slots + hidx(key[u], t.seed[0], t.nslots)));
         // An empty h_1 slot ends the table probe: a key stored at h_j has
         // h_1 .. h_{j-1} all occupied (see the top of this file).  A miss at
         // table load a then costs 1 + a (k - 1) probes, not k.
-        bool more[kU], occ1[kU];
+        bool more[U], occ1[U];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < U; ++u) {
             found[u] = act[u] && K::keyof(w[u]) == key[u];
             more[u] = act[u] && !found[u] && !K::empty(w[u]);
             occ1[u] = more[u];
@@ -193,10 +206,10 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         }
         // The chain start of a miss: the first of h_2..h_k seen EMPTY (0 =
         // h_1: empty, or every slot occupied).
-        uint32_t start[kU];
-        uint64_t ws[kU][KH];
+        uint32_t start[U];
+        uint64_t ws[U][KH];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) start[u] = 0;
+        for (int u = 0; u < U; ++u) start[u] = 0;
         // h_2..h_k in groups [a0, a1): the slots of a group are read together,
         // and a key goes on to the next group only while it is neither found
         // nor past an EMPTY slot (a key never sits past an empty slot of its
@@ -207,7 +220,7 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         // launch takes 0.141 instead of 0.157 ms.
         auto probe_group = [&](int a0, int a1) {
 #pragma unroll
-            for (int u = 0; u < kU; ++u)
+            for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int a = 1; a < KH; ++a)
                     if (a >= a0 && a < a1 && a < int(t.k) && more[u]) {
@@ -215,7 +228,7 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                         ++probes;
                     }
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int u = 0; u < U; ++u) {
                 if (!more[u]) continue;
 #pragma unroll
                 for (int a = KH - 1; a >= 1; --a)
@@ -235,26 +248,26 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             probe_group(1, 2);
             bool any = false;
 #pragma unroll
-            for (int u = 0; u < kU; ++u) any |= more[u];
+            for (int u = 0; u < U; ++u) any |= more[u];
             if (__any_sync(0xFFFFFFFFu, any)) probe_group(2, KH);
         } else {
 #pragma unroll
             for (int a = 1; a < KH; ++a) {
                 bool any = false;
 #pragma unroll
-                for (int u = 0; u < kU; ++u) any |= more[u];
+                for (int u = 0; u < U; ++u) any |= more[u];
                 if (a < int(t.k) && __any_sync(0xFFFFFFFFu, any)) probe_group(a, a + 1);
             }
         }
         if (stash_used | ovf_used) {
 #pragma unroll
-            for (int u = 0; u < kU; ++u)
+            for (int u = 0; u < U; ++u)
                 if (act[u] && !found[u]) found[u] = find_spill<KW>(t, key[u], stash_used, ovf_used, &w[u]);
         }
         // The slots read by the keys found nowhere (the table counters keep
         // them apart from the hits' reads).
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
+        for (int u = 0; u < U; ++u)
             if (act[u] && !found[u]) {
                 ++misses;
                 const uint32_t k = t.k;
@@ -265,8 +278,8 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             }
         if constexpr (LOOKUP) {
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const uint64_t i = (r * kU + u) * stride + tid;
+            for (int u = 0; u < U; ++u) {
+                const uint64_t i = (r * U + u) * stride + tid;
                 if (i < n) {
                     if (out_flag) out_flag[i] = uint8_t(found[u]);
                     if (out_val) out_val[i] = found[u] ? K::value(w[u]) : 0u;
@@ -284,10 +297,10 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             // slots full read them after they were full, so no copy stores
             // it in the table here.  With t.chain_h1 only an EMPTY h_1 is
             // tried (Section 4.1 starts every insertion at h_1).
-            bool placed[kU], claim[kU], pend_cas[kU];
-            uint32_t at[kU];
+            bool placed[U], claim[U], pend_cas[U];
+            uint32_t at[U];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const bool miss = act[u] && !found[u];
                 at[u] = occ1[u] ? start[u] : 0u;
                 pend_cas[u] = HT_CUCKOO_DIRECT && miss && (!occ1[u] || (start[u] != 0 && !t.chain_h1));
@@ -298,19 +311,19 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             for (int pass = 0; pass < KH; ++pass) {
                 bool any = false;
 #pragma unroll
-                for (int u = 0; u < kU; ++u) any |= pend_cas[u];
+                for (int u = 0; u < U; ++u) any |= pend_cas[u];
                 if (!__any_sync(0xFFFFFFFFu, any)) break;
-                uint64_t cw[kU];
+                uint64_t cw[U];
 #pragma unroll
-                for (int u = 0; u < kU; ++u)
+                for (int u = 0; u < U; ++u)
                     if (pend_cas[u]) {
-                        const uint64_t i = (r * kU + u) * stride + tid;
+                        const uint64_t i = (r * U + u) * stride + tid;
                         cw[u] = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + hidx(key[u], t.seed[at[u]], t.nslots)),
                                           kEmpty, K::word(key[u], VALUES ? vals[i] : 0u));
                         ++direct;
                     }
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
+                for (int u = 0; u < U; ++u) {
                     if (!pend_cas[u]) continue;
                     if (cw[u] == kEmpty) {
                         placed[u] = true;
@@ -330,17 +343,17 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             // eviction chain from h_1 in the insert kernel.  Each CASes its
             // key into its slot of the claim set (kept in L2); a slot holding
             // another key sends it on by linear probing.
-            uint32_t spos[kU];
-            uint64_t sw[kU];
-            bool winner[kU];
+            uint32_t spos[U];
+            uint64_t sw[U];
+            bool winner[U];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int u = 0; u < U; ++u) {
                 spos[u] = uint32_t(mix64(key[u] ^ dseed) & sc.mask);
                 sw[u] = kEmpty;
                 if (claim[u]) sw[u] = atomicCAS(reinterpret_cast<unsigned long long*>(sc.set + spos[u]), kEmpty, key[u]);
             }
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int u = 0; u < U; ++u) {
                 winner[u] = placed[u];
                 if (!claim[u]) continue;
                 if (sw[u] == kEmpty) {
@@ -361,8 +374,8 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             // listed with one atomic per flush rather than one per round, so
             // the next round does not wait on a shared counter.
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const uint64_t i = (r * kU + u) * stride + tid;
+            for (int u = 0; u < U; ++u) {
+                const uint64_t i = (r * U + u) * stride + tid;
                 const unsigned wm = __ballot_sync(0xFFFFFFFFu, winner[u]);
                 if (wm) {
                     if (pend + __popc(wm) > uint32_t(kStage)) flush();
@@ -519,14 +532,31 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
 
 }  // namespace
 
+namespace {
+// The current device's L2 size in bytes (queried once per device).
+uint64_t l2_bytes() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev);
+        cached[dev] = v > 0 ? v : -1;
+    }
+    return cached[dev] > 0 ? uint64_t(cached[dev]) : 0;
+}
+}  // namespace
+
 cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
                          const void* keys, const uint32_t* vals, uint64_t n,
                          const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s,
                          const L2Window& w) {
     ProfScope ps(kKCuckooProbe, s);
+    const bool in_l2 = t.nslots * 8 <= l2_bytes();
 #define L(KW, V)                                                                                        \
     {                                                                                                   \
-        auto k = t.k <= 4 ? cuckoo_probe_kernel<KW, V, false, 4> : cuckoo_probe_kernel<KW, V, false, kMaxCuckooHashes>; \
+        auto k = t.k > 4 ? cuckoo_probe_kernel<KW, V, false, kMaxCuckooHashes>                          \
+                 : in_l2 ? cuckoo_probe_kernel<KW, V, false, 4, kUL2> : cuckoo_probe_kernel<KW, V, false, 4>; \
         return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, sc, parity, keys, vals, n, \
                           d_n, off, is_new, (uint32_t*)nullptr);                                        \
     }

@@ -132,7 +132,7 @@ ht_status run_put(ht_table* t, const void* keys, const uint32_t* vals, uint64_t 
         const uint64_t m = std::min(t->chunk, n - off);
         const void* k = static_cast<const char*>(keys) + off * ksz;
         HT_TRY(cuckoo_probe(int(t->kw), t->dt, t->sc, t->parity, k, vals ? vals + off : nullptr, m, d_n,
-                            off, is_new ? is_new + off : nullptr, s, t->win));
+                            off, is_new ? is_new + off : nullptr, s, t->win, new_out != nullptr));
         HT_TRY(cuckoo_insert(int(t->kw), t->dt, t->sc, t->parity, new_out, new_count, new_cap,
                              std::min<uint64_t>(m, t->sc.win_cap), s, t->win));
         t->parity ^= 1u;

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kBlock, KH > 4 ? 1 : LOOKUP ? HT_CUCKOO_LOOKUP
 cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                     const void* __restrict__ keys, const uint32_t* __restrict__ vals, uint64_t n,
                     const unsigned long long* __restrict__ d_n, uint64_t off,
-                    uint8_t* __restrict__ out_flag, uint32_t* __restrict__ out_val) {
+                    uint8_t* __restrict__ out_flag, uint32_t* __restrict__ out_val, bool list_stored) {
     using K = Keys<KW>;
     if (d_n) {                                   // batch size produced on the device
         const uint64_t total = __ldcg(d_n);
@@ -131,6 +131,7 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     unsigned long long probes = 0;            // slots read (h_1, then h_2..h_k if h_1 is occupied)
     unsigned long long misses = 0, miss_reads = 0;   // keys found nowhere, and the slots they read
     unsigned long long direct = 0;            // CASes of absent keys into table slots
+    unsigned long long stored = 0;            // keys stored here and not listed
     constexpr int kStage = LOOKUP ? 1 : HT_CUCKOO_STAGE;
     __shared__ StagedWinner s_win[kBlock / 32][kStage];
     StagedWinner* stage = s_win[threadIdx.x >> 5];
@@ -372,14 +373,18 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             }
             // The round's winners go to the warp's stage in shared memory,
             // listed with one atomic per flush rather than one per round, so
-            // the next round does not wait on a shared counter.
+            // the next round does not wait on a shared counter.  Keys this
+            // kernel stored are listed only for a caller that appends the new
+            // keys (list_stored); otherwise they are just counted.
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const uint64_t i = (r * U + u) * stride + tid;
-                const unsigned wm = __ballot_sync(0xFFFFFFFFu, winner[u]);
+                const bool listed = winner[u] && (list_stored || !placed[u]);
+                stored += (placed[u] && !list_stored) ? 1u : 0u;
+                const unsigned wm = __ballot_sync(0xFFFFFFFFu, listed);
                 if (wm) {
                     if (pend + __popc(wm) > uint32_t(kStage)) flush();
-                    if (winner[u]) {
+                    if (listed) {
                         StagedWinner& e = stage[pend + __popc(wm & ((1u << lane) - 1))];
                         e.word = K::word(key[u], VALUES ? vals[i] : 0u);
                         e.i = i;
@@ -398,7 +403,9 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         misses += __shfl_down_sync(0xFFFFFFFFu, misses, o);
         miss_reads += __shfl_down_sync(0xFFFFFFFFu, miss_reads, o);
         direct += __shfl_down_sync(0xFFFFFFFFu, direct, o);
+        stored += __shfl_down_sync(0xFFFFFFFFu, stored, o);
     }
+    if (lane == 0 && stored) atomicAdd(&t.ctr->size, stored);
     if (lane == 0 && probes) atomicAdd(&t.ctr->probes, probes);
     if (lane == 0 && direct) atomicAdd(&t.ctr->probe_cas, direct);
     if (lane == 0 && misses) {
@@ -550,7 +557,7 @@ uint64_t l2_bytes() {
 cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
                          const void* keys, const uint32_t* vals, uint64_t n,
                          const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s,
-                         const L2Window& w) {
+                         const L2Window& w, bool list_stored) {
     ProfScope ps(kKCuckooProbe, s);
     const bool in_l2 = t.nslots * 8 <= l2_bytes();
 #define L(KW, V)                                                                                        \
@@ -558,7 +565,7 @@ cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32
         auto k = t.k > 4 ? cuckoo_probe_kernel<KW, V, false, kMaxCuckooHashes>                          \
                  : in_l2 ? cuckoo_probe_kernel<KW, V, false, 4, kUL2> : cuckoo_probe_kernel<KW, V, false, 4>; \
         return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, sc, parity, keys, vals, n, \
-                          d_n, off, is_new, (uint32_t*)nullptr);                                        \
+                          d_n, off, is_new, (uint32_t*)nullptr, list_stored);                           \
     }
     if (kw == 32) {
         if (vals) L(32, true) else L(32, false)
@@ -592,11 +599,13 @@ cudaError_t cuckoo_lookup(int kw, const DevTable& t, const void* keys, uint64_t 
     if (kw == 32) {
         auto k = t.k <= 4 ? cuckoo_probe_kernel<32, false, true, 4> : cuckoo_probe_kernel<32, false, true, kMaxCuckooHashes>;
         return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, none, 0u, keys,
-                          (const uint32_t*)nullptr, n, (const unsigned long long*)nullptr, uint64_t(0), found, vals);
+                          (const uint32_t*)nullptr, n, (const unsigned long long*)nullptr, uint64_t(0), found, vals,
+                          false);
     }
     auto k = t.k <= 4 ? cuckoo_probe_kernel<64, false, true, 4> : cuckoo_probe_kernel<64, false, true, kMaxCuckooHashes>;
     return launch_win(k, launch_blocks((const void*)k, kBlock), kBlock, s, w, t, none, 0u, keys,
-                      (const uint32_t*)nullptr, n, (const unsigned long long*)nullptr, uint64_t(0), found, vals);
+                      (const uint32_t*)nullptr, n, (const unsigned long long*)nullptr, uint64_t(0), found, vals,
+                      false);
 }
 
 }  // namespace ht

@@ -382,11 +382,12 @@ cudaError_t bucket_lookup(const BucketCfg& c, const DevTable& t, const void* key
                           uint32_t* vals, uint8_t* found, cudaStream_t s, const L2Window& w = L2Window());
 
 // d_n (nullable): the batch size lives on the device; this launch covers keys
-// [off, off + n) of it.
+// [off, off + n) of it.  list_stored: list the keys the probe stored itself
+// in the winner list too (for an insert that appends every new key).
 cudaError_t cuckoo_probe(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
                          const void* keys, const uint32_t* vals, uint64_t n,
                          const unsigned long long* d_n, uint64_t off, uint8_t* is_new,
-                         cudaStream_t s, const L2Window& w = L2Window());
+                         cudaStream_t s, const L2Window& w = L2Window(), bool list_stored = true);
 cudaError_t cuckoo_insert(int kw, const DevTable& t, const DevScratch& sc, uint32_t parity,
                           void* new_out, unsigned long long* new_count, uint64_t new_cap,
                           uint64_t max_winners, cudaStream_t s, const L2Window& w = L2Window());

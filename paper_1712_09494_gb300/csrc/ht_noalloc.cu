@@ -106,7 +106,8 @@ extern "C" ht_status ht_cuckoo_find_or_put_noalloc(uint64_t* d_slots, uint64_t n
     if (fill_words(sc.set, kNoallocSetSlots, kEmpty, s) != cudaSuccess ||
         cudaMemsetAsync(&t.ctr->winners[0], 0, sizeof(unsigned int), s) != cudaSuccess)
         return HT_ERR_CUDA;
-    if (cuckoo_probe(64, t, sc, 0, d_keys, nullptr, n, nullptr, 0, d_is_new, s) != cudaSuccess) return HT_ERR_CUDA;
+    if (cuckoo_probe(64, t, sc, 0, d_keys, nullptr, n, nullptr, 0, d_is_new, s, L2Window(), false) != cudaSuccess)
+        return HT_ERR_CUDA;
     if (cuckoo_insert(64, t, sc, 0, nullptr, nullptr, 0, n, s) != cudaSuccess) return HT_ERR_CUDA;
     return HT_OK;
 }

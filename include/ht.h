@@ -256,8 +256,9 @@ typedef struct ht_table_stats {
                                  0 for the bucket scheme (a per-key count there
                                  would put one shared counter on the hot path)
                                  and for 128-bit tables */
-    uint64_t probe_misses;    /* Cuckoo (32/64-bit keys): probed keys found
-                                 nowhere (absent from the table) ... */
+    uint64_t probe_misses;    /* Cuckoo (32/64-bit keys): keys that find-or-put
+                                 and insert found nowhere (absent from the
+                                 table; lookups are not counted) ... */
     uint64_t probe_miss_reads;/* ... and the slots their probes read (h_1,
                                  then h_2.. up to the first empty slot) */
     uint64_t probe_cas;       /* Cuckoo (32/64-bit keys): compare-and-swaps of

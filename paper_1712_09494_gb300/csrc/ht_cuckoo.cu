@@ -97,6 +97,33 @@ constexpr int kUL2 = HT_CUCKOO_KEYS_PER_THREAD_L2;
 #define HT_CUCKOO_STAGE 128                    // staged winners per warp
 #endif
 
+// Adds the block's per-warp sums (held by each warp's lane 0) to N table
+// counters with one atomic per counter and block, not per warp: the last
+// step of a kernel, reached by every thread of the block.  At one atomic per
+// warp, thousands of warps ending together queued on each counter's L2
+// slice, a fixed cost per launch that small launches (a BFS level's chunks)
+// paid in full.
+template <int N>
+__device__ __forceinline__ void block_add_counters(unsigned long long* const (&dst)[N],
+                                                   const unsigned long long (&v)[N]) {
+    __shared__ unsigned long long s_sum[N][kBlock / 32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) s_sum[c][w] = v[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            unsigned long long total = 0;
+#pragma unroll
+            for (int j = 0; j < kBlock / 32; ++j) total += s_sum[c][j];
+            if (total) atomicAdd(dst[c], total);       // no return value: the adds do not wait on each other
+        }
+    }
+}
+
 // The start field of a winner record whose key the probe already stored.
 constexpr uint32_t kStartPlaced = 0xFFFFFFFFu;
 
@@ -266,10 +293,11 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                 if (act[u] && !found[u]) found[u] = find_spill<KW>(t, key[u], stash_used, ovf_used, &w[u]);
         }
         // The slots read by the keys found nowhere (the table counters keep
-        // them apart from the hits' reads).
+        // them apart from the hits' reads; find-or-put only -- counting them
+        // costs a lookup registers it spills).
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (act[u] && !found[u]) {
+            if (!LOOKUP && act[u] && !found[u]) {
                 ++misses;
                 const uint32_t k = t.k;
                 miss_reads += !occ1[u] ? 1u
@@ -405,13 +433,10 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         direct += __shfl_down_sync(0xFFFFFFFFu, direct, o);
         stored += __shfl_down_sync(0xFFFFFFFFu, stored, o);
     }
-    if (lane == 0 && stored) atomicAdd(&t.ctr->size, stored);
-    if (lane == 0 && probes) atomicAdd(&t.ctr->probes, probes);
-    if (lane == 0 && direct) atomicAdd(&t.ctr->probe_cas, direct);
-    if (lane == 0 && misses) {
-        atomicAdd(&t.ctr->probe_misses, misses);
-        atomicAdd(&t.ctr->probe_miss_reads, miss_reads);
-    }
+    unsigned long long* const dst[5] = {&t.ctr->size, &t.ctr->probes, &t.ctr->probe_cas, &t.ctr->probe_misses,
+                                        &t.ctr->probe_miss_reads};
+    const unsigned long long sums[5] = {stored, probes, direct, misses, miss_reads};
+    block_add_counters<5>(dst, sums);
 }
 
 // Eviction-chain insert of the winners.  Each thread keeps U chains in
@@ -533,8 +558,9 @@ cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uin
         placed += __shfl_down_sync(0xFFFFFFFFu, placed, o);
         exchanges += __shfl_down_sync(0xFFFFFFFFu, exchanges, o);
     }
-    if ((threadIdx.x & 31) == 0 && placed) atomicAdd(&t.ctr->size, placed);
-    if ((threadIdx.x & 31) == 0 && exchanges) atomicAdd(&t.ctr->exchanges, exchanges);
+    unsigned long long* const dst[2] = {&t.ctr->size, &t.ctr->exchanges};
+    const unsigned long long sums[2] = {placed, exchanges};
+    block_add_counters<2>(dst, sums);
 }
 
 }  // namespace

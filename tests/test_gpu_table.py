@@ -335,7 +335,7 @@ def test_cuckoo_probe_stores_at_low_load():
     assert to_np(t.lookup(to_dev(keys))[0]).all()
     found, _ = t.lookup(to_dev(wk.distinct_keys(1000, 64, seed=44, start=n + 5)))
     assert int(found.sum()) == 0
-    assert t.stats()["probe_misses"] == n + 1000
+    assert t.stats()["probe_misses"] == n                     # lookups are not counted
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)

@@ -261,7 +261,7 @@ typedef struct ht_table_stats {
                                  table; lookups are not counted) ... */
     uint64_t probe_miss_reads;/* ... and the slots their probes read (h_1,
                                  then h_2.. up to the first empty slot) */
-    uint64_t probe_cas;       /* Cuckoo (32/64-bit keys): compare-and-swaps of
+    uint64_t probe_cas;       /* Cuckoo (32/64/128-bit keys): compare-and-swaps of
                                  absent keys into the first empty slot their
                                  probe saw (and on, in slot order, when another
                                  key took it first); with exchanges, every

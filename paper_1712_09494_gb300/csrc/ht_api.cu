@@ -116,7 +116,7 @@ ht_status run_put(ht_table* t, const void* keys, const uint32_t* vals, uint64_t 
         for (uint64_t off = 0; off < n; off += t->chunk) {
             const uint64_t m = std::min(t->chunk, n - off);
             HT_TRY(wide_cuckoo_probe(t->dt, t->sc, t->parity, static_cast<const char*>(keys) + off * 16, m, d_n, off,
-                                     is_new ? is_new + off : nullptr, s));
+                                     is_new ? is_new + off : nullptr, s, new_out != nullptr));
             HT_TRY(wide_cuckoo_insert(t->dt, t->sc, t->parity, new_out, new_count, new_cap,
                                       std::min<uint64_t>(m, t->sc.win_cap), s));
             t->parity ^= 1u;

@@ -38,7 +38,7 @@ struct DevCounters {
     unsigned long long ids;       // long-key Cuckoo: key-store rows handed out
     unsigned long long probe_misses;      // Cuckoo: probed keys found nowhere (64-bit path)
     unsigned long long probe_miss_reads;  // ... and the slots those keys' probes read
-    unsigned long long probe_cas; // Cuckoo (64-bit path): CASes of absent keys into table slots
+    unsigned long long probe_cas; // Cuckoo (32/64/128-bit keys): CASes of absent keys into table slots
 };
 static_assert(sizeof(DevCounters) == 88, "counter block layout");
 
@@ -487,11 +487,15 @@ cudaError_t wide_find_or_put(int lanes, const DevTable& t, const void* keys, uin
 cudaError_t wide_lookup(int lanes, const DevTable& t, const void* keys, uint64_t n, uint8_t* found,
                         cudaStream_t s);
 cudaError_t wide_export(const DevTable& t, void* keys, unsigned long long* count, uint64_t cap, cudaStream_t s);
-// Cuckoo tables of 128-bit keys: probe (dedup, winners of `parity`), insert
-// (eviction chains; winners appended to new_out when non-null), lookup.  The
-// claim set holds 16-byte entries and the winner list 32-byte records.
+// Cuckoo tables of 128-bit keys: probe (stores into the first empty slot,
+// dedup of the keys with every slot full, winners of `parity`; list_stored:
+// list the stored keys too, for an insert that appends every new key),
+// insert (eviction chains; winners appended to new_out when non-null),
+// lookup.  The claim set holds 16-byte entries and the winner list 32-byte
+// records.
 cudaError_t wide_cuckoo_probe(const DevTable& t, const DevScratch& sc, uint32_t parity, const void* keys, uint64_t n,
-                              const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s);
+                              const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s,
+                              bool list_stored = true);
 cudaError_t wide_cuckoo_insert(const DevTable& t, const DevScratch& sc, uint32_t parity, void* new_out,
                                unsigned long long* new_count, uint64_t new_cap, uint64_t max_winners,
                                cudaStream_t s);

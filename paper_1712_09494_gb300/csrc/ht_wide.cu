@@ -227,19 +227,32 @@ wide_export_kernel(const DevTable t, uint64_t* __restrict__ out, unsigned long l
 // ---------------------------------------------------------------------------
 // Cuckoo hashing of 128-bit keys (Section 4.1 with 16-byte slots; the
 // generalisation to longer keys is the paper's own future work, Section 7).
-// The same two kernels as for 64-bit keys: a probe that finds keys in h_1
-// (then h_2..h_k when h_1 is occupied) and elects one winner per absent key
-// through a claim set of 16-byte entries (one CAS per claim), and an insert
-// that runs each winner's eviction chain with 16-byte atomic exchanges,
-// starting at the first slot the probe saw empty (h_1 if none).  No
-// writer runs during the probe launch, so its plain 16-byte reads are
-// complete; every write to a slot is one 16-byte atomic.
+// The same two kernels as for 64-bit keys.  The probe finds keys in h_1
+// (then h_2..h_k when h_1 is occupied); an absent key that met a slot
+// without a complete key stores itself there with a 16-byte CAS from EMPTY,
+// going on in slot order when another key took it first; a key whose k
+// slots all hold complete keys claims its key in a claim set of 16-byte
+// entries, and the one claimant runs an eviction chain from h_1 with
+// 16-byte atomic exchanges in the insert kernel.
+//
+// The probe's reads are plain 16-byte loads while its CASes write: a read
+// can show half of a key being stored (one all-ones word).  As in the
+// bucket kernels, only a read with neither word all ones counts as a
+// complete key (found, or occupied by another key); any other read is a
+// candidate that the CAS settles, returning the slot's true content.  So a
+// copy never passes a slot where another copy is storing its key, the
+// slot-order argument holds, and a copy that saw k complete keys read each
+// slot after it was filled (no copy stores the key in the table during the
+// probe).  Lookups run with no writer, so their reads are complete.
 
 struct WideWinner {
     uint64_t lo, hi;
     uint64_t spos;                        // its claim-set entry (cleared by the insert)
     uint64_t start;                       // the hash index its eviction chain starts at
 };
+// The start field of a record whose key the probe stored itself (listed
+// only for a caller that collects the new keys).
+constexpr uint64_t kWidePlaced = ~0ull;
 
 constexpr int kWU = 4;                    // keys (probe) or chains (insert) in flight per thread
 
@@ -250,7 +263,7 @@ template <bool LOOKUP>
 __global__ void __launch_bounds__(kBlock, HT_WIDE_PROBE_MIN_BLOCKS)
 wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity, const ulonglong2* __restrict__ keys,
                          uint64_t n, const unsigned long long* __restrict__ d_n, uint64_t off,
-                         uint8_t* __restrict__ out) {
+                         uint8_t* __restrict__ out, bool list_stored) {
     if (d_n) {
         const uint64_t total = __ldcg(d_n);
         n = total > off ? min(n, total - off) : 0;
@@ -262,10 +275,12 @@ wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
     const int lane = threadIdx.x & 31;
     const uint64_t dseed = t.aux_seed * 3 + 1;
     WideWinner* win = reinterpret_cast<WideWinner*>(sc.win);
+    unsigned long long stored_here = 0, cas_count = 0;
     for (uint64_t r = 0; r < rounds; ++r) {
         ulonglong2 k[kWU];
         uint64_t fold[kWU];
-        bool act[kWU], ok[kWU], found[kWU], more[kWU];
+        bool act[kWU], ok[kWU], found[kWU], more[kWU], cand[kWU];
+        uint32_t at[kWU];                     // the slot a search stopped at (a candidate)
 #pragma unroll
         for (int u = 0; u < kWU; ++u) {
             const uint64_t i = (r * kWU + u) * stride + tid;
@@ -274,36 +289,34 @@ wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
             ok[u] = act[u] && !wide_reserved(k[u].y);
             if (act[u] && !ok[u]) set_flag(t.ctr, kFlagInvalidKey);
             fold[u] = wide_fold(k[u].x, k[u].y);
+            found[u] = cand[u] = false;
+            more[u] = ok[u];
+            at[u] = 0;
         }
-        // h_1 of every key first; an empty h_1 proves the key absent (a key
+        // h_1, h_2, ... one function at a time (16-byte words of four keys in
+        // flight per thread), each key until it is found or meets a slot
+        // without a complete key.  An EMPTY h_a proves the key absent (a key
         // stored at h_j has h_1..h_(j-1) occupied: slots never return to
-        // EMPTY and a chain starts only past slots seen occupied).
-        ulonglong2 w[kWU];
+        // EMPTY and a key is stored only past slots seen occupied).
+        for (uint32_t a = 0; a < t.k; ++a) {
+            ulonglong2 w[kWU];
 #pragma unroll
-        for (int u = 0; u < kWU; ++u)
-            if (ok[u]) w[u] = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold[u], t.seed[0], t.nslots)));
-        uint32_t start[kWU];                  // first of h_2..h_k seen EMPTY (0: none)
+            for (int u = 0; u < kWU; ++u)
+                if (more[u])
+                    w[u] = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold[u], t.seed[a], t.nslots)));
 #pragma unroll
-        for (int u = 0; u < kWU; ++u) {
-            found[u] = ok[u] && w[u].x == k[u].x && w[u].y == k[u].y;
-            more[u] = ok[u] && !found[u] && !(w[u].x == kOnes && w[u].y == kOnes);
-            start[u] = 0;
-        }
-        // h_2..h_k one function at a time (16-byte words of four keys in
-        // flight per thread); an EMPTY h_a ends the search: a key never sits
-        // past an empty slot of its own.  The first EMPTY is the chain start.
-        {
-            for (uint32_t a = 1; a < t.k; ++a) {
-#pragma unroll
-                for (int u = 0; u < kWU; ++u)
-                    if (more[u] && !found[u] && !start[u])
-                        w[u] = __ldcg(reinterpret_cast<const ulonglong2*>(t.slots + 2 * hidx(fold[u], t.seed[a], t.nslots)));
-#pragma unroll
-                for (int u = 0; u < kWU; ++u)
-                    if (more[u] && !found[u] && !start[u]) {
-                        found[u] = w[u].x == k[u].x && w[u].y == k[u].y;
-                        if (w[u].x == kOnes && w[u].y == kOnes) start[u] = a;
-                    }
+            for (int u = 0; u < kWU; ++u) {
+                if (!more[u]) continue;
+                const bool same = w[u].x == k[u].x && w[u].y == k[u].y;
+                const bool empty = w[u].x == kOnes && w[u].y == kOnes;
+                if (LOOKUP ? same : (same && slot_class(w[u].x, w[u].y) == 2)) {
+                    found[u] = true;
+                    more[u] = false;
+                } else if (LOOKUP ? empty : slot_class(w[u].x, w[u].y) == 1) {
+                    cand[u] = true;
+                    at[u] = a;
+                    more[u] = false;
+                }
             }
         }
         if (ovf_used) {
@@ -318,17 +331,60 @@ wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                 if (act[u] && out) out[i] = uint8_t(found[u]);
             }
         } else {
-        // In-batch dedup: one winner per distinct absent key; every miss's
-        // first claim together, collisions probe on.
+        // Stores: a CAS from EMPTY at the candidate slot, on in slot order
+        // while the CAS returns another complete key (with t.chain_h1 only
+        // at h_1, Section 4.1's start).  The rest claim.
+        bool placed[kWU], claim[kWU], pend[kWU];
+#pragma unroll
+        for (int u = 0; u < kWU; ++u) {
+            const bool miss = ok[u] && !found[u];
+            pend[u] = miss && cand[u] && (!t.chain_h1 || at[u] == 0);
+            claim[u] = miss && !pend[u];
+            placed[u] = false;
+        }
+        for (uint32_t pass = 0; pass < t.k; ++pass) {
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < kWU; ++u) any |= pend[u];
+            if (!__any_sync(kFull, any)) break;
+            ulonglong2 cw[kWU];
+#pragma unroll
+            for (int u = 0; u < kWU; ++u)
+                if (pend[u]) {
+                    uint64_t ol, oh;
+                    cas128(t.slots + 2 * hidx(fold[u], t.seed[at[u]], t.nslots), k[u].x, k[u].y, ol, oh);
+                    cw[u] = make_ulonglong2(ol, oh);
+                    ++cas_count;
+                }
+#pragma unroll
+            for (int u = 0; u < kWU; ++u) {
+                if (!pend[u]) continue;
+                if (cw[u].x == kOnes && cw[u].y == kOnes) {
+                    placed[u] = true;
+                    pend[u] = false;
+                } else if (cw[u].x == k[u].x && cw[u].y == k[u].y) {
+                    found[u] = true;                     // another copy stored it
+                    pend[u] = false;
+                } else if (t.chain_h1 || at[u] + 1 >= t.k) {
+                    claim[u] = true;                     // every slot holds another key now
+                    pend[u] = false;
+                } else {
+                    ++at[u];
+                }
+            }
+        }
+        // In-batch dedup of the keys with all k slots full: one winner per
+        // distinct key; every such miss's first claim together, collisions
+        // probe on.
         bool winner[kWU];
         uint64_t spos[kWU];
         ulonglong2 old[kWU];
 #pragma unroll
         for (int u = 0; u < kWU; ++u) {
-            winner[u] = false;
+            winner[u] = placed[u];
             spos[u] = mix64(fold[u] ^ dseed) & sc.mask;
             old[u] = make_ulonglong2(0, 0);
-            if (ok[u] && !found[u]) {
+            if (claim[u]) {
                 uint64_t ol, oh;
                 cas128(sc.set + 2 * spos[u], k[u].x, k[u].y, ol, oh);
                 old[u] = make_ulonglong2(ol, oh);
@@ -336,7 +392,7 @@ wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
         }
 #pragma unroll
         for (int u = 0; u < kWU; ++u) {
-            if (!ok[u] || found[u]) continue;
+            if (!claim[u]) continue;
             bool settled = false;
             for (uint64_t probe = 0; probe <= sc.mask; ++probe) {
                 if (probe) {
@@ -359,12 +415,16 @@ wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
                 atomicAdd(&t.ctr->dropped, 1ull);
             }
         }
-        // Append the round's winners: one atomic per warp.
+        // List the round's claim winners (and the stored keys, for a caller
+        // that collects the new keys): one atomic per warp.
+        bool listed[kWU];
         unsigned wm[kWU];
         unsigned total = 0;
 #pragma unroll
         for (int u = 0; u < kWU; ++u) {
-            wm[u] = __ballot_sync(kFull, winner[u]);
+            listed[u] = winner[u] && (!placed[u] || list_stored);
+            stored_here += (placed[u] && !list_stored) ? 1u : 0u;
+            wm[u] = __ballot_sync(kFull, listed[u]);
             total += __popc(wm[u]);
         }
         unsigned int b = 0;
@@ -375,34 +435,46 @@ wide_cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
 #pragma unroll
         for (int u = 0; u < kWU; ++u) {
             const uint64_t i = (r * kWU + u) * stride + tid;
-            bool stored = winner[u];
-            if (stored) {
-                const uint64_t at = uint64_t(b) + __popc(wm[u] & ((1u << lane) - 1));
-                if (at < sc.win_cap) {
+            bool is_new = winner[u];
+            if (listed[u]) {
+                const uint64_t p = uint64_t(b) + __popc(wm[u] & ((1u << lane) - 1));
+                if (p < sc.win_cap) {
                     WideWinner wn;
                     wn.lo = k[u].x;
                     wn.hi = k[u].y;
                     wn.spos = spos[u];
-                    wn.start = t.chain_h1 ? 0u : start[u];
-                    win[at] = wn;
+                    wn.start = placed[u] ? kWidePlaced : 0u;
+                    win[p] = wn;
+                } else if (placed[u]) {
+                    atomicAdd(&t.ctr->size, 1ull);       // stored already; it holds no claim
                 } else {                                 // more winners than the table holds
-                    stored = false;
+                    is_new = false;
                     sc.set[2 * spos[u]] = kOnes;
                     sc.set[2 * spos[u] + 1] = kOnes;
                     set_flag(t.ctr, kFlagDropped);
                     atomicAdd(&t.ctr->dropped, 1ull);
                 }
             }
-            if (act[u] && out) out[i] = uint8_t(stored);
+            if (act[u] && out) out[i] = uint8_t(is_new);
             b += __popc(wm[u]);
         }
         }
     }
+    if (!LOOKUP) {
+        for (int o = 16; o; o >>= 1) {
+            stored_here += __shfl_down_sync(kFull, stored_here, o);
+            cas_count += __shfl_down_sync(kFull, cas_count, o);
+        }
+        if (lane == 0 && stored_here) atomicAdd(&t.ctr->size, stored_here);
+        if (lane == 0 && cas_count) atomicAdd(&t.ctr->probe_cas, cas_count);
+    }
 }
 
-// Eviction chains of the winners: each thread keeps kWU chains in flight and
-// replaces a chain that ends (an empty slot, or the overflow set) with its
-// next winner at once.
+// Eviction chains of the claim winners: each thread keeps kWU chains in
+// flight and replaces a chain that ends (an empty slot, or the overflow set)
+// with its next winner at once.  Records of keys the probe stored are only
+// counted (they are listed for a caller that collects the new keys, which
+// takes every record).
 template <bool APPEND>
 __global__ void __launch_bounds__(kBlock)
 wide_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uint64_t max_winners,
@@ -443,9 +515,13 @@ wide_cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity
         bool any = false;
 #pragma unroll
         for (int u = 0; u < kWU; ++u) {
-            if (!live[u] && next < count) {
+            while (!live[u] && next < count) {
                 const WideWinner wn = win[next];
                 next += stride;
+                if (wn.start == kWidePlaced) {           // stored by the probe: only counted
+                    ++placed;
+                    continue;
+                }
                 sc.set[2 * wn.spos] = kOnes;             // leave the claim set empty for the next batch
                 sc.set[2 * wn.spos + 1] = kOnes;
                 lo[u] = wn.lo;
@@ -543,11 +619,12 @@ cudaError_t wide_lookup(int lanes, const DevTable& t, const void* keys, uint64_t
 }
 
 cudaError_t wide_cuckoo_probe(const DevTable& t, const DevScratch& sc, uint32_t parity, const void* keys, uint64_t n,
-                              const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s) {
+                              const unsigned long long* d_n, uint64_t off, uint8_t* is_new, cudaStream_t s,
+                              bool list_stored) {
     ProfScope ps(kKCuckooProbe, s);
     auto k = wide_cuckoo_probe_kernel<false>;
     k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, sc, parity, static_cast<const ulonglong2*>(keys),
-                                                              n, d_n, off, is_new);
+                                                              n, d_n, off, is_new, list_stored);
     return cudaGetLastError();
 }
 
@@ -572,7 +649,7 @@ cudaError_t wide_cuckoo_lookup(const DevTable& t, const void* keys, uint64_t n, 
     DevScratch none{};
     auto k = wide_cuckoo_probe_kernel<true>;
     k<<<launch_blocks((const void*)k, kBlock), kBlock, 0, s>>>(t, none, 0u, static_cast<const ulonglong2*>(keys), n,
-                                                              nullptr, 0, found);
+                                                              nullptr, 0, found, false);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
-"""128-bit keys (state vectors wider than 64 bits) in the bucket scheme:
-parity with the 128-bit oracle set, exactly as for 64-bit keys."""
+"""128-bit keys (state vectors wider than 64 bits) in both schemes: parity
+with the 128-bit oracle set, exactly as for 64-bit keys."""
 import numpy as np
 import pytest
 import torch
@@ -90,6 +90,40 @@ def test_edge_keys_and_reserved(oracle_lib, scheme):
     bad = np.array([[3, 2 ** 63]], dtype=np.uint64)                  # reserved bit set
     t.find_or_put(_dev(bad))
     assert t.sync() == 1
+
+
+def test_cuckoo_keys_with_an_all_ones_low_word(oracle_lib):
+    # A key whose low word is all ones reads like a half-written slot, so the
+    # Cuckoo probe settles such a slot with its CAS, never by the read.  Many
+    # such keys, repeated within and across batches, stay exact.
+    ones = np.uint64(2 ** 64 - 1)
+    keys = np.stack([np.full(4000, ones, dtype=np.uint64), wk.distinct_keys(4000, 64, seed=81)], axis=1)
+    t = ht.HashTable(8000, "cuckoo", 128)
+    orc = oracle_lib.OracleTable128()
+    rng = np.random.default_rng(5)
+    for lo in range(0, 4000, 1000):
+        b = np.concatenate([keys[lo:lo + 1000], keys[rng.integers(0, lo + 1000, size=1000)]])
+        b = b[rng.permutation(len(b))]
+        assert_flags_per_key(_ids(b), t.find_or_put(_dev(b)).cpu().numpy(), orc.find_or_put(b))
+    assert t.sync() == 0 and t.size() == 4000
+    f, _ = t.lookup(_dev(keys))
+    assert f.cpu().numpy().all()
+
+
+def test_cuckoo_probe_stores_at_low_load():
+    # At load 0.05 nearly every key sees an empty slot: the probe stores it
+    # with one 16-byte CAS (a few more where keys of the batch race for a
+    # slot) and almost no key runs an eviction chain; a second pass finds
+    # every key and stores nothing.
+    n = 50_000
+    keys = _pairs(n, seed=82)
+    t = ht.HashTable(n * 20, "cuckoo", 128)
+    assert t.find_or_put(_dev(keys)).cpu().numpy().sum() == n and t.size() == n
+    st = t.stats()
+    assert n <= st["probe_cas"] <= n + n // 20
+    assert st["exchanges"] <= n // 1000
+    assert t.find_or_put(_dev(keys)).cpu().numpy().sum() == 0
+    assert t.stats()["probe_cas"] == st["probe_cas"]
 
 
 @pytest.mark.parametrize("scheme", ["bucket", "cuckoo"])

@@ -117,10 +117,11 @@ __device__ void place_initial_states(const MultiDev& m, uint64_t gtid, uint64_t 
 // key per lane, against the tile's exploration e.  A key is looked up at h_1, then (h_1 occupied by another
 // key) at h_2..h_k, then in the stash / overflow set when those are in use;
 // a key stored at h_j has h_1..h_(j-1) occupied, so an empty h_1 proves it
-// absent.  An absent key claims its key in e's claim set; the one claimant
-// per distinct key is the winner: it is appended to e's states and to the
-// group's winner list with its exploration and the first empty slot the
-// probe saw (its chain start).
+// absent.  An absent key that saw an EMPTY slot stores itself there (a CAS
+// in slot order); one whose k slots are all full claims its key in e's
+// claim set, and the one claimant per distinct key joins the group's
+// winner list with its exploration, for a chain from h_1.  Every new key is
+// appended to e's states.
 constexpr int kWinStage = 64;            // staged winner records per warp
 
 __device__ void cuckoo_probe_tiles(const MultiDev& m, const multi::TileMap& tm, uint64_t gw, uint64_t nwarps,
@@ -170,6 +171,8 @@ __device__ void cuckoo_probe_tiles(const MultiDev& m, const multi::TileMap& tm, 
         ovf_used = __ldcg(&m.tables[e].ctr->ovf_used);
     };
     load_desc();
+    uint32_t run_e = e;                        // keys stored by this warp's CASes, per run of e
+    unsigned long long run_n = 0;
     uint64_t next_key = __ldcg(reinterpret_cast<const unsigned long long*>(m.succ + cur.key_index(m, t_begin, lane)));
     for (uint64_t tile = t_begin; tile < t_end; ++tile) {
         const uint64_t cur_key = next_key;
@@ -212,9 +215,49 @@ __device__ void cuckoo_probe_tiles(const MultiDev& m, const multi::TileMap& tm, 
             uint64_t sw;
             found = find_spill<KW>(t, key, stash_used, ovf_used, &sw);
         }
-        // In-batch dedup in e's claim set: the one claimant of each absent key wins.
-        const bool need = ok && !found;
-        bool winner = false;
+        // An absent key that saw an EMPTY slot (h_1, or the first of
+        // h_2..h_k; with t.chain_h1 only h_1) stores itself there with a CAS
+        // from EMPTY, going on in slot order while the CAS returns another
+        // key; a CAS that returns the key means another copy stored it.  Only
+        // keys whose k slots are all full claim and run a chain.  (The
+        // argument is the single-table kernel's: nothing moves a key during
+        // the probe phase, the grid barrier ends it before any chain runs.)
+        bool placed = false;
+        bool pend = ok && !found && (!more || (start != 0 && !t.chain_h1));
+        bool claim = ok && !found && !pend;
+        uint32_t at = more ? start : 0u;
+        for (uint32_t pass = 0; pass < t.k && __any_sync(0xFFFFFFFFu, pend); ++pass) {
+            if (pend) {
+                const uint64_t cw = atomicCAS(reinterpret_cast<unsigned long long*>(t.slots + hidx(key, t.seed[at], t.nslots)),
+                                              kEmpty, K::word(key, 0u));
+                if (cw == kEmpty) {
+                    placed = true;
+                    pend = false;
+                } else if (K::keyof(cw) == key) {
+                    found = true;                      // another copy stored it
+                    pend = false;
+                } else if (t.chain_h1 || at + 1 >= t.k) {
+                    claim = true;                      // every slot holds another key now
+                    pend = false;
+                } else {
+                    ++at;
+                }
+            }
+        }
+        // The stored keys count toward e's size, per run of tiles of e.
+        {
+            const unsigned pm = __ballot_sync(0xFFFFFFFFu, placed);
+            if (e != run_e) {
+                if (lane == 0 && run_n) atomicAdd(&m.tables[run_e].ctr->size, run_n);
+                run_e = e;
+                run_n = 0;
+            }
+            run_n += __popc(pm);
+        }
+        // In-batch dedup in e's claim set of the keys with every slot full:
+        // the one claimant of each such key wins.
+        const bool need = claim;
+        bool winner = placed;
         uint32_t spos = 0;
         if (need) {
             const DevScratch& sc = m.scratch[e];
@@ -234,31 +277,34 @@ __device__ void cuckoo_probe_tiles(const MultiDev& m, const multi::TileMap& tm, 
                 }
             }
         }
-        // Winners to the warp's stage of winner records (listed with one
-        // atomic per flush) and to e's states.
-        const unsigned wm = __ballot_sync(0xFFFFFFFFu, winner);
+        // Claim winners to the warp's stage of winner records (listed with
+        // one atomic per flush; their chains start at h_1); every new key to
+        // e's states.
+        const bool listed = winner && !placed;
+        const unsigned wm = __ballot_sync(0xFFFFFFFFu, listed);
         if (wm) {
             if (wpend + __popc(wm) > uint32_t(kWinStage)) flush_winners();
-            if (winner) {
+            if (listed) {
                 MultiWinner& wn = wstage[wpend + __popc(wm & ((1u << lane) - 1))];
                 wn.word = K::word(key, 0u);
                 wn.spos = spos;
-                wn.tag = (e << 8) | (t.chain_h1 ? 0u : start);
+                wn.tag = e << 8;
             }
             wpend += __popc(wm);
         }
         stage.push(winner, key, m, e);
     }
+    if (lane == 0 && run_n) atomicAdd(&m.tables[run_e].ctr->size, run_n);
     stage.flush(m, e);
     flush_winners();
 }
 
-// Cuckoo insert of the step's winners over threads [gtid] of [nthreads]:
-// each thread keeps four eviction chains in flight (Section 4.1, Fig. 2)
-// and refills a chain as soon as it ends.  A chain starts at the slot its
-// probe saw empty (h_1 if none), exchanges its word in, and moves an
-// evicted key k' from h_a(k') (the smallest a naming the slot) to h_(a+1);
-// after max_evictions the held word goes to the stash.  Each winner's claim
+// Cuckoo insert of the step's claim winners over threads [gtid] of
+// [nthreads]: each thread keeps four eviction chains in flight (Section
+// 4.1, Fig. 2) and refills a chain as soon as it ends.  A chain starts at
+// h_1, exchanges its word in, and moves an evicted key k' from h_a(k') (the
+// smallest a naming the slot) to h_(a+1); after max_evictions the held word
+// goes to the stash.  Each winner's claim
 // is cleared from its table's claim set when the winner is taken.
 __device__ void cuckoo_insert_winners(const MultiDev& m, uint64_t gtid, uint64_t nthreads) {
     constexpr int KW = 64;

@@ -619,7 +619,9 @@ def run_e2e(a, ht, torch, dev, fs, tables, schemes, world, nbuf=3):
             raise RuntimeError("e2e fill did not end exact")
     # The host link's own rate: pinned host -> device copies of one batch of
     # keys into a device buffer, timed alone on one stream (best of five);
-    # the step cannot beat its bytes at this rate.
+    # the step cannot beat its bytes at this rate.  Then every batch of the
+    # stream copied alone once: the whole buffer's rate, which shows pages
+    # of the pinned buffer that copy slower than the first batch's.
     m = offs[1] - offs[0]
     rates = []
     for _ in range(5):
@@ -630,6 +632,16 @@ def run_e2e(a, ht, torch, dev, fs, tables, schemes, world, nbuf=3):
         torch.cuda.synchronize()
         rates.append(m * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9)
     h2d_gbs = max(rates)
+    per_batch = []
+    for b in range(fs.n_batches):
+        mb = offs[b + 1] - offs[b]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(comp)
+        kbuf[0][:mb].copy_(keys_h[offs[b]:offs[b + 1]], non_blocking=True)
+        e1.record(comp)
+        torch.cuda.synchronize()
+        per_batch.append(mb * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    all_ms = sum((offs[b + 1] - offs[b]) * 8 / (r * 1e9) for b, r in enumerate(per_batch)) * 1e3
     h2d_bytes = fs.n_issued * 8 * len(schemes)
     return {"value": round(fs.n_issued * len(schemes) * world / (ms / 1e3) / 1e6, 1), "unit": "Mops/s",
             "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d_bytes),
@@ -637,6 +649,8 @@ def run_e2e(a, ht, torch, dev, fs, tables, schemes, world, nbuf=3):
             "overlap": "3 streams (copy-in, kernels, copy-out), %d device buffers round robin" % nbuf,
             "h2d_gbs_measured": round(h2d_gbs, 1),
             "link_bound_ms_per_step": round(h2d_bytes / (h2d_gbs * 1e9) * 1e3, 2),
+            "h2d_gbs_every_batch_min_median": [round(min(per_batch), 1), round(statistics.median(per_batch), 1)],
+            "link_bound_ms_per_step_every_batch": round(all_ms * len(schemes), 2),
             "find_or_put_busy_ms_per_step": round(busy_ms, 3),
             "kernel_stream_waiting_ms_per_step": round(ms - busy_ms, 3)}
 

@@ -71,14 +71,14 @@ typedef enum {
  *                  per key spread each round's fixed cost over more keys).
  *   max_rebuilds   rebuild attempts with fresh hash constants, default 8.
  *   max_batch      cuckoo keys per probe/insert launch pair (sizes the
- *                  in-batch dedup scratch), default 2^21.
+ *                  in-batch dedup scratch), default 2^22.
  *   seed           hash-constant seed.
  *   l2_persist     1: launches on this table carry an L2 access-policy
  *                  window marking the slot array persisting when it fits
  *                  the device's persisting L2 (else, for Cuckoo, the dedup
  *                  claim set); this raises the process's persisting L2
- *                  set-aside (cudaLimitPersistingL2CacheSize).  Default: 1
- *                  for Cuckoo, 0 for the bucket scheme.
+ *                  set-aside (cudaLimitPersistingL2CacheSize), which stays
+ *                  reserved after the table is destroyed.  Default: 0.
  *   grow_load_permille  0 (default): fixed capacity.  Else a synchronising
  *                  call (ht_sync, ht_size, ht_export) that finds
  *                  the table above this load (per mille of its slots), or

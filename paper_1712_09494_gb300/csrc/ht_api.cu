@@ -1,6 +1,7 @@
 // Host side of the C ABI: table lifecycle, batching, rebuild and status.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -292,10 +293,36 @@ ht_params complete_params(ht_scheme scheme, const ht_params* in) {
     return p;
 }
 
+// Tables holding an L2 access-policy window, per device, and the context's
+// persisting set-aside before the first of them raised it.  When the last
+// one is freed the set-aside goes back to that value and persisting lines
+// turn normal: a set-aside left behind would shrink the L2 of all later work
+// in the process (a 128-bit bucket fill took 9.0 instead of 5.4 ms after a
+// Cuckoo table with a window had come and gone).
+std::mutex g_win_mu;
+int g_win_tables[64];
+size_t g_win_prev[64];
+
+void window_acquire(int dev, size_t before) {
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> g(g_win_mu);
+    if (g_win_tables[dev]++ == 0) g_win_prev[dev] = before;
+}
+
+void window_release(int dev) {
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> g(g_win_mu);
+    if (g_win_tables[dev] > 0 && --g_win_tables[dev] == 0) {
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_win_prev[dev]);
+        cudaCtxResetPersistingL2Cache();
+    }
+}
+
 // Table memory is stream-ordered (cudaMallocAsync / cudaFreeAsync), so a
 // table can be released without synchronising the whole device.
 void free_table(ht_table* t, cudaStream_t s) {
     if (!t) return;
+    if (t->win.base) window_release(t->device);
     void* ptrs[] = {t->dt.slots, t->dt.stash, t->dt.ovf, t->dt.ctr, t->sc.set, t->sc.win, t->dt.kstore};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
@@ -400,11 +427,19 @@ ht_status ht_default_params(ht_scheme scheme, ht_params* p) {
     p->bucket_slots = 16;
     p->lanes_per_key = 2;
     p->max_rebuilds = 8;
-    p->max_batch = scheme == HT_CUCKOO ? (1ull << 21) : (1ull << 22);
+    // Cuckoo: 2^22 keys per launch pair.  Each insert launch ends with its
+    // longest eviction chain, so fewer, larger launches pay fewer tails (a
+    // BFS of 10^8 states: insert 41.7 -> 24.1 ms); 2^23 keys would put the
+    // claim set past the persisting L2 (fill of 2^27 keys: 15.9 ms at 2^22,
+    // 16.5 at 2^21, 24.5 at 2^23).
+    p->max_batch = 1ull << 22;
     p->seed = 0x243F6A8885A308D3ull;
-    // Cuckoo: keep the dedup claim set (2 x max_batch words) persisting in
-    // L2 -- measured +8% on the fill of 2^27 keys; bucket: no gain measured.
-    p->l2_persist = scheme == HT_CUCKOO ? 1 : 0;
+    // Off by default for both schemes.  Most new Cuckoo keys no longer claim
+    // in the dedup set, and the persisting set-aside a window raises stays
+    // reserved for the context after the table is gone: with it on, the
+    // Cuckoo fill of 2^27 keys took 15.9 instead of 14.8 ms, and a later
+    // 128-bit bucket fill 9.0 instead of 5.4 ms.
+    p->l2_persist = 0;
     return HT_OK;
 }
 
@@ -515,8 +550,11 @@ ht_status ht_create(uint64_t capacity, ht_scheme scheme, uint32_t key_width, con
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
         const size_t table_bytes = t->dt.nslots * slot_bytes;
+        size_t before = 0;
+        cudaDeviceGetLimit(&before, cudaLimitPersistingL2CacheSize);
         if (table_bytes <= size_t(max_persist)) t->win = l2_window(t->dt.slots, table_bytes);
         else if (scheme == HT_CUCKOO) t->win = l2_window(t->sc.set, (t->sc.mask + 1) * (key_width >= 128 ? 16 : 8));
+        if (t->win.base) window_acquire(dev, before);
     }
     *out = t;
     return HT_OK;

@@ -610,10 +610,10 @@ ht_status ht_probe_random_rmw(void* d_buf, uint64_t bytes, uint64_t n_access, ui
  *           first call for a table; uses fills, no allocation).
  * Semantics per call are those of ht_find_or_put on a Cuckoo table with 4
  * hash functions and an eviction bound of 256.
- * The first call on each device looks up the static array's device address
- * (cudaGetSymbolAddress) and keeps it; make that first call before any
- * stream capture.  A cudaDeviceReset ends the context that address belongs
- * to: do not call this entry point on that device afterwards.
+ * Every call looks up the static array's device address on the current
+ * device (cudaGetSymbolAddress, a host-side lookup), so the address stays
+ * right after a cudaDeviceReset; make the first call on a device before any
+ * stream capture (it may load the library's module).
  * All calls share the array.  Each call with n > 0 first empties the whole
  * dedup set (a 4 MiB fill, a fixed cost of a few microseconds per call) and
  * zeroes its winner count, so no call depends on what an earlier, possibly

@@ -15,7 +15,6 @@
 // whose work overlaps on the GPU (different streams, or several host threads)
 // race on it; callers must order them.
 #include <cstring>
-#include <mutex>
 
 #include "ht_internal.cuh"
 
@@ -37,24 +36,15 @@ constexpr uint32_t kStateOvf = 64;            // power of two
 static_assert(sizeof(DevCounters) <= kStateCtrWords * 8, "counters fit the header");
 static_assert((kStateCtrWords + kStateStashWords + kStateOvf) * 8 <= HT_NOALLOC_STATE_BYTES, "state fits");
 
-std::mutex g_mu;
-uint64_t* g_scratch_addr[64] = {};            // device address of the array, per device
-
-// Once per device, with that device current: the array's name is only a
-// host-side stand-in, so its device address is looked up and cached.
+// The array's device address on the current device.  The name is only a
+// host-side stand-in, so the address is looked up on every call (a host-side
+// lookup, no allocation): a cached address would go stale when the module is
+// loaded again after a device reset.
 cudaError_t scratch_on_current_device(uint64_t** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<uint64_t*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<uint64_t*>(p);
     return cudaSuccess;
 }
 

@@ -445,8 +445,8 @@ cuckoo_probe_kernel(const DevTable t, const DevScratch sc, uint32_t parity,
 // lengths vary widely at high load, and refilling keeps every slot of the
 // thread busy instead of waiting for the longest chain of a round.  Each
 // step reads the next records for all free chain slots together with the
-// live chains' exchanges; a record whose key the probe stored only gives
-// its claim back, so most records cost no round trip of their own.
+// live chains' exchanges.  A record of a key the probe stored (listed only
+// for a caller that collects the new keys) holds no claim and is counted.
 template <int KW, bool APPEND>
 __global__ void __launch_bounds__(kBlock, HT_CUCKOO_INSERT_MIN_BLOCKS)
 cuckoo_insert_kernel(const DevTable t, const DevScratch sc, uint32_t parity, uint64_t max_winners,

@@ -92,13 +92,18 @@ typedef enum {
  *                  it makes the full-key comparisons that tell such keys
  *                  apart run often (results are unchanged; placement gets
  *                  worse).  Other key widths: must be 0.
- *   cuckoo_chain_h1  Cuckoo, 64-bit and narrower keys: 0 (default) starts a
- *                  new key's eviction chain at the first of its slots
- *                  h_1..h_k that the probe of the same batch saw empty (h_1
- *                  when it saw none); 1 always starts it at h_1, as Section
- *                  4.1 describes.  Both keep "a key stored at h_j has h_1 ..
- *                  h_(j-1) occupied" (slots never become empty again), so
- *                  results are the same; the default makes fewer exchanges.
+ *   cuckoo_chain_h1  Cuckoo: 0 (default) inserts a new key at the first of
+ *                  its slots h_1..h_k that its probe saw empty -- for keys of
+ *                  up to 128 bits the probe stores it there with a CAS from
+ *                  EMPTY (in slot order when another key took the slot
+ *                  first) and only a key whose k slots were all full runs an
+ *                  eviction chain, from h_1; for longer keys the chain
+ *                  starts at that slot.  1 keeps Section 4.1's rule: an
+ *                  insertion starts at h_1 (a CAS there only when h_1 was
+ *                  empty, otherwise an eviction chain from h_1).  Both keep
+ *                  "a key stored at h_j has h_1 .. h_(j-1) occupied" (slots
+ *                  never become empty again), so results are the same; the
+ *                  default makes fewer atomics.
  *   publish_wait_polls  keys wider than 128 bits, bucket scheme: how many
  *                  times a reader polls a claimed, unpublished slot header
  *                  of its key's tag (with back-off) before it gives up and

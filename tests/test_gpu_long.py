@@ -202,6 +202,19 @@ def test_cuckoo_overflow_and_rebuild_stay_exact(oracle_lib):
     assert st["overflow_used"] > 0 or st["rebuilds"] > 0
 
 
+def test_cuckoo_paper_insertion_rule_parity(oracle_lib):
+    # cuckoo_chain_h1 = 1: every long-key chain starts at h_1 (Section 4.1).
+    keys = wk.distinct_keys(6000, 256, seed=74)
+    t = ht.HashTable(int(6000 / 0.85), "cuckoo", 256, dict(cuckoo_chain_h1=1))
+    orc = oracle_lib.OracleTableLong(4)
+    rng = np.random.default_rng(4)
+    for lo in range(0, 6000, 1500):
+        b = np.concatenate([keys[lo:lo + 1500], keys[rng.integers(0, lo + 1500, size=500)]])
+        b = b[rng.permutation(len(b))]
+        assert_flags_per_key(_ids(b), t.find_or_put(_dev(b)).cpu().numpy(), orc.find_or_put(b))
+    assert t.sync() == 0 and t.size() == orc.size() == 6000
+
+
 def test_large_batch_parity(oracle_lib):
     # 2^21 keys of 256 bits in batches of 2^19, both schemes, against the oracle.
     n = 1 << 21

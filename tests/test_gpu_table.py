@@ -53,6 +53,19 @@ def test_find_or_put_parity(oracle_lib, scheme, kw, dup):
     _fill_and_check(oracle_lib, scheme, kw, n_distinct=100_003, batch=1 << 15, dup=dup, lf=0.8)
 
 
+@pytest.mark.parametrize("kw", [32, 64])
+@pytest.mark.parametrize("lf", [0.8, 0.9])
+def test_cuckoo_paper_insertion_rule_parity(oracle_lib, kw, lf):
+    # cuckoo_chain_h1 = 1: Section 4.1's rule, every insertion starting at
+    # h_1 (a CAS in the probe only when h_1 was empty, else a claim and an
+    # eviction chain from h_1), with many keys finding h_1 taken at these
+    # loads; results equal the oracle's like the default rule's.
+    t, _, fs = _fill_and_check(oracle_lib, "cuckoo", kw, n_distinct=100_003, batch=1 << 15, dup=0.25, lf=lf,
+                               params=dict(cuckoo_chain_h1=1), seed=17)
+    st = t.stats()
+    assert st["exchanges"] > 0 and st["probe_cas"] > 0
+
+
 @pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("lf", [0.5, 0.9])
 def test_find_or_put_loads(oracle_lib, scheme, lf):

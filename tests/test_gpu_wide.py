@@ -110,6 +110,21 @@ def test_cuckoo_keys_with_an_all_ones_low_word(oracle_lib):
     assert f.cpu().numpy().all()
 
 
+def test_cuckoo_paper_insertion_rule_parity(oracle_lib):
+    # cuckoo_chain_h1 = 1 (Section 4.1's start at h_1) for 128-bit keys, at
+    # load 0.85 with repeats within and across batches, against the oracle.
+    keys = _pairs(20_000, seed=83)
+    t = ht.HashTable(int(20_000 / 0.85), "cuckoo", 128, dict(cuckoo_chain_h1=1))
+    orc = oracle_lib.OracleTable128()
+    rng = np.random.default_rng(9)
+    for lo in range(0, 20_000, 5000):
+        b = np.concatenate([keys[lo:lo + 5000], keys[rng.integers(0, lo + 5000, size=2000)]])
+        b = b[rng.permutation(len(b))]
+        assert_flags_per_key(_ids(b), t.find_or_put(_dev(b)).cpu().numpy(), orc.find_or_put(b))
+    assert t.sync() == 0 and t.size() == 20_000
+    assert t.stats()["exchanges"] > 0
+
+
 def test_cuckoo_probe_stores_at_low_load():
     # At load 0.05 nearly every key sees an empty slot: the probe stores it
     # with one 16-byte CAS (a few more where keys of the batch race for a

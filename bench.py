@@ -168,6 +168,12 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def section_wanted(only, section, off):
+    """Whether an optional section runs: with --only, exactly the sections it
+    names; otherwise every section whose --no-* flag is not set."""
+    return section in only if only else not off
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
     kernel's source has not changed since the capture (else None)."""
@@ -509,7 +515,7 @@ def run_ours(a, rank, world, local):
     only = {x for x in a.only.split(",") if x}
 
     def want(section, off):
-        return section in only if only else not off
+        return section_wanted(only, section, off)
 
     if want("small", a.no_small):
         out["small_map_config1"] = run_small_map(ht, torch, dev, schemes)

@@ -62,3 +62,43 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["host"]["nproc"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "Mops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["n_distinct"] == 1 << 18
+
+
+def test_random_access_bound_cuckoo_counts_probe_cas_as_claims():
+    # Cuckoo: reads are the counted probes past one per new key; claims are
+    # every table atomic of the insertions -- the probe's CASes into the
+    # first empty slot plus the chains' exchanges (at least one per new key).
+    fs = wk.fill_stream(30_000, 4096, 0.25, 64, seed=4)
+    stats = {"probes": 2 * fs.n_issued, "probe_cas": fs.n_distinct + 500, "exchanges": 1000}
+    reads = 2 * fs.n_issued - fs.n_distinct
+    claims = fs.n_distinct + 1500
+    t_min = reads / 40e9 + claims / 25e9
+    got = bench.random_access_roofline("cuckoo", fs, None, stats, t_min * 1e3 * 2, PROBE)
+    assert got["frac"] == pytest.approx(0.5, abs=2e-3)
+    assert got["lines_claimed_per_key"] == pytest.approx(claims / fs.n_issued, abs=1e-3)
+    few = dict(stats, probe_cas=10, exchanges=10)              # never fewer claims than new keys
+    got = bench.random_access_roofline("cuckoo", fs, None, few, 1.0, PROBE)
+    assert got["lines_claimed_per_key"] == pytest.approx(fs.n_distinct / fs.n_issued, abs=1e-3)
+
+
+def test_recorded_traffic_follows_the_sources(tmp_path, monkeypatch):
+    # A record counts only while its source files hash to the recorded
+    # prefix: an edited source makes it None.
+    import hashlib
+    src = tmp_path / "k.cu"
+    src.write_text("kernel one\n")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.txt").write_text("# comment\ntraffic probe k.cu 123000000 %s\n" % h)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.recorded_traffic("probe") == (123000000, "k.cu")
+    assert bench.recorded_traffic("insert") == (None, None)
+    src.write_text("kernel two\n")
+    assert bench.recorded_traffic("probe") == (None, None)
+
+
+def test_only_selects_named_sections():
+    assert bench.section_wanted(set(), "long", False)
+    assert not bench.section_wanted(set(), "long", True)
+    assert bench.section_wanted({"long", "wide"}, "long", True)
+    assert not bench.section_wanted({"long"}, "replay", False)
